@@ -1,0 +1,178 @@
+/*
+ * hawkes.h -- C ABI of the GB300 (sm_103a) spatiotemporal Hawkes likelihood library.
+ *
+ * The library evaluates the log-likelihood of the self-exciting spatiotemporal
+ * Hawkes process of Holbrook, Loeffler, Flaxman and Suchard ("Scalable Bayesian
+ * inference for self-excitatory stochastic processes applied to big American
+ * gunfire data"), Section 2.1, Eq. 1, and its gradient with respect to the six
+ * model parameters, on one GPU:
+ *
+ *   lambda_n = mu0/(tau_x^2 tau_t) sum_{n'} phi2((x_n - x_n')/tau_x) phi1((t_n - t_n')/tau_t)
+ *            + theta*omega/h^2 sum_{t_n' < t_n} exp(-omega (t_n - t_n')) phi2((x_n - x_n')/h)
+ *   Lambda_n = mu0 (Phi((t_N - t_n)/tau_t) - Phi(-t_n/tau_t)) + theta (1 - exp(-omega (t_N - t_n)))
+ *   ell      = sum_n (log lambda_n - Lambda_n)
+ *
+ * with d = 2 spatial dimensions, phi1/phi2 the standard normal densities on R and
+ * R^2, Phi the standard normal CDF, and t_N the last event time. Two readings of
+ * the paper are built in:
+ *   - the trigger prefactor is theta*omega/h^2 (the paper prints theta/(omega h^d),
+ *     which does not integrate to its own closed-form compensator);
+ *   - the background sum includes n' = n unless HAWKES_FLAG_EXCLUDE_SELF is set.
+ * The trigger indicator is strict (t_n' < t_n) on the stored times, so events with
+ * equal stored times never trigger one another.
+ *
+ * Precision modes. HAWKES_FP64 runs every step in double precision. HAWKES_MIXED
+ * stores coordinates as float32 (rounded from the uploaded doubles), computes pair
+ * distances and kernel values in float32, accumulates each row in float32 over
+ * 256-column tiles and folds every tile into float64; the log, the compensator and
+ * all reductions are float64. All reductions run in a fixed order: the same call on
+ * the same inputs returns bit-identical results, alone or batched with others.
+ *
+ * Threading. A context may be used from several host threads; calls on one
+ * context are serialised internally, except hawkes_poll/hawkes_wait, which only
+ * read completed results. Every function returns a status code and never aborts.
+ */
+#ifndef HAWKES_H
+#define HAWKES_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes --------------------------------------------------------------- */
+#define HAWKES_OK 0
+#define HAWKES_E_INVAL -1     /* bad argument: NULL pointer, n < 1, non-finite value,  */
+                              /* negative time, parameter out of its domain            */
+#define HAWKES_E_UNSORTED -2  /* event times are not non-decreasing                    */
+#define HAWKES_E_NOSET -3     /* unknown or released event-set id                      */
+#define HAWKES_E_ADMISSION -4 /* the request's device footprint exceeds the budget     */
+#define HAWKES_E_NOMEM -5     /* a device or pinned-host allocation failed             */
+#define HAWKES_E_TIMEOUT -6   /* hawkes_wait: the result was not ready in time         */
+#define HAWKES_E_PENDING -7   /* hawkes_poll: the result is not ready yet              */
+#define HAWKES_E_CUDA -8      /* a CUDA runtime call failed (see hawkes_last_cuda_error) */
+#define HAWKES_E_TICKET -9    /* unknown ticket, or its result was already collected   */
+#define HAWKES_E_SHUTDOWN -10 /* the context is being destroyed                        */
+
+/* ---- flags (hawkes_set_flags) ----------------------------------------------------- */
+#define HAWKES_FLAG_EXCLUDE_SELF 1 /* drop n' = n from the background sum of lambda_n    */
+
+typedef struct hawkes_ctx hawkes_ctx;
+
+/* Theta = (mu0, tau_x, tau_t, theta, omega, h), in the order of Section 2.1.
+ * Domain: mu0, tau_x, tau_t, omega, h > 0 and finite; theta >= 0 and finite. */
+typedef struct {
+  double mu0, tau_x, tau_t, theta, omega, h;
+} hawkes_params;
+
+typedef enum {
+  HAWKES_FP64 = 0,  /* double precision throughout                                */
+  HAWKES_MIXED = 1  /* float32 pair terms, float64 row accumulation and reductions */
+} hawkes_mode;
+
+/* Create a context on CUDA device `device`. `hbm_budget_bytes` caps the device
+ * memory the context may hold (event sets plus per-request workspaces); 0 means
+ * 90% of the device's free memory at creation. `cuda_stream` is a cudaStream_t to
+ * run on (for example PyTorch's current stream); NULL makes the context create
+ * and own a non-blocking stream. The serving queue (hawkes_submit) always runs on
+ * streams the context owns. Errors: E_INVAL (NULL out, bad device), E_CUDA, E_NOMEM. */
+int hawkes_create(hawkes_ctx **out, int device, size_t hbm_budget_bytes, void *cuda_stream);
+
+/* Wait for all queued work, free every device buffer and the context.
+ * Pending tickets complete with E_SHUTDOWN. NULL is accepted (no-op). */
+int hawkes_destroy(hawkes_ctx *ctx);
+
+/* Set context flags (HAWKES_FLAG_*); they apply to calls made afterwards. */
+int hawkes_set_flags(hawkes_ctx *ctx, int flags);
+
+/* Copy an event set to the device (Section 2.1: events (x_n, t_n), x_n in R^2).
+ * x, y (km) and t (days) are host arrays of n doubles; the caller keeps ownership
+ * and may free them when the call returns. t must be non-decreasing and >= 0
+ * (the compensator integrates from 0 to t_N, the last event). The library stores
+ * float64 and float32 copies in structure-of-arrays layout, padded to a multiple
+ * of 512 with sentinel events that contribute exactly zero. The set stays resident
+ * until hawkes_release_events or hawkes_destroy.
+ * Errors: E_INVAL (NULL, n < 1, non-finite, t < 0), E_UNSORTED, E_ADMISSION
+ * (set does not fit the budget), E_NOMEM, E_CUDA. */
+int hawkes_upload_events(hawkes_ctx *ctx, const double *x, const double *y, const double *t,
+                         int64_t n, int32_t *set_id_out);
+
+/* Free a resident event set. Requests already queued on it still complete. */
+int hawkes_release_events(hawkes_ctx *ctx, int32_t set_id);
+
+/* Number of events of a resident set and the device bytes it occupies (coordinates in
+ * both precisions, tie indices and work schedules). Either out pointer may be NULL. */
+int hawkes_set_info(hawkes_ctx *ctx, int32_t set_id, int64_t *n_out, size_t *device_bytes_out);
+
+/* ell(Theta) of Eq. 1 for a resident set. Blocks until the result is on the host.
+ * Errors: E_INVAL, E_NOSET, E_ADMISSION, E_NOMEM, E_CUDA. If some lambda_n is zero
+ * (possible only with HAWKES_FLAG_EXCLUDE_SELF) the result is -inf with status OK. */
+int hawkes_loglik(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *params,
+                  hawkes_mode mode, double *loglik_out);
+
+/* ell(Theta) and d ell / d Theta (six entries in Theta order) in one pass over the
+ * pairs. The paper has no gradient; it is the exact derivative of Eq. 1, computed
+ * from per-row moments of the same pair terms. Blocks like hawkes_loglik. */
+int hawkes_loglik_grad(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *params,
+                       hawkes_mode mode, double *loglik_out, double grad_out[6]);
+
+/* Asynchronous form for callers that keep results on the device: enqueue the
+ * evaluation on the context's stream and return at once. `device_out` is a device
+ * pointer to 7 doubles (ell, then the gradient if want_grad; the gradient entries
+ * are left unchanged otherwise). The caller synchronises the stream before reading
+ * it. Calls on one context share its workspace and therefore run in stream order. */
+int hawkes_loglik_async(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *params,
+                        hawkes_mode mode, int want_grad, double *device_out);
+
+/* K parameter vectors on one resident set in one launch (K <= 64): the batched
+ * evaluation of many MCMC chains that share a data set. loglik_out has K entries;
+ * grad_out (K x 6, row-major) may be NULL when want_grad is 0. Each result is
+ * bit-identical to the same request evaluated alone. */
+int hawkes_loglik_batch(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_params *params,
+                        hawkes_mode mode, int want_grad, double *loglik_out, double *grad_out);
+
+/* Per-event terms of Eq. 2: mu_out[n] = mu(x_n, t_n) (background rate at event n)
+ * and xi_out[n] = lambda_n - mu_n (the self-excitation part), so lambda_n =
+ * mu_n + xi_n and pi_n = xi_n / lambda_n. Host arrays of n doubles each, owned by
+ * the caller. The log-likelihood of the same pass goes to loglik_out if not NULL. */
+int hawkes_event_terms(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *params,
+                       hawkes_mode mode, double *mu_out, double *xi_out, double *loglik_out);
+
+/* ---- serving: continuous batching of requests from many chains ----------------------
+ * hawkes_submit queues one request (set, Theta, gradient flag, mode) and returns a
+ * ticket at once. A scheduler thread admits queued requests while their device
+ * footprint fits the budget, groups them into persistent launches (up to 64
+ * requests each, several launches in flight on separate streams) and completes
+ * tickets as launches finish. A request's result does not depend on what it was
+ * batched with. */
+int hawkes_submit(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *params, int want_grad,
+                  hawkes_mode mode, uint64_t *ticket_out);
+
+/* Non-blocking. done_out = 1 and the result copied (grad_out may be NULL) when the
+ * request has finished; the ticket is then consumed. done_out = 0 and status
+ * E_PENDING otherwise. A failed request returns its error status (and is consumed). */
+int hawkes_poll(hawkes_ctx *ctx, uint64_t ticket, int *done_out, double *loglik_out,
+                double grad_out[6]);
+
+/* Block until the request finishes or `timeout_ms` elapses (E_TIMEOUT; the ticket
+ * stays valid). timeout_ms < 0 waits without limit. */
+int hawkes_wait(hawkes_ctx *ctx, uint64_t ticket, int timeout_ms, double *loglik_out,
+                double grad_out[6]);
+
+/* Serving counters: submitted, completed, failed, launches, requests in flight, queued,
+ * and the device bytes currently held for requests. `out` has 7 entries. */
+int hawkes_stats(hawkes_ctx *ctx, int64_t out[7]);
+
+/* Human-readable text for a status code. Never NULL. */
+const char *hawkes_strerror(int status);
+
+/* Text of the most recent CUDA error seen on this context ("" if none). */
+const char *hawkes_last_cuda_error(hawkes_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HAWKES_H */

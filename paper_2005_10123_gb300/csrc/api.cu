@@ -1,0 +1,948 @@
+// Host runtime behind include/hawkes.h: contexts, resident event sets, work
+// schedules, synchronous and batched evaluation, and the serving queue.
+//
+// Every evaluation is one "batch" launch pair on a stream: the persistent pair kernel
+// (mixed or fp64) fills per-row partial sums, then the epilogue kernel turns them into
+// log lambda_n - Lambda_n and the gradient terms and reduces them per request in a
+// fixed order. A request's arithmetic depends only on its own set, parameters and
+// schedule, never on the other requests of its batch.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/hawkes.h"
+#include "hk_internal.h"
+
+using namespace hk;
+
+namespace {
+
+constexpr int kKinds = 3;  // schedule kinds: 0 mixed loglik, 1 mixed grad, 2 fp64
+constexpr int kFlights = 3;  // serving launches in flight at once
+constexpr double kLog2e = 1.4426950408889634074;
+
+int kind_of(int mode, int grad) { return mode == HAWKES_MIXED ? (grad ? 1 : 0) : 2; }
+int sums_of(int grad) { return grad ? kSumsGrad : kSumsLoglik; }
+
+struct DevSchedule {
+  int4 *pieces = nullptr;
+  int *range_first = nullptr;
+  int *slot_first = nullptr;
+  int npieces = 0, nranges = 0;
+};
+
+struct EventSetRec {
+  int32_t id = 0;
+  int64_t n = 0, npad = 0;
+  int nrt = 0, nct = 0;
+  void *dev = nullptr;  // one allocation for coordinates, lo arrays and schedules
+  size_t bytes = 0;
+  float *x32 = nullptr, *y32 = nullptr, *t32 = nullptr;
+  double *x64 = nullptr, *y64 = nullptr, *t64 = nullptr;
+  int *lo32 = nullptr, *lo64 = nullptr;
+  double t_first32 = 0, t_last32 = 0, t_first64 = 0, t_last64 = 0;
+  DevSchedule sched[kKinds];
+  int refs = 0;  // queued or running serving requests
+  bool released = false;
+};
+
+struct Workspace {
+  void *dev = nullptr;
+  size_t bytes = 0;
+};
+
+struct TicketRec {
+  int32_t set_id = 0;
+  hawkes_params p{};
+  int grad = 0, mode = 0, flags = 0;
+  int status = HAWKES_E_PENDING;
+  bool done = false;
+  double ll = 0, g[6] = {0, 0, 0, 0, 0, 0};
+  size_t footprint = 0;
+};
+
+struct Flight {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  bool busy = false;
+  std::vector<uint64_t> ids;
+  void *ws = nullptr;
+  size_t ws_bytes = 0;
+  double *host_out = nullptr;  // pinned, kMaxBatch * 8
+  std::vector<EventSetRec *> sets;
+};
+
+}  // namespace
+
+struct hawkes_ctx {
+  int device = 0;
+  int sms = 0;
+  int occ[kKinds] = {1, 1, 1};
+  int occ_launch[2][2] = {{1, 1}, {1, 1}};  // [mode][grad]
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  size_t budget = 0;
+  std::atomic<size_t> used{0};
+  int flags = 0;
+  std::mutex mu;  // sets, sync workspace, synchronous calls
+  std::map<int32_t, EventSetRec *> sets;
+  int32_t next_set = 1;
+  Workspace sync_ws;
+  double *pinned_out = nullptr;  // kMaxBatch * 8 doubles
+  std::string last_cuda;
+  // serving
+  std::mutex smu;
+  std::condition_variable scv;   // scheduler wake-ups
+  std::condition_variable done_cv;  // ticket completions
+  std::unordered_map<uint64_t, TicketRec> tickets;
+  std::deque<uint64_t> pending;
+  uint64_t next_ticket = 1;
+  Flight flights[kFlights];
+  bool flights_ready = false;
+  std::thread sched_thread;
+  bool sched_running = false;
+  bool shutdown = false;
+  int64_t n_submitted = 0, n_completed = 0, n_failed = 0, n_launches = 0;
+  size_t serving_bytes = 0;
+};
+
+namespace {
+
+int cuda_fail(hawkes_ctx *ctx, cudaError_t e) {
+  if (ctx) ctx->last_cuda = cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) return HAWKES_E_NOMEM;
+  return HAWKES_E_CUDA;
+}
+
+#define HK_CUDA(ctx, call)                         \
+  do {                                             \
+    cudaError_t _e = (call);                       \
+    if (_e != cudaSuccess) return cuda_fail(ctx, _e); \
+  } while (0)
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+int check_params(const hawkes_params *p) {
+  if (!p) return HAWKES_E_INVAL;
+  if (!finite_pos(p->mu0) || !finite_pos(p->tau_x) || !finite_pos(p->tau_t) || !finite_pos(p->omega) ||
+      !finite_pos(p->h))
+    return HAWKES_E_INVAL;
+  if (!std::isfinite(p->theta) || p->theta < 0.0) return HAWKES_E_INVAL;
+  return HAWKES_OK;
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// lo[i] = first index whose stored time equals t[i] (times sorted); padded entries get n.
+template <typename F>
+std::vector<int> tie_starts(const std::vector<F> &t, int64_t n, int64_t npad) {
+  std::vector<int> lo((size_t)npad, (int)n);
+  int64_t start = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (i > 0 && t[(size_t)i] != t[(size_t)(i - 1)]) start = i;
+    lo[(size_t)i] = (int)start;
+  }
+  return lo;
+}
+
+struct HostSchedule {
+  std::vector<int4> pieces;
+  std::vector<int> range_first, slot_first;
+};
+
+// Split the (row tile x column tile) units of a set into ranges of about equal cost
+// (row-major order), then split each range at row-tile boundaries into pieces. The
+// cost of a unit is, per warp of the row tile, wb (background) plus wt if the warp's
+// rows have at least one causal column in the tile.
+HostSchedule build_schedule(const std::vector<int> &lo, int64_t n, int nrt, int nct, double wb, double wt,
+                            int target_ranges) {
+  const int64_t nunits = (int64_t)nrt * nct;
+  std::vector<double> cost((size_t)nunits);
+  double total = 0;
+  for (int rt = 0; rt < nrt; ++rt) {
+    for (int ct = 0; ct < nct; ++ct) {
+      const int c0 = ct * kColTile, c1 = c0 + kColTile;
+      double c = 0;
+      for (int w = 0; w < kRowTile / kWarpRows; ++w) {
+        const int wa = rt * kRowTile + w * kWarpRows, wbr = wa + kWarpRows - 1;
+        const int lo_a = lo[(size_t)wa], lo_b = lo[(size_t)wbr];
+        const bool any_causal = !(c0 >= lo_b) || (c1 <= lo_a);
+        c += wb + (any_causal ? wt : 0.0);
+      }
+      cost[(size_t)rt * nct + ct] = c;
+      total += c;
+    }
+  }
+  (void)n;
+  int64_t nranges = std::max<int64_t>(target_ranges, (nunits + 95) / 96);
+  nranges = std::min<int64_t>(std::max<int64_t>(nranges, 1), nunits);
+  // cut points: the first unit whose cumulative cost reaches k * total / nranges
+  std::vector<int64_t> cuts;
+  cuts.push_back(0);
+  double cum = 0;
+  int64_t k = 1;
+  for (int64_t u = 0; u < nunits && k < nranges; ++u) {
+    cum += cost[(size_t)u];
+    while (k < nranges && cum >= total * (double)k / (double)nranges) {
+      if (u + 1 > cuts.back() && u + 1 < nunits) cuts.push_back(u + 1);
+      ++k;
+    }
+  }
+  cuts.push_back(nunits);
+  HostSchedule s;
+  s.slot_first.assign((size_t)nrt + 1, 0);
+  for (size_t r = 0; r + 1 < cuts.size(); ++r) {
+    s.range_first.push_back((int)s.pieces.size());
+    int64_t u = cuts[r];
+    const int64_t end = cuts[r + 1];
+    while (u < end) {
+      const int rt = (int)(u / nct), ct = (int)(u % nct);
+      const int64_t row_end = (int64_t)(rt + 1) * nct;
+      const int64_t stop = std::min(end, row_end);
+      s.pieces.push_back(make_int4(rt, ct, (int)(stop - (int64_t)rt * nct), 0));
+      u = stop;
+    }
+  }
+  s.range_first.push_back((int)s.pieces.size());
+  // slot_first: pieces are in (row tile, column) order
+  std::vector<int> count((size_t)nrt, 0);
+  for (auto &p : s.pieces) count[(size_t)p.x]++;
+  for (int rt = 0; rt < nrt; ++rt) s.slot_first[(size_t)rt + 1] = s.slot_first[(size_t)rt] + count[(size_t)rt];
+  return s;
+}
+
+// Request descriptor for one evaluation of set `S` at Theta `p`.
+int make_request(hawkes_ctx *ctx, const EventSetRec *S, const hawkes_params *p, int mode, int grad,
+                 int flags, Request *R) {
+  std::memset(R, 0, sizeof(*R));
+  R->set.x32 = S->x32; R->set.y32 = S->y32; R->set.t32 = S->t32;
+  R->set.x64 = S->x64; R->set.y64 = S->y64; R->set.t64 = S->t64;
+  R->set.lo32 = S->lo32; R->set.lo64 = S->lo64;
+  R->set.n = (int)S->n; R->set.npad = (int)S->npad; R->set.nrt = S->nrt; R->set.nct = S->nct;
+  const DevSchedule &D = S->sched[kind_of(mode, grad)];
+  R->sched.pieces = D.pieces; R->sched.range_first = D.range_first; R->sched.slot_first = D.slot_first;
+  R->sched.npieces = D.npieces; R->sched.nranges = D.nranges;
+  R->grad = grad;
+  R->flags = flags;
+  const double beta = std::sqrt(kLog2e / (2.0 * p->tau_t * p->tau_t));
+  R->a2 = (float)(kLog2e / (2.0 * p->tau_x * p->tau_x));
+  R->beta = (float)beta;
+  R->wn = (float)(-p->omega * kLog2e / (double)R->beta);
+  R->cn = (float)(-kLog2e / (2.0 * p->h * p->h));
+  R->da = 1.0 / (2.0 * p->tau_x * p->tau_x);
+  R->db = 1.0 / (2.0 * p->tau_t * p->tau_t);
+  R->dc = 1.0 / (2.0 * p->h * p->h);
+  R->mu0 = p->mu0; R->tau_x = p->tau_x; R->tau_t = p->tau_t;
+  R->theta = p->theta; R->omega = p->omega; R->h = p->h;
+  if (mode == HAWKES_MIXED) {
+    // the float32 path must keep every scaled quantity finite and below the padding value
+    const double span = (S->t_last32 - S->t_first32) * (double)R->beta;
+    if (!(R->a2 > 0.f) || !(R->beta > 0.f) || !std::isfinite(R->wn) || !(R->cn < 0.f) ||
+        !std::isfinite(R->a2) || !std::isfinite(R->cn) || span > 1.0e15)
+      return HAWKES_E_INVAL;
+    R->t_last = S->t_last32;
+    R->tscale = 1.0 / (double)R->beta;
+  } else {
+    R->t_last = S->t_last64;
+    R->tscale = 1.0;
+  }
+  (void)ctx;
+  return HAWKES_OK;
+}
+
+int epi_blocks(int64_t n) { return (int)((n + kEpiThreads - 1) / kEpiThreads); }
+
+// Device bytes one request needs: partial sums, epilogue block partials, ticket, output.
+size_t request_footprint(const EventSetRec *S, int mode, int grad) {
+  const DevSchedule &D = S->sched[kind_of(mode, grad)];
+  size_t b = align_up((size_t)D.npieces * sums_of(grad) * kRowTile * sizeof(double), 256);
+  b += align_up((size_t)epi_blocks(S->n) * 8 * sizeof(double), 256);
+  return b;
+}
+
+// Batch workspace header: the pair-kernel counter at byte 0, one epilogue ticket per
+// request at kTicketOff + 4 r, then the per-request outputs (8 doubles each). One
+// memset of the header clears the counter and every ticket.
+constexpr size_t kTicketOff = 256;
+constexpr size_t kHdrBytes = 1024;
+constexpr size_t kOutBytes = (size_t)kMaxBatch * 8 * sizeof(double);
+constexpr size_t kFixedBytes = kHdrBytes + kOutBytes;
+
+// Carve one request's workspace out of `base` (as sized by request_footprint).
+void bind_workspace(Request *R, const EventSetRec *S, int mode, int grad, char *base, double *out,
+                    unsigned *ticket) {
+  const DevSchedule &D = S->sched[kind_of(mode, grad)];
+  R->partials = (double *)base;
+  R->block_part = (double *)(base + align_up((size_t)D.npieces * sums_of(grad) * kRowTile * sizeof(double), 256));
+  R->ticket = ticket;
+  R->out = out;
+}
+
+int pair_grid(hawkes_ctx *ctx, int mode, int grad, int total_items) {
+  const int cap = ctx->sms * std::max(1, ctx->occ_launch[mode == HAWKES_MIXED ? 1 : 0][grad]);
+  return std::max(1, std::min(total_items, cap));
+}
+
+// Enqueue pair + epilogue kernels for a prepared batch on `s`. The counter and every
+// request's ticket must already be zero (the caller clears the batch header).
+int launch_batch(hawkes_ctx *ctx, Batch &b, int mode, int grad, cudaStream_t s) {
+  b.mode = mode == HAWKES_MIXED ? 1 : 0;
+  int items = 0, epi = 0;
+  for (int r = 0; r < b.nreq; ++r) {
+    b.req[r].item_begin = items;
+    b.req[r].epi_begin = epi;
+    items += b.req[r].sched.nranges;
+    epi += epi_blocks(b.req[r].set.n);
+  }
+  b.total_items = items;
+  b.total_epi = epi;
+  const int grid = pair_grid(ctx, mode, grad, items);
+  if (mode == HAWKES_MIXED) HK_CUDA(ctx, launch_pair_mixed(b, grad != 0, grid, s));
+  else HK_CUDA(ctx, launch_pair_fp64(b, grad != 0, grid, s));
+  const int egrid = std::max(1, std::min(epi, ctx->sms * 8));
+  HK_CUDA(ctx, launch_epilogue(b, grad != 0, egrid, s));
+  return HAWKES_OK;
+}
+
+int ensure_sync_ws(hawkes_ctx *ctx, size_t need) {
+  if (ctx->sync_ws.bytes >= need) return HAWKES_OK;
+  need = align_up(need + need / 4, 1 << 20);
+  const size_t old = ctx->sync_ws.bytes;
+  if (ctx->used.load() - old + need > ctx->budget) return HAWKES_E_ADMISSION;
+  if (ctx->sync_ws.dev) {
+    HK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    cudaFree(ctx->sync_ws.dev);
+    ctx->sync_ws.dev = nullptr;
+    ctx->used -= old;
+    ctx->sync_ws.bytes = 0;
+  }
+  void *p = nullptr;
+  cudaError_t e = cudaMalloc(&p, need);
+  if (e != cudaSuccess) return cuda_fail(ctx, e);
+  ctx->sync_ws.dev = p;
+  ctx->sync_ws.bytes = need;
+  ctx->used += need;
+  return HAWKES_OK;
+}
+
+EventSetRec *find_set(hawkes_ctx *ctx, int32_t id) {
+  auto it = ctx->sets.find(id);
+  if (it == ctx->sets.end() || it->second->released) return nullptr;
+  return it->second;
+}
+
+void free_set(hawkes_ctx *ctx, EventSetRec *S) {
+  if (S->dev) cudaFree(S->dev);
+  ctx->used -= S->bytes;
+  delete S;
+}
+
+// Synchronous evaluation of k requests on one set (k = 1 for the single calls).
+// Results (7 doubles per request) land in host_out[8 * r]; device_out, if given
+// (k = 1 only), receives them on the device instead and the call does not block.
+int eval_sync(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_params *params, int mode, int grad,
+              double *host_out, double *device_out, double *mu_out, double *xi_out) {
+  if (mode != HAWKES_FP64 && mode != HAWKES_MIXED) return HAWKES_E_INVAL;
+  if (k < 1 || k > kMaxBatch) return HAWKES_E_INVAL;
+  for (int r = 0; r < k; ++r)
+    if (int rc = check_params(&params[r])) return rc;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  EventSetRec *S = find_set(ctx, set_id);
+  if (!S) return HAWKES_E_NOSET;
+  const size_t per = request_footprint(S, mode, grad);
+  const size_t rows_bytes = (mu_out || xi_out) ? align_up((size_t)S->n * sizeof(double), 256) * 2 : 0;
+  const size_t need = kFixedBytes + rows_bytes + per * k;
+  if (int rc = ensure_sync_ws(ctx, need)) return rc;
+  char *base = (char *)ctx->sync_ws.dev;
+  std::unique_ptr<Batch> b(new Batch());
+  std::memset(b.get(), 0, sizeof(Batch));
+  b->nreq = k;
+  b->counter = (unsigned *)base;
+  double *outs = (double *)(base + kHdrBytes);
+  char *rows_base = base + kFixedBytes;
+  char *req_base = rows_base + rows_bytes;
+  for (int r = 0; r < k; ++r) {
+    if (int rc = make_request(ctx, S, &params[r], mode, grad, ctx->flags, &b->req[r])) return rc;
+    bind_workspace(&b->req[r], S, mode, grad, req_base + (size_t)r * per,
+                   device_out ? device_out : outs + 8 * r, (unsigned *)(base + kTicketOff) + r);
+  }
+  if (rows_bytes) {
+    b->req[0].mu_out = (double *)rows_base;
+    b->req[0].xi_out = (double *)(rows_base + rows_bytes / 2);
+  }
+  HK_CUDA(ctx, cudaMemsetAsync(base, 0, kHdrBytes, ctx->stream));
+  if (int rc = launch_batch(ctx, *b, mode, grad, ctx->stream)) return rc;
+  if (device_out) return HAWKES_OK;
+  HK_CUDA(ctx, cudaMemcpyAsync(ctx->pinned_out, outs, (size_t)k * 8 * sizeof(double), cudaMemcpyDeviceToHost,
+                               ctx->stream));
+  if (mu_out) HK_CUDA(ctx, cudaMemcpyAsync(mu_out, b->req[0].mu_out, (size_t)S->n * sizeof(double),
+                                           cudaMemcpyDeviceToHost, ctx->stream));
+  if (xi_out) HK_CUDA(ctx, cudaMemcpyAsync(xi_out, b->req[0].xi_out, (size_t)S->n * sizeof(double),
+                                           cudaMemcpyDeviceToHost, ctx->stream));
+  HK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  std::memcpy(host_out, ctx->pinned_out, (size_t)k * 8 * sizeof(double));
+  return HAWKES_OK;
+}
+
+// ---- serving -------------------------------------------------------------------------
+
+void complete_ticket(hawkes_ctx *ctx, uint64_t id, int status, const double *vals) {
+  auto it = ctx->tickets.find(id);
+  if (it == ctx->tickets.end()) return;
+  TicketRec &T = it->second;
+  T.status = status;
+  T.done = true;
+  if (status == HAWKES_OK && vals) {
+    T.ll = vals[0];
+    for (int q = 0; q < 6; ++q) T.g[q] = vals[1 + q];
+  }
+  if (status == HAWKES_OK) ctx->n_completed++;
+  else ctx->n_failed++;
+}
+
+void release_set_ref(hawkes_ctx *ctx, EventSetRec *S) {
+  // caller holds ctx->mu
+  if (--S->refs == 0 && S->released) {
+    ctx->sets.erase(S->id);
+    free_set(ctx, S);
+  }
+}
+
+// Collect finished flights. Holds smu; takes mu briefly for set references.
+void reap_flights(hawkes_ctx *ctx) {
+  for (auto &F : ctx->flights) {
+    if (!F.busy) continue;
+    cudaError_t q = cudaEventQuery(F.done);
+    if (q == cudaErrorNotReady) continue;
+    const int status = q == cudaSuccess ? HAWKES_OK : HAWKES_E_CUDA;
+    if (q != cudaSuccess) ctx->last_cuda = cudaGetErrorString(q);
+    for (size_t r = 0; r < F.ids.size(); ++r) complete_ticket(ctx, F.ids[r], status, F.host_out + 8 * r);
+    {
+      std::lock_guard<std::mutex> lock(ctx->mu);
+      for (auto *S : F.sets) release_set_ref(ctx, S);
+    }
+    ctx->used -= F.ws_bytes;
+    ctx->serving_bytes -= F.ws_bytes;
+    F.ws = nullptr;
+    F.ws_bytes = 0;
+    F.ids.clear();
+    F.sets.clear();
+    F.busy = false;
+    ctx->done_cv.notify_all();
+  }
+}
+
+// Form and launch one batch on flight F from the pending queue. Holds smu.
+// Returns true if a batch was launched.
+bool launch_pending(hawkes_ctx *ctx, Flight &F) {
+  if (ctx->pending.empty()) return false;
+  const TicketRec &H = ctx->tickets[ctx->pending.front()];
+  const int mode = H.mode, grad = H.grad;
+  std::vector<uint64_t> take;
+  std::vector<EventSetRec *> sets;
+  size_t bytes = kFixedBytes;
+  const size_t used = ctx->used.load();
+  const size_t room = ctx->budget > used ? ctx->budget - used : 0;
+  const size_t fixed_used = used - ctx->serving_bytes;  // resident sets and the sync workspace
+  bool any_flight = false;
+  for (auto &G : ctx->flights) any_flight |= G.busy;
+  {
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    for (auto it = ctx->pending.begin(); it != ctx->pending.end() && (int)take.size() < kMaxBatch;) {
+      TicketRec &T = ctx->tickets[*it];
+      if (T.mode != mode || T.grad != grad) { ++it; continue; }
+      auto sit = ctx->sets.find(T.set_id);
+      if (sit == ctx->sets.end()) {  // cannot happen while the request holds a reference
+        complete_ticket(ctx, *it, HAWKES_E_NOSET, nullptr);
+        it = ctx->pending.erase(it);
+        ctx->done_cv.notify_all();
+        continue;
+      }
+      if (bytes + T.footprint > room) {
+        const bool never_fits = kFixedBytes + T.footprint + fixed_used > ctx->budget;
+        if (take.empty() && !any_flight && never_fits) {
+          complete_ticket(ctx, *it, HAWKES_E_ADMISSION, nullptr);
+          release_set_ref(ctx, sit->second);
+          it = ctx->pending.erase(it);
+          ctx->done_cv.notify_all();
+          continue;
+        }
+        break;  // first-come first-served within a kind: wait for memory to free up
+      }
+      bytes += T.footprint;
+      take.push_back(*it);
+      sets.push_back(sit->second);
+      it = ctx->pending.erase(it);
+    }
+  }
+  if (take.empty()) return false;
+  void *ws = nullptr;
+  std::unique_ptr<Batch> b(new Batch());
+  std::memset(b.get(), 0, sizeof(Batch));
+  int rc = HAWKES_OK;
+  cudaError_t e = cudaMallocAsync(&ws, bytes, F.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ws, 0, kHdrBytes, F.stream);
+  if (e != cudaSuccess) rc = cuda_fail(ctx, e);
+  if (rc == HAWKES_OK) {
+    char *base = (char *)ws;
+    b->counter = (unsigned *)base;
+    double *outs = (double *)(base + kHdrBytes);
+    char *cur = base + kFixedBytes;
+    b->nreq = (int)take.size();
+    for (size_t r = 0; r < take.size() && rc == HAWKES_OK; ++r) {
+      TicketRec &T = ctx->tickets[take[r]];
+      rc = make_request(ctx, sets[r], &T.p, mode, grad, T.flags, &b->req[r]);
+      bind_workspace(&b->req[r], sets[r], mode, grad, cur, outs + 8 * r, (unsigned *)(base + kTicketOff) + r);
+      cur += T.footprint;
+    }
+    if (rc == HAWKES_OK) rc = launch_batch(ctx, *b, mode, grad, F.stream);
+    if (rc == HAWKES_OK) {
+      e = cudaMemcpyAsync(F.host_out, outs, take.size() * 8 * sizeof(double), cudaMemcpyDeviceToHost, F.stream);
+      if (e != cudaSuccess) rc = cuda_fail(ctx, e);
+    }
+    cudaFreeAsync(ws, F.stream);
+    if (rc == HAWKES_OK) {
+      e = cudaEventRecord(F.done, F.stream);
+      if (e != cudaSuccess) rc = cuda_fail(ctx, e);
+    }
+  }
+  if (rc != HAWKES_OK) {
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    for (size_t r = 0; r < take.size(); ++r) {
+      complete_ticket(ctx, take[r], rc, nullptr);
+      release_set_ref(ctx, sets[r]);
+    }
+    ctx->done_cv.notify_all();
+    return false;
+  }
+  ctx->used += bytes;
+  ctx->serving_bytes += bytes;
+  F.ws = ws;
+  F.ws_bytes = bytes;
+  F.ids = std::move(take);
+  F.sets = std::move(sets);
+  F.busy = true;
+  ctx->n_launches++;
+  return true;
+}
+
+void scheduler_loop(hawkes_ctx *ctx) {
+  cudaSetDevice(ctx->device);
+  std::unique_lock<std::mutex> lk(ctx->smu);
+  while (true) {
+    reap_flights(ctx);
+    bool launched = false;
+    for (auto &F : ctx->flights) {
+      if (F.busy || ctx->pending.empty()) continue;
+      if (launch_pending(ctx, F)) launched = true;
+    }
+    bool inflight = false;
+    for (auto &F : ctx->flights) inflight |= F.busy;
+    if (ctx->shutdown && !inflight) break;
+    if (launched) continue;
+    if (inflight) ctx->scv.wait_for(lk, std::chrono::microseconds(100));
+    else ctx->scv.wait_for(lk, std::chrono::milliseconds(50));
+  }
+}
+
+int init_flights(hawkes_ctx *ctx) {
+  if (ctx->flights_ready) return HAWKES_OK;
+  for (auto &F : ctx->flights) {  // resumable: members created by an earlier failed call are kept
+    if (!F.stream) HK_CUDA(ctx, cudaStreamCreateWithFlags(&F.stream, cudaStreamNonBlocking));
+    if (!F.done) HK_CUDA(ctx, cudaEventCreateWithFlags(&F.done, cudaEventDisableTiming));
+    if (!F.host_out) HK_CUDA(ctx, cudaMallocHost((void **)&F.host_out, kMaxBatch * 8 * sizeof(double)));
+  }
+  ctx->flights_ready = true;
+  return HAWKES_OK;
+}
+
+}  // namespace
+
+// ---- public ABI ------------------------------------------------------------------------
+
+extern "C" {
+
+const char *hawkes_strerror(int status) {
+  switch (status) {
+    case HAWKES_OK: return "ok";
+    case HAWKES_E_INVAL: return "invalid argument";
+    case HAWKES_E_UNSORTED: return "event times are not sorted";
+    case HAWKES_E_NOSET: return "unknown event set";
+    case HAWKES_E_ADMISSION: return "device memory budget exceeded";
+    case HAWKES_E_NOMEM: return "out of memory";
+    case HAWKES_E_TIMEOUT: return "timed out";
+    case HAWKES_E_PENDING: return "pending";
+    case HAWKES_E_CUDA: return "CUDA error";
+    case HAWKES_E_TICKET: return "unknown or consumed ticket";
+    case HAWKES_E_SHUTDOWN: return "context shut down";
+    default: return "unknown status";
+  }
+}
+
+const char *hawkes_last_cuda_error(hawkes_ctx *ctx) { return ctx ? ctx->last_cuda.c_str() : ""; }
+
+int hawkes_create(hawkes_ctx **out, int device, size_t hbm_budget_bytes, void *cuda_stream) {
+  if (!out) return HAWKES_E_INVAL;
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e);
+  if (device < 0 || device >= ndev) return HAWKES_E_INVAL;
+  e = cudaSetDevice(device);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e);
+  std::unique_ptr<hawkes_ctx> ctx(new (std::nothrow) hawkes_ctx());
+  if (!ctx) return HAWKES_E_NOMEM;
+  ctx->device = device;
+  cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device);
+  ctx->occ_launch[1][0] = occupancy_pair_mixed(false);
+  ctx->occ_launch[1][1] = occupancy_pair_mixed(true);
+  ctx->occ_launch[0][0] = occupancy_pair_fp64(false);
+  ctx->occ_launch[0][1] = occupancy_pair_fp64(true);
+  ctx->occ[0] = ctx->occ_launch[1][0];
+  ctx->occ[1] = ctx->occ_launch[1][1];
+  ctx->occ[2] = std::min(ctx->occ_launch[0][0], ctx->occ_launch[0][1]);
+  for (int &o : ctx->occ) o = std::max(1, o);
+  if (cuda_stream) {
+    ctx->stream = (cudaStream_t)cuda_stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e);
+    ctx->own_stream = true;
+  }
+  size_t free_b = 0, total_b = 0;
+  e = cudaMemGetInfo(&free_b, &total_b);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e);
+  ctx->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.9 * (double)free_b);
+  e = cudaMallocHost((void **)&ctx->pinned_out, kMaxBatch * 8 * sizeof(double));
+  if (e != cudaSuccess) return cuda_fail(nullptr, e);
+  *out = ctx.release();
+  return HAWKES_OK;
+}
+
+int hawkes_destroy(hawkes_ctx *ctx) {
+  if (!ctx) return HAWKES_OK;
+  cudaSetDevice(ctx->device);
+  {
+    std::unique_lock<std::mutex> lk(ctx->smu);
+    ctx->shutdown = true;
+    for (uint64_t id : ctx->pending) complete_ticket(ctx, id, HAWKES_E_SHUTDOWN, nullptr);
+    {
+      std::lock_guard<std::mutex> lock(ctx->mu);
+      for (uint64_t id : ctx->pending) {
+        auto it = ctx->sets.find(ctx->tickets[id].set_id);
+        if (it != ctx->sets.end()) it->second->refs--;
+      }
+    }
+    ctx->pending.clear();
+    ctx->scv.notify_all();
+    ctx->done_cv.notify_all();
+  }
+  if (ctx->sched_thread.joinable()) ctx->sched_thread.join();
+  cudaStreamSynchronize(ctx->stream);
+  for (auto &F : ctx->flights) {
+    if (F.stream) { cudaStreamSynchronize(F.stream); cudaStreamDestroy(F.stream); }
+    if (F.done) cudaEventDestroy(F.done);
+    if (F.host_out) cudaFreeHost(F.host_out);
+  }
+  for (auto &kv : ctx->sets) {
+    if (kv.second->dev) cudaFree(kv.second->dev);
+    delete kv.second;
+  }
+  ctx->sets.clear();
+  if (ctx->sync_ws.dev) cudaFree(ctx->sync_ws.dev);
+  if (ctx->pinned_out) cudaFreeHost(ctx->pinned_out);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return HAWKES_OK;
+}
+
+int hawkes_set_flags(hawkes_ctx *ctx, int flags) {
+  if (!ctx || (flags & ~HAWKES_FLAG_EXCLUDE_SELF)) return HAWKES_E_INVAL;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  ctx->flags = flags;
+  return HAWKES_OK;
+}
+
+int hawkes_upload_events(hawkes_ctx *ctx, const double *x, const double *y, const double *t, int64_t n,
+                         int32_t *set_id_out) {
+  if (!ctx || !x || !y || !t || !set_id_out || n < 1) return HAWKES_E_INVAL;
+  if (n > (int64_t)1 << 30) return HAWKES_E_INVAL;
+  for (int64_t i = 0; i < n; ++i) {
+    if (!std::isfinite(x[i]) || !std::isfinite(y[i]) || !std::isfinite(t[i]) || t[i] < 0.0) return HAWKES_E_INVAL;
+    if (std::fabs(x[i]) > 1e30 || std::fabs(y[i]) > 1e30 || t[i] > 1e30) return HAWKES_E_INVAL;
+  }
+  for (int64_t i = 1; i < n; ++i)
+    if (!(t[i] >= t[i - 1])) return HAWKES_E_UNSORTED;
+  cudaSetDevice(ctx->device);
+  const int64_t npad = (int64_t)align_up((size_t)n, kRowTile);
+  std::unique_ptr<EventSetRec> S(new EventSetRec());
+  S->n = n;
+  S->npad = npad;
+  S->nrt = (int)(npad / kRowTile);
+  S->nct = (int)(npad / kColTile);
+  // host staging: float64 and float32 SoA, padded with zeros (the kernels substitute
+  // a sentinel time for padded events)
+  std::vector<double> X64((size_t)npad, 0.0), Y64((size_t)npad, 0.0), T64((size_t)npad, 0.0);
+  std::vector<float> X32((size_t)npad, 0.f), Y32((size_t)npad, 0.f), T32((size_t)npad, 0.f);
+  for (int64_t i = 0; i < n; ++i) {
+    X64[(size_t)i] = x[i]; Y64[(size_t)i] = y[i]; T64[(size_t)i] = t[i];
+    X32[(size_t)i] = (float)x[i]; Y32[(size_t)i] = (float)y[i]; T32[(size_t)i] = (float)t[i];
+  }
+  for (int64_t i = n; i < npad; ++i) { T64[(size_t)i] = t[n - 1]; T32[(size_t)i] = (float)t[n - 1]; }
+  std::vector<int> lo32 = tie_starts(T32, n, npad), lo64 = tie_starts(T64, n, npad);
+  S->t_first32 = T32[0]; S->t_last32 = T32[(size_t)n - 1];
+  S->t_first64 = T64[0]; S->t_last64 = T64[(size_t)n - 1];
+  // schedules
+  const double wb[kKinds] = {8.0, 10.0, 1.0}, wt[kKinds] = {3.0, 5.0, 1.0};
+  HostSchedule hs[kKinds];
+  for (int k = 0; k < kKinds; ++k)
+    hs[k] = build_schedule(k == 2 ? lo64 : lo32, n, S->nrt, S->nct, wb[k], wt[k], ctx->sms * ctx->occ[k]);
+  // one device allocation
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off += align_up(bytes, 256); return o; };
+  const size_t o_x32 = take(npad * 4), o_y32 = take(npad * 4), o_t32 = take(npad * 4);
+  const size_t o_x64 = take(npad * 8), o_y64 = take(npad * 8), o_t64 = take(npad * 8);
+  const size_t o_lo32 = take(npad * 4), o_lo64 = take(npad * 4);
+  size_t o_pc[kKinds], o_rf[kKinds], o_sf[kKinds];
+  for (int k = 0; k < kKinds; ++k) {
+    o_pc[k] = take(hs[k].pieces.size() * sizeof(int4));
+    o_rf[k] = take(hs[k].range_first.size() * sizeof(int));
+    o_sf[k] = take(hs[k].slot_first.size() * sizeof(int));
+  }
+  const size_t bytes = off;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  if (ctx->used.load() + bytes > ctx->budget) return HAWKES_E_ADMISSION;
+  void *dev = nullptr;
+  cudaError_t e = cudaMalloc(&dev, bytes);
+  if (e != cudaSuccess) return cuda_fail(ctx, e);
+  char *d = (char *)dev;
+  std::vector<char> host(bytes, 0);
+  auto put = [&](size_t o, const void *src, size_t nb) { std::memcpy(host.data() + o, src, nb); };
+  put(o_x32, X32.data(), npad * 4); put(o_y32, Y32.data(), npad * 4); put(o_t32, T32.data(), npad * 4);
+  put(o_x64, X64.data(), npad * 8); put(o_y64, Y64.data(), npad * 8); put(o_t64, T64.data(), npad * 8);
+  put(o_lo32, lo32.data(), npad * 4); put(o_lo64, lo64.data(), npad * 4);
+  for (int k = 0; k < kKinds; ++k) {
+    put(o_pc[k], hs[k].pieces.data(), hs[k].pieces.size() * sizeof(int4));
+    put(o_rf[k], hs[k].range_first.data(), hs[k].range_first.size() * sizeof(int));
+    put(o_sf[k], hs[k].slot_first.data(), hs[k].slot_first.size() * sizeof(int));
+  }
+  e = cudaMemcpyAsync(dev, host.data(), bytes, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) { cudaFree(dev); return cuda_fail(ctx, e); }
+  S->dev = dev;
+  S->bytes = bytes;
+  S->x32 = (float *)(d + o_x32); S->y32 = (float *)(d + o_y32); S->t32 = (float *)(d + o_t32);
+  S->x64 = (double *)(d + o_x64); S->y64 = (double *)(d + o_y64); S->t64 = (double *)(d + o_t64);
+  S->lo32 = (int *)(d + o_lo32); S->lo64 = (int *)(d + o_lo64);
+  for (int k = 0; k < kKinds; ++k) {
+    S->sched[k].pieces = (int4 *)(d + o_pc[k]);
+    S->sched[k].range_first = (int *)(d + o_rf[k]);
+    S->sched[k].slot_first = (int *)(d + o_sf[k]);
+    S->sched[k].npieces = (int)hs[k].pieces.size();
+    S->sched[k].nranges = (int)hs[k].range_first.size() - 1;
+  }
+  ctx->used += bytes;
+  const int32_t id = ctx->next_set++;
+  S->id = id;
+  ctx->sets[id] = S.release();
+  *set_id_out = id;
+  return HAWKES_OK;
+}
+
+int hawkes_release_events(hawkes_ctx *ctx, int32_t set_id) {
+  if (!ctx) return HAWKES_E_INVAL;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  auto it = ctx->sets.find(set_id);
+  if (it == ctx->sets.end() || it->second->released) return HAWKES_E_NOSET;
+  EventSetRec *S = it->second;
+  S->released = true;
+  if (S->refs == 0) {
+    cudaStreamSynchronize(ctx->stream);
+    ctx->sets.erase(it);
+    free_set(ctx, S);
+  }
+  return HAWKES_OK;
+}
+
+int hawkes_set_info(hawkes_ctx *ctx, int32_t set_id, int64_t *n_out, size_t *device_bytes_out) {
+  if (!ctx) return HAWKES_E_INVAL;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  EventSetRec *S = find_set(ctx, set_id);
+  if (!S) return HAWKES_E_NOSET;
+  if (n_out) *n_out = S->n;
+  if (device_bytes_out) *device_bytes_out = S->bytes;
+  return HAWKES_OK;
+}
+
+int hawkes_loglik(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *params, hawkes_mode mode,
+                  double *loglik_out) {
+  if (!ctx || !params || !loglik_out) return HAWKES_E_INVAL;
+  cudaSetDevice(ctx->device);
+  double out[8];
+  int rc = eval_sync(ctx, set_id, 1, params, mode, 0, out, nullptr, nullptr, nullptr);
+  if (rc == HAWKES_OK) *loglik_out = out[0];
+  return rc;
+}
+
+int hawkes_loglik_grad(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *params, hawkes_mode mode,
+                       double *loglik_out, double grad_out[6]) {
+  if (!ctx || !params || !loglik_out || !grad_out) return HAWKES_E_INVAL;
+  cudaSetDevice(ctx->device);
+  double out[8];
+  int rc = eval_sync(ctx, set_id, 1, params, mode, 1, out, nullptr, nullptr, nullptr);
+  if (rc == HAWKES_OK) {
+    *loglik_out = out[0];
+    for (int q = 0; q < 6; ++q) grad_out[q] = out[1 + q];
+  }
+  return rc;
+}
+
+int hawkes_loglik_async(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *params, hawkes_mode mode,
+                        int want_grad, double *device_out) {
+  if (!ctx || !params || !device_out) return HAWKES_E_INVAL;
+  cudaSetDevice(ctx->device);
+  return eval_sync(ctx, set_id, 1, params, mode, want_grad ? 1 : 0, nullptr, device_out, nullptr, nullptr);
+}
+
+int hawkes_loglik_batch(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_params *params, hawkes_mode mode,
+                        int want_grad, double *loglik_out, double *grad_out) {
+  if (!ctx || !params || !loglik_out || (want_grad && !grad_out) || k < 1 || k > kMaxBatch)
+    return HAWKES_E_INVAL;
+  cudaSetDevice(ctx->device);
+  std::vector<double> out((size_t)k * 8);
+  int rc = eval_sync(ctx, set_id, k, params, mode, want_grad ? 1 : 0, out.data(), nullptr, nullptr, nullptr);
+  if (rc != HAWKES_OK) return rc;
+  for (int r = 0; r < k; ++r) {
+    loglik_out[r] = out[(size_t)r * 8];
+    if (want_grad)
+      for (int q = 0; q < 6; ++q) grad_out[(size_t)r * 6 + q] = out[(size_t)r * 8 + 1 + q];
+  }
+  return HAWKES_OK;
+}
+
+int hawkes_event_terms(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *params, hawkes_mode mode,
+                       double *mu_out, double *xi_out, double *loglik_out) {
+  if (!ctx || !params || !mu_out || !xi_out) return HAWKES_E_INVAL;
+  cudaSetDevice(ctx->device);
+  double out[8];
+  int rc = eval_sync(ctx, set_id, 1, params, mode, 0, out, nullptr, mu_out, xi_out);
+  if (rc == HAWKES_OK && loglik_out) *loglik_out = out[0];
+  return rc;
+}
+
+int hawkes_submit(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *params, int want_grad, hawkes_mode mode,
+                  uint64_t *ticket_out) {
+  if (!ctx || !params || !ticket_out) return HAWKES_E_INVAL;
+  if (mode != HAWKES_FP64 && mode != HAWKES_MIXED) return HAWKES_E_INVAL;
+  if (int rc = check_params(params)) return rc;
+  cudaSetDevice(ctx->device);
+  TicketRec T;
+  T.set_id = set_id;
+  T.p = *params;
+  T.grad = want_grad ? 1 : 0;
+  T.mode = mode;
+  {
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    EventSetRec *S = find_set(ctx, set_id);
+    if (!S) return HAWKES_E_NOSET;
+    Request probe;
+    if (int rc = make_request(ctx, S, params, mode, T.grad, ctx->flags, &probe)) return rc;
+    T.flags = ctx->flags;
+    T.footprint = request_footprint(S, mode, T.grad);
+    if (T.footprint + 4096 > ctx->budget) return HAWKES_E_ADMISSION;
+    S->refs++;
+  }
+  std::lock_guard<std::mutex> lk(ctx->smu);
+  if (ctx->shutdown) {
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    auto it = ctx->sets.find(set_id);
+    if (it != ctx->sets.end()) release_set_ref(ctx, it->second);
+    return HAWKES_E_SHUTDOWN;
+  }
+  if (int rc = init_flights(ctx)) {
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    auto it = ctx->sets.find(set_id);
+    if (it != ctx->sets.end()) release_set_ref(ctx, it->second);
+    return rc;
+  }
+  const uint64_t id = ctx->next_ticket++;
+  ctx->tickets[id] = T;
+  ctx->pending.push_back(id);
+  ctx->n_submitted++;
+  if (!ctx->sched_running) {
+    ctx->sched_running = true;
+    ctx->sched_thread = std::thread(scheduler_loop, ctx);
+  }
+  ctx->scv.notify_all();
+  *ticket_out = id;
+  return HAWKES_OK;
+}
+
+int hawkes_poll(hawkes_ctx *ctx, uint64_t ticket, int *done_out, double *loglik_out, double grad_out[6]) {
+  if (!ctx || !done_out) return HAWKES_E_INVAL;
+  std::lock_guard<std::mutex> lk(ctx->smu);
+  auto it = ctx->tickets.find(ticket);
+  if (it == ctx->tickets.end()) return HAWKES_E_TICKET;
+  if (!it->second.done) {
+    *done_out = 0;
+    return HAWKES_E_PENDING;
+  }
+  *done_out = 1;
+  const TicketRec T = it->second;
+  ctx->tickets.erase(it);
+  if (T.status != HAWKES_OK) return T.status;
+  if (loglik_out) *loglik_out = T.ll;
+  if (grad_out)
+    for (int q = 0; q < 6; ++q) grad_out[q] = T.grad ? T.g[q] : 0.0;
+  return HAWKES_OK;
+}
+
+int hawkes_wait(hawkes_ctx *ctx, uint64_t ticket, int timeout_ms, double *loglik_out, double grad_out[6]) {
+  if (!ctx) return HAWKES_E_INVAL;
+  std::unique_lock<std::mutex> lk(ctx->smu);
+  auto ready = [&] {
+    auto it = ctx->tickets.find(ticket);
+    return it == ctx->tickets.end() || it->second.done;
+  };
+  if (timeout_ms < 0) ctx->done_cv.wait(lk, ready);
+  else if (!ctx->done_cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready)) return HAWKES_E_TIMEOUT;
+  auto it = ctx->tickets.find(ticket);
+  if (it == ctx->tickets.end()) return HAWKES_E_TICKET;
+  const TicketRec T = it->second;
+  ctx->tickets.erase(it);
+  if (T.status != HAWKES_OK) return T.status;
+  if (loglik_out) *loglik_out = T.ll;
+  if (grad_out)
+    for (int q = 0; q < 6; ++q) grad_out[q] = T.grad ? T.g[q] : 0.0;
+  return HAWKES_OK;
+}
+
+int hawkes_stats(hawkes_ctx *ctx, int64_t out[7]) {
+  if (!ctx || !out) return HAWKES_E_INVAL;
+  std::lock_guard<std::mutex> lk(ctx->smu);
+  int64_t inflight = 0;
+  for (auto &F : ctx->flights) inflight += F.busy ? (int64_t)F.ids.size() : 0;
+  out[0] = ctx->n_submitted;
+  out[1] = ctx->n_completed;
+  out[2] = ctx->n_failed;
+  out[3] = ctx->n_launches;
+  out[4] = inflight;
+  out[5] = (int64_t)ctx->pending.size();
+  out[6] = (int64_t)ctx->serving_bytes;
+  return HAWKES_OK;
+}
+
+}  // extern "C"

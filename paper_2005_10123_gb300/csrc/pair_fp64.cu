@@ -1,0 +1,249 @@
+// Double-precision pair kernel and the epilogue shared by both precision modes.
+//
+// pair_fp64_kernel forms the same per-row sums as the mixed kernel (S_b, S_s and the
+// gradient moments R_b, T_b, R_s, U_s of Section 2.1, Eq. 1), entirely in float64 with
+// the library exp(), and the moments in raw units (r^2 in km^2, dt in days).
+//
+// epilogue_kernel turns each row's sums into (Section 2.1)
+//   lambda_n = A S_b + C S_s,  A = mu0 / ((2 pi)^{3/2} tau_x^2 tau_t),  C = theta omega / (2 pi h^2)
+//   Lambda_n = mu0 (Phi((t_N - t_n)/tau_t) - Phi(-t_n/tau_t)) + theta (1 - exp(-omega (t_N - t_n)))
+//   ell_n    = log lambda_n - Lambda_n
+// plus the gradient terms (d lambda_n / d Theta) / lambda_n - d Lambda_n / d Theta, and
+// reduces them over n in a fixed order: a warp-shuffle tree and an in-order warp sum
+// per block, then the last block to finish sums the block partials in block order.
+#include "hk_internal.h"
+
+namespace hk {
+namespace {
+
+constexpr double kPadTime = 1.0e150;  // time of a padded event: dt^2 = 1e300 stays finite
+
+template <int KIND, bool GRAD>
+__device__ __forceinline__ void tile_pass64(const double *__restrict__ sx, const double *__restrict__ sy,
+                                            const double *__restrict__ st, const double (&X)[4],
+                                            const double (&Y)[4], const double (&T)[4], const int (&LO)[4],
+                                            int row_a0, int c0, bool excl, double da, double db, double dc,
+                                            double omega, double (&acc)[GRAD ? kSumsGrad : kSumsLoglik][4]) {
+#pragma unroll 2
+  for (int j = 0; j < kColTile; ++j) {
+    const double cx = sx[j], cy = sy[j], ctj = st[j];
+    const int col = c0 + j;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const double dx = X[k] - cx, dy = Y[k] - cy, dt = T[k] - ctj;
+      const double r2 = __fma_rn(dx, dx, __dmul_rn(dy, dy));
+      const double u = __dmul_rn(dt, dt);
+      double eb = exp(-__fma_rn(r2, da, __dmul_rn(u, db)));
+      if (KIND == 2 && excl && col == row_a0 + 32 * k) eb = 0.0;
+      acc[0][k] += eb;
+      if (GRAD) {
+        acc[2][k] = __fma_rn(r2, eb, acc[2][k]);
+        acc[3][k] = __fma_rn(u, eb, acc[3][k]);
+      }
+      if (KIND != 0) {
+        double es = exp(-__fma_rn(omega, dt, __dmul_rn(r2, dc)));
+        if (KIND == 2) es = (col < LO[k]) ? es : 0.0;
+        acc[1][k] += es;
+        if (GRAD) {
+          acc[4][k] = __fma_rn(r2, es, acc[4][k]);
+          acc[5][k] = __fma_rn(dt, es, acc[5][k]);
+        }
+      }
+    }
+  }
+}
+
+template <bool GRAD>
+__device__ void run_piece64(const Request &R, int4 piece, int slot, double (*sx)[kColTile],
+                            double (*sy)[kColTile], double (*st)[kColTile]) {
+  constexpr int NS = GRAD ? kSumsGrad : kSumsLoglik;
+  const SetView &S = R.set;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int row0 = piece.x * kRowTile;
+  const int n = S.n;
+  const int wa = row0 + warp * kWarpRows, wb = wa + kWarpRows - 1;
+  const int lo_wa = S.lo64[wa], lo_wb = S.lo64[wb];
+  const bool excl = (R.flags & 1) != 0;
+  const double da = R.da, db = R.db, dc = R.dc, omega = R.omega;
+
+  double X[4], Y[4], T[4];
+  int LO[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int r = wa + lane + 32 * k;
+    X[k] = S.x64[r];
+    Y[k] = S.y64[r];
+    T[k] = r < n ? S.t64[r] : kPadTime;
+    LO[k] = S.lo64[r];
+  }
+  double acc[NS][4];
+#pragma unroll
+  for (int s = 0; s < NS; ++s)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[s][k] = 0.0;
+
+  auto stage = [&](int ct, int buf) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int jj = threadIdx.x + h * kThreads, j = ct * kColTile + jj;
+      sx[buf][jj] = S.x64[j];
+      sy[buf][jj] = S.y64[j];
+      st[buf][jj] = j < n ? S.t64[j] : kPadTime;
+    }
+  };
+  int ct = piece.y;
+  stage(ct, 0);
+  __syncthreads();
+  for (int k = 0; ct < piece.z; ++ct, ++k) {
+    const int buf = k & 1;
+    const int c0 = ct * kColTile, c1 = c0 + kColTile;
+    int kind = (c1 <= lo_wa) ? 1 : (c0 >= lo_wb ? 0 : 2);
+    if (excl && c0 <= wb && c1 > wa) kind = 2;
+    const int row_a0 = wa + lane;
+    if (kind == 0)
+      tile_pass64<0, GRAD>(sx[buf], sy[buf], st[buf], X, Y, T, LO, row_a0, c0, excl, da, db, dc, omega, acc);
+    else if (kind == 1)
+      tile_pass64<1, GRAD>(sx[buf], sy[buf], st[buf], X, Y, T, LO, row_a0, c0, excl, da, db, dc, omega, acc);
+    else
+      tile_pass64<2, GRAD>(sx[buf], sy[buf], st[buf], X, Y, T, LO, row_a0, c0, excl, da, db, dc, omega, acc);
+    if (ct + 1 < piece.z) stage(ct + 1, buf ^ 1);
+    __syncthreads();
+  }
+  double *dst = R.partials + (size_t)slot * NS * kRowTile;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int li = warp * kWarpRows + lane + 32 * k;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) dst[s * kRowTile + li] = acc[s][k];
+  }
+}
+
+template <bool GRAD>
+__global__ void __launch_bounds__(kThreads) pair_fp64_kernel(const __grid_constant__ Batch B) {
+  __shared__ double sx[2][kColTile], sy[2][kColTile], st[2][kColTile];
+  __shared__ int s_item;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(B.counter, 1u);
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();
+    if (item >= B.total_items) break;
+    const Request &R = B.req[find_request(B, item, false)];
+    const int range = item - R.item_begin;
+    const int p0 = R.sched.range_first[range], p1 = R.sched.range_first[range + 1];
+    for (int pc = p0; pc < p1; ++pc) run_piece64<GRAD>(R, R.sched.pieces[pc], pc, sx, sy, st);
+  }
+}
+
+__device__ __forceinline__ double std_normal_pdf(double u) {
+  return exp(-0.5 * u * u) * 0.39894228040143267794;  // 1 / sqrt(2 pi)
+}
+
+template <bool GRAD>
+__global__ void __launch_bounds__(kEpiThreads) epilogue_kernel(const __grid_constant__ Batch B) {
+  constexpr int NS = GRAD ? kSumsGrad : kSumsLoglik;
+  constexpr int NV = GRAD ? 7 : 1;
+  constexpr int NW = kEpiThreads / 32;
+  __shared__ double red[NW][8];
+  __shared__ int s_last;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int item = blockIdx.x; item < B.total_epi; item += gridDim.x) {
+    const Request &R = B.req[find_request(B, item, true)];
+    const SetView &S = R.set;
+    const int blk = item - R.epi_begin;
+    const int nblk = (S.n + kEpiThreads - 1) / kEpiThreads;
+    const int i = blk * kEpiThreads + tid;
+    double v[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] = 0.0;
+    if (i < S.n) {
+      const int rt = i / kRowTile, li = i - rt * kRowTile;
+      double sums[NS];
+#pragma unroll
+      for (int s = 0; s < NS; ++s) sums[s] = 0.0;
+      const int k0 = R.sched.slot_first[rt], k1 = R.sched.slot_first[rt + 1];
+      for (int k = k0; k < k1; ++k) {
+        const double *src = R.partials + (size_t)k * NS * kRowTile + li;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) sums[s] += src[s * kRowTile];
+      }
+      const double two_pi = 6.28318530717958647693;
+      const double mu0 = R.mu0, tx = R.tau_x, tt = R.tau_t, th = R.theta, om = R.omega, h = R.h;
+      const double Ab = 1.0 / (two_pi * sqrt(two_pi) * tx * tx * tt);  // A / mu0
+      const double Cw = om / (two_pi * h * h);                         // C / theta
+      const double A = mu0 * Ab, C = th * Cw;
+      const double mu = A * sums[0], xi = C * sums[1], lam = mu + xi;
+      if (R.mu_out) R.mu_out[i] = mu;
+      if (R.xi_out) R.xi_out[i] = xi;
+      const double tn = B.mode == 1 ? (double)S.t32[i] : S.t64[i];
+      const double a = (R.t_last - tn) / tt, b = -tn / tt, D = R.t_last - tn;
+      const double e = exp(-om * D);
+      const double Pa = normcdf(a), Pb = normcdf(b);
+      v[0] = log(lam) - (mu0 * (Pa - Pb) + th * (1.0 - e));
+      if (GRAD) {
+        const double Rb = sums[2], Tb = sums[3] * R.tscale * R.tscale;
+        const double Rs = sums[4], Us = sums[5] * R.tscale;
+        const double Sb = sums[0], Ss = sums[1];
+        const double inv = 1.0 / lam;
+        v[1] = Ab * Sb * inv - (Pa - Pb);
+        v[2] = A * (-2.0 * Sb / tx + Rb / (tx * tx * tx)) * inv;
+        v[3] = A * (-Sb / tt + Tb / (tt * tt * tt)) * inv - mu0 / tt * (-a * std_normal_pdf(a) + b * std_normal_pdf(b));
+        v[4] = Cw * Ss * inv - (1.0 - e);
+        v[5] = C * (Ss / om - Us) * inv - th * D * e;
+        v[6] = C * (-2.0 * Ss / h + Rs / (h * h * h)) * inv;
+      }
+    }
+    // fixed-order block reduction
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double x = v[q];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+      if (lane == 0) red[warp][q] = x;
+    }
+    __syncthreads();
+    if (tid < NV) {
+      double x = 0.0;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) x += red[w][tid];
+      R.block_part[(size_t)blk * 8 + tid] = x;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = (atomicAdd(R.ticket, 1u) == (unsigned)(nblk - 1));
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      if (tid < NV) {
+        double x = 0.0;
+        for (int bb = 0; bb < nblk; ++bb) x += __ldcg(R.block_part + (size_t)bb * 8 + tid);
+        R.out[tid] = x;
+      }
+      if (tid == 0) *R.ticket = 0u;
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_pair_fp64(const Batch &b, bool grad, int grid, cudaStream_t s) {
+  if (grad) pair_fp64_kernel<true><<<grid, kThreads, 0, s>>>(b);
+  else pair_fp64_kernel<false><<<grid, kThreads, 0, s>>>(b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_epilogue(const Batch &b, bool grad, int grid, cudaStream_t s) {
+  if (grad) epilogue_kernel<true><<<grid, kEpiThreads, 0, s>>>(b);
+  else epilogue_kernel<false><<<grid, kEpiThreads, 0, s>>>(b);
+  return cudaGetLastError();
+}
+
+int occupancy_pair_fp64(bool grad) {
+  int n = 0;
+  if (grad) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_fp64_kernel<true>, kThreads, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_fp64_kernel<false>, kThreads, 0);
+  return n;
+}
+
+}  // namespace hk

@@ -1,0 +1,166 @@
+// A fake CUDA runtime for testing the library's host logic on a machine without a GPU.
+//
+// Test infrastructure only. The library's host runtime (api.cu, compiled here as plain
+// C++) is linked against this file instead of libcudart: "device" memory is host memory,
+// streams and events are counters, and the kernel launchers are replaced by stubs that
+// (1) check the work schedule of every request (each (row tile, column tile) unit of the
+// set covered exactly once, pieces inside their ranges, partial-sum slots consistent) and
+// (2) write a recognisable value per request into its output so the tests can check that
+// results reach the right ticket. No likelihood arithmetic happens here.
+//
+// Fault injection: fake_fail_alloc_after(k) makes the k-th following allocation fail;
+// fake_event_delay(k) makes every event report "not ready" k times before completing;
+// fake_release_events() completes every event recorded so far.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "../../paper_2005_10123_gb300/csrc/hk_internal.h"
+
+namespace {
+std::atomic<long> g_fail_after{-1};
+std::atomic<int> g_event_delay{0};
+std::atomic<long> g_schedule_errors{0};
+std::atomic<long> g_launches{0};
+std::atomic<long> g_live_allocs{0};
+std::mutex g_mu;
+std::atomic<long> g_epoch{0};  // events recorded before fake_release_events() complete
+struct FakeEvent { int remaining; long epoch; };
+
+bool alloc_fails() {
+  long v = g_fail_after.load();
+  if (v < 0) return false;
+  if (v == 0) { g_fail_after = -1; return true; }
+  g_fail_after = v - 1;
+  return false;
+}
+}  // namespace
+
+extern "C" {
+void fake_fail_alloc_after(long k) { g_fail_after = k; }
+void fake_event_delay(int k) { g_event_delay = k; }
+void fake_release_events() { g_epoch++; }
+long fake_schedule_errors() { return g_schedule_errors.load(); }
+long fake_launches() { return g_launches.load(); }
+long fake_live_allocs() { return g_live_allocs.load(); }
+
+cudaError_t cudaGetDeviceCount(int *c) { *c = 1; return cudaSuccess; }
+cudaError_t cudaSetDevice(int) { return cudaSuccess; }
+cudaError_t cudaDeviceGetAttribute(int *v, cudaDeviceAttr a, int) {
+  *v = a == cudaDevAttrMultiProcessorCount ? 152 : 0;
+  return cudaSuccess;
+}
+cudaError_t cudaMemGetInfo(size_t *f, size_t *t) { *f = (size_t)64 << 30; *t = (size_t)80 << 30; return cudaSuccess; }
+const char *cudaGetErrorString(cudaError_t e) { return e == cudaSuccess ? "no error" : "fake cuda error"; }
+cudaError_t cudaMalloc(void **p, size_t n) {
+  if (alloc_fails()) return cudaErrorMemoryAllocation;
+  *p = std::aligned_alloc(256, (n + 255) / 256 * 256);
+  if (!*p) return cudaErrorMemoryAllocation;
+  std::memset(*p, 0xA5, n);  // garbage, as fresh device memory would be
+  g_live_allocs++;
+  return cudaSuccess;
+}
+cudaError_t cudaMallocAsync(void **p, size_t n, cudaStream_t) { return cudaMalloc(p, n); }
+cudaError_t cudaFree(void *p) { if (p) { std::free(p); g_live_allocs--; } return cudaSuccess; }
+cudaError_t cudaFreeAsync(void *p, cudaStream_t) { return cudaFree(p); }
+cudaError_t cudaMallocHost(void **p, size_t n) {
+  if (alloc_fails()) return cudaErrorMemoryAllocation;
+  *p = std::malloc(n);
+  g_live_allocs++;
+  return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+}
+cudaError_t cudaFreeHost(void *p) { if (p) { std::free(p); g_live_allocs--; } return cudaSuccess; }
+cudaError_t cudaMemcpyAsync(void *d, const void *s, size_t n, cudaMemcpyKind, cudaStream_t) {
+  std::memcpy(d, s, n);
+  return cudaSuccess;
+}
+cudaError_t cudaMemsetAsync(void *d, int v, size_t n, cudaStream_t) { std::memset(d, v, n); return cudaSuccess; }
+cudaError_t cudaStreamCreateWithFlags(cudaStream_t *s, unsigned) {
+  *s = reinterpret_cast<cudaStream_t>(new int(0));
+  return cudaSuccess;
+}
+cudaError_t cudaStreamDestroy(cudaStream_t s) { delete reinterpret_cast<int *>(s); return cudaSuccess; }
+cudaError_t cudaStreamSynchronize(cudaStream_t) { return cudaSuccess; }
+cudaError_t cudaEventCreateWithFlags(cudaEvent_t *e, unsigned) {
+  *e = reinterpret_cast<cudaEvent_t>(new FakeEvent{0, 0});
+  return cudaSuccess;
+}
+cudaError_t cudaEventDestroy(cudaEvent_t e) { delete reinterpret_cast<FakeEvent *>(e); return cudaSuccess; }
+cudaError_t cudaEventRecord(cudaEvent_t e, cudaStream_t) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  reinterpret_cast<FakeEvent *>(e)->remaining = g_event_delay.load();
+  reinterpret_cast<FakeEvent *>(e)->epoch = g_epoch.load();
+  return cudaSuccess;
+}
+cudaError_t cudaEventQuery(cudaEvent_t e) {
+  auto *f = reinterpret_cast<FakeEvent *>(e);
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (f->epoch < g_epoch.load()) return cudaSuccess;
+  if (f->remaining > 0) { f->remaining--; return cudaErrorNotReady; }
+  return cudaSuccess;
+}
+}  // extern "C"
+
+namespace hk {
+
+// Check one request's schedule against its set.
+static void check_schedule(const Request &R) {
+  const SetView &S = R.set;
+  const Schedule &D = R.sched;
+  std::vector<int> cover((size_t)S.nrt * S.nct, 0);
+  bool ok = D.nranges >= 1 && D.range_first[0] == 0 && D.range_first[D.nranges] == D.npieces;
+  for (int r = 0; ok && r < D.nranges; ++r) {
+    if (D.range_first[r] >= D.range_first[r + 1]) ok = false;  // every range has a piece
+    for (int pc = D.range_first[r]; ok && pc < D.range_first[r + 1]; ++pc) {
+      const int4 p = D.pieces[pc];
+      if (p.x < 0 || p.x >= S.nrt || p.y < 0 || p.y >= p.z || p.z > S.nct) { ok = false; break; }
+      if (pc < D.slot_first[p.x] || pc >= D.slot_first[p.x + 1]) ok = false;  // slot of its row tile
+      for (int ct = p.y; ct < p.z; ++ct) cover[(size_t)p.x * S.nct + ct]++;
+    }
+  }
+  for (int c : cover) if (c != 1) ok = false;
+  if (D.slot_first[0] != 0 || D.slot_first[S.nrt] != D.npieces) ok = false;
+  if (S.npad != S.nrt * kRowTile || S.nct * kColTile != S.npad || S.n > S.npad) ok = false;
+  if (!ok) g_schedule_errors++;
+}
+
+static cudaError_t fake_pair(const Batch &b) {
+  g_launches++;
+  int items = 0;
+  for (int r = 0; r < b.nreq; ++r) {
+    if (b.req[r].item_begin != items) g_schedule_errors++;
+    items += b.req[r].sched.nranges;
+    check_schedule(b.req[r]);
+  }
+  if (items != b.total_items || *b.counter != 0u) g_schedule_errors++;
+  return cudaSuccess;
+}
+
+cudaError_t launch_pair_mixed(const Batch &b, bool, int, cudaStream_t) { return fake_pair(b); }
+cudaError_t launch_pair_fp64(const Batch &b, bool, int, cudaStream_t) { return fake_pair(b); }
+
+// Output of a request: a function of its own inputs only, so the tests can tell where it went.
+cudaError_t launch_epilogue(const Batch &b, bool grad, int, cudaStream_t) {
+  for (int r = 0; r < b.nreq; ++r) {
+    const Request &R = b.req[r];
+    if (*R.ticket != 0u) g_schedule_errors++;
+    R.out[0] = R.mu0 * 1000.0 + R.set.n + (b.mode ? 0.5 : 0.0);
+    if (grad) {
+      const double th[6] = {R.mu0, R.tau_x, R.tau_t, R.theta, R.omega, R.h};
+      for (int q = 0; q < 6; ++q) R.out[1 + q] = th[q];
+    }
+    if (R.mu_out)
+      for (int i = 0; i < R.set.n; ++i) { R.mu_out[i] = i; R.xi_out[i] = -i; }
+  }
+  return cudaSuccess;
+}
+
+int occupancy_pair_mixed(bool) { return 4; }
+int occupancy_pair_fp64(bool) { return 2; }
+
+}  // namespace hk

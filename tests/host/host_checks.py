@@ -1,0 +1,178 @@
+"""Host-logic checks of the library runtime against the fake CUDA runtime.
+
+Run as a script (tests/test_host_runtime.py starts it in a subprocess, under
+AddressSanitizer when available). Exits non-zero on the first failed check.
+"""
+import ctypes
+import os
+import sys
+import threading
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+
+from paper_2005_10123_gb300 import binding, synth  # noqa: E402
+
+LIB_PATH = os.path.join(HERE, "_build", "libhawkes_hosttest.so")
+TH = (0.01, 1.0, 30.0, 0.5, 1.0, 0.1)
+
+
+def fake_value(theta, n, mode):
+    return theta[0] * 1000.0 + n + (0.5 if mode == 1 else 0.0)
+
+
+def expect_status(fn, status):
+    try:
+        fn()
+    except binding.HawkesError as e:
+        assert e.status == status, (e.status, status)
+        return
+    raise AssertionError(f"expected status {status}")
+
+
+def main():
+    lib = binding.load(path=LIB_PATH)
+    fake = ctypes.CDLL(LIB_PATH)
+    base_allocs = fake.fake_live_allocs()
+
+    # ---- uploads, validation, schedules ----------------------------------------------------
+    ctx = binding.Context(lib=lib)
+    expect_status(lambda: ctx.hawkes_upload_events([0, 1], [0, 1], [2.0, 1.0]), -2)
+    expect_status(lambda: ctx.hawkes_upload_events([0, np.inf], [0, 1], [1.0, 2.0]), -1)
+    expect_status(lambda: ctx.hawkes_upload_events([0], [0], [-1.0]), -1)
+    expect_status(lambda: ctx.hawkes_upload_events([], [], []), -1)
+    sizes = [1, 2, 3, 255, 256, 257, 511, 512, 513, 1000, 4097, 20000, 85000]
+    sids = {}
+    for n in sizes:
+        ev = synth.simulate(n, max(5.0, n / 17.0), seed=n)
+        if n == 4097:
+            ev.t = np.round(ev.t)  # ties
+        sid = ctx.hawkes_upload_events(ev.x, ev.y, ev.t)
+        nn, nbytes = ctx.hawkes_set_info(sid)
+        assert nn == n and nbytes >= 44 * n
+        sids[n] = sid
+    for n, sid in sids.items():
+        for mode in (0, 1):
+            ll = ctx.hawkes_loglik(sid, TH, mode)
+            assert ll == fake_value(TH, n, mode), (n, mode, ll)
+            ll, g = ctx.hawkes_loglik_grad(sid, TH, mode)
+            assert ll == fake_value(TH, n, mode) and np.array_equal(g, TH)
+    assert fake.fake_schedule_errors() == 0, "schedule coverage errors"
+    ths = synth.theta_batch(64, seed=3)
+    ll, g = ctx.hawkes_loglik_batch(sids[20000], ths, 1, want_grad=True)
+    for k in range(64):
+        assert ll[k] == fake_value(ths[k], 20000, 1) and np.array_equal(g[k], ths[k])
+    expect_status(lambda: ctx.hawkes_loglik_batch(sids[20000], np.tile(ths, (2, 1)), 1), -1)  # K > 64
+    mu, xi, _ = ctx.hawkes_event_terms(sids[1000], TH, 1)
+    assert np.array_equal(mu, np.arange(1000)) and np.array_equal(xi, -np.arange(1000))
+    # invalid parameters, unknown set
+    for bad in [(0, 1, 1, 0.5, 1, 1), (1, 1, -1, 0.5, 1, 1), (1, 1, 1, -1, 1, 1), (1, 1, 1, 0.5, 1, np.nan)]:
+        expect_status(lambda: ctx.hawkes_loglik(sids[2], bad, 1), -1)
+    expect_status(lambda: ctx.hawkes_loglik(999, TH, 1), -3)
+    expect_status(lambda: ctx.hawkes_loglik(sids[2], TH, 7), -1)
+    expect_status(lambda: ctx.hawkes_set_flags(8), -1)
+
+    # ---- serving: tickets, batching, polling ---------------------------------------------------
+    rng = np.random.default_rng(1)
+    reqs = []
+    for i in range(300):
+        n = sizes[int(rng.integers(len(sizes)))]
+        th = ths[i % 64]
+        reqs.append((n, th, bool(rng.integers(2)), int(rng.integers(2))))
+    tickets = [ctx.hawkes_submit(sids[n], th, g, m) for n, th, g, m in reqs]
+    res = {}
+    deadline = time.time() + 30
+    while len(res) < len(tickets) and time.time() < deadline:
+        for t in tickets:
+            if t not in res:
+                r = ctx.hawkes_poll(t)
+                if r is not None:
+                    res[t] = r
+    assert len(res) == len(tickets)
+    for t, (n, th, g, m) in zip(tickets, reqs):
+        ll, gr = res[t]
+        assert ll == fake_value(th, n, m)
+        assert np.array_equal(gr, th if g else np.zeros(6))
+    st = ctx.hawkes_stats()
+    assert st["submitted"] == 300 and st["completed"] == 300 and st["failed"] == 0
+    assert st["launches"] < 300, st
+    expect_status(lambda: ctx.hawkes_poll(tickets[0]), -9)  # consumed
+    assert fake.fake_schedule_errors() == 0
+
+    # concurrent submitters
+    out = {}
+
+    def worker(w):
+        for i in range(50):
+            t = ctx.hawkes_submit(sids[513], ths[(w * 50 + i) % 64], True, 1)
+            out[(w, i)] = ctx.hawkes_wait(t, 5000)
+
+    ths_ = [threading.Thread(target=worker, args=(w,)) for w in range(4)]
+    for th_ in ths_:
+        th_.start()
+    for th_ in ths_:
+        th_.join()
+    assert len(out) == 200
+    for (w, i), (ll, gr) in out.items():
+        assert ll == fake_value(ths[(w * 50 + i) % 64], 513, 1)
+
+    # timeouts: an event that stays "not ready"
+    fake.fake_event_delay(10 ** 9)
+    t = ctx.hawkes_submit(sids[1000], TH, False, 1)
+    expect_status(lambda: ctx.hawkes_wait(t, 20), -6)
+    assert ctx.hawkes_poll(t) is None  # still pending, ticket still valid
+    fake.fake_event_delay(0)
+    fake.fake_release_events()
+    assert ctx.hawkes_wait(t, 5000)[0] == fake_value(TH, 1000, 1)
+    ctx.close()
+
+    # ---- admission and allocation faults ---------------------------------------------------------
+    ev = synth.simulate(20000, 2000.0, seed=2)
+    small = binding.Context(hbm_budget_bytes=1 << 18, lib=lib)
+    expect_status(lambda: small.hawkes_upload_events(ev.x, ev.y, ev.t), -4)
+    small.close()
+    tight = binding.Context(hbm_budget_bytes=2_300_000, lib=lib)
+    sid = tight.hawkes_upload_events(ev.x, ev.y, ev.t)
+    expect_status(lambda: tight.hawkes_loglik_grad(sid, TH, 1), -4)
+    expect_status(lambda: tight.hawkes_submit(sid, TH, True, 1), -4)
+    tight.close()
+
+    c3 = binding.Context(lib=lib)
+    fake.fake_fail_alloc_after(0)
+    expect_status(lambda: c3.hawkes_upload_events(ev.x, ev.y, ev.t), -5)
+    sid = c3.hawkes_upload_events(ev.x, ev.y, ev.t)
+    fake.fake_fail_alloc_after(0)
+    expect_status(lambda: c3.hawkes_loglik(sid, TH, 1), -5)
+    assert c3.hawkes_loglik(sid, TH, 1) == fake_value(TH, 20000, 1)  # recovers
+    fake.fake_fail_alloc_after(0)  # the first submit sets up the serving streams: fails cleanly
+    expect_status(lambda: c3.hawkes_submit(sid, TH, False, 1), -5)
+    t = c3.hawkes_submit(sid, TH, False, 1)
+    assert c3.hawkes_wait(t, 5000)[0] == fake_value(TH, 20000, 1)
+    fake.fake_fail_alloc_after(0)  # the serving workspace allocation fails
+    t = c3.hawkes_submit(sid, TH, False, 1)
+    expect_status(lambda: c3.hawkes_wait(t, 5000), -5)
+    t = c3.hawkes_submit(sid, TH, False, 1)
+    assert c3.hawkes_wait(t, 5000)[0] == fake_value(TH, 20000, 1)
+    # release while queued: the set lives until its requests finish
+    fake.fake_event_delay(3)
+    ts = [c3.hawkes_submit(sid, TH, True, 0) for _ in range(10)]
+    c3.hawkes_release_events(sid)
+    expect_status(lambda: c3.hawkes_submit(sid, TH, True, 0), -3)
+    for t in ts:
+        assert c3.hawkes_wait(t, 5000)[0] == fake_value(TH, 20000, 0)
+    fake.fake_event_delay(0)
+    # destroy with queued work
+    sid = c3.hawkes_upload_events(ev.x, ev.y, ev.t)
+    for _ in range(20):
+        c3.hawkes_submit(sid, TH, True, 1)
+    c3.close()
+    assert fake.fake_live_allocs() == base_allocs, (fake.fake_live_allocs(), base_allocs)
+    print("ALL OK")
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,91 @@
+"""Error paths of the C ABI on a GPU: every status code comes back, none aborts."""
+import numpy as np
+import pytest
+
+from paper_2005_10123_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def binding():
+    from paper_2005_10123_gb300 import binding as b
+    b.load()
+    return b
+
+
+def test_invalid_inputs(binding):
+    with binding.Context(device=0) as ctx:
+        with pytest.raises(binding.HawkesError) as e:
+            ctx.hawkes_upload_events([0, 1], [0, 1], [2.0, 1.0])
+        assert e.value.status == -2
+        with pytest.raises(binding.HawkesError) as e:
+            ctx.hawkes_upload_events([0, np.nan], [0, 1], [1.0, 2.0])
+        assert e.value.status == -1
+        with pytest.raises(binding.HawkesError) as e:
+            ctx.hawkes_upload_events([0, 1], [0, 1], [-1.0, 2.0])
+        assert e.value.status == -1
+        sid = ctx.hawkes_upload_events([0.0, 1.0], [0.0, 0.5], [1.0, 2.0])
+        for bad in [(0, 1, 1, 0.5, 1, 1), (1, -1, 1, 0.5, 1, 1), (1, 1, 1, -0.1, 1, 1), (1, 1, 1, 0.5, np.inf, 1)]:
+            with pytest.raises(binding.HawkesError) as e:
+                ctx.hawkes_loglik(sid, bad, 1)
+            assert e.value.status == -1
+        with pytest.raises(binding.HawkesError) as e:
+            ctx.hawkes_loglik(sid + 100, synth.THETA0, 1)
+        assert e.value.status == -3
+        ctx.hawkes_release_events(sid)
+        with pytest.raises(binding.HawkesError) as e:
+            ctx.hawkes_loglik(sid, synth.THETA0, 1)
+        assert e.value.status == -3
+        with pytest.raises(binding.HawkesError) as e:
+            ctx.hawkes_poll(12345)
+        assert e.value.status == -9
+
+
+def test_admission_budget(binding):
+    ev = synth.simulate(20000, 2000.0, seed=2)
+    with binding.Context(device=0, hbm_budget_bytes=1 << 18) as ctx:
+        with pytest.raises(binding.HawkesError) as e:
+            ctx.hawkes_upload_events(ev.x, ev.y, ev.t)
+        assert e.value.status == -4
+    # a set fits but its evaluation workspace does not
+    with binding.Context(device=0, hbm_budget_bytes=2_300_000) as ctx:
+        sid = ctx.hawkes_upload_events(ev.x, ev.y, ev.t)
+        with pytest.raises(binding.HawkesError) as e:
+            ctx.hawkes_loglik_grad(sid, synth.THETA0, 1)
+        assert e.value.status == -4
+        with pytest.raises(binding.HawkesError) as e:
+            ctx.hawkes_submit(sid, synth.THETA0, True, 1)
+        assert e.value.status == -4
+
+
+def test_wait_timeout_then_complete(binding):
+    ev = synth.large_workload()
+    with binding.Context(device=0) as ctx:
+        sid = ctx.hawkes_upload_events(ev.x, ev.y, ev.t)
+        t = ctx.hawkes_submit(sid, synth.THETA0, True, 0)  # fp64: hundreds of ms
+        with pytest.raises(binding.HawkesError) as e:
+            ctx.hawkes_wait(t, timeout_ms=0)
+        assert e.value.status == -6
+        ll, g = ctx.hawkes_wait(t, timeout_ms=-1)
+        assert np.isfinite(ll)
+        with pytest.raises(binding.HawkesError) as e:  # consumed
+            ctx.hawkes_wait(t, timeout_ms=0)
+        assert e.value.status == -9
+
+
+def test_release_while_queued_then_destroy(binding):
+    ev = synth.simulate(30000, 2000.0, seed=9)
+    ctx = binding.Context(device=0)
+    sid = ctx.hawkes_upload_events(ev.x, ev.y, ev.t)
+    tickets = [ctx.hawkes_submit(sid, synth.THETA0, False, 1) for _ in range(4)]
+    ctx.hawkes_release_events(sid)  # deferred until the queued requests finish
+    res = [ctx.hawkes_wait(t) for t in tickets]
+    assert all(r[0] == res[0][0] for r in res)
+    with pytest.raises(binding.HawkesError):
+        ctx.hawkes_submit(sid, synth.THETA0, False, 1)
+    # destroy with work queued: pending tickets end, nothing hangs
+    sid2 = ctx.hawkes_upload_events(ev.x, ev.y, ev.t)
+    for _ in range(8):
+        ctx.hawkes_submit(sid2, synth.THETA0, True, 0)
+    ctx.close()

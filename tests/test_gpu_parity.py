@@ -1,0 +1,196 @@
+"""CUDA path against the FP64 CPU oracle, element by element, through the C ABI.
+
+Mixed mode is compared with the oracle evaluated on the float32-rounded coordinates
+(the values the mixed path stores); FP64 mode with the oracle on the doubles.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2005_10123_gb300 import synth
+from gpu_util import TOL_FP64_G, TOL_FP64_LL, TOL_MIXED_G, TOL_MIXED_LL, grad_err, rel
+
+pytestmark = pytest.mark.gpu
+
+TH0 = synth.THETA0
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2005_10123_gb300 import binding
+    binding.load()
+    c = binding.Context(device=0)
+    yield c
+    c.close()
+
+
+def _check(ctx, ev, theta, mode, flags=0, grad=True):
+    from paper_2005_10123_gb300 import binding
+    ctx.hawkes_set_flags(flags)
+    sid = ctx.hawkes_upload_events(ev.x, ev.y, ev.t)
+    try:
+        ref = ev.rounded32() if mode == binding.HAWKES_MIXED else ev
+        tol_ll, tol_g = (TOL_MIXED_LL, TOL_MIXED_G) if mode == binding.HAWKES_MIXED else (TOL_FP64_LL, TOL_FP64_G)
+        if grad:
+            ll, g = ctx.hawkes_loglik_grad(sid, theta, mode)
+            rll, rg = oracle.loglik(ref.x, ref.y, ref.t, theta, flags=flags, grad=True)
+            assert rel(ll, rll) <= tol_ll, (ll, rll, rel(ll, rll))
+            assert grad_err(g, rg) <= tol_g, (g, rg, grad_err(g, rg))
+        ll1 = ctx.hawkes_loglik(sid, theta, mode)
+        rll = oracle.loglik(ref.x, ref.y, ref.t, theta, flags=flags)
+        assert rel(ll1, rll) <= tol_ll, (ll1, rll)
+    finally:
+        ctx.hawkes_release_events(sid)
+        ctx.hawkes_set_flags(0)
+
+
+# sizes spanning several 256-column / 512-row tiles with ragged tails
+SIZES = [1, 2, 3, 31, 33, 127, 129, 255, 257, 511, 513, 1007, 2000, 4099]
+
+
+@pytest.mark.parametrize("n", SIZES)
+@pytest.mark.parametrize("mode", [0, 1], ids=["fp64", "mixed"])
+def test_ragged_sizes(ctx, n, mode):
+    ev = synth.simulate(n, max(10.0, n / 2.0), seed=1000 + n)
+    _check(ctx, ev, TH0, mode)
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["fp64", "mixed"])
+def test_config0_workload(ctx, mode):
+    _check(ctx, synth.small_workload(), TH0, mode)
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["fp64", "mixed"])
+def test_tied_times(ctx, mode):
+    ev = synth.simulate(3000, 300.0, seed=77)
+    ev.t = np.round(ev.t * 4) / 4  # many exact ties (in both precisions)
+    _check(ctx, ev, (0.05, 0.7, 5.0, 0.5, 2.0, 0.2), mode)
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["fp64", "mixed"])
+def test_exclude_self(ctx, mode):
+    from paper_2005_10123_gb300 import binding
+    ev = synth.simulate(1500, 600.0, seed=5)
+    _check(ctx, ev, TH0, mode, flags=binding.HAWKES_FLAG_EXCLUDE_SELF)
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["fp64", "mixed"])
+def test_theta_zero_and_parameter_spread(ctx, mode):
+    ev = synth.simulate(2500, 900.0, seed=8)
+    _check(ctx, ev, (0.3, 1.2, 20.0, 0.0, 0.8, 0.3), mode)
+    for k, th in enumerate(synth.theta_batch(4, seed=99)):
+        _check(ctx, ev, th, mode)
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["fp64", "mixed"])
+def test_event_terms_rows(ctx, mode):
+    ev = synth.simulate(3000, 1000.0, seed=21)
+    sid = ctx.hawkes_upload_events(ev.x, ev.y, ev.t)
+    try:
+        mu, xi, ll = ctx.hawkes_event_terms(sid, TH0, mode)
+    finally:
+        ctx.hawkes_release_events(sid)
+    ref = ev.rounded32() if mode == 1 else ev
+    r = oracle.rows(ref.x, ref.y, ref.t, TH0, np.arange(ev.n))
+    tol = 5e-6 if mode == 1 else 1e-12
+    np.testing.assert_allclose(mu, r["mu"], rtol=tol)
+    np.testing.assert_allclose(xi, r["xi"], rtol=tol, atol=tol * np.max(r["xi"]))
+    pi = xi / (mu + xi)
+    assert np.all((pi >= 0) & (pi <= 1))
+
+
+def test_repeatable_bitwise(ctx):
+    ev = synth.simulate(5000, 1500.0, seed=3)
+    sid = ctx.hawkes_upload_events(ev.x, ev.y, ev.t)
+    try:
+        for mode in (0, 1):
+            a = ctx.hawkes_loglik_grad(sid, TH0, mode)
+            b = ctx.hawkes_loglik_grad(sid, TH0, mode)
+            assert a[0] == b[0] and np.array_equal(a[1], b[1])
+    finally:
+        ctx.hawkes_release_events(sid)
+
+
+def test_batch_matches_single_bitwise(ctx):
+    ev = synth.simulate(6000, 2000.0, seed=4)
+    sid = ctx.hawkes_upload_events(ev.x, ev.y, ev.t)
+    try:
+        ths = synth.theta_batch(8, seed=12)
+        for mode in (0, 1):
+            ll, g = ctx.hawkes_loglik_batch(sid, ths, mode, want_grad=True)
+            for k in range(len(ths)):
+                a, ga = ctx.hawkes_loglik_grad(sid, ths[k], mode)
+                assert ll[k] == a and np.array_equal(g[k], ga)
+            ll0 = ctx.hawkes_loglik_batch(sid, ths, mode, want_grad=False)
+            for k in range(len(ths)):
+                assert ll0[k] == ctx.hawkes_loglik(sid, ths[k], mode)
+    finally:
+        ctx.hawkes_release_events(sid)
+
+
+def test_async_device_output(ctx):
+    torch = pytest.importorskip("torch")
+    ev = synth.simulate(3000, 1000.0, seed=6)
+    sid = ctx.hawkes_upload_events(ev.x, ev.y, ev.t)
+    try:
+        out = torch.zeros(7, dtype=torch.float64, device="cuda")
+        ctx.hawkes_loglik_async(sid, TH0, 1, True, out.data_ptr())
+        torch.cuda.synchronize()
+        ll, g = ctx.hawkes_loglik_grad(sid, TH0, 1)
+        assert out[0].item() == ll and np.array_equal(out[1:].cpu().numpy(), g)
+    finally:
+        ctx.hawkes_release_events(sid)
+
+
+# ---- full size (85,000 events): sampled rows and properties ---------------------------------
+
+@pytest.fixture(scope="module")
+def big(ctx):
+    ev = synth.large_workload()
+    sid = ctx.hawkes_upload_events(ev.x, ev.y, ev.t)
+    yield ev, sid
+    ctx.hawkes_release_events(sid)
+
+
+def _sample_rows(ev):
+    n = ev.n
+    idx = set(np.linspace(0, n - 1, 48).astype(int).tolist())
+    idx |= {0, 1, 511, 512, 513, n - 2, n - 1}
+    ties = np.nonzero(np.diff(ev.t) == 0)[0]
+    idx |= set(ties[:8].tolist()) | set((ties[:8] + 1).tolist())
+    return np.array(sorted(idx))
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["fp64", "mixed"])
+def test_full_size_sampled_rows(ctx, big, mode):
+    ev, sid = big
+    mu, xi, ll = ctx.hawkes_event_terms(sid, TH0, mode)
+    idx = _sample_rows(ev)
+    r = oracle.rows(ev.x, ev.y, ev.t, TH0, idx)  # ev is already float32-representable
+    tol = 1e-5 if mode == 1 else 1e-11
+    np.testing.assert_allclose(mu[idx], r["mu"], rtol=tol)
+    np.testing.assert_allclose(xi[idx], r["xi"], rtol=tol, atol=tol * np.max(r["xi"]))
+    # the sum over every row of log lambda_n - Lambda_n is the reported ell
+    Lam, _ = oracle.compensator(ev.t, TH0)
+    assert rel(float(np.sum(np.log(mu + xi))) - Lam, ll) <= (1e-9 if mode == 1 else 1e-12)
+
+
+def test_full_size_mixed_vs_fp64(ctx, big):
+    ev, sid = big
+    ll64, g64 = ctx.hawkes_loglik_grad(sid, TH0, 0)
+    llm, gm = ctx.hawkes_loglik_grad(sid, TH0, 1)
+    assert rel(llm, ll64) <= TOL_MIXED_LL
+    assert grad_err(gm, g64) <= TOL_MIXED_G
+
+
+def test_full_size_gradient_finite_differences(ctx, big):
+    """The FP64 GPU gradient at N = 85,000 against central differences of the FP64 GPU
+    log-likelihood (step 1e-6 relative)."""
+    ev, sid = big
+    ll, g = ctx.hawkes_loglik_grad(sid, TH0, 0)
+    for k in range(6):
+        h = 1e-6 * TH0[k]
+        up = list(TH0); dn = list(TH0)
+        up[k] += h; dn[k] -= h
+        fd = (ctx.hawkes_loglik(sid, up, 0) - ctx.hawkes_loglik(sid, dn, 0)) / (2 * h)
+        assert abs(fd - g[k]) <= 1e-6 * max(abs(g[k]), 1e-3 * np.max(np.abs(g))), (k, fd, g[k])
