@@ -165,6 +165,29 @@ int hawkes_wait(hawkes_ctx *ctx, uint64_t ticket, int timeout_ms, double *loglik
  * and the device bytes currently held for requests. `out` has 7 entries. */
 int hawkes_stats(hawkes_ctx *ctx, int64_t out[7]);
 
+/* ---- evaluation without allocation -----------------------------------------------------
+ * The paper has no counterpart to this entry point; it serves callers that must not allocate
+ * device memory when they evaluate, for example a program whose device memory is reserved in
+ * full by another allocator, or a sampler loop in which cudaMalloc/cudaFree could stall on
+ * device-wide synchronisation. It computes the same mixed-precision ell(Theta) as
+ * hawkes_loglik(..., HAWKES_MIXED) without a context, from events the caller already holds
+ * on the device, and calls no allocator: its temporaries live in one fixed device array of
+ * the library (about 5.3 MB, reserved on every GPU that loads the library, until exit).
+ *
+ * x, y, t: device pointers to n float32 values each (km, km, days), t non-decreasing and
+ * >= 0 (not checked: the values are never read on the host); 1 <= n <=
+ * HAWKES_NOALLOC_MAX_EVENTS, larger n returns HAWKES_E_INVAL. flags: HAWKES_FLAG_*.
+ * device_out: device pointer to one double that receives ell. cuda_stream: the stream to
+ * enqueue on (NULL = the legacy default stream). The call is asynchronous: the caller
+ * synchronises the stream before reading device_out.
+ * The first call on each device sets up the array's device address (cudaGetSymbolAddress),
+ * so make that first call before any stream capture. Every call reuses the same array:
+ * calls that may overlap on the GPU (on different streams, or from several threads) race
+ * and must be serialised by the caller. Errors: E_INVAL, E_CUDA. */
+#define HAWKES_NOALLOC_MAX_EVENTS 65536
+int hawkes_loglik_noalloc(const float *x, const float *y, const float *t, int64_t n,
+                          const hawkes_params *params, int flags, double *device_out, void *cuda_stream);
+
 /* Human-readable text for a status code. Never NULL. */
 const char *hawkes_strerror(int status);
 

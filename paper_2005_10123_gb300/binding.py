@@ -30,7 +30,9 @@ EXPORTS = (
     "hawkes_release_events", "hawkes_set_info", "hawkes_loglik", "hawkes_loglik_grad",
     "hawkes_loglik_async", "hawkes_loglik_batch", "hawkes_event_terms", "hawkes_submit",
     "hawkes_poll", "hawkes_wait", "hawkes_stats", "hawkes_strerror", "hawkes_last_cuda_error",
+    "hawkes_loglik_noalloc",
 )
+HAWKES_NOALLOC_MAX_EVENTS = 65536
 
 
 class HawkesError(RuntimeError):
@@ -84,8 +86,11 @@ def load(build_if_missing: bool = False, path: str | None = None):
         "hawkes_poll": [vp, u64, ctypes.POINTER(ctypes.c_int), _D, _D],
         "hawkes_wait": [vp, u64, ctypes.c_int, _D, _D],
         "hawkes_stats": [vp, ctypes.POINTER(i64)],
+        "hawkes_loglik_noalloc": [vp, vp, vp, i64, P, ctypes.c_int, vp, vp],
     }
     for name, args in sig.items():
+        if path is not None and not hasattr(lib, name):
+            continue  # a partial build of the ABI (host-logic tests link only the runtime)
         f = getattr(lib, name)
         f.argtypes = args
         f.restype = ctypes.c_int
@@ -245,6 +250,19 @@ class Context:
         self._check(self.lib.hawkes_stats(self.h, out), "hawkes_stats")
         keys = ("submitted", "completed", "failed", "launches", "in_flight", "queued", "serving_bytes")
         return dict(zip(keys, list(out)))
+
+
+def hawkes_loglik_noalloc(x_ptr: int, y_ptr: int, t_ptr: int, n: int, theta, flags: int, out_ptr: int,
+                          stream: int = 0, lib=None) -> None:
+    """Device pointers in, device pointer out; enqueues on `stream` and returns (no context,
+    no allocation). Raises HawkesError on a non-zero status."""
+    lib = lib if lib is not None else load()
+    p = _params(theta)
+    rc = lib.hawkes_loglik_noalloc(ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr), ctypes.c_void_p(t_ptr), int(n),
+                                   ctypes.byref(p), int(flags), ctypes.c_void_p(out_ptr),
+                                   ctypes.c_void_p(stream) if stream else None)
+    if rc != 0:
+        raise HawkesError(rc, "hawkes_loglik_noalloc")
 
 
 def hawkes_strerror(status: int) -> str:

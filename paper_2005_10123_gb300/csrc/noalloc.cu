@@ -1,0 +1,251 @@
+// hawkes_loglik_noalloc: the mixed-precision log-likelihood for callers that cannot
+// allocate device memory.
+//
+// Who needs it: code that may not call cudaMalloc/cudaFree at evaluation time, for
+// example a host program whose device memory is entirely reserved up front by another
+// allocator (a framework's memory pool), or a latency-critical sampler loop in which an
+// allocation or free could block on device-wide synchronisation. Such callers keep their
+// events in device buffers they already own and pass those in; every temporary the
+// evaluation needs lives in one file-scope device array, g_scratch, that the library
+// reserves when it is loaded and keeps until the process exits (on every GPU that loads
+// it, kScratchBytes each).
+//
+// The pair sums come from the library's ordinary mixed-precision pair kernel, unchanged;
+// this file prepares its inputs inside g_scratch (padded float32 copies, tie indices, a
+// fixed work schedule) with one small kernel, and finishes with its own epilogue, which
+// reads t_N from the device so that the whole call stays asynchronous.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "../../include/hawkes.h"
+#include "hk_internal.h"
+
+namespace hk {
+namespace {
+
+constexpr int kNoallocMax = HAWKES_NOALLOC_MAX_EVENTS;  // 65,536 events
+constexpr int kChunks = 4;                               // most column chunks per row tile
+constexpr int kMaxRowTiles = kNoallocMax / kRowTile;     // 128
+constexpr int kMaxPieces = kMaxRowTiles * kChunks;       // 512
+
+// Layout of g_scratch (byte offsets, all 256-aligned).
+constexpr size_t kOffHeader = 0;                                              // counter, ticket
+constexpr size_t kOffX = 1024;
+constexpr size_t kOffY = kOffX + (size_t)kNoallocMax * 4;
+constexpr size_t kOffT = kOffY + (size_t)kNoallocMax * 4;
+constexpr size_t kOffLo = kOffT + (size_t)kNoallocMax * 4;
+constexpr size_t kOffPieces = kOffLo + (size_t)kNoallocMax * 4;
+constexpr size_t kOffRangeFirst = kOffPieces + (size_t)kMaxPieces * 16;
+constexpr size_t kOffSlotFirst = kOffRangeFirst + (size_t)(kMaxPieces + 64) * 4;
+constexpr size_t kOffBlockPart = kOffSlotFirst + (size_t)(kMaxRowTiles + 64) * 4;
+constexpr size_t kOffPartials = kOffBlockPart + (size_t)(kNoallocMax / kEpiThreads) * 8 * 8;
+constexpr size_t kScratchBytes = kOffPartials + (size_t)kMaxPieces * kSumsLoglik * kRowTile * 8;
+static_assert(kOffRangeFirst % 256 == 0 && kOffSlotFirst % 256 == 0 && kOffBlockPart % 256 == 0 &&
+                  kOffPartials % 256 == 0,
+              "scratch regions must stay 256-byte aligned");
+
+// The scratch array. In host code this name is only a stand-in symbol, not a device
+// address: host code obtains the address with cudaGetSymbolAddress (see scratch_base).
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+// Fill the padded float32 copies, the tie indices lo[i] (first index whose time equals
+// t[i], by binary search; sorted times assumed) and the fixed schedule: row tile rt is
+// split into `chunks` (<= the number of column tiles) non-empty column chunks of near-equal
+// length, one piece and one range each.
+__global__ void noalloc_prep(const float *__restrict__ x, const float *__restrict__ y,
+                             const float *__restrict__ t, int n, int npad, int nrt, int nct, int chunks,
+                             unsigned char *scratch) {
+  float *sx = (float *)(scratch + kOffX), *sy = (float *)(scratch + kOffY), *st = (float *)(scratch + kOffT);
+  int *lo = (int *)(scratch + kOffLo);
+  int4 *pieces = (int4 *)(scratch + kOffPieces);
+  int *range_first = (int *)(scratch + kOffRangeFirst), *slot_first = (int *)(scratch + kOffSlotFirst);
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += stride) {
+    if (i < n) {
+      const float ti = t[i];
+      sx[i] = x[i];
+      sy[i] = y[i];
+      st[i] = ti;
+      int a = 0, b = i;  // first index in [0, i] whose time is >= t[i]
+      while (a < b) {
+        const int m = (a + b) >> 1;
+        if (t[m] < ti) a = m + 1; else b = m;
+      }
+      lo[i] = a;
+    } else {
+      sx[i] = 0.f;
+      sy[i] = 0.f;
+      st[i] = t[n - 1];
+      lo[i] = n;
+    }
+  }
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nrt * chunks; p += stride) {
+    const int rt = p / chunks, c = p % chunks;
+    pieces[p] = make_int4(rt, c * nct / chunks, (c + 1) * nct / chunks, 0);
+    range_first[p] = p;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) range_first[nrt * chunks] = nrt * chunks;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r <= nrt; r += stride) slot_first[r] = r * chunks;
+}
+
+// log lambda_n - Lambda_n per event and a fixed-order sum (warp tree, warps in order,
+// blocks in order by the last block to finish), as the library's epilogue does, with
+// t_N = t[n-1] taken from the float32 copy on the device.
+__global__ void __launch_bounds__(kEpiThreads) noalloc_epilogue(const __grid_constant__ Request R, int chunks,
+                                                                unsigned char *scratch) {
+  constexpr int NW = kEpiThreads / 32;
+  __shared__ double red[NW];
+  __shared__ int s_last;
+  const float *st = (const float *)(scratch + kOffT);
+  const double *partials = (const double *)(scratch + kOffPartials);
+  double *block_part = (double *)(scratch + kOffBlockPart);
+  unsigned *ticket = (unsigned *)(scratch + kOffHeader + 256);
+  const int n = R.set.n, nblk = (n + kEpiThreads - 1) / kEpiThreads;
+  const double t_last = (double)st[n - 1];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+    const int i = blk * kEpiThreads + tid;
+    double v = 0.0;
+    if (i < n) {
+      const int rt = i / kRowTile, li = i - rt * kRowTile;
+      double sb = 0.0, ss = 0.0;
+      for (int c = 0; c < chunks; ++c) {
+        const double *src = partials + (size_t)(rt * chunks + c) * kSumsLoglik * kRowTile + li;
+        sb += src[0];
+        ss += src[kRowTile];
+      }
+      const double two_pi = 6.28318530717958647693;
+      const double A = R.mu0 / (two_pi * sqrt(two_pi) * R.tau_x * R.tau_x * R.tau_t);
+      const double C = R.theta * R.omega / (two_pi * R.h * R.h);
+      const double tn = (double)st[i];
+      const double Lam = R.mu0 * (normcdf((t_last - tn) / R.tau_t) - normcdf(-tn / R.tau_t)) +
+                         R.theta * (1.0 - exp(-R.omega * (t_last - tn)));
+      v = log(A * sb + C * ss) - Lam;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (tid == 0) {
+      double x = 0.0;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) x += red[w];
+      block_part[blk] = x;
+      __threadfence();
+      s_last = (atomicAdd(ticket, 1u) == (unsigned)(nblk - 1));
+    }
+    __syncthreads();
+    if (s_last && tid == 0) {
+      __threadfence();
+      double x = 0.0;
+      for (int b = 0; b < nblk; ++b) x += __ldcg(block_part + b);
+      R.out[0] = x;
+    }
+    __syncthreads();
+  }
+}
+
+struct DeviceScratch {
+  unsigned char *base = nullptr;
+  int sms = 0, occ = 0;
+  bool ready = false;
+};
+constexpr int kMaxDevices = 64;
+DeviceScratch g_dev[kMaxDevices];
+std::mutex g_setup_mu;
+
+// Once per device, with that device current: the device address of g_scratch and the
+// launch geometry of the pair kernel.
+int scratch_base(int device, DeviceScratch **out) {
+  if (device < 0 || device >= kMaxDevices) return HAWKES_E_INVAL;
+  std::lock_guard<std::mutex> lk(g_setup_mu);
+  DeviceScratch &d = g_dev[device];
+  if (!d.ready) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess) return HAWKES_E_CUDA;
+    if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return HAWKES_E_CUDA;
+    d.occ = occupancy_pair_mixed(false);
+    if (d.occ < 1) d.occ = 1;
+    d.base = (unsigned char *)p;
+    d.ready = true;
+  }
+  *out = &d;
+  return HAWKES_OK;
+}
+
+}  // namespace
+}  // namespace hk
+
+using namespace hk;
+
+extern "C" int hawkes_loglik_noalloc(const float *x, const float *y, const float *t, int64_t n,
+                                     const hawkes_params *p, int flags, double *device_out,
+                                     void *cuda_stream) {
+  if (!x || !y || !t || !p || !device_out) return HAWKES_E_INVAL;
+  if (n < 1 || n > kNoallocMax) return HAWKES_E_INVAL;  // above HAWKES_NOALLOC_MAX_EVENTS
+  if (flags & ~HAWKES_FLAG_EXCLUDE_SELF) return HAWKES_E_INVAL;
+  const double vals[6] = {p->mu0, p->tau_x, p->tau_t, p->theta, p->omega, p->h};
+  for (int k = 0; k < 6; ++k)
+    if (!std::isfinite(vals[k]) || (k == 3 ? vals[k] < 0.0 : vals[k] <= 0.0)) return HAWKES_E_INVAL;
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess) return HAWKES_E_CUDA;
+  DeviceScratch *d = nullptr;
+  if (int rc = scratch_base(device, &d)) return rc;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const int npad = (int)((n + kRowTile - 1) / kRowTile * kRowTile);
+  const int nrt = npad / kRowTile, nct = npad / kColTile;
+  const int chunks = std::min(kChunks, nct);
+  unsigned char *base = d->base;
+
+  // the request, exactly as the ordinary path describes a mixed loglik evaluation
+  Batch b;
+  std::memset(&b, 0, sizeof(b));
+  b.nreq = 1;
+  b.mode = 1;
+  b.counter = (unsigned *)(base + kOffHeader);
+  Request &R = b.req[0];
+  R.set.x32 = (const float *)(base + kOffX);
+  R.set.y32 = (const float *)(base + kOffY);
+  R.set.t32 = (const float *)(base + kOffT);
+  R.set.lo32 = (const int *)(base + kOffLo);
+  R.set.n = (int)n; R.set.npad = npad; R.set.nrt = nrt; R.set.nct = nct;
+  R.sched.pieces = (const int4 *)(base + kOffPieces);
+  R.sched.range_first = (const int *)(base + kOffRangeFirst);
+  R.sched.slot_first = (const int *)(base + kOffSlotFirst);
+  R.sched.npieces = nrt * chunks;
+  R.sched.nranges = nrt * chunks;
+  R.grad = 0;
+  R.flags = flags;
+  const double log2e = 1.4426950408889634074;
+  R.a2 = (float)(log2e / (2.0 * p->tau_x * p->tau_x));
+  R.beta = (float)std::sqrt(log2e / (2.0 * p->tau_t * p->tau_t));
+  R.wn = (float)(-p->omega * log2e / (double)R.beta);
+  R.cn = (float)(-log2e / (2.0 * p->h * p->h));
+  if (!(R.a2 > 0.f) || !(R.beta > 0.f) || !std::isfinite(R.a2) || !std::isfinite(R.wn) || !(R.cn < 0.f))
+    return HAWKES_E_INVAL;
+  R.mu0 = p->mu0; R.tau_x = p->tau_x; R.tau_t = p->tau_t;
+  R.theta = p->theta; R.omega = p->omega; R.h = p->h;
+  R.tscale = 1.0 / (double)R.beta;
+  R.partials = (double *)(base + kOffPartials);
+  R.block_part = (double *)(base + kOffBlockPart);
+  R.ticket = (unsigned *)(base + kOffHeader + 256);
+  R.out = device_out;
+  R.t_last = 0.0;  // unused here: noalloc_epilogue reads t_N on the device
+
+  // the work counter and the epilogue ticket must start at zero on every call
+  if (cudaMemsetAsync(base + kOffHeader, 0, 1024, s) != cudaSuccess) return HAWKES_E_CUDA;
+  noalloc_prep<<<std::min(d->sms * 4, (npad + 255) / 256 + 1), 256, 0, s>>>(x, y, t, (int)n, npad, nrt, nct,
+                                                                            chunks, base);
+  if (cudaGetLastError() != cudaSuccess) return HAWKES_E_CUDA;
+  b.req[0].item_begin = 0;
+  b.req[0].epi_begin = 0;
+  b.total_items = nrt * chunks;
+  b.total_epi = (int)((n + kEpiThreads - 1) / kEpiThreads);
+  const int grid = std::max(1, std::min(b.total_items, d->sms * d->occ));
+  if (launch_pair_mixed(b, false, grid, s) != cudaSuccess) return HAWKES_E_CUDA;
+  noalloc_epilogue<<<std::max(1, std::min(b.total_epi, d->sms * 8)), kEpiThreads, 0, s>>>(b.req[0], chunks,
+                                                                                        base);
+  if (cudaGetLastError() != cudaSuccess) return HAWKES_E_CUDA;
+  return HAWKES_OK;
+}
