@@ -58,6 +58,12 @@ extern "C" {
 
 /* ---- flags (hawkes_set_flags) ----------------------------------------------------- */
 #define HAWKES_FLAG_EXCLUDE_SELF 1 /* drop n' = n from the background sum of lambda_n    */
+#define HAWKES_FLAG_DENSE 2        /* visit all N^2 pairs (see below)                      */
+/* By default each row only visits the columns whose pair terms can be nonzero at the working
+ * precision: a pair term whose exponent is so negative that float32 ex2 (flushing subnormals
+ * to zero) or float64 exp returns exactly +0 cannot change a sum. Every term computed is the
+ * same as when all N^2 pairs are visited; only the grouping of the float64 partial sums
+ * differs (results agree to about 1e-16 relative). HAWKES_FLAG_DENSE visits all pairs. */
 
 typedef struct hawkes_ctx hawkes_ctx;
 
@@ -132,6 +138,12 @@ int hawkes_loglik_async(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *pa
  * bit-identical to the same request evaluated alone. */
 int hawkes_loglik_batch(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_params *params,
                         hawkes_mode mode, int want_grad, double *loglik_out, double *grad_out);
+
+/* Work accounting: the number of (row, column) pairs an evaluation at Theta visits (the
+ * exact-zero window described at HAWKES_FLAG_DENSE, counted over real events) and N^2. Host
+ * computation only; no GPU work. */
+int hawkes_pair_work(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *params, hawkes_mode mode,
+                     int64_t *visited_pairs_out, int64_t *all_pairs_out);
 
 /* Per-event terms of Eq. 2: mu_out[n] = mu(x_n, t_n) (background rate at event n)
  * and xi_out[n] = lambda_n - mu_n (the self-excitation part), so lambda_n =

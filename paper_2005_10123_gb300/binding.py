@@ -17,6 +17,7 @@ from . import build as _build
 HAWKES_FP64 = 0
 HAWKES_MIXED = 1
 HAWKES_FLAG_EXCLUDE_SELF = 1
+HAWKES_FLAG_DENSE = 2
 
 STATUS = {
     0: "HAWKES_OK", -1: "HAWKES_E_INVAL", -2: "HAWKES_E_UNSORTED", -3: "HAWKES_E_NOSET",
@@ -30,7 +31,7 @@ EXPORTS = (
     "hawkes_release_events", "hawkes_set_info", "hawkes_loglik", "hawkes_loglik_grad",
     "hawkes_loglik_async", "hawkes_loglik_batch", "hawkes_event_terms", "hawkes_submit",
     "hawkes_poll", "hawkes_wait", "hawkes_stats", "hawkes_strerror", "hawkes_last_cuda_error",
-    "hawkes_loglik_noalloc",
+    "hawkes_loglik_noalloc", "hawkes_pair_work",
 )
 HAWKES_NOALLOC_MAX_EVENTS = 65536
 
@@ -87,6 +88,7 @@ def load(build_if_missing: bool = False, path: str | None = None):
         "hawkes_wait": [vp, u64, ctypes.c_int, _D, _D],
         "hawkes_stats": [vp, ctypes.POINTER(i64)],
         "hawkes_loglik_noalloc": [vp, vp, vp, i64, P, ctypes.c_int, vp, vp],
+        "hawkes_pair_work": [vp, i32, P, ctypes.c_int, ctypes.POINTER(i64), ctypes.POINTER(i64)],
     }
     for name, args in sig.items():
         if path is not None and not hasattr(lib, name):
@@ -218,6 +220,15 @@ class Context:
                                                 mu.ctypes.data_as(_D), xi.ctypes.data_as(_D),
                                                 ctypes.byref(ll)), "hawkes_event_terms")
         return mu, xi, ll.value
+
+    def hawkes_pair_work(self, set_id: int, theta, mode: int = HAWKES_MIXED):
+        """(pairs visited by an evaluation at theta, N^2)"""
+        v = ctypes.c_int64()
+        a = ctypes.c_int64()
+        p = _params(theta)
+        self._check(self.lib.hawkes_pair_work(self.h, int(set_id), ctypes.byref(p), int(mode), ctypes.byref(v),
+                                              ctypes.byref(a)), "hawkes_pair_work")
+        return v.value, a.value
 
     def hawkes_submit(self, set_id: int, theta, want_grad: bool = False, mode: int = HAWKES_MIXED) -> int:
         p = _params(theta)

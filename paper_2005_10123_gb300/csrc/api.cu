@@ -1,11 +1,11 @@
-// Host runtime behind include/hawkes.h: contexts, resident event sets, work
-// schedules, synchronous and batched evaluation, and the serving queue.
+// Host runtime behind include/hawkes.h: contexts, resident event sets, synchronous and
+// batched evaluation, and the serving queue.
 //
 // Every evaluation is one "batch" launch pair on a stream: the persistent pair kernel
 // (mixed or fp64) fills per-row partial sums, then the epilogue kernel turns them into
 // log lambda_n - Lambda_n and the gradient terms and reduces them per request in a
 // fixed order. A request's arithmetic depends only on its own set, parameters and
-// schedule, never on the other requests of its batch.
+// work decomposition, never on the other requests of its batch.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -30,31 +30,26 @@ using namespace hk;
 
 namespace {
 
-constexpr int kKinds = 3;  // schedule kinds: 0 mixed loglik, 1 mixed grad, 2 fp64
+constexpr int kKinds = 3;  // kernel kinds: 0 mixed loglik, 1 mixed grad, 2 fp64
 constexpr int kFlights = 3;  // serving launches in flight at once
 constexpr double kLog2e = 1.4426950408889634074;
 
 int kind_of(int mode, int grad) { return mode == HAWKES_MIXED ? (grad ? 1 : 0) : 2; }
 int sums_of(int grad) { return grad ? kSumsGrad : kSumsLoglik; }
 
-struct DevSchedule {
-  int4 *pieces = nullptr;
-  int *range_first = nullptr;
-  int *slot_first = nullptr;
-  int npieces = 0, nranges = 0;
-};
-
 struct EventSetRec {
   int32_t id = 0;
   int64_t n = 0, npad = 0;
   int nrt = 0, nct = 0;
-  void *dev = nullptr;  // one allocation for coordinates, lo arrays and schedules
+  void *dev = nullptr;  // one allocation for coordinates and tie indices
   size_t bytes = 0;
   float *x32 = nullptr, *y32 = nullptr, *t32 = nullptr;
   double *x64 = nullptr, *y64 = nullptr, *t64 = nullptr;
   int *lo32 = nullptr, *lo64 = nullptr;
   double t_first32 = 0, t_last32 = 0, t_first64 = 0, t_last64 = 0;
-  DevSchedule sched[kKinds];
+  std::vector<float> t32h;   // host copies of the stored times (for hawkes_pair_work)
+  std::vector<double> t64h;
+  int slices[kKinds] = {1, 1, 1};  // slices per row tile, per kernel kind
   int refs = 0;  // queued or running serving requests
   bool released = false;
 };
@@ -158,70 +153,31 @@ std::vector<int> tie_starts(const std::vector<F> &t, int64_t n, int64_t npad) {
   return lo;
 }
 
-struct HostSchedule {
-  std::vector<int4> pieces;
-  std::vector<int> range_first, slot_first;
-};
+// Slices per row tile for a kernel kind: enough items for about kItemsPerSlot items per
+// resident CTA, at most one column tile per slice.
+constexpr int kItemsPerSlot = 2;
+int slices_for(int nrt, int nct, int resident_ctas) {
+  const int want = (kItemsPerSlot * resident_ctas + nrt - 1) / nrt;
+  return std::max(1, std::min(want, nct));
+}
 
-// Split the (row tile x column tile) units of a set into ranges of about equal cost
-// (row-major order), then split each range at row-tile boundaries into pieces. The
-// cost of a unit is, per warp of the row tile, wb (background) plus wt if the warp's
-// rows have at least one causal column in the tile.
-HostSchedule build_schedule(const std::vector<int> &lo, int64_t n, int nrt, int nct, double wb, double wt,
-                            int target_ranges) {
-  const int64_t nunits = (int64_t)nrt * nct;
-  std::vector<double> cost((size_t)nunits);
-  double total = 0;
-  for (int rt = 0; rt < nrt; ++rt) {
-    for (int ct = 0; ct < nct; ++ct) {
-      const int c0 = ct * kColTile, c1 = c0 + kColTile;
-      double c = 0;
-      for (int w = 0; w < kRowTile / kWarpRows; ++w) {
-        const int wa = rt * kRowTile + w * kWarpRows, wbr = wa + kWarpRows - 1;
-        const int lo_a = lo[(size_t)wa], lo_b = lo[(size_t)wbr];
-        const bool any_causal = !(c0 >= lo_b) || (c1 <= lo_a);
-        c += wb + (any_causal ? wt : 0.0);
-      }
-      cost[(size_t)rt * nct + ct] = c;
-      total += c;
-    }
+// Exact-zero cut-offs (days) of Section 2.1's pair terms at the working precision:
+// float32 ex2.approx.ftz returns +0 for every exponent <= -126, float64 exp returns +0 far
+// below -745. A background term is zero once dt' = beta dt reaches sqrt(130) (float32) or
+// dt^2 / (2 tau_t^2) reaches 805 (float64); a trigger term once omega dt log2(e) reaches 131
+// (float32) or omega dt reaches 805 (float64). One percent of margin covers the rounding
+// of the time differences. Columns later than a row only carry background terms.
+void exact_zero_cutoffs(const hawkes_params *p, int mode, float beta32, double *early, double *late) {
+  double bg, trig;
+  if (mode == HAWKES_MIXED) {
+    bg = 1.01 * std::sqrt(130.0) / (double)beta32;
+    trig = 1.01 * 131.0 / (p->omega * kLog2e);
+  } else {
+    bg = 1.01 * std::sqrt(805.0 * 2.0) * p->tau_t;
+    trig = 1.01 * 805.0 / p->omega;
   }
-  (void)n;
-  int64_t nranges = std::max<int64_t>(target_ranges, (nunits + 95) / 96);
-  nranges = std::min<int64_t>(std::max<int64_t>(nranges, 1), nunits);
-  // cut points: the first unit whose cumulative cost reaches k * total / nranges
-  std::vector<int64_t> cuts;
-  cuts.push_back(0);
-  double cum = 0;
-  int64_t k = 1;
-  for (int64_t u = 0; u < nunits && k < nranges; ++u) {
-    cum += cost[(size_t)u];
-    while (k < nranges && cum >= total * (double)k / (double)nranges) {
-      if (u + 1 > cuts.back() && u + 1 < nunits) cuts.push_back(u + 1);
-      ++k;
-    }
-  }
-  cuts.push_back(nunits);
-  HostSchedule s;
-  s.slot_first.assign((size_t)nrt + 1, 0);
-  for (size_t r = 0; r + 1 < cuts.size(); ++r) {
-    s.range_first.push_back((int)s.pieces.size());
-    int64_t u = cuts[r];
-    const int64_t end = cuts[r + 1];
-    while (u < end) {
-      const int rt = (int)(u / nct), ct = (int)(u % nct);
-      const int64_t row_end = (int64_t)(rt + 1) * nct;
-      const int64_t stop = std::min(end, row_end);
-      s.pieces.push_back(make_int4(rt, ct, (int)(stop - (int64_t)rt * nct), 0));
-      u = stop;
-    }
-  }
-  s.range_first.push_back((int)s.pieces.size());
-  // slot_first: pieces are in (row tile, column) order
-  std::vector<int> count((size_t)nrt, 0);
-  for (auto &p : s.pieces) count[(size_t)p.x]++;
-  for (int rt = 0; rt < nrt; ++rt) s.slot_first[(size_t)rt + 1] = s.slot_first[(size_t)rt] + count[(size_t)rt];
-  return s;
+  *early = std::max(bg, trig);
+  *late = bg;
 }
 
 // Request descriptor for one evaluation of set `S` at Theta `p`.
@@ -232,9 +188,7 @@ int make_request(hawkes_ctx *ctx, const EventSetRec *S, const hawkes_params *p, 
   R->set.x64 = S->x64; R->set.y64 = S->y64; R->set.t64 = S->t64;
   R->set.lo32 = S->lo32; R->set.lo64 = S->lo64;
   R->set.n = (int)S->n; R->set.npad = (int)S->npad; R->set.nrt = S->nrt; R->set.nct = S->nct;
-  const DevSchedule &D = S->sched[kind_of(mode, grad)];
-  R->sched.pieces = D.pieces; R->sched.range_first = D.range_first; R->sched.slot_first = D.slot_first;
-  R->sched.npieces = D.npieces; R->sched.nranges = D.nranges;
+  R->slices = S->slices[kind_of(mode, grad)];
   R->grad = grad;
   R->flags = flags;
   const double beta = std::sqrt(kLog2e / (2.0 * p->tau_t * p->tau_t));
@@ -259,16 +213,18 @@ int make_request(hawkes_ctx *ctx, const EventSetRec *S, const hawkes_params *p, 
     R->t_last = S->t_last64;
     R->tscale = 1.0;
   }
+  exact_zero_cutoffs(p, mode, R->beta, &R->cut_early, &R->cut_late);
   (void)ctx;
   return HAWKES_OK;
 }
 
 int epi_blocks(int64_t n) { return (int)((n + kEpiThreads - 1) / kEpiThreads); }
 
-// Device bytes one request needs: partial sums, epilogue block partials, ticket, output.
+// Device bytes one request needs: partial sums, compensator sums, epilogue block partials.
 size_t request_footprint(const EventSetRec *S, int mode, int grad) {
-  const DevSchedule &D = S->sched[kind_of(mode, grad)];
-  size_t b = align_up((size_t)D.npieces * sums_of(grad) * kRowTile * sizeof(double), 256);
+  const size_t items = (size_t)S->nrt * S->slices[kind_of(mode, grad)];
+  size_t b = align_up(items * sums_of(grad) * kRowTile * sizeof(double), 256);
+  b += align_up((size_t)S->nrt * 8 * sizeof(double), 256);
   b += align_up((size_t)epi_blocks(S->n) * 8 * sizeof(double), 256);
   return b;
 }
@@ -284,9 +240,13 @@ constexpr size_t kFixedBytes = kHdrBytes + kOutBytes;
 // Carve one request's workspace out of `base` (as sized by request_footprint).
 void bind_workspace(Request *R, const EventSetRec *S, int mode, int grad, char *base, double *out,
                     unsigned *ticket) {
-  const DevSchedule &D = S->sched[kind_of(mode, grad)];
-  R->partials = (double *)base;
-  R->block_part = (double *)(base + align_up((size_t)D.npieces * sums_of(grad) * kRowTile * sizeof(double), 256));
+  const size_t items = (size_t)S->nrt * S->slices[kind_of(mode, grad)];
+  size_t off = 0;
+  R->partials = (double *)(base + off);
+  off += align_up(items * sums_of(grad) * kRowTile * sizeof(double), 256);
+  R->comp = (double *)(base + off);
+  off += align_up((size_t)S->nrt * 8 * sizeof(double), 256);
+  R->block_part = (double *)(base + off);
   R->ticket = ticket;
   R->out = out;
 }
@@ -304,7 +264,7 @@ int launch_batch(hawkes_ctx *ctx, Batch &b, int mode, int grad, cudaStream_t s) 
   for (int r = 0; r < b.nreq; ++r) {
     b.req[r].item_begin = items;
     b.req[r].epi_begin = epi;
-    items += b.req[r].sched.nranges;
+    items += b.req[r].set.nrt * b.req[r].slices;
     epi += epi_blocks(b.req[r].set.n);
   }
   b.total_items = items;
@@ -670,7 +630,7 @@ int hawkes_destroy(hawkes_ctx *ctx) {
 }
 
 int hawkes_set_flags(hawkes_ctx *ctx, int flags) {
-  if (!ctx || (flags & ~HAWKES_FLAG_EXCLUDE_SELF)) return HAWKES_E_INVAL;
+  if (!ctx || (flags & ~(HAWKES_FLAG_EXCLUDE_SELF | HAWKES_FLAG_DENSE))) return HAWKES_E_INVAL;
   std::lock_guard<std::mutex> lock(ctx->mu);
   ctx->flags = flags;
   return HAWKES_OK;
@@ -703,25 +663,17 @@ int hawkes_upload_events(hawkes_ctx *ctx, const double *x, const double *y, cons
   }
   for (int64_t i = n; i < npad; ++i) { T64[(size_t)i] = t[n - 1]; T32[(size_t)i] = (float)t[n - 1]; }
   std::vector<int> lo32 = tie_starts(T32, n, npad), lo64 = tie_starts(T64, n, npad);
+  S->t32h.assign(T32.begin(), T32.begin() + n);
+  S->t64h.assign(T64.begin(), T64.begin() + n);
   S->t_first32 = T32[0]; S->t_last32 = T32[(size_t)n - 1];
   S->t_first64 = T64[0]; S->t_last64 = T64[(size_t)n - 1];
-  // schedules
-  const double wb[kKinds] = {8.0, 10.0, 1.0}, wt[kKinds] = {3.0, 5.0, 1.0};
-  HostSchedule hs[kKinds];
-  for (int k = 0; k < kKinds; ++k)
-    hs[k] = build_schedule(k == 2 ? lo64 : lo32, n, S->nrt, S->nct, wb[k], wt[k], ctx->sms * ctx->occ[k]);
+  for (int k = 0; k < kKinds; ++k) S->slices[k] = slices_for(S->nrt, S->nct, ctx->sms * ctx->occ[k]);
   // one device allocation
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off += align_up(bytes, 256); return o; };
   const size_t o_x32 = take(npad * 4), o_y32 = take(npad * 4), o_t32 = take(npad * 4);
   const size_t o_x64 = take(npad * 8), o_y64 = take(npad * 8), o_t64 = take(npad * 8);
   const size_t o_lo32 = take(npad * 4), o_lo64 = take(npad * 4);
-  size_t o_pc[kKinds], o_rf[kKinds], o_sf[kKinds];
-  for (int k = 0; k < kKinds; ++k) {
-    o_pc[k] = take(hs[k].pieces.size() * sizeof(int4));
-    o_rf[k] = take(hs[k].range_first.size() * sizeof(int));
-    o_sf[k] = take(hs[k].slot_first.size() * sizeof(int));
-  }
   const size_t bytes = off;
   std::lock_guard<std::mutex> lock(ctx->mu);
   if (ctx->used.load() + bytes > ctx->budget) return HAWKES_E_ADMISSION;
@@ -734,11 +686,6 @@ int hawkes_upload_events(hawkes_ctx *ctx, const double *x, const double *y, cons
   put(o_x32, X32.data(), npad * 4); put(o_y32, Y32.data(), npad * 4); put(o_t32, T32.data(), npad * 4);
   put(o_x64, X64.data(), npad * 8); put(o_y64, Y64.data(), npad * 8); put(o_t64, T64.data(), npad * 8);
   put(o_lo32, lo32.data(), npad * 4); put(o_lo64, lo64.data(), npad * 4);
-  for (int k = 0; k < kKinds; ++k) {
-    put(o_pc[k], hs[k].pieces.data(), hs[k].pieces.size() * sizeof(int4));
-    put(o_rf[k], hs[k].range_first.data(), hs[k].range_first.size() * sizeof(int));
-    put(o_sf[k], hs[k].slot_first.data(), hs[k].slot_first.size() * sizeof(int));
-  }
   e = cudaMemcpyAsync(dev, host.data(), bytes, cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) { cudaFree(dev); return cuda_fail(ctx, e); }
@@ -747,13 +694,6 @@ int hawkes_upload_events(hawkes_ctx *ctx, const double *x, const double *y, cons
   S->x32 = (float *)(d + o_x32); S->y32 = (float *)(d + o_y32); S->t32 = (float *)(d + o_t32);
   S->x64 = (double *)(d + o_x64); S->y64 = (double *)(d + o_y64); S->t64 = (double *)(d + o_t64);
   S->lo32 = (int *)(d + o_lo32); S->lo64 = (int *)(d + o_lo64);
-  for (int k = 0; k < kKinds; ++k) {
-    S->sched[k].pieces = (int4 *)(d + o_pc[k]);
-    S->sched[k].range_first = (int *)(d + o_rf[k]);
-    S->sched[k].slot_first = (int *)(d + o_sf[k]);
-    S->sched[k].npieces = (int)hs[k].pieces.size();
-    S->sched[k].nranges = (int)hs[k].range_first.size() - 1;
-  }
   ctx->used += bytes;
   const int32_t id = ctx->next_set++;
   S->id = id;
@@ -784,6 +724,44 @@ int hawkes_set_info(hawkes_ctx *ctx, int32_t set_id, int64_t *n_out, size_t *dev
   if (!S) return HAWKES_E_NOSET;
   if (n_out) *n_out = S->n;
   if (device_bytes_out) *device_bytes_out = S->bytes;
+  return HAWKES_OK;
+}
+
+int hawkes_pair_work(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *params, hawkes_mode mode,
+                     int64_t *visited_pairs_out, int64_t *all_pairs_out) {
+  if (!ctx || !params || (mode != HAWKES_FP64 && mode != HAWKES_MIXED)) return HAWKES_E_INVAL;
+  if (int rc = check_params(params)) return rc;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  EventSetRec *S = find_set(ctx, set_id);
+  if (!S) return HAWKES_E_NOSET;
+  Request R;
+  if (int rc = make_request(ctx, S, params, mode, 0, ctx->flags, &R)) return rc;
+  const int64_t n = S->n;
+  int64_t visited = 0;
+  for (int rt = 0; rt < S->nrt; ++rt) {
+    const int64_t r0 = (int64_t)rt * kRowTile, r1 = std::min<int64_t>(r0 + kRowTile, n) - 1;
+    int c0 = 0, c1 = S->nct;
+    if (!(ctx->flags & HAWKES_FLAG_DENSE)) {  // the window of column_window() in the kernels
+      int64_t j0, j1;
+      if (mode == HAWKES_MIXED) {
+        const double lo = (double)S->t32h[(size_t)r0] - R.cut_early, hi = (double)S->t32h[(size_t)r1] + R.cut_late;
+        j0 = std::lower_bound(S->t32h.begin(), S->t32h.end(), lo, [](float a, double v) { return (double)a < v; }) -
+             S->t32h.begin();
+        j1 = std::upper_bound(S->t32h.begin(), S->t32h.end(), hi, [](double v, float a) { return v < (double)a; }) -
+             S->t32h.begin();
+      } else {
+        const double lo = S->t64h[(size_t)r0] - R.cut_early, hi = S->t64h[(size_t)r1] + R.cut_late;
+        j0 = std::lower_bound(S->t64h.begin(), S->t64h.end(), lo) - S->t64h.begin();
+        j1 = std::upper_bound(S->t64h.begin(), S->t64h.end(), hi) - S->t64h.begin();
+      }
+      c0 = (int)(j0 / kColTile);
+      c1 = std::max(std::min((int)((j1 + kColTile - 1) / kColTile), S->nct), c0 + 1);
+    }
+    const int64_t cols = std::min<int64_t>((int64_t)c1 * kColTile, n) - (int64_t)c0 * kColTile;
+    visited += (r1 - r0 + 1) * cols;
+  }
+  if (visited_pairs_out) *visited_pairs_out = visited;
+  if (all_pairs_out) *all_pairs_out = n * n;
   return HAWKES_OK;
 }
 

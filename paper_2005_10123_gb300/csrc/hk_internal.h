@@ -11,20 +11,20 @@ namespace hk {
 // A pair-kernel CTA holds kRowTile consecutive rows (events n) in registers,
 // kRowsPerThread per thread, and streams column tiles of kColTile events (n')
 // through shared memory. Event arrays are padded to a multiple of kRowTile.
+#ifndef HK_ROWS_PER_THREAD
+#define HK_ROWS_PER_THREAD 4
+#endif
 constexpr int kThreads = 128;
-constexpr int kRowsPerThread = 4;
-constexpr int kRowTile = kThreads * kRowsPerThread;  // 512
+constexpr int kRowsPerThread = HK_ROWS_PER_THREAD;  // even: rows are processed in packed pairs
+constexpr int kRowTile = kThreads * kRowsPerThread;  // 512 with 4 rows per thread
 constexpr int kColTile = 256;
-constexpr int kWarpRows = 32 * kRowsPerThread;       // 128 consecutive rows per warp
+constexpr int kWarpRows = 32 * kRowsPerThread;       // consecutive rows per warp
 constexpr int kEpiThreads = 256;                     // epilogue rows per CTA
 constexpr int kMaxBatch = 64;                        // requests per launch
 constexpr int kSumsLoglik = 2;                       // S_b, S_s
 constexpr int kSumsGrad = 6;                         // S_b, S_s, R_b, T_b, R_s, U_s
-
-// Sentinel for padded events: a time so large that every pair term involving a
-// padded event is exactly zero (its squared time distance overflows to +inf).
-constexpr float kPadTime32 = 1.0e30f;
-constexpr double kPadTime64 = 1.0e300;
+constexpr int kFlagExcludeSelf = 1;                  // HAWKES_FLAG_EXCLUDE_SELF
+constexpr int kFlagDense = 2;                        // HAWKES_FLAG_DENSE
 
 // One resident event set, as the kernels see it.
 struct SetView {
@@ -34,40 +34,40 @@ struct SetView {
   int n, npad, nrt, nct;   // events, padded length, row tiles, column tiles
 };
 
-// Work schedule of one request kind on one set. A "piece" is a run of column tiles
-// of one row tile; pieces are sorted by (row tile, first column tile), so the piece
-// index is also the partial-sum slot and slot_first[rt] is the first piece of row
-// tile rt. A "range" (one work item of the persistent pair kernel) is a run of
-// consecutive pieces of about equal cost.
-struct Schedule {
-  const int4 *pieces;      // {row_tile, col_tile_begin, col_tile_end, 0}
-  const int *range_first;  // nranges + 1
-  const int *slot_first;   // nrt + 1
-  int npieces, nranges;
-};
-
+// Work decomposition: item = (row tile rt, slice s), s < slices. For each request the
+// pair kernel finds the window of column tiles of rt that can hold a nonzero pair term
+// (every other pair term is exactly zero at the working precision, see cut_early and
+// cut_late) and gives slice s the s-th of `slices` near-equal parts of that window. The
+// item index rt * slices + s is also the partial-sum slot, so results do not depend on
+// which CTA ran which item.
 struct Request {
   SetView set;
-  Schedule sched;
+  int slices;      // slices per row tile (fixed per set and kernel kind)
   int grad;        // 0: loglik only; 1: loglik and gradient
   int flags;       // HAWKES_FLAG_* of the context at submission
-  int item_begin;  // first pair-kernel item (range) of this request in the batch
+  int item_begin;  // first pair-kernel item of this request in the batch
   int epi_begin;   // first epilogue item (block of kEpiThreads rows) in the batch
+  // Column window: column n' can only contribute to row n if
+  //   t_n - cut_early <= t_n' <= t_n + cut_late   (days; +inf keeps every column)
+  double cut_early, cut_late;
   // float32 pair constants (mixed mode)
-  float a2;    // log2(e) / (2 tau_x^2)                  multiplies raw r^2
+  float a2;    // log2(e) / (2 tau_x^2)                  multiplies r^2
   float beta;  // sqrt(log2(e) / (2 tau_t^2))            scales (t - t0)
   float wn;    // -omega log2(e) / beta                  multiplies scaled dt
-  float cn;    // -log2(e) / (2 h^2)                     multiplies raw r^2
+  float cn;    // -log2(e) / (2 h^2)                     multiplies r^2
   // float64 pair constants (fp64 mode)
   double da;   // 1 / (2 tau_x^2)
   double db;   // 1 / (2 tau_t^2)
   double dc;   // 1 / (2 h^2)
-  // Theta and t_N for the epilogue
+  // Theta and t_N for the compensator and the epilogue
   double mu0, tau_x, tau_t, theta, omega, h;
   double t_last;
   double tscale;  // scaled-to-raw time factor of the moments: 1/beta (mixed) or 1 (fp64)
   // workspace (device)
-  double *partials;    // npieces * S * kRowTile
+  double *partials;    // nrt * slices * S * kRowTile
+  double *comp;        // nrt * 8: per row tile, the sums of Lambda_n and d Lambda_n / d Theta
+                       // (written by slice 0 of the pair kernel), or nullptr: the epilogue
+                       // then computes the compensator itself
   double *block_part;  // epilogue blocks * 8
   unsigned *ticket;    // epilogue completion counter, zero between launches
   double *out;         // 7 doubles: ell, d ell / d Theta
@@ -77,7 +77,7 @@ struct Request {
 
 struct Batch {
   int nreq;
-  int total_items;  // pair-kernel items (ranges) over all requests
+  int total_items;  // pair-kernel items over all requests
   int total_epi;    // epilogue items over all requests
   int mode;         // 0 fp64, 1 mixed (one mode per launch)
   unsigned *counter;  // pair-kernel work counter, zeroed before the launch
@@ -89,7 +89,7 @@ struct Batch {
 cudaError_t launch_pair_mixed(const Batch &b, bool grad, int grid, cudaStream_t s);
 cudaError_t launch_pair_fp64(const Batch &b, bool grad, int grid, cudaStream_t s);
 cudaError_t launch_epilogue(const Batch &b, bool grad, int grid, cudaStream_t s);
-// Resident CTAs per SM of each pair kernel (for the persistent grid and schedule).
+// Resident CTAs per SM of each pair kernel (for the persistent grid and the slices).
 int occupancy_pair_mixed(bool grad);
 int occupancy_pair_fp64(bool grad);
 
@@ -103,5 +103,99 @@ __host__ __device__ inline int find_request(const Batch &b, int item, bool epi) 
   }
   return lo;
 }
+
+#ifdef __CUDACC__
+// First index k in [0, n) with t[k] >= v (strict = false) or t[k] > v (strict = true),
+// n if none, for sorted t; computed by one whole warp with 32-way probing (at most
+// ceil(log32 n) + 1 rounds of one load per lane). Every lane returns the result.
+template <typename TT>
+__device__ inline int warp_search(const TT *t, int n, double v, bool strict) {
+  const int lane = threadIdx.x & 31;
+  int a = 0, b = n;  // the answer lies in [a, b]
+  while (a < b) {
+    const int step = (b - a + 31) / 32;
+    const int p = a + lane * step;
+    bool hit = true;
+    if (p < b) {
+      const double tp = (double)t[p];
+      hit = strict ? (tp > v) : (tp >= v);
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, hit);
+    if (m == 0u) {  // every probe falls before the answer
+      a = a + 31 * step + 1;
+      continue;
+    }
+    const int f = __ffs(m) - 1;
+    if (f == 0) {
+      b = a;
+      break;
+    }
+    const int pf = a + f * step;
+    a = a + (f - 1) * step + 1;
+    b = min(pf, b);
+  }
+  return b;
+}
+
+// Column-tile window [x, y) of row tile rt for request R: every column outside it is
+// more than cut_early before the tile's first row or more than cut_late after its last
+// row, so each of its pair terms with the tile's rows is exactly zero. Called by one
+// full warp; every lane returns the window.
+template <typename TT>
+__device__ inline int2 column_window(const Request &R, const TT *t, int rt) {
+  const SetView &S = R.set;
+  if (R.flags & kFlagDense) return make_int2(0, S.nct);
+  const int r0 = rt * kRowTile, r1 = min(r0 + kRowTile, S.n) - 1;
+  const int j0 = warp_search(t, S.n, (double)t[r0] - R.cut_early, false);
+  const int j1 = warp_search(t, S.n, (double)t[r1] + R.cut_late, true);
+  const int c0 = j0 / kColTile;
+  const int c1 = min((j1 + kColTile - 1) / kColTile, S.nct);
+  return make_int2(c0, max(c1, c0 + 1));
+}
+
+__device__ __forceinline__ double std_normal_pdf(double u) {
+  return exp(-0.5 * u * u) * 0.39894228040143267794;  // 1 / sqrt(2 pi)
+}
+
+// Compensator of Section 2.1 for the rows of row tile rt, summed in a fixed order over the
+// CTA: Lambda_n = mu0 (Phi((t_N - t_n)/tau_t) - Phi(-t_n/tau_t)) + theta (1 - e^{-omega (t_N -
+// t_n)}) and, with `grad`, its derivatives with respect to (mu0, tau_x, tau_t, theta, omega,
+// h). Thread 0 writes the 7 sums to R.comp[8 rt ...]. Called by every thread of the CTA.
+template <typename TT>
+__device__ void compensator_tile(const Request &R, const TT *t, int rt, bool grad) {
+  __shared__ double red[32][8];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = (blockDim.x + 31) >> 5;
+  const double mu0 = R.mu0, tt = R.tau_t, th = R.theta, om = R.omega, tN = R.t_last;
+  double v[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  const int end = min((rt + 1) * kRowTile, R.set.n);
+  for (int i = rt * kRowTile + tid; i < end; i += blockDim.x) {
+    const double tn = (double)t[i];
+    const double a = (tN - tn) / tt, b = -tn / tt, D = tN - tn;
+    const double e = exp(-om * D);
+    const double Pa = normcdf(a), Pb = normcdf(b);
+    v[0] += mu0 * (Pa - Pb) + th * (1.0 - e);
+    if (grad) {
+      v[1] += Pa - Pb;
+      v[3] += mu0 / tt * (-a * std_normal_pdf(a) + b * std_normal_pdf(b));
+      v[4] += 1.0 - e;
+      v[5] += th * D * e;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    double x = v[q];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+    if (lane == 0) red[warp][q] = x;
+  }
+  __syncthreads();
+  if (tid < 7) {
+    double x = 0.0;
+    for (int w = 0; w < nw; ++w) x += red[w][tid];
+    R.comp[(size_t)rt * 8 + tid] = x;
+  }
+  __syncthreads();
+}
+#endif
 
 }  // namespace hk

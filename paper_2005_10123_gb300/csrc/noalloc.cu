@@ -10,10 +10,10 @@
 // reserves when it is loaded and keeps until the process exits (on every GPU that loads
 // it, kScratchBytes each).
 //
-// The pair sums come from the library's ordinary mixed-precision pair kernel, unchanged;
-// this file prepares its inputs inside g_scratch (padded float32 copies, tie indices, a
-// fixed work schedule) with one small kernel, and finishes with its own epilogue, which
-// reads t_N from the device so that the whole call stays asynchronous.
+// The pair sums come from the library's ordinary mixed-precision pair kernel; this file
+// prepares its inputs inside g_scratch (padded float32 copies, tie indices) with one small
+// kernel and finishes with its own epilogue, which reads t_N from the device so that the
+// whole call stays asynchronous.
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -27,7 +27,7 @@ namespace {
 constexpr int kNoallocMax = HAWKES_NOALLOC_MAX_EVENTS;  // 65,536 events
 constexpr int kChunks = 4;                               // most column chunks per row tile
 constexpr int kMaxRowTiles = kNoallocMax / kRowTile;     // 128
-constexpr int kMaxPieces = kMaxRowTiles * kChunks;       // 512
+constexpr int kMaxItems = kMaxRowTiles * kChunks;        // 512
 
 // Layout of g_scratch (byte offsets, all 256-aligned).
 constexpr size_t kOffHeader = 0;                                              // counter, ticket
@@ -35,31 +35,21 @@ constexpr size_t kOffX = 1024;
 constexpr size_t kOffY = kOffX + (size_t)kNoallocMax * 4;
 constexpr size_t kOffT = kOffY + (size_t)kNoallocMax * 4;
 constexpr size_t kOffLo = kOffT + (size_t)kNoallocMax * 4;
-constexpr size_t kOffPieces = kOffLo + (size_t)kNoallocMax * 4;
-constexpr size_t kOffRangeFirst = kOffPieces + (size_t)kMaxPieces * 16;
-constexpr size_t kOffSlotFirst = kOffRangeFirst + (size_t)(kMaxPieces + 64) * 4;
-constexpr size_t kOffBlockPart = kOffSlotFirst + (size_t)(kMaxRowTiles + 64) * 4;
+constexpr size_t kOffBlockPart = kOffLo + (size_t)kNoallocMax * 4;
 constexpr size_t kOffPartials = kOffBlockPart + (size_t)(kNoallocMax / kEpiThreads) * 8 * 8;
-constexpr size_t kScratchBytes = kOffPartials + (size_t)kMaxPieces * kSumsLoglik * kRowTile * 8;
-static_assert(kOffRangeFirst % 256 == 0 && kOffSlotFirst % 256 == 0 && kOffBlockPart % 256 == 0 &&
-                  kOffPartials % 256 == 0,
-              "scratch regions must stay 256-byte aligned");
+constexpr size_t kScratchBytes = kOffPartials + (size_t)kMaxItems * kSumsLoglik * kRowTile * 8;
+static_assert(kOffBlockPart % 256 == 0 && kOffPartials % 256 == 0, "scratch regions must stay 256-byte aligned");
 
 // The scratch array. In host code this name is only a stand-in symbol, not a device
 // address: host code obtains the address with cudaGetSymbolAddress (see scratch_base).
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-// Fill the padded float32 copies, the tie indices lo[i] (first index whose time equals
-// t[i], by binary search; sorted times assumed) and the fixed schedule: row tile rt is
-// split into `chunks` (<= the number of column tiles) non-empty column chunks of near-equal
-// length, one piece and one range each.
+// Fill the padded float32 copies and the tie indices lo[i] (first index whose time equals
+// t[i], by binary search; sorted times assumed).
 __global__ void noalloc_prep(const float *__restrict__ x, const float *__restrict__ y,
-                             const float *__restrict__ t, int n, int npad, int nrt, int nct, int chunks,
-                             unsigned char *scratch) {
+                             const float *__restrict__ t, int n, int npad, unsigned char *scratch) {
   float *sx = (float *)(scratch + kOffX), *sy = (float *)(scratch + kOffY), *st = (float *)(scratch + kOffT);
   int *lo = (int *)(scratch + kOffLo);
-  int4 *pieces = (int4 *)(scratch + kOffPieces);
-  int *range_first = (int *)(scratch + kOffRangeFirst), *slot_first = (int *)(scratch + kOffSlotFirst);
   const int stride = gridDim.x * blockDim.x;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += stride) {
     if (i < n) {
@@ -80,13 +70,6 @@ __global__ void noalloc_prep(const float *__restrict__ x, const float *__restric
       lo[i] = n;
     }
   }
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nrt * chunks; p += stride) {
-    const int rt = p / chunks, c = p % chunks;
-    pieces[p] = make_int4(rt, c * nct / chunks, (c + 1) * nct / chunks, 0);
-    range_first[p] = p;
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) range_first[nrt * chunks] = nrt * chunks;
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r <= nrt; r += stride) slot_first[r] = r * chunks;
 }
 
 // log lambda_n - Lambda_n per event and a fixed-order sum (warp tree, warps in order,
@@ -210,11 +193,7 @@ extern "C" int hawkes_loglik_noalloc(const float *x, const float *y, const float
   R.set.t32 = (const float *)(base + kOffT);
   R.set.lo32 = (const int *)(base + kOffLo);
   R.set.n = (int)n; R.set.npad = npad; R.set.nrt = nrt; R.set.nct = nct;
-  R.sched.pieces = (const int4 *)(base + kOffPieces);
-  R.sched.range_first = (const int *)(base + kOffRangeFirst);
-  R.sched.slot_first = (const int *)(base + kOffSlotFirst);
-  R.sched.npieces = nrt * chunks;
-  R.sched.nranges = nrt * chunks;
+  R.slices = chunks;
   R.grad = 0;
   R.flags = flags;
   const double log2e = 1.4426950408889634074;
@@ -222,11 +201,17 @@ extern "C" int hawkes_loglik_noalloc(const float *x, const float *y, const float
   R.beta = (float)std::sqrt(log2e / (2.0 * p->tau_t * p->tau_t));
   R.wn = (float)(-p->omega * log2e / (double)R.beta);
   R.cn = (float)(-log2e / (2.0 * p->h * p->h));
-  if (!(R.a2 > 0.f) || !(R.beta > 0.f) || !std::isfinite(R.a2) || !std::isfinite(R.wn) || !(R.cn < 0.f))
+  if (!(R.a2 > 0.f) || !(R.beta > 0.f) || !std::isfinite(R.a2) || !std::isfinite(R.wn) || !(R.cn < 0.f) ||
+      !std::isfinite(R.cn))
     return HAWKES_E_INVAL;
   R.mu0 = p->mu0; R.tau_x = p->tau_x; R.tau_t = p->tau_t;
   R.theta = p->theta; R.omega = p->omega; R.h = p->h;
   R.tscale = 1.0 / (double)R.beta;
+  // the same exact-zero column window as the context path (see exact_zero_cutoffs there)
+  const double bg = 1.01 * std::sqrt(130.0) / (double)R.beta, trig = 1.01 * 131.0 / (p->omega * log2e);
+  R.cut_early = std::max(bg, trig);
+  R.cut_late = bg;
+  R.comp = nullptr;  // noalloc_epilogue computes the compensator
   R.partials = (double *)(base + kOffPartials);
   R.block_part = (double *)(base + kOffBlockPart);
   R.ticket = (unsigned *)(base + kOffHeader + 256);
@@ -235,8 +220,7 @@ extern "C" int hawkes_loglik_noalloc(const float *x, const float *y, const float
 
   // the work counter and the epilogue ticket must start at zero on every call
   if (cudaMemsetAsync(base + kOffHeader, 0, 1024, s) != cudaSuccess) return HAWKES_E_CUDA;
-  noalloc_prep<<<std::min(d->sms * 4, (npad + 255) / 256 + 1), 256, 0, s>>>(x, y, t, (int)n, npad, nrt, nct,
-                                                                            chunks, base);
+  noalloc_prep<<<std::min(d->sms * 4, (npad + 255) / 256 + 1), 256, 0, s>>>(x, y, t, (int)n, npad, base);
   if (cudaGetLastError() != cudaSuccess) return HAWKES_E_CUDA;
   b.req[0].item_begin = 0;
   b.req[0].epi_begin = 0;

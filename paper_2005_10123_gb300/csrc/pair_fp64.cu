@@ -6,17 +6,24 @@
 //
 // epilogue_kernel turns each row's sums into (Section 2.1)
 //   lambda_n = A S_b + C S_s,  A = mu0 / ((2 pi)^{3/2} tau_x^2 tau_t),  C = theta omega / (2 pi h^2)
-//   Lambda_n = mu0 (Phi((t_N - t_n)/tau_t) - Phi(-t_n/tau_t)) + theta (1 - exp(-omega (t_N - t_n)))
 //   ell_n    = log lambda_n - Lambda_n
 // plus the gradient terms (d lambda_n / d Theta) / lambda_n - d Lambda_n / d Theta, and
 // reduces them over n in a fixed order: a warp-shuffle tree and an in-order warp sum
-// per block, then the last block to finish sums the block partials in block order.
+// per block, then the last block to finish sums the block partials in block order and
+// subtracts the compensator sums Lambda = sum_n Lambda_n (and its gradient) that slice 0 of
+// each row tile formed in the pair kernel, in row-tile order, where its float64 work
+// overlaps the float32 pair work of other CTAs.
 #include "hk_internal.h"
 
 namespace hk {
 namespace {
 
 constexpr double kPadTime = 1.0e150;  // time of a padded event: dt^2 = 1e300 stays finite
+// Each thread holds 4 rows; a CTA covers the row tile with kRowTile / 4 threads and each
+// warp owns 128 consecutive rows.
+constexpr int kRows64 = 4;
+constexpr int kThreads64 = kRowTile / kRows64;
+constexpr int kWarpRows64 = 32 * kRows64;
 
 template <int KIND, bool GRAD>
 __device__ __forceinline__ void tile_pass64(const double *__restrict__ sx, const double *__restrict__ sy,
@@ -61,7 +68,7 @@ __device__ void run_piece64(const Request &R, int4 piece, int slot, double (*sx)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int row0 = piece.x * kRowTile;
   const int n = S.n;
-  const int wa = row0 + warp * kWarpRows, wb = wa + kWarpRows - 1;
+  const int wa = row0 + warp * kWarpRows64, wb = wa + kWarpRows64 - 1;
   const int lo_wa = S.lo64[wa], lo_wb = S.lo64[wb];
   const bool excl = (R.flags & 1) != 0;
   const double da = R.da, db = R.db, dc = R.dc, omega = R.omega;
@@ -83,17 +90,18 @@ __device__ void run_piece64(const Request &R, int4 piece, int slot, double (*sx)
     for (int k = 0; k < 4; ++k) acc[s][k] = 0.0;
 
   auto stage = [&](int ct, int buf) {
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int jj = threadIdx.x + h * kThreads, j = ct * kColTile + jj;
+    for (int jj = threadIdx.x; jj < kColTile; jj += kThreads64) {
+      const int j = ct * kColTile + jj;
       sx[buf][jj] = S.x64[j];
       sy[buf][jj] = S.y64[j];
       st[buf][jj] = j < n ? S.t64[j] : kPadTime;
     }
   };
   int ct = piece.y;
-  stage(ct, 0);
-  __syncthreads();
+  if (ct < piece.z) {  // an empty slice of the window writes zero partial sums
+    stage(ct, 0);
+    __syncthreads();
+  }
   for (int k = 0; ct < piece.z; ++ct, ++k) {
     const int buf = k & 1;
     const int c0 = ct * kColTile, c1 = c0 + kColTile;
@@ -112,31 +120,38 @@ __device__ void run_piece64(const Request &R, int4 piece, int slot, double (*sx)
   double *dst = R.partials + (size_t)slot * NS * kRowTile;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    const int li = warp * kWarpRows + lane + 32 * k;
+    const int li = warp * kWarpRows64 + lane + 32 * k;
 #pragma unroll
     for (int s = 0; s < NS; ++s) dst[s * kRowTile + li] = acc[s][k];
   }
 }
 
 template <bool GRAD>
-__global__ void __launch_bounds__(kThreads) pair_fp64_kernel(const __grid_constant__ Batch B) {
+__global__ void __launch_bounds__(kThreads64) pair_fp64_kernel(const __grid_constant__ Batch B) {
   __shared__ double sx[2][kColTile], sy[2][kColTile], st[2][kColTile];
   __shared__ int s_item;
+  __shared__ int2 s_win;
   for (;;) {
     if (threadIdx.x == 0) s_item = (int)atomicAdd(B.counter, 1u);
     __syncthreads();
     const int item = s_item;
-    __syncthreads();
     if (item >= B.total_items) break;
     const Request &R = B.req[find_request(B, item, false)];
-    const int range = item - R.item_begin;
-    const int p0 = R.sched.range_first[range], p1 = R.sched.range_first[range + 1];
-    for (int pc = p0; pc < p1; ++pc) run_piece64<GRAD>(R, R.sched.pieces[pc], pc, sx, sy, st);
+    const int local = item - R.item_begin;
+    const int rt = local / R.slices, sl = local - rt * R.slices;
+    if (threadIdx.x < 32) {
+      const int2 w = column_window(R, R.set.t64, rt);
+      if (threadIdx.x == 0) s_win = w;
+    }
+    __syncthreads();
+    const int2 w = s_win;
+    const int width = w.y - w.x;
+    const int c_begin = w.x + (int)((long long)width * sl / R.slices);
+    const int c_end = w.x + (int)((long long)width * (sl + 1) / R.slices);
+    run_piece64<GRAD>(R, make_int4(rt, c_begin, c_end, 0), local, sx, sy, st);
+    if (sl == 0 && R.comp) compensator_tile(R, R.set.t64, rt, GRAD);
+    __syncthreads();  // s_item, s_win and the staging buffers are reused by the next item
   }
-}
-
-__device__ __forceinline__ double std_normal_pdf(double u) {
-  return exp(-0.5 * u * u) * 0.39894228040143267794;  // 1 / sqrt(2 pi)
 }
 
 template <bool GRAD>
@@ -153,6 +168,7 @@ __global__ void __launch_bounds__(kEpiThreads) epilogue_kernel(const __grid_cons
     const int blk = item - R.epi_begin;
     const int nblk = (S.n + kEpiThreads - 1) / kEpiThreads;
     const int i = blk * kEpiThreads + tid;
+    const bool own_comp = R.comp == nullptr;  // compensator not summed by the pair kernel
     double v[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) v[q] = 0.0;
@@ -161,7 +177,7 @@ __global__ void __launch_bounds__(kEpiThreads) epilogue_kernel(const __grid_cons
       double sums[NS];
 #pragma unroll
       for (int s = 0; s < NS; ++s) sums[s] = 0.0;
-      const int k0 = R.sched.slot_first[rt], k1 = R.sched.slot_first[rt + 1];
+      const int k0 = rt * R.slices, k1 = k0 + R.slices;
       for (int k = k0; k < k1; ++k) {
         const double *src = R.partials + (size_t)k * NS * kRowTile + li;
 #pragma unroll
@@ -175,22 +191,32 @@ __global__ void __launch_bounds__(kEpiThreads) epilogue_kernel(const __grid_cons
       const double mu = A * sums[0], xi = C * sums[1], lam = mu + xi;
       if (R.mu_out) R.mu_out[i] = mu;
       if (R.xi_out) R.xi_out[i] = xi;
-      const double tn = B.mode == 1 ? (double)S.t32[i] : S.t64[i];
-      const double a = (R.t_last - tn) / tt, b = -tn / tt, D = R.t_last - tn;
-      const double e = exp(-om * D);
-      const double Pa = normcdf(a), Pb = normcdf(b);
-      v[0] = log(lam) - (mu0 * (Pa - Pb) + th * (1.0 - e));
+      v[0] = log(lam);
       if (GRAD) {
+        // raw moments: r^2 in km^2, dt in days (the mixed kernel keeps dt in scaled units)
         const double Rb = sums[2], Tb = sums[3] * R.tscale * R.tscale;
         const double Rs = sums[4], Us = sums[5] * R.tscale;
         const double Sb = sums[0], Ss = sums[1];
         const double inv = 1.0 / lam;
-        v[1] = Ab * Sb * inv - (Pa - Pb);
+        v[1] = Ab * Sb * inv;
         v[2] = A * (-2.0 * Sb / tx + Rb / (tx * tx * tx)) * inv;
-        v[3] = A * (-Sb / tt + Tb / (tt * tt * tt)) * inv - mu0 / tt * (-a * std_normal_pdf(a) + b * std_normal_pdf(b));
-        v[4] = Cw * Ss * inv - (1.0 - e);
-        v[5] = C * (Ss / om - Us) * inv - th * D * e;
+        v[3] = A * (-Sb / tt + Tb / (tt * tt * tt)) * inv;
+        v[4] = Cw * Ss * inv;
+        v[5] = C * (Ss / om - Us) * inv;
         v[6] = C * (-2.0 * Ss / h + Rs / (h * h * h)) * inv;
+      }
+      if (own_comp) {
+        const double tn = B.mode == 1 ? (double)S.t32[i] : S.t64[i];
+        const double a = (R.t_last - tn) / tt, b = -tn / tt, D = R.t_last - tn;
+        const double e = exp(-om * D);
+        const double Pa = normcdf(a), Pb = normcdf(b);
+        v[0] -= mu0 * (Pa - Pb) + th * (1.0 - e);
+        if (GRAD) {
+          v[1] -= Pa - Pb;
+          v[3] -= mu0 / tt * (-a * std_normal_pdf(a) + b * std_normal_pdf(b));
+          v[4] -= 1.0 - e;
+          v[5] -= th * D * e;
+        }
       }
     }
     // fixed-order block reduction
@@ -217,6 +243,11 @@ __global__ void __launch_bounds__(kEpiThreads) epilogue_kernel(const __grid_cons
       if (tid < NV) {
         double x = 0.0;
         for (int bb = 0; bb < nblk; ++bb) x += __ldcg(R.block_part + (size_t)bb * 8 + tid);
+        if (!own_comp) {  // minus the compensator sums of the row tiles, in row-tile order
+          double c = 0.0;
+          for (int rt = 0; rt < S.nrt; ++rt) c += __ldcg(R.comp + (size_t)rt * 8 + tid);
+          x -= c;
+        }
         R.out[tid] = x;
       }
       if (tid == 0) *R.ticket = 0u;
@@ -228,8 +259,8 @@ __global__ void __launch_bounds__(kEpiThreads) epilogue_kernel(const __grid_cons
 }  // namespace
 
 cudaError_t launch_pair_fp64(const Batch &b, bool grad, int grid, cudaStream_t s) {
-  if (grad) pair_fp64_kernel<true><<<grid, kThreads, 0, s>>>(b);
-  else pair_fp64_kernel<false><<<grid, kThreads, 0, s>>>(b);
+  if (grad) pair_fp64_kernel<true><<<grid, kThreads64, 0, s>>>(b);
+  else pair_fp64_kernel<false><<<grid, kThreads64, 0, s>>>(b);
   return cudaGetLastError();
 }
 
@@ -241,8 +272,8 @@ cudaError_t launch_epilogue(const Batch &b, bool grad, int grid, cudaStream_t s)
 
 int occupancy_pair_fp64(bool grad) {
   int n = 0;
-  if (grad) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_fp64_kernel<true>, kThreads, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_fp64_kernel<false>, kThreads, 0);
+  if (grad) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_fp64_kernel<true>, kThreads64, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_fp64_kernel<false>, kThreads64, 0);
   return n;
 }
 

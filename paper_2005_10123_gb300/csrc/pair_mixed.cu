@@ -1,24 +1,50 @@
 // Mixed-precision pair kernel: float32 pair terms, float32 accumulation over one
 // 256-column tile, float64 accumulation across tiles.
 //
-// For every row (event n) of its row tile the kernel forms, over the columns n' of
-// its work range (Section 2.1, Eq. 1 inner sum; gradient moments added here):
-//   S_b = sum_n'          e_b,  e_b = exp(-r^2/(2 tau_x^2) - dt^2/(2 tau_t^2))
-//   S_s = sum_{t_n' < t_n} e_s,  e_s = exp(-omega dt - r^2/(2 h^2))
+// For every row (event n) of its row tile the kernel forms, over the columns n' of its
+// work range (Section 2.1, Eq. 1 inner sum; the gradient moments are added here):
+//   S_b = sum_n'           e_b,   e_b = exp(-r^2/(2 tau_x^2) - dt^2/(2 tau_t^2))
+//   S_s = sum_{t_n' < t_n} e_s,   e_s = exp(-omega dt - r^2/(2 h^2))
 //   R_b = sum r^2 e_b,  T_b = sum dt'^2 e_b,  R_s = sum r^2 e_s,  U_s = sum dt' e_s
-// with r^2 = |x_n - x_n'|^2, dt = t_n - t_n' and dt' = beta dt (beta^2 = log2(e)/(2 tau_t^2)).
+// with r^2 = |x_n - x_n'|^2 from exact float32 differences of the stored coordinates, and
+// dt' = beta (t_n - t_n'), beta^2 = log2(e)/(2 tau_t^2); times enter relative to the first
+// row of the tile before scaling, so nearby time differences keep full relative precision.
 // The epilogue kernel turns the row sums into lambda_n, log lambda_n and the gradient.
 //
-// Arithmetic per (row, column) pair, two rows per packed f32x2 instruction:
-//   dx, dy exact differences of the stored float32 coordinates; r^2 = dx^2 + dy^2;
-//   dt' = T_n - t'_n' where both times are taken relative to the first row of the
-//   tile before scaling, so nearby times keep full relative precision;
-//   e_b = 2^-(a2 r^2 + dt'^2),  e_s = 2^(cn r^2 + wn dt')  (ex2.approx.ftz).
+// Arithmetic per (row, column) pair, two rows per packed f32x2 value:
+//   e_b = 2^-q with q = a2 r^2 + dt'^2, a2 = log2(e)/(2 tau_x^2);
+//   e_s = 2^(cn r^2 + wn dt'), cn = -log2(e)/(2 h^2), wn = -omega log2(e)/beta.
+// In tiles where every pair is causal the trigger factor 2^(wn dt') splits into a column
+// factor 2^(wn (t'_ref - t'_n')) folded into the exponent at staging and a row factor
+// 2^(wn (t'_n - t'_ref)) applied to the tile's trigger sums, with t'_ref the tile's latest
+// column time (both factors <= 1).
 // The causal indicator t_n' < t_n is tested on stored times through lo[n] (the first
 // index whose stored time equals t_n): for sorted times, t_n' < t_n  <=>  n' < lo[n].
-// Column tiles entirely before a warp's rows skip the test, tiles entirely after skip
-// the trigger term; only tiles straddling the rows test pair by pair.
+// Column tiles entirely before a warp's rows skip the test, tiles entirely after skip the
+// trigger term; only tiles straddling the rows test pair by pair.
+//
+// The HK_PACK_* switches choose, per operation kind, packed f32x2 instructions or two
+// scalar ones (same rounding either way: each is one IEEE round-to-nearest operation).
 #include "hk_internal.h"
+
+#ifndef HK_MIN_CTAS
+#define HK_MIN_CTAS 4
+#endif
+#ifndef HK_COL_UNROLL
+#define HK_COL_UNROLL 4
+#endif
+#ifndef HK_PACK_ADD
+#define HK_PACK_ADD 1  // differences dx, dy, dt
+#endif
+#ifndef HK_PACK_MUL
+#define HK_PACK_MUL 1
+#endif
+#ifndef HK_PACK_FMA
+#define HK_PACK_FMA 1
+#endif
+#ifndef HK_PACK_ACC
+#define HK_PACK_ACC 1  // accumulation of the exponentials
+#endif
 
 namespace hk {
 namespace {
@@ -31,56 +57,98 @@ __device__ __forceinline__ float ex2(float x) {
   return y;
 }
 
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+#if HK_PACK_ADD
+  return __fadd2_rn(a, b);
+#else
+  return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y));
+#endif
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+#if HK_PACK_MUL
+  return __fmul2_rn(a, b);
+#else
+  return make_float2(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y));
+#endif
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+#if HK_PACK_FMA
+  return __ffma2_rn(a, b, c);
+#else
+  return make_float2(__fmaf_rn(a.x, b.x, c.x), __fmaf_rn(a.y, b.y, c.y));
+#endif
+}
+__device__ __forceinline__ float2 acc2(float2 s, float2 e) {
+#if HK_PACK_ACC
+  return __fadd2_rn(s, e);
+#else
+  return make_float2(__fadd_rn(s.x, e.x), __fadd_rn(s.y, e.y));
+#endif
+}
+__device__ __forceinline__ float2 accfma2(float2 a, float2 e, float2 s) {
+#if HK_PACK_ACC
+  return __ffma2_rn(a, e, s);
+#else
+  return make_float2(__fmaf_rn(a.x, e.x, s.x), __fmaf_rn(a.y, e.y, s.y));
+#endif
+}
+
+constexpr int kPairs = kRowsPerThread / 2;  // packed row pairs per thread
+constexpr int kColUnroll = HK_COL_UNROLL;
+
 template <int NS>
 struct Acc32 {
-  float2 v[NS][kRowsPerThread / 2];
+  float2 v[NS][kPairs];
 };
 
-// One column tile against this thread's rows. KIND 0: no causal pair in the tile for
-// this warp; 1: every pair causal; 2: test each pair (and mask n' = n if excluding self).
+// One column tile against this thread's rows. KIND 0: no causal pair in the tile for this
+// warp; 1: every pair causal (separable trigger factor); 2: test each pair (and mask
+// n' = n when excluding self).
 template <int KIND, bool GRAD>
-__device__ __forceinline__ void tile_pass(const float4 *__restrict__ sxy, const float2 *__restrict__ st,
-                                          const float2 (&X)[2], const float2 (&Y)[2], const float2 (&T)[2],
-                                          const int (&LO)[4], int row_a0, int c0, bool excl, float2 A2,
-                                          float2 WN, float2 CN, Acc32<GRAD ? kSumsGrad : kSumsLoglik> &acc) {
-#pragma unroll 4
+__device__ __forceinline__ void tile_pass(const float4 *__restrict__ sxy, const float4 *__restrict__ stb,
+                                          const float2 (&X)[kPairs], const float2 (&Y)[kPairs],
+                                          const float2 (&T)[kPairs], const int (&LO)[kRowsPerThread], int row_a0,
+                                          int c0, bool excl, float2 A2, float2 CN,
+                                          float2 WN, Acc32<GRAD ? kSumsGrad : kSumsLoglik> &acc) {
+#pragma unroll kColUnroll
   for (int j = 0; j < kColTile; ++j) {
-    const float4 c = sxy[j];   // {-x, -x, -y, -y}
-    const float2 ctn = st[j];  // {-t', -t'}
+    const float4 c = sxy[j];  // {-x, -x, -y, -y}
+    const float4 d = stb[j];  // {-t', -t', b, b}, b = wn (t'_ref - t')
     const float2 cx = make_float2(c.x, c.y), cy = make_float2(c.z, c.w);
+    const float2 ct = make_float2(d.x, d.y), bj = make_float2(d.z, d.w);
     const int col = c0 + j;
 #pragma unroll
-    for (int p = 0; p < 2; ++p) {
-      const float2 dx = __fadd2_rn(X[p], cx);
-      const float2 dy = __fadd2_rn(Y[p], cy);
-      float2 rho = __fmul2_rn(dx, dx);
-      rho = __ffma2_rn(dy, dy, rho);
-      const float2 dt = __fadd2_rn(T[p], ctn);
-      const float2 u = __fmul2_rn(dt, dt);
-      const float2 q = __ffma2_rn(rho, A2, u);
+    for (int p = 0; p < kPairs; ++p) {
+      const float2 dx = add2(X[p], cx);
+      const float2 dy = add2(Y[p], cy);
+      const float2 rho = fma2(dy, dy, mul2(dx, dx));
+      const float2 dt = add2(T[p], ct);
+      const float2 u = mul2(dt, dt);
+      const float2 q = fma2(rho, A2, u);
       float2 eb = make_float2(ex2(-q.x), ex2(-q.y));
       if (KIND == 2 && excl) {
         const int ra = row_a0 + 64 * p;
         if (col == ra) eb.x = 0.f;
         if (col == ra + 32) eb.y = 0.f;
       }
-      acc.v[0][p] = __fadd2_rn(acc.v[0][p], eb);
+      acc.v[0][p] = acc2(acc.v[0][p], eb);
       if (GRAD) {
-        acc.v[2][p] = __ffma2_rn(rho, eb, acc.v[2][p]);
-        acc.v[3][p] = __ffma2_rn(u, eb, acc.v[3][p]);
+        acc.v[2][p] = accfma2(rho, eb, acc.v[2][p]);
+        acc.v[3][p] = accfma2(u, eb, acc.v[3][p]);
       }
       if (KIND != 0) {
-        const float2 v = __fmul2_rn(dt, WN);
-        const float2 arg = __ffma2_rn(rho, CN, v);
+        float2 arg;
+        if (KIND == 1) arg = fma2(rho, CN, bj);
+        else arg = fma2(rho, CN, mul2(dt, WN));
         float2 es = make_float2(ex2(arg.x), ex2(arg.y));
         if (KIND == 2) {
           es.x = (col < LO[2 * p]) ? es.x : 0.f;
           es.y = (col < LO[2 * p + 1]) ? es.y : 0.f;
         }
-        acc.v[1][p] = __fadd2_rn(acc.v[1][p], es);
+        acc.v[1][p] = acc2(acc.v[1][p], es);
         if (GRAD) {
-          acc.v[4][p] = __ffma2_rn(rho, es, acc.v[4][p]);
-          acc.v[5][p] = __ffma2_rn(dt, es, acc.v[5][p]);
+          acc.v[4][p] = accfma2(rho, es, acc.v[4][p]);
+          acc.v[5][p] = accfma2(dt, es, acc.v[5][p]);
         }
       }
     }
@@ -88,46 +156,50 @@ __device__ __forceinline__ void tile_pass(const float4 *__restrict__ sxy, const 
 }
 
 struct RawCols {
-  float x0, y0, t0, x1, y1, t1;
+  float x0, y0, t0, x1, y1, t1, tref;
 };
 
 __device__ __forceinline__ RawCols load_cols(const SetView &S, int ct, int tid) {
   const int j0 = ct * kColTile + tid, j1 = j0 + kThreads;
+  const int last = min((ct + 1) * kColTile, S.n) - 1;  // latest real column of the tile
   RawCols r;
   r.x0 = __ldg(S.x32 + j0); r.y0 = __ldg(S.y32 + j0); r.t0 = __ldg(S.t32 + j0);
   r.x1 = __ldg(S.x32 + j1); r.y1 = __ldg(S.y32 + j1); r.t1 = __ldg(S.t32 + j1);
+  r.tref = __ldg(S.t32 + max(last, 0));
   return r;
 }
 
-__device__ __forceinline__ void store_cols(const RawCols &r, int ct, int tid, int n, float t_origin,
-                                           float beta, float4 *sxy, float2 *st) {
+__device__ __forceinline__ void store_cols(const RawCols &r, int ct, int tid, int n, float t_origin, float beta,
+                                           float wn, float4 *sxy, float4 *stb) {
   const int j0 = ct * kColTile + tid, j1 = j0 + kThreads;
   const float s0 = j0 < n ? (r.t0 - t_origin) * beta : kPadScaled;
   const float s1 = j1 < n ? (r.t1 - t_origin) * beta : kPadScaled;
+  const float sref = (r.tref - t_origin) * beta;
+  const float b0 = wn * (sref - s0), b1 = wn * (sref - s1);
   sxy[tid] = make_float4(-r.x0, -r.x0, -r.y0, -r.y0);
-  st[tid] = make_float2(-s0, -s0);
+  stb[tid] = make_float4(-s0, -s0, b0, b0);
   sxy[tid + kThreads] = make_float4(-r.x1, -r.x1, -r.y1, -r.y1);
-  st[tid + kThreads] = make_float2(-s1, -s1);
+  stb[tid + kThreads] = make_float4(-s1, -s1, b1, b1);
 }
 
 template <bool GRAD>
 __device__ void run_piece(const Request &R, int4 piece, int slot, float4 (*sxy)[kColTile],
-                          float2 (*st)[kColTile]) {
+                          float4 (*stb)[kColTile], double *sacc) {
   constexpr int NS = GRAD ? kSumsGrad : kSumsLoglik;
   const SetView &S = R.set;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int row0 = piece.x * kRowTile;
   const float t_origin = S.t32[row0];
-  const float beta = R.beta;
+  const float beta = R.beta, wn = R.wn;
   const int n = S.n;
   const int wa = row0 + warp * kWarpRows, wb = wa + kWarpRows - 1;
   const int lo_wa = S.lo32[wa], lo_wb = S.lo32[wb];
   const bool excl = (R.flags & 1) != 0;
 
-  float2 X[2], Y[2], T[2];
-  int LO[4];
+  float2 X[kPairs], Y[kPairs], T[kPairs];
+  int LO[kRowsPerThread];
 #pragma unroll
-  for (int p = 0; p < 2; ++p) {
+  for (int p = 0; p < kPairs; ++p) {
     const int ra = wa + lane + 64 * p, rb = ra + 32;
     X[p] = make_float2(S.x32[ra], S.x32[rb]);
     Y[p] = make_float2(S.y32[ra], S.y32[rb]);
@@ -136,17 +208,19 @@ __device__ void run_piece(const Request &R, int4 piece, int slot, float4 (*sxy)[
     LO[2 * p] = S.lo32[ra];
     LO[2 * p + 1] = S.lo32[rb];
   }
-  const float2 A2 = make_float2(R.a2, R.a2), WN = make_float2(R.wn, R.wn), CN = make_float2(R.cn, R.cn);
+  const float2 A2 = make_float2(R.a2, R.a2), CN = make_float2(R.cn, R.cn), WN = make_float2(wn, wn);
 
-  double acc64[NS][kRowsPerThread];
+  // float64 row accumulators live in shared memory, one slot per (sum, row, thread)
 #pragma unroll
   for (int s = 0; s < NS; ++s)
 #pragma unroll
-    for (int k = 0; k < kRowsPerThread; ++k) acc64[s][k] = 0.0;
+    for (int k = 0; k < kRowsPerThread; ++k) sacc[(s * kRowsPerThread + k) * kThreads + tid] = 0.0;
 
   int ct = piece.y;
-  store_cols(load_cols(S, ct, tid), ct, tid, n, t_origin, beta, sxy[0], st[0]);
-  __syncthreads();
+  if (ct < piece.z) {  // an empty slice of the window writes zero partial sums
+    store_cols(load_cols(S, ct, tid), ct, tid, n, t_origin, beta, wn, sxy[0], stb[0]);
+    __syncthreads();
+  }
   for (int k = 0; ct < piece.z; ++ct, ++k) {
     const int buf = k & 1;
     const bool has_next = ct + 1 < piece.z;
@@ -157,51 +231,80 @@ __device__ void run_piece(const Request &R, int4 piece, int slot, float4 (*sxy)[
     if (excl && c0 <= wb && c1 > wa) kind = 2;
     Acc32<NS> acc;
 #pragma unroll
-    for (int s = 0; s < NS; ++s) acc.v[s][0] = acc.v[s][1] = make_float2(0.f, 0.f);
+    for (int s = 0; s < NS; ++s)
+#pragma unroll
+      for (int p = 0; p < kPairs; ++p) acc.v[s][p] = make_float2(0.f, 0.f);
     const int row_a0 = wa + lane;
-    if (kind == 0)
-      tile_pass<0, GRAD>(sxy[buf], st[buf], X, Y, T, LO, row_a0, c0, excl, A2, WN, CN, acc);
-    else if (kind == 1)
-      tile_pass<1, GRAD>(sxy[buf], st[buf], X, Y, T, LO, row_a0, c0, excl, A2, WN, CN, acc);
-    else
-      tile_pass<2, GRAD>(sxy[buf], st[buf], X, Y, T, LO, row_a0, c0, excl, A2, WN, CN, acc);
+    if (kind == 0) {
+      tile_pass<0, GRAD>(sxy[buf], stb[buf], X, Y, T, LO, row_a0, c0, excl, A2, CN, WN, acc);
+    } else if (kind == 1) {
+      tile_pass<1, GRAD>(sxy[buf], stb[buf], X, Y, T, LO, row_a0, c0, excl, A2, CN, WN, acc);
+      // row factor 2^(wn (t'_n - t'_ref)) of the separable trigger term
+      const float sref = -stb[buf][kColTile - 1].x;
+      const float2 sr = make_float2(-sref, -sref);
+#pragma unroll
+      for (int p = 0; p < kPairs; ++p) {
+        const float2 w = __fmul2_rn(__fadd2_rn(T[p], sr), WN);
+        const float2 a = make_float2(ex2(w.x), ex2(w.y));
+        acc.v[1][p] = __fmul2_rn(acc.v[1][p], a);
+        if (GRAD) {
+          acc.v[4][p] = __fmul2_rn(acc.v[4][p], a);
+          acc.v[5][p] = __fmul2_rn(acc.v[5][p], a);
+        }
+      }
+    } else {
+      tile_pass<2, GRAD>(sxy[buf], stb[buf], X, Y, T, LO, row_a0, c0, excl, A2, CN, WN, acc);
+    }
 #pragma unroll
     for (int s = 0; s < NS; ++s)
 #pragma unroll
-      for (int p = 0; p < 2; ++p) {
-        acc64[s][2 * p] += (double)acc.v[s][p].x;
-        acc64[s][2 * p + 1] += (double)acc.v[s][p].y;
+      for (int p = 0; p < kPairs; ++p) {
+        sacc[(s * kRowsPerThread + 2 * p) * kThreads + tid] += (double)acc.v[s][p].x;
+        sacc[(s * kRowsPerThread + 2 * p + 1) * kThreads + tid] += (double)acc.v[s][p].y;
       }
-    if (has_next) store_cols(nxt, ct + 1, tid, n, t_origin, beta, sxy[buf ^ 1], st[buf ^ 1]);
+    if (has_next) store_cols(nxt, ct + 1, tid, n, t_origin, beta, wn, sxy[buf ^ 1], stb[buf ^ 1]);
     __syncthreads();
   }
   double *dst = R.partials + (size_t)slot * NS * kRowTile;
 #pragma unroll
-  for (int p = 0; p < 2; ++p) {
+  for (int p = 0; p < kPairs; ++p) {
     const int la = warp * kWarpRows + lane + 64 * p;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-      dst[s * kRowTile + la] = acc64[s][2 * p];
-      dst[s * kRowTile + la + 32] = acc64[s][2 * p + 1];
+      dst[s * kRowTile + la] = sacc[(s * kRowsPerThread + 2 * p) * kThreads + tid];
+      dst[s * kRowTile + la + 32] = sacc[(s * kRowsPerThread + 2 * p + 1) * kThreads + tid];
     }
   }
 }
 
 template <bool GRAD>
-__global__ void __launch_bounds__(kThreads, 4) pair_mixed_kernel(const __grid_constant__ Batch B) {
+__global__ void __launch_bounds__(kThreads, HK_MIN_CTAS) pair_mixed_kernel(const __grid_constant__ Batch B) {
+  constexpr int NS = GRAD ? kSumsGrad : kSumsLoglik;
   __shared__ __align__(16) float4 sxy[2][kColTile];
-  __shared__ __align__(16) float2 st[2][kColTile];
+  __shared__ __align__(16) float4 stb[2][kColTile];
+  __shared__ double sacc[NS * kRowsPerThread * kThreads];
   __shared__ int s_item;
+  __shared__ int2 s_win;
   for (;;) {
     if (threadIdx.x == 0) s_item = (int)atomicAdd(B.counter, 1u);
     __syncthreads();
     const int item = s_item;
-    __syncthreads();
     if (item >= B.total_items) break;
     const Request &R = B.req[find_request(B, item, false)];
-    const int range = item - R.item_begin;
-    const int p0 = R.sched.range_first[range], p1 = R.sched.range_first[range + 1];
-    for (int pc = p0; pc < p1; ++pc) run_piece<GRAD>(R, R.sched.pieces[pc], pc, sxy, st);
+    const int local = item - R.item_begin;
+    const int rt = local / R.slices, sl = local - rt * R.slices;
+    if (threadIdx.x < 32) {
+      const int2 w = column_window(R, R.set.t32, rt);
+      if (threadIdx.x == 0) s_win = w;
+    }
+    __syncthreads();
+    const int2 w = s_win;
+    const int width = w.y - w.x;
+    const int c_begin = w.x + (int)((long long)width * sl / R.slices);
+    const int c_end = w.x + (int)((long long)width * (sl + 1) / R.slices);
+    run_piece<GRAD>(R, make_int4(rt, c_begin, c_end, 0), local, sxy, stb, sacc);
+    if (sl == 0 && R.comp) compensator_tile(R, R.set.t32, rt, GRAD);
+    __syncthreads();  // s_item, s_win and the staging buffers are reused by the next item
   }
 }
 

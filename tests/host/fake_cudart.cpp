@@ -3,8 +3,8 @@
 // Test infrastructure only. The library's host runtime (api.cu, compiled here as plain
 // C++) is linked against this file instead of libcudart: "device" memory is host memory,
 // streams and events are counters, and the kernel launchers are replaced by stubs that
-// (1) check the work schedule of every request (each (row tile, column tile) unit of the
-// set covered exactly once, pieces inside their ranges, partial-sum slots consistent) and
+// (1) check the work decomposition of every request (item counts, slices, window cut-offs,
+// workspace pointers) and
 // (2) write a recognisable value per request into its output so the tests can check that
 // results reach the right ticket. No likelihood arithmetic happens here.
 //
@@ -108,24 +108,13 @@ cudaError_t cudaEventQuery(cudaEvent_t e) {
 
 namespace hk {
 
-// Check one request's schedule against its set.
+// Check one request's work decomposition against its set.
 static void check_schedule(const Request &R) {
   const SetView &S = R.set;
-  const Schedule &D = R.sched;
-  std::vector<int> cover((size_t)S.nrt * S.nct, 0);
-  bool ok = D.nranges >= 1 && D.range_first[0] == 0 && D.range_first[D.nranges] == D.npieces;
-  for (int r = 0; ok && r < D.nranges; ++r) {
-    if (D.range_first[r] >= D.range_first[r + 1]) ok = false;  // every range has a piece
-    for (int pc = D.range_first[r]; ok && pc < D.range_first[r + 1]; ++pc) {
-      const int4 p = D.pieces[pc];
-      if (p.x < 0 || p.x >= S.nrt || p.y < 0 || p.y >= p.z || p.z > S.nct) { ok = false; break; }
-      if (pc < D.slot_first[p.x] || pc >= D.slot_first[p.x + 1]) ok = false;  // slot of its row tile
-      for (int ct = p.y; ct < p.z; ++ct) cover[(size_t)p.x * S.nct + ct]++;
-    }
-  }
-  for (int c : cover) if (c != 1) ok = false;
-  if (D.slot_first[0] != 0 || D.slot_first[S.nrt] != D.npieces) ok = false;
-  if (S.npad != S.nrt * kRowTile || S.nct * kColTile != S.npad || S.n > S.npad) ok = false;
+  bool ok = R.slices >= 1 && R.slices <= S.nct;
+  if (S.npad != S.nrt * kRowTile || S.nct * kColTile != S.npad || S.n > S.npad || S.n < 1) ok = false;
+  if (!(R.cut_early > 0.0) || !(R.cut_late > 0.0)) ok = false;
+  if (!R.partials || !R.comp || !R.block_part || !R.ticket || !R.out) ok = false;
   if (!ok) g_schedule_errors++;
 }
 
@@ -134,7 +123,7 @@ static cudaError_t fake_pair(const Batch &b) {
   int items = 0;
   for (int r = 0; r < b.nreq; ++r) {
     if (b.req[r].item_begin != items) g_schedule_errors++;
-    items += b.req[r].sched.nranges;
+    items += b.req[r].set.nrt * b.req[r].slices;
     check_schedule(b.req[r]);
   }
   if (items != b.total_items || *b.counter != 0u) g_schedule_errors++;

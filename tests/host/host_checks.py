@@ -67,6 +67,16 @@ def main():
     for k in range(64):
         assert ll[k] == fake_value(ths[k], 20000, 1) and np.array_equal(g[k], ths[k])
     expect_status(lambda: ctx.hawkes_loglik_batch(sids[20000], np.tile(ths, (2, 1)), 1), -1)  # K > 64
+    # work accounting: the exact-zero window visits a subset of the N^2 pairs; dense visits all
+    for n in (1, 513, 20000, 85000):
+        for mode in (0, 1):
+            v, a = ctx.hawkes_pair_work(sids[n], TH, mode)
+            assert a == n * n and 0 < v <= a, (n, mode, v, a)
+    v85, _ = ctx.hawkes_pair_work(sids[85000], TH, 1)
+    assert v85 < 0.5 * 85000 ** 2  # T = 5,000 days >> the 400-day background reach at tau_t = 30
+    ctx.hawkes_set_flags(2)
+    assert ctx.hawkes_pair_work(sids[85000], TH, 1)[0] == 85000 ** 2
+    ctx.hawkes_set_flags(0)
     mu, xi, _ = ctx.hawkes_event_terms(sids[1000], TH, 1)
     assert np.array_equal(mu, np.arange(1000)) and np.array_equal(xi, -np.arange(1000))
     # invalid parameters, unknown set

@@ -99,6 +99,26 @@ def test_event_terms_rows(ctx, mode):
     assert np.all((pi >= 0) & (pi <= 1))
 
 
+@pytest.mark.parametrize("mode", [0, 1], ids=["fp64", "mixed"])
+def test_exact_zero_window_matches_dense(ctx, mode):
+    """Skipping the columns whose pair terms are exactly zero at the working precision changes
+    nothing but the grouping of the float64 partial sums."""
+    from paper_2005_10123_gb300 import binding
+    ev = synth.simulate(20000, 5000.0, seed=71)  # long time span: most column tiles skipped
+    sid = ctx.hawkes_upload_events(ev.x, ev.y, ev.t)
+    try:
+        for th in [TH0, (0.02, 0.5, 5.0, 0.6, 3.0, 0.05), (0.01, 2.0, 300.0, 0.4, 0.05, 0.3)]:
+            ctx.hawkes_set_flags(0)
+            a, ga = ctx.hawkes_loglik_grad(sid, th, mode)
+            ctx.hawkes_set_flags(binding.HAWKES_FLAG_DENSE)
+            b, gb = ctx.hawkes_loglik_grad(sid, th, mode)
+            assert rel(a, b) <= 1e-14, (th, a, b)
+            assert grad_err(ga, gb) <= 1e-13, (th, ga, gb)
+    finally:
+        ctx.hawkes_set_flags(0)
+        ctx.hawkes_release_events(sid)
+
+
 def test_repeatable_bitwise(ctx):
     ev = synth.simulate(5000, 1500.0, seed=3)
     sid = ctx.hawkes_upload_events(ev.x, ev.y, ev.t)
