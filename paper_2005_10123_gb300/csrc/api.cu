@@ -155,7 +155,10 @@ std::vector<int> tie_starts(const std::vector<F> &t, int64_t n, int64_t npad) {
 
 // Slices per row tile for a kernel kind: enough items for about kItemsPerSlot items per
 // resident CTA, at most one column tile per slice.
-constexpr int kItemsPerSlot = 2;
+#ifndef HK_ITEMS_PER_SLOT
+#define HK_ITEMS_PER_SLOT 4
+#endif
+constexpr int kItemsPerSlot = HK_ITEMS_PER_SLOT;
 int slices_for(int nrt, int nct, int resident_ctas) {
   const int want = (kItemsPerSlot * resident_ctas + nrt - 1) / nrt;
   return std::max(1, std::min(want, nct));

@@ -240,14 +240,22 @@ __global__ void __launch_bounds__(kEpiThreads) epilogue_kernel(const __grid_cons
     __syncthreads();
     if (s_last) {
       __threadfence();
+      // every thread sums a fixed strided subset of the block partials (and of the row-tile
+      // compensator sums), then a fixed-shape tree over the threads: a deterministic order
+      for (int q = 0; q < NV; ++q) {
+        double x = 0.0;
+        for (int bb = tid; bb < nblk; bb += kEpiThreads) x += __ldcg(R.block_part + (size_t)bb * 8 + q);
+        if (!own_comp)
+          for (int rt = tid; rt < S.nrt; rt += kEpiThreads) x -= __ldcg(R.comp + (size_t)rt * 8 + q);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+        if (lane == 0) red[warp][q] = x;
+      }
+      __syncthreads();
       if (tid < NV) {
         double x = 0.0;
-        for (int bb = 0; bb < nblk; ++bb) x += __ldcg(R.block_part + (size_t)bb * 8 + tid);
-        if (!own_comp) {  // minus the compensator sums of the row tiles, in row-tile order
-          double c = 0.0;
-          for (int rt = 0; rt < S.nrt; ++rt) c += __ldcg(R.comp + (size_t)rt * 8 + tid);
-          x -= c;
-        }
+#pragma unroll
+        for (int w = 0; w < NW; ++w) x += red[w][tid];
         R.out[tid] = x;
       }
       if (tid == 0) *R.ticket = 0u;

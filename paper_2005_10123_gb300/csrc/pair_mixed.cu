@@ -28,7 +28,7 @@
 #include "hk_internal.h"
 
 #ifndef HK_MIN_CTAS
-#define HK_MIN_CTAS 4
+#define HK_MIN_CTAS 5
 #endif
 #ifndef HK_COL_UNROLL
 #define HK_COL_UNROLL 4
