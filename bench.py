@@ -136,6 +136,69 @@ def cpu_baseline(ev, seconds: float = 12.0):
             "sample": f"{m} of {ev.n} rows (each row: all {ev.n} columns, loglik+grad terms), {dt:.1f} s"}
 
 
+def batched_chains(ctx, sid, n, stream):
+    """64 chains on one resident set, each a loglik+grad request at its own Theta (log-uniform
+    within +-50% of Theta0), all in one launch."""
+    import torch
+    from paper_2005_10123_gb300 import binding
+    ths = synth.theta_batch(64, seed=20053)
+    for _ in range(2):
+        ctx.hawkes_loglik_batch(sid, ths, binding.HAWKES_MIXED, want_grad=True)
+    reps = 5
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        ctx.hawkes_loglik_batch(sid, ths, binding.HAWKES_MIXED, want_grad=True)
+    dt = (time.perf_counter() - t0) / reps
+    visited = sum(ctx.hawkes_pair_work(sid, th, binding.HAWKES_MIXED)[0] for th in ths)
+    return {"chains": 64, "ms_per_launch": dt * 1e3, "value": 64 * float(n) ** 2 / dt, "unit": "pair-evals/s",
+            "pairs_visited_per_launch": visited, "note": "host-timed, results copied back each launch"}
+
+
+def mh_chain(ctx, sid, iters):
+    """Algorithm 1 over all six parameters with log-normal proposals, mixed-precision likelihood.
+    With tau_x and tau_t free the background sum must leave out n' = n: with the self term,
+    lambda_n >= mu0 / ((2 pi)^{3/2} tau_x^2 tau_t) grows without bound as the bandwidths shrink
+    (the paper fixes both bandwidths), so the chain runs with HAWKES_FLAG_EXCLUDE_SELF."""
+    from paper_2005_10123_gb300 import binding, mcmc
+
+    def loglik(th):
+        try:
+            return ctx.hawkes_loglik(sid, th, binding.HAWKES_MIXED)
+        except binding.HawkesError as e:  # a proposal outside the float32 path's range: reject it
+            if e.status == -1:
+                return -float("inf")
+            raise
+
+    ctx.hawkes_set_flags(binding.HAWKES_FLAG_EXCLUDE_SELF)
+    try:
+        ch = mcmc.AdaptiveMH(loglik, THETA0, sample=range(6), proposal="lognormal", seed=20051)
+        t0 = time.perf_counter()
+        ch.run(iters)
+        dt = time.perf_counter() - t0
+    finally:
+        ctx.hawkes_set_flags(0)
+    acc = [a / max(p, 1) for a, p in zip(ch.state.accepted, ch.state.proposed)]
+    return {"iterations": iters, "wall_s": dt, "iter_per_s": iters / dt, "acceptance": acc,
+            "final_theta": ch.state.theta, "flags": "exclude_self"}
+
+
+def serving_runs(ctx, n_requests):
+    """16 resident sets (N log-uniform in [1k, 300k]), Poisson arrivals, gradient flag p = 0.5."""
+    from paper_2005_10123_gb300 import binding, serving
+    sets = synth.serving_sets()
+    sids = [ctx.hawkes_upload_events(ev.x, ev.y, ev.t) for ev in sets]
+    sizes = [ev.n for ev in sets]
+    ths = synth.theta_batch(256, seed=20054)
+    out = {"sets": sizes}
+    for rate, nreq in ((2000.0, n_requests), (200.0, max(50, n_requests // 4))):
+        r = serving.run_open_loop(ctx, sids, sizes, ths, rate=rate, n_requests=nreq, grad_prob=0.5, seed=20054)
+        out[f"rate_{int(rate)}"] = r
+    for sid_ in sids:
+        ctx.hawkes_release_events(sid_)
+    return out
+
+
 def run_reference(args):
     rank, world, _ = _dist_env()
     if rank != 0:
@@ -266,12 +329,17 @@ def run_ours(args):
         torch.cuda.synchronize()
         ll_ms = e0.elapsed_time(e1) / 10
         extra = {
-            "fp64_path": {"value": pairs / (fp64_ms * 1e-3), "unit": "pair-evals/s", "ms_per_step": fp64_ms},
+            "fp64_path": {"value": pairs / (fp64_ms * 1e-3), "unit": "pair-evals/s", "ms_per_step": fp64_ms,
+                          "pairs_visited_per_step": ctx.hawkes_pair_work(sid, THETA0, binding.HAWKES_FP64)[0]},
             "loglik_only_mixed": {"value": pairs / (ll_ms * 1e-3), "unit": "pair-evals/s", "ms_per_step": ll_ms},
             "mixed_vs_fp64": {"rel_err_loglik": abs(ll_mixed - ll64) / abs(ll64),
                               "rel_err_grad_inf": float(np.max(np.abs(gm - g64)) / np.max(np.abs(g64)))},
             "speedup_mixed_over_fp64": fp64_ms / step_ms,
         }
+        if not args.no_extras:
+            extra["batched_chains"] = batched_chains(ctx, sid, n, stream)
+            extra["mh_chain"] = mh_chain(ctx, sid, args.mh_iters)
+            extra["serving"] = serving_runs(ctx, args.serving_requests)
 
     # end to end through the public API with host buffers: upload (H2D), evaluate, read back
     e2e_steps = max(3, min(args.steps, 10))
@@ -342,6 +410,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip batched chains, MH chain and serving")
+    ap.add_argument("--mh-iters", type=int, default=10000)
+    ap.add_argument("--serving-requests", type=int, default=1000)
     ap.add_argument("--profile", action="store_true",
                     help="run only warm-up + steps of the mixed loglik+grad call (the case profiled with ncu)")
     args = ap.parse_args()

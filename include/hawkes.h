@@ -168,6 +168,12 @@ int hawkes_submit(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *params, 
 int hawkes_poll(hawkes_ctx *ctx, uint64_t ticket, int *done_out, double *loglik_out,
                 double grad_out[6]);
 
+/* hawkes_poll plus the request's timing on the host's steady clock: queued_ns from submission
+ * to the launch that carried it, total_ns from submission to the scheduler observing its
+ * completion (either pointer may be NULL; both are written only when done_out is 1). */
+int hawkes_poll_timed(hawkes_ctx *ctx, uint64_t ticket, int *done_out, double *loglik_out,
+                      double grad_out[6], int64_t *queued_ns_out, int64_t *total_ns_out);
+
 /* Block until the request finishes or `timeout_ms` elapses (E_TIMEOUT; the ticket
  * stays valid). timeout_ms < 0 waits without limit. */
 int hawkes_wait(hawkes_ctx *ctx, uint64_t ticket, int timeout_ms, double *loglik_out,

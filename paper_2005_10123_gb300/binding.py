@@ -31,7 +31,7 @@ EXPORTS = (
     "hawkes_release_events", "hawkes_set_info", "hawkes_loglik", "hawkes_loglik_grad",
     "hawkes_loglik_async", "hawkes_loglik_batch", "hawkes_event_terms", "hawkes_submit",
     "hawkes_poll", "hawkes_wait", "hawkes_stats", "hawkes_strerror", "hawkes_last_cuda_error",
-    "hawkes_loglik_noalloc", "hawkes_pair_work",
+    "hawkes_loglik_noalloc", "hawkes_pair_work", "hawkes_poll_timed",
 )
 HAWKES_NOALLOC_MAX_EVENTS = 65536
 
@@ -89,6 +89,8 @@ def load(build_if_missing: bool = False, path: str | None = None):
         "hawkes_stats": [vp, ctypes.POINTER(i64)],
         "hawkes_loglik_noalloc": [vp, vp, vp, i64, P, ctypes.c_int, vp, vp],
         "hawkes_pair_work": [vp, i32, P, ctypes.c_int, ctypes.POINTER(i64), ctypes.POINTER(i64)],
+        "hawkes_poll_timed": [vp, u64, ctypes.POINTER(ctypes.c_int), _D, _D, ctypes.POINTER(i64),
+                              ctypes.POINTER(i64)],
     }
     for name, args in sig.items():
         if path is not None and not hasattr(lib, name):
@@ -248,6 +250,22 @@ class Context:
             return None
         self._check(rc, "hawkes_poll")
         return ll.value, g
+
+    def hawkes_poll_timed(self, ticket: int):
+        """None while pending, else (loglik, grad[6], queued_s, total_s)."""
+        done = ctypes.c_int()
+        ll = ctypes.c_double()
+        g = np.zeros(6)
+        q = ctypes.c_int64()
+        t = ctypes.c_int64()
+        rc = self.lib.hawkes_poll_timed(self.h, ctypes.c_uint64(ticket), ctypes.byref(done), ctypes.byref(ll),
+                                        g.ctypes.data_as(_D), ctypes.byref(q), ctypes.byref(t))
+        if rc == -7:
+            return None
+        if rc != 0 and done.value:
+            raise HawkesError(rc, "hawkes_poll_timed (request failed)")
+        self._check(rc, "hawkes_poll_timed")
+        return ll.value, g, q.value * 1e-9, t.value * 1e-9
 
     def hawkes_wait(self, ticket: int, timeout_ms: int = -1):
         ll = ctypes.c_double()

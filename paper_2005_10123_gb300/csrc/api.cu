@@ -67,7 +67,13 @@ struct TicketRec {
   bool done = false;
   double ll = 0, g[6] = {0, 0, 0, 0, 0, 0};
   size_t footprint = 0;
+  int64_t t_submit = 0, t_launch = 0, t_done = 0;  // steady-clock nanoseconds
 };
+
+int64_t now_ns() {
+  return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
 
 struct Flight {
   cudaStream_t stream = nullptr;
@@ -368,6 +374,7 @@ void complete_ticket(hawkes_ctx *ctx, uint64_t id, int status, const double *val
   TicketRec &T = it->second;
   T.status = status;
   T.done = true;
+  T.t_done = now_ns();
   if (status == HAWKES_OK && vals) {
     T.ll = vals[0];
     for (int q = 0; q < 6; ++q) T.g[q] = vals[1 + q];
@@ -452,6 +459,8 @@ bool launch_pending(hawkes_ctx *ctx, Flight &F) {
     }
   }
   if (take.empty()) return false;
+  const int64_t t_launch = now_ns();
+  for (uint64_t id : take) ctx->tickets[id].t_launch = t_launch;
   void *ws = nullptr;
   std::unique_ptr<Batch> b(new Batch());
   std::memset(b.get(), 0, sizeof(Batch));
@@ -516,7 +525,7 @@ void scheduler_loop(hawkes_ctx *ctx) {
     for (auto &F : ctx->flights) inflight |= F.busy;
     if (ctx->shutdown && !inflight) break;
     if (launched) continue;
-    if (inflight) ctx->scv.wait_for(lk, std::chrono::microseconds(100));
+    if (inflight) ctx->scv.wait_for(lk, std::chrono::microseconds(20));
     else ctx->scv.wait_for(lk, std::chrono::milliseconds(50));
   }
 }
@@ -860,6 +869,7 @@ int hawkes_submit(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *params, 
     return rc;
   }
   const uint64_t id = ctx->next_ticket++;
+  T.t_submit = now_ns();
   ctx->tickets[id] = T;
   ctx->pending.push_back(id);
   ctx->n_submitted++;
@@ -869,6 +879,28 @@ int hawkes_submit(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *params, 
   }
   ctx->scv.notify_all();
   *ticket_out = id;
+  return HAWKES_OK;
+}
+
+int hawkes_poll_timed(hawkes_ctx *ctx, uint64_t ticket, int *done_out, double *loglik_out, double grad_out[6],
+                      int64_t *queued_ns_out, int64_t *total_ns_out) {
+  if (!ctx || !done_out) return HAWKES_E_INVAL;
+  std::lock_guard<std::mutex> lk(ctx->smu);
+  auto it = ctx->tickets.find(ticket);
+  if (it == ctx->tickets.end()) return HAWKES_E_TICKET;
+  if (!it->second.done) {
+    *done_out = 0;
+    return HAWKES_E_PENDING;
+  }
+  *done_out = 1;
+  const TicketRec T = it->second;
+  ctx->tickets.erase(it);
+  if (queued_ns_out) *queued_ns_out = (T.t_launch ? T.t_launch : T.t_done) - T.t_submit;
+  if (total_ns_out) *total_ns_out = T.t_done - T.t_submit;
+  if (T.status != HAWKES_OK) return T.status;
+  if (loglik_out) *loglik_out = T.ll;
+  if (grad_out)
+    for (int q = 0; q < 6; ++q) grad_out[q] = T.grad ? T.g[q] : 0.0;
   return HAWKES_OK;
 }
 

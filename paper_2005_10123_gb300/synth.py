@@ -5,7 +5,8 @@ CUDA path and the CPU oracle can both be fed from it.
 
 Generator (a branching simulation of the self-exciting model of Section 2.1):
   * a square region of side ``box`` km and a time window [0, T] days;
-  * background events: a Poisson count with mean ``bg_fraction * n``, times uniform on
+  * background events: a Poisson count with mean ``bg_fraction * n`` (by default 1.1 (1 - theta) n,
+    so that with branching ratio theta about 1.1 n events are drawn in all), times uniform on
     [0, T], locations from an equal-weight mixture of ``n_centres`` isotropic Gaussians
     (sd ``centre_sd`` km) whose centres are uniform in the square;
   * every event, background or offspring, has Poisson(``theta``) offspring, each delayed
@@ -14,8 +15,8 @@ Generator (a branching simulation of the self-exciting model of Section 2.1):
     ``n`` are kept. If fewer than ``n`` were drawn, the draw is repeated with seed + 1.
 
 The paper does not state its generator for the timing runs ("randomly generated"); the
-mean of the background count is not fixed anywhere either and is read as 0.55 n, so that
-with branching ratio 0.5 about 1.1 n events are drawn before truncation.
+mean of the background count is not fixed anywhere either and is read as 1.1 (1 - theta) n
+(0.55 n for theta = 0.5), so that about 1.1 n events are drawn before truncation.
 """
 from __future__ import annotations
 
@@ -47,10 +48,12 @@ class EventSet:
 
 def simulate(n: int, T: float, seed: int, box: float = 20.0, n_centres: int = 5,
              centre_sd: float = 0.5, theta: float = 0.5, omega: float = 1.0, h: float = 0.1,
-             bg_fraction: float = 0.55, max_redraws: int = 50) -> EventSet:
+             bg_fraction: float | None = None, max_redraws: int = 50) -> EventSet:
     """Draw one event set of exactly ``n`` events (see the module docstring)."""
     if n < 1:
         raise ValueError("n must be >= 1")
+    if bg_fraction is None:
+        bg_fraction = 1.1 * (1.0 - theta)
     for attempt in range(max_redraws):
         s = seed + attempt
         rng = np.random.Generator(np.random.PCG64(s))

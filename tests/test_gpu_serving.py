@@ -44,3 +44,16 @@ def test_alone_vs_mix_bitwise():
                 assert np.array_equal(d[1], a[1])
         assert stats["completed"] == 2 * len(reqs)
         assert stats["launches"] < 2 * len(reqs)  # the mix was batched
+
+
+def test_open_loop_poisson_arrivals_latency():
+    from paper_2005_10123_gb300 import binding, serving
+    sets = [synth.simulate(n, 2000.0, seed=800 + i) for i, n in enumerate([1500, 9000, 40000])]
+    with binding.Context(device=0) as ctx:
+        sids = [ctx.hawkes_upload_events(s.x, s.y, s.t) for s in sets]
+        res = serving.run_open_loop(ctx, sids, [s.n for s in sets], synth.theta_batch(16, seed=2), rate=400.0,
+                                    n_requests=150, grad_prob=0.5, seed=1)
+    assert res["completed"] == 150 and res["rejected"] == 0 and res["failed"] == 0
+    lat = res["latency_ms"]
+    assert 0 < lat["p50"] <= lat["p90"] <= lat["p99"]
+    assert res["throughput_pair_evals_per_s"] > 0
