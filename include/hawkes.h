@@ -139,11 +139,16 @@ int hawkes_loglik_async(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *pa
 int hawkes_loglik_batch(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_params *params,
                         hawkes_mode mode, int want_grad, double *loglik_out, double *grad_out);
 
-/* Work accounting: the number of (row, column) pairs an evaluation at Theta visits (the
- * exact-zero window described at HAWKES_FLAG_DENSE, counted over real events) and N^2. Host
- * computation only; no GPU work. */
+/* Work accounting for an evaluation at Theta (host computation only, no GPU work):
+ *   out[0] (row, column) pairs inside the exact-zero windows the kernels visit (see
+ *          HAWKES_FLAG_DENSE), counted over real events;
+ *   out[1] N^2, the pairs of Eq. 1's double sum;
+ *   out[2] ordered pairs whose background term can be nonzero at the mode's precision
+ *          (|t_n - t_n'| below the background's exact-zero reach, n' = n included);
+ *   out[3] ordered pairs whose trigger term can be nonzero (0 <= t_n - t_n' below the trigger's
+ *          exact-zero reach; pairs with equal times counted although their term is zero). */
 int hawkes_pair_work(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *params, hawkes_mode mode,
-                     int64_t *visited_pairs_out, int64_t *all_pairs_out);
+                     int64_t out[4]);
 
 /* Per-event terms of Eq. 2: mu_out[n] = mu(x_n, t_n) (background rate at event n)
  * and xi_out[n] = lambda_n - mu_n (the self-excitation part), so lambda_n =

@@ -88,7 +88,7 @@ def load(build_if_missing: bool = False, path: str | None = None):
         "hawkes_wait": [vp, u64, ctypes.c_int, _D, _D],
         "hawkes_stats": [vp, ctypes.POINTER(i64)],
         "hawkes_loglik_noalloc": [vp, vp, vp, i64, P, ctypes.c_int, vp, vp],
-        "hawkes_pair_work": [vp, i32, P, ctypes.c_int, ctypes.POINTER(i64), ctypes.POINTER(i64)],
+        "hawkes_pair_work": [vp, i32, P, ctypes.c_int, ctypes.POINTER(i64)],
         "hawkes_poll_timed": [vp, u64, ctypes.POINTER(ctypes.c_int), _D, _D, ctypes.POINTER(i64),
                               ctypes.POINTER(i64)],
     }
@@ -223,14 +223,14 @@ class Context:
                                                 ctypes.byref(ll)), "hawkes_event_terms")
         return mu, xi, ll.value
 
-    def hawkes_pair_work(self, set_id: int, theta, mode: int = HAWKES_MIXED):
-        """(pairs visited by an evaluation at theta, N^2)"""
-        v = ctypes.c_int64()
-        a = ctypes.c_int64()
+    def hawkes_pair_work(self, set_id: int, theta, mode: int = HAWKES_MIXED) -> dict:
+        """Pair counts of an evaluation at theta: visited (inside the windows), all (N^2),
+        bg (background term possibly nonzero), trig (trigger term possibly nonzero)."""
+        out = (ctypes.c_int64 * 4)()
         p = _params(theta)
-        self._check(self.lib.hawkes_pair_work(self.h, int(set_id), ctypes.byref(p), int(mode), ctypes.byref(v),
-                                              ctypes.byref(a)), "hawkes_pair_work")
-        return v.value, a.value
+        self._check(self.lib.hawkes_pair_work(self.h, int(set_id), ctypes.byref(p), int(mode), out),
+                    "hawkes_pair_work")
+        return {"visited": out[0], "all": out[1], "bg": out[2], "trig": out[3]}
 
     def hawkes_submit(self, set_id: int, theta, want_grad: bool = False, mode: int = HAWKES_MIXED) -> int:
         p = _params(theta)

@@ -659,7 +659,7 @@ int hawkes_upload_events(hawkes_ctx *ctx, const double *x, const double *y, cons
   for (int64_t i = 1; i < n; ++i)
     if (!(t[i] >= t[i - 1])) return HAWKES_E_UNSORTED;
   cudaSetDevice(ctx->device);
-  const int64_t npad = (int64_t)align_up((size_t)n, kRowTile);
+  const int64_t npad = (int64_t)align_up((size_t)n, kPadTo);
   std::unique_ptr<EventSetRec> S(new EventSetRec());
   S->n = n;
   S->npad = npad;
@@ -740,8 +740,8 @@ int hawkes_set_info(hawkes_ctx *ctx, int32_t set_id, int64_t *n_out, size_t *dev
 }
 
 int hawkes_pair_work(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *params, hawkes_mode mode,
-                     int64_t *visited_pairs_out, int64_t *all_pairs_out) {
-  if (!ctx || !params || (mode != HAWKES_FP64 && mode != HAWKES_MIXED)) return HAWKES_E_INVAL;
+                     int64_t out[4]) {
+  if (!ctx || !params || !out || (mode != HAWKES_FP64 && mode != HAWKES_MIXED)) return HAWKES_E_INVAL;
   if (int rc = check_params(params)) return rc;
   std::lock_guard<std::mutex> lock(ctx->mu);
   EventSetRec *S = find_set(ctx, set_id);
@@ -749,31 +749,42 @@ int hawkes_pair_work(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *param
   Request R;
   if (int rc = make_request(ctx, S, params, mode, 0, ctx->flags, &R)) return rc;
   const int64_t n = S->n;
-  int64_t visited = 0;
-  for (int rt = 0; rt < S->nrt; ++rt) {
+  // stored times of the mode, as doubles
+  std::vector<double> t((size_t)n);
+  for (int64_t i = 0; i < n; ++i) t[(size_t)i] = mode == HAWKES_MIXED ? (double)S->t32h[(size_t)i] : S->t64h[(size_t)i];
+  // exact-zero reach (days) of each term on its own (the window uses the larger on the early side)
+  double bg_reach, trig_reach;
+  if (mode == HAWKES_MIXED) {
+    bg_reach = std::sqrt(130.0) / (double)R.beta;
+    trig_reach = 131.0 / (params->omega * kLog2e);
+  } else {
+    bg_reach = std::sqrt(805.0 * 2.0) * params->tau_t;
+    trig_reach = 805.0 / params->omega;
+  }
+  int64_t visited = 0, bg_pairs = 0, trig_pairs = 0;
+  for (int rt = 0; rt < S->nrt; ++rt) {  // the window of column_window() in the kernels
     const int64_t r0 = (int64_t)rt * kRowTile, r1 = std::min<int64_t>(r0 + kRowTile, n) - 1;
     int c0 = 0, c1 = S->nct;
-    if (!(ctx->flags & HAWKES_FLAG_DENSE)) {  // the window of column_window() in the kernels
-      int64_t j0, j1;
-      if (mode == HAWKES_MIXED) {
-        const double lo = (double)S->t32h[(size_t)r0] - R.cut_early, hi = (double)S->t32h[(size_t)r1] + R.cut_late;
-        j0 = std::lower_bound(S->t32h.begin(), S->t32h.end(), lo, [](float a, double v) { return (double)a < v; }) -
-             S->t32h.begin();
-        j1 = std::upper_bound(S->t32h.begin(), S->t32h.end(), hi, [](double v, float a) { return v < (double)a; }) -
-             S->t32h.begin();
-      } else {
-        const double lo = S->t64h[(size_t)r0] - R.cut_early, hi = S->t64h[(size_t)r1] + R.cut_late;
-        j0 = std::lower_bound(S->t64h.begin(), S->t64h.end(), lo) - S->t64h.begin();
-        j1 = std::upper_bound(S->t64h.begin(), S->t64h.end(), hi) - S->t64h.begin();
-      }
+    if (!(ctx->flags & HAWKES_FLAG_DENSE)) {
+      const int64_t j0 = std::lower_bound(t.begin(), t.end(), t[(size_t)r0] - R.cut_early) - t.begin();
+      const int64_t j1 = std::upper_bound(t.begin(), t.end(), t[(size_t)r1] + R.cut_late) - t.begin();
       c0 = (int)(j0 / kColTile);
       c1 = std::max(std::min((int)((j1 + kColTile - 1) / kColTile), S->nct), c0 + 1);
     }
     const int64_t cols = std::min<int64_t>((int64_t)c1 * kColTile, n) - (int64_t)c0 * kColTile;
     visited += (r1 - r0 + 1) * cols;
   }
-  if (visited_pairs_out) *visited_pairs_out = visited;
-  if (all_pairs_out) *all_pairs_out = n * n;
+  for (int64_t i = 0; i < n; ++i) {  // pairs whose term can be nonzero at the working precision
+    const double ti = t[(size_t)i];
+    bg_pairs += (std::upper_bound(t.begin(), t.end(), ti + bg_reach) - t.begin()) -
+                (std::lower_bound(t.begin(), t.end(), ti - bg_reach) - t.begin());
+    trig_pairs += (std::lower_bound(t.begin(), t.end(), ti) - t.begin()) -
+                  (std::lower_bound(t.begin(), t.end(), ti - trig_reach) - t.begin());
+  }
+  out[0] = visited;
+  out[1] = n * n;
+  out[2] = bg_pairs;
+  out[3] = trig_pairs;
   return HAWKES_OK;
 }
 

@@ -10,15 +10,22 @@ namespace hk {
 // ---- tiling -------------------------------------------------------------------------
 // A pair-kernel CTA holds kRowTile consecutive rows (events n) in registers,
 // kRowsPerThread per thread, and streams column tiles of kColTile events (n')
-// through shared memory. Event arrays are padded to a multiple of kRowTile.
+// through shared memory. Event arrays are padded to a multiple of both tile sizes.
 #ifndef HK_ROWS_PER_THREAD
 #define HK_ROWS_PER_THREAD 4
 #endif
-constexpr int kThreads = 128;
+#ifndef HK_THREADS
+#define HK_THREADS 128
+#endif
+#ifndef HK_COL_TILE
+#define HK_COL_TILE 256
+#endif
+constexpr int kThreads = HK_THREADS;
 constexpr int kRowsPerThread = HK_ROWS_PER_THREAD;  // even: rows are processed in packed pairs
 constexpr int kRowTile = kThreads * kRowsPerThread;  // 512 with 4 rows per thread
-constexpr int kColTile = 256;
+constexpr int kColTile = HK_COL_TILE;
 constexpr int kWarpRows = 32 * kRowsPerThread;       // consecutive rows per warp
+constexpr int kPadTo = kRowTile > kColTile ? kRowTile : kColTile;  // event arrays padded to this
 constexpr int kEpiThreads = 256;                     // epilogue rows per CTA
 constexpr int kMaxBatch = 64;                        // requests per launch
 constexpr int kSumsLoglik = 2;                       // S_b, S_s

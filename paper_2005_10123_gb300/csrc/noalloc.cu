@@ -186,7 +186,7 @@ extern "C" int hawkes_loglik_noalloc(const float *x, const float *y, const float
   DeviceScratch *d = nullptr;
   if (int rc = scratch_base(device, &d)) return rc;
   cudaStream_t s = (cudaStream_t)cuda_stream;
-  const int npad = (int)((n + kRowTile - 1) / kRowTile * kRowTile);
+  const int npad = (int)((n + kPadTo - 1) / kPadTo * kPadTo);
   const int nrt = npad / kRowTile, nct = npad / kColTile;
   const int chunks = std::min(kChunks, nct);
   unsigned char *base = d->base;

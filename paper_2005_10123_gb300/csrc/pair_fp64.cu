@@ -39,13 +39,15 @@ __device__ __forceinline__ void tile_pass64(const double *__restrict__ sx, const
     for (int k = 0; k < 4; ++k) {
       const double dx = X[k] - cx, dy = Y[k] - cy, dt = T[k] - ctj;
       const double r2 = __fma_rn(dx, dx, __dmul_rn(dy, dy));
-      const double u = __dmul_rn(dt, dt);
-      double eb = exp(-__fma_rn(r2, da, __dmul_rn(u, db)));
-      if (KIND == 2 && excl && col == row_a0 + 32 * k) eb = 0.0;
-      acc[0][k] += eb;
-      if (GRAD) {
-        acc[2][k] = __fma_rn(r2, eb, acc[2][k]);
-        acc[3][k] = __fma_rn(u, eb, acc[3][k]);
+      if (KIND != 3) {  // KIND 3: every background term of the tile is exactly zero
+        const double u = __dmul_rn(dt, dt);
+        double eb = exp(-__fma_rn(r2, da, __dmul_rn(u, db)));
+        if (KIND == 2 && excl && col == row_a0 + 32 * k) eb = 0.0;
+        acc[0][k] += eb;
+        if (GRAD) {
+          acc[2][k] = __fma_rn(r2, eb, acc[2][k]);
+          acc[3][k] = __fma_rn(u, eb, acc[3][k]);
+        }
       }
       if (KIND != 0) {
         double es = exp(-__fma_rn(omega, dt, __dmul_rn(r2, dc)));
@@ -72,6 +74,10 @@ __device__ void run_piece64(const Request &R, int4 piece, int slot, double (*sx)
   const int lo_wa = S.lo64[wa], lo_wb = S.lo64[wb];
   const bool excl = (R.flags & 1) != 0;
   const double da = R.da, db = R.db, dc = R.dc, omega = R.omega;
+  // exact-zero gaps (days) between the warp's earliest row and a tile's latest column: the
+  // background exponent exceeds 805 past bg_gap, the trigger exponent past trig_gap (exp
+  // returns +0 far below -745); one percent of margin
+  const double bg_gap = 1.01 * sqrt(805.0 / db), trig_gap = 1.01 * 805.0 / omega;
 
   double X[4], Y[4], T[4];
   int LO[4];
@@ -83,6 +89,8 @@ __device__ void run_piece64(const Request &R, int4 piece, int slot, double (*sx)
     T[k] = r < n ? S.t64[r] : kPadTime;
     LO[k] = S.lo64[r];
   }
+  const double t_first = __shfl_sync(0xffffffffu, T[0], 0);  // the warp's earliest row
+  const double t_last = __shfl_sync(0xffffffffu, T[3], 31);  // and its latest (padding: +huge)
   double acc[NS][4];
 #pragma unroll
   for (int s = 0; s < NS; ++s)
@@ -105,15 +113,26 @@ __device__ void run_piece64(const Request &R, int4 piece, int slot, double (*sx)
   for (int k = 0; ct < piece.z; ++ct, ++k) {
     const int buf = k & 1;
     const int c0 = ct * kColTile, c1 = c0 + kColTile;
-    int kind = (c1 <= lo_wa) ? 1 : (c0 >= lo_wb ? 0 : 2);
+    int kind;
+    if (c1 <= lo_wa) {  // every pair causal: which of the two terms can be nonzero?
+      const double gap = t_first - st[buf][kColTile - 1];
+      const bool bg_zero = gap >= bg_gap, trig_zero = gap >= trig_gap;
+      kind = bg_zero ? (trig_zero ? -1 : 3) : (trig_zero ? 0 : 1);
+    } else if (c0 >= lo_wb) {  // no causal pair: background only, zero past its reach
+      kind = st[buf][0] - t_last >= bg_gap ? -1 : 0;
+    } else {
+      kind = 2;
+    }
     if (excl && c0 <= wb && c1 > wa) kind = 2;
     const int row_a0 = wa + lane;
     if (kind == 0)
       tile_pass64<0, GRAD>(sx[buf], sy[buf], st[buf], X, Y, T, LO, row_a0, c0, excl, da, db, dc, omega, acc);
     else if (kind == 1)
       tile_pass64<1, GRAD>(sx[buf], sy[buf], st[buf], X, Y, T, LO, row_a0, c0, excl, da, db, dc, omega, acc);
-    else
+    else if (kind == 2)
       tile_pass64<2, GRAD>(sx[buf], sy[buf], st[buf], X, Y, T, LO, row_a0, c0, excl, da, db, dc, omega, acc);
+    else if (kind == 3)
+      tile_pass64<3, GRAD>(sx[buf], sy[buf], st[buf], X, Y, T, LO, row_a0, c0, excl, da, db, dc, omega, acc);
     if (ct + 1 < piece.z) stage(ct + 1, buf ^ 1);
     __syncthreads();
   }

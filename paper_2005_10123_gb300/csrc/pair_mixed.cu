@@ -101,15 +101,19 @@ struct Acc32 {
   float2 v[NS][kPairs];
 };
 
-// One column tile against this thread's rows. KIND 0: no causal pair in the tile for this
-// warp; 1: every pair causal (separable trigger factor); 2: test each pair (and mask
-// n' = n when excluding self).
+// One column tile against this thread's rows. KIND 0: background only (no causal pair, or
+// every trigger term of the tile is exactly zero); 1: every pair causal (separable trigger
+// factor); 2: test each pair (and mask n' = n when excluding self); 3: every pair causal and
+// every background term exactly zero (trigger only, separable).
 template <int KIND, bool GRAD>
 __device__ __forceinline__ void tile_pass(const float4 *__restrict__ sxy, const float4 *__restrict__ stb,
                                           const float2 (&X)[kPairs], const float2 (&Y)[kPairs],
                                           const float2 (&T)[kPairs], const int (&LO)[kRowsPerThread], int row_a0,
                                           int c0, bool excl, float2 A2, float2 CN,
                                           float2 WN, Acc32<GRAD ? kSumsGrad : kSumsLoglik> &acc) {
+  constexpr bool kBg = KIND != 3;
+  constexpr bool kTrig = KIND != 0;
+  constexpr bool kNeedDt = kBg || KIND == 2 || GRAD;
 #pragma unroll kColUnroll
   for (int j = 0; j < kColTile; ++j) {
     const float4 c = sxy[j];  // {-x, -x, -y, -y}
@@ -122,24 +126,27 @@ __device__ __forceinline__ void tile_pass(const float4 *__restrict__ sxy, const 
       const float2 dx = add2(X[p], cx);
       const float2 dy = add2(Y[p], cy);
       const float2 rho = fma2(dy, dy, mul2(dx, dx));
-      const float2 dt = add2(T[p], ct);
-      const float2 u = mul2(dt, dt);
-      const float2 q = fma2(rho, A2, u);
-      float2 eb = make_float2(ex2(-q.x), ex2(-q.y));
-      if (KIND == 2 && excl) {
-        const int ra = row_a0 + 64 * p;
-        if (col == ra) eb.x = 0.f;
-        if (col == ra + 32) eb.y = 0.f;
+      float2 dt = make_float2(0.f, 0.f);
+      if (kNeedDt) dt = add2(T[p], ct);
+      if (kBg) {
+        const float2 u = mul2(dt, dt);
+        const float2 q = fma2(rho, A2, u);
+        float2 eb = make_float2(ex2(-q.x), ex2(-q.y));
+        if (KIND == 2 && excl) {
+          const int ra = row_a0 + 64 * p;
+          if (col == ra) eb.x = 0.f;
+          if (col == ra + 32) eb.y = 0.f;
+        }
+        acc.v[0][p] = acc2(acc.v[0][p], eb);
+        if (GRAD) {
+          acc.v[2][p] = accfma2(rho, eb, acc.v[2][p]);
+          acc.v[3][p] = accfma2(u, eb, acc.v[3][p]);
+        }
       }
-      acc.v[0][p] = acc2(acc.v[0][p], eb);
-      if (GRAD) {
-        acc.v[2][p] = accfma2(rho, eb, acc.v[2][p]);
-        acc.v[3][p] = accfma2(u, eb, acc.v[3][p]);
-      }
-      if (KIND != 0) {
+      if (kTrig) {
         float2 arg;
-        if (KIND == 1) arg = fma2(rho, CN, bj);
-        else arg = fma2(rho, CN, mul2(dt, WN));
+        if (KIND == 2) arg = fma2(rho, CN, mul2(dt, WN));
+        else arg = fma2(rho, CN, bj);
         float2 es = make_float2(ex2(arg.x), ex2(arg.y));
         if (KIND == 2) {
           es.x = (col < LO[2 * p]) ? es.x : 0.f;
@@ -155,31 +162,54 @@ __device__ __forceinline__ void tile_pass(const float4 *__restrict__ sxy, const 
   }
 }
 
+// Exact-zero gaps in scaled time dt' between a warp's earliest row and a tile's latest
+// column: past kBgZeroGap every background exponent exceeds 130 (ex2 flushes 2^-130 to
+// zero); past kTrigZeroExp / -wn every trigger row factor 2^(wn dt') is below 2^-131.
+// One percent of margin covers the float32 rounding of the differences.
+constexpr float kBgZeroGap = 11.5157f;    // 1.01 * sqrt(130)
+constexpr float kTrigZeroExp = 132.31f;   // 1.01 * 131
+
+// Each thread stages kStage columns of a tile: raw values are loaded into registers one
+// tile ahead, then scaled, negated and duplicated into shared memory.
+constexpr int kStage = kColTile / kThreads;
+static_assert(kColTile % kThreads == 0, "column tile must be a multiple of the CTA width");
+
 struct RawCols {
-  float x0, y0, t0, x1, y1, t1, tref;
+  float x[kStage], y[kStage], t[kStage];
+  float tref;
 };
 
 __device__ __forceinline__ RawCols load_cols(const SetView &S, int ct, int tid) {
-  const int j0 = ct * kColTile + tid, j1 = j0 + kThreads;
   const int last = min((ct + 1) * kColTile, S.n) - 1;  // latest real column of the tile
   RawCols r;
-  r.x0 = __ldg(S.x32 + j0); r.y0 = __ldg(S.y32 + j0); r.t0 = __ldg(S.t32 + j0);
-  r.x1 = __ldg(S.x32 + j1); r.y1 = __ldg(S.y32 + j1); r.t1 = __ldg(S.t32 + j1);
+#pragma unroll
+  for (int h = 0; h < kStage; ++h) {
+    const int j = ct * kColTile + tid + h * kThreads;
+    r.x[h] = __ldg(S.x32 + j);
+    r.y[h] = __ldg(S.y32 + j);
+    r.t[h] = __ldg(S.t32 + j);
+  }
   r.tref = __ldg(S.t32 + max(last, 0));
   return r;
 }
 
 __device__ __forceinline__ void store_cols(const RawCols &r, int ct, int tid, int n, float t_origin, float beta,
                                            float wn, float4 *sxy, float4 *stb) {
-  const int j0 = ct * kColTile + tid, j1 = j0 + kThreads;
-  const float s0 = j0 < n ? (r.t0 - t_origin) * beta : kPadScaled;
-  const float s1 = j1 < n ? (r.t1 - t_origin) * beta : kPadScaled;
   const float sref = (r.tref - t_origin) * beta;
-  const float b0 = wn * (sref - s0), b1 = wn * (sref - s1);
-  sxy[tid] = make_float4(-r.x0, -r.x0, -r.y0, -r.y0);
-  stb[tid] = make_float4(-s0, -s0, b0, b0);
-  sxy[tid + kThreads] = make_float4(-r.x1, -r.x1, -r.y1, -r.y1);
-  stb[tid + kThreads] = make_float4(-s1, -s1, b1, b1);
+#pragma unroll
+  for (int h = 0; h < kStage; ++h) {
+    const int jj = tid + h * kThreads, j = ct * kColTile + jj;
+    const float sj = j < n ? (r.t[h] - t_origin) * beta : kPadScaled;
+    const float bj = wn * (sref - sj);
+    sxy[jj] = make_float4(-r.x[h], -r.x[h], -r.y[h], -r.y[h]);
+    stb[jj] = make_float4(-sj, -sj, bj, bj);
+  }
+}
+
+// CTA-wide barrier; a single-warp CTA only needs the warp to converge.
+__device__ __forceinline__ void cta_sync() {
+  if (kThreads == 32) __syncwarp();
+  else __syncthreads();
 }
 
 template <bool GRAD>
@@ -209,6 +239,8 @@ __device__ void run_piece(const Request &R, int4 piece, int slot, float4 (*sxy)[
     LO[2 * p + 1] = S.lo32[rb];
   }
   const float2 A2 = make_float2(R.a2, R.a2), CN = make_float2(R.cn, R.cn), WN = make_float2(wn, wn);
+  const float s_first = __shfl_sync(0xffffffffu, T[0].x, 0);            // scaled time of the warp's
+  const float s_last = __shfl_sync(0xffffffffu, T[kPairs - 1].y, 31);  // first and last rows
 
   // float64 row accumulators live in shared memory, one slot per (sum, row, thread)
 #pragma unroll
@@ -219,7 +251,7 @@ __device__ void run_piece(const Request &R, int4 piece, int slot, float4 (*sxy)[
   int ct = piece.y;
   if (ct < piece.z) {  // an empty slice of the window writes zero partial sums
     store_cols(load_cols(S, ct, tid), ct, tid, n, t_origin, beta, wn, sxy[0], stb[0]);
-    __syncthreads();
+    cta_sync();
   }
   for (int k = 0; ct < piece.z; ++ct, ++k) {
     const int buf = k & 1;
@@ -227,7 +259,17 @@ __device__ void run_piece(const Request &R, int4 piece, int slot, float4 (*sxy)[
     RawCols nxt;
     if (has_next) nxt = load_cols(S, ct + 1, tid);
     const int c0 = ct * kColTile, c1 = c0 + kColTile;
-    int kind = (c1 <= lo_wa) ? 1 : (c0 >= lo_wb ? 0 : 2);
+    int kind;
+    if (c1 <= lo_wa) {  // every pair causal: which of the two terms can be nonzero?
+      const float gap = s_first + stb[buf][kColTile - 1].x;  // t'(first row) - t'(latest column)
+      const bool bg_zero = gap >= kBgZeroGap, trig_zero = wn * gap <= -kTrigZeroExp;
+      kind = bg_zero ? (trig_zero ? -1 : 3) : (trig_zero ? 0 : 1);
+    } else if (c0 >= lo_wb) {  // no causal pair: background only, zero past its reach
+      const float gap = -stb[buf][0].x - s_last;  // t'(earliest column) - t'(last row)
+      kind = gap >= kBgZeroGap ? -1 : 0;
+    } else {
+      kind = 2;
+    }
     if (excl && c0 <= wb && c1 > wa) kind = 2;
     Acc32<NS> acc;
 #pragma unroll
@@ -237,8 +279,9 @@ __device__ void run_piece(const Request &R, int4 piece, int slot, float4 (*sxy)[
     const int row_a0 = wa + lane;
     if (kind == 0) {
       tile_pass<0, GRAD>(sxy[buf], stb[buf], X, Y, T, LO, row_a0, c0, excl, A2, CN, WN, acc);
-    } else if (kind == 1) {
-      tile_pass<1, GRAD>(sxy[buf], stb[buf], X, Y, T, LO, row_a0, c0, excl, A2, CN, WN, acc);
+    } else if (kind == 1 || kind == 3) {
+      if (kind == 1) tile_pass<1, GRAD>(sxy[buf], stb[buf], X, Y, T, LO, row_a0, c0, excl, A2, CN, WN, acc);
+      else tile_pass<3, GRAD>(sxy[buf], stb[buf], X, Y, T, LO, row_a0, c0, excl, A2, CN, WN, acc);
       // row factor 2^(wn (t'_n - t'_ref)) of the separable trigger term
       const float sref = -stb[buf][kColTile - 1].x;
       const float2 sr = make_float2(-sref, -sref);
@@ -252,9 +295,9 @@ __device__ void run_piece(const Request &R, int4 piece, int slot, float4 (*sxy)[
           acc.v[5][p] = __fmul2_rn(acc.v[5][p], a);
         }
       }
-    } else {
+    } else if (kind == 2) {
       tile_pass<2, GRAD>(sxy[buf], stb[buf], X, Y, T, LO, row_a0, c0, excl, A2, CN, WN, acc);
-    }
+    }  // kind -1: every term of the tile is exactly zero for this warp
 #pragma unroll
     for (int s = 0; s < NS; ++s)
 #pragma unroll
@@ -263,7 +306,7 @@ __device__ void run_piece(const Request &R, int4 piece, int slot, float4 (*sxy)[
         sacc[(s * kRowsPerThread + 2 * p + 1) * kThreads + tid] += (double)acc.v[s][p].y;
       }
     if (has_next) store_cols(nxt, ct + 1, tid, n, t_origin, beta, wn, sxy[buf ^ 1], stb[buf ^ 1]);
-    __syncthreads();
+    cta_sync();
   }
   double *dst = R.partials + (size_t)slot * NS * kRowTile;
 #pragma unroll
@@ -287,7 +330,7 @@ __global__ void __launch_bounds__(kThreads, HK_MIN_CTAS) pair_mixed_kernel(const
   __shared__ int2 s_win;
   for (;;) {
     if (threadIdx.x == 0) s_item = (int)atomicAdd(B.counter, 1u);
-    __syncthreads();
+    cta_sync();
     const int item = s_item;
     if (item >= B.total_items) break;
     const Request &R = B.req[find_request(B, item, false)];
@@ -297,14 +340,14 @@ __global__ void __launch_bounds__(kThreads, HK_MIN_CTAS) pair_mixed_kernel(const
       const int2 w = column_window(R, R.set.t32, rt);
       if (threadIdx.x == 0) s_win = w;
     }
-    __syncthreads();
+    cta_sync();
     const int2 w = s_win;
     const int width = w.y - w.x;
     const int c_begin = w.x + (int)((long long)width * sl / R.slices);
     const int c_end = w.x + (int)((long long)width * (sl + 1) / R.slices);
     run_piece<GRAD>(R, make_int4(rt, c_begin, c_end, 0), local, sxy, stb, sacc);
     if (sl == 0 && R.comp) compensator_tile(R, R.set.t32, rt, GRAD);
-    __syncthreads();  // s_item, s_win and the staging buffers are reused by the next item
+    cta_sync();  // s_item, s_win and the staging buffers are reused by the next item
   }
 }
 

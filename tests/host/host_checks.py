@@ -70,12 +70,13 @@ def main():
     # work accounting: the exact-zero window visits a subset of the N^2 pairs; dense visits all
     for n in (1, 513, 20000, 85000):
         for mode in (0, 1):
-            v, a = ctx.hawkes_pair_work(sids[n], TH, mode)
-            assert a == n * n and 0 < v <= a, (n, mode, v, a)
-    v85, _ = ctx.hawkes_pair_work(sids[85000], TH, 1)
-    assert v85 < 0.5 * 85000 ** 2  # T = 5,000 days >> the 400-day background reach at tau_t = 30
+            w = ctx.hawkes_pair_work(sids[n], TH, mode)
+            assert w["all"] == n * n and 0 < w["visited"] <= w["all"], (n, mode, w)
+            assert n <= w["bg"] <= w["visited"] and 0 <= w["trig"] <= w["bg"], (n, mode, w)
+    w85 = ctx.hawkes_pair_work(sids[85000], TH, 1)
+    assert w85["visited"] < 0.5 * 85000 ** 2  # T = 5,000 days >> the 400-day background reach
     ctx.hawkes_set_flags(2)
-    assert ctx.hawkes_pair_work(sids[85000], TH, 1)[0] == 85000 ** 2
+    assert ctx.hawkes_pair_work(sids[85000], TH, 1)["visited"] == 85000 ** 2
     ctx.hawkes_set_flags(0)
     mu, xi, _ = ctx.hawkes_event_terms(sids[1000], TH, 1)
     assert np.array_equal(mu, np.arange(1000)) and np.array_equal(xi, -np.arange(1000))

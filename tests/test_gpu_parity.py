@@ -83,6 +83,16 @@ def test_theta_zero_and_parameter_spread(ctx, mode):
 
 
 @pytest.mark.parametrize("mode", [0, 1], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("theta", [(0.02, 0.5, 5.0, 0.6, 0.02, 0.05), (0.05, 0.8, 200.0, 0.4, 4.0, 0.1)],
+                         ids=["trigger_reaches_further", "background_reaches_further"])
+def test_long_time_span(ctx, mode, theta):
+    """Sets spanning many bandwidths, where whole tiles carry only background or only trigger
+    terms (every other term in them is exactly zero at the working precision)."""
+    ev = synth.simulate(6000, 3000.0, seed=321)
+    _check(ctx, ev, theta, mode)
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["fp64", "mixed"])
 def test_event_terms_rows(ctx, mode):
     ev = synth.simulate(3000, 1000.0, seed=21)
     sid = ctx.hawkes_upload_events(ev.x, ev.y, ev.t)
@@ -107,7 +117,8 @@ def test_exact_zero_window_matches_dense(ctx, mode):
     ev = synth.simulate(20000, 5000.0, seed=71)  # long time span: most column tiles skipped
     sid = ctx.hawkes_upload_events(ev.x, ev.y, ev.t)
     try:
-        for th in [TH0, (0.02, 0.5, 5.0, 0.6, 3.0, 0.05), (0.01, 2.0, 300.0, 0.4, 0.05, 0.3)]:
+        for th in [TH0, (0.02, 0.5, 5.0, 0.6, 3.0, 0.05), (0.01, 2.0, 300.0, 0.4, 0.05, 0.3),
+                   (0.02, 0.5, 5.0, 0.6, 0.02, 0.05)]:
             ctx.hawkes_set_flags(0)
             a, ga = ctx.hawkes_loglik_grad(sid, th, mode)
             ctx.hawkes_set_flags(binding.HAWKES_FLAG_DENSE)
