@@ -189,6 +189,17 @@ void exact_zero_cutoffs(const hawkes_params *p, int mode, float beta32, double *
   *late = bg;
 }
 
+// Float64 constants of the epilogue and compensator, from Theta (Section 2.1, d = 2).
+void set_epilogue_constants(Request *R) {
+  const double two_pi = 6.28318530717958647693;
+  R->k_ab = 1.0 / (two_pi * std::sqrt(two_pi) * R->tau_x * R->tau_x * R->tau_t);
+  R->k_cw = R->omega / (two_pi * R->h * R->h);
+  R->inv_tx = 1.0 / R->tau_x;
+  R->inv_tt = 1.0 / R->tau_t;
+  R->inv_h = 1.0 / R->h;
+  R->inv_om = 1.0 / R->omega;
+}
+
 // Request descriptor for one evaluation of set `S` at Theta `p`.
 int make_request(hawkes_ctx *ctx, const EventSetRec *S, const hawkes_params *p, int mode, int grad,
                  int flags, Request *R) {
@@ -210,6 +221,7 @@ int make_request(hawkes_ctx *ctx, const EventSetRec *S, const hawkes_params *p, 
   R->dc = 1.0 / (2.0 * p->h * p->h);
   R->mu0 = p->mu0; R->tau_x = p->tau_x; R->tau_t = p->tau_t;
   R->theta = p->theta; R->omega = p->omega; R->h = p->h;
+  set_epilogue_constants(R);
   if (mode == HAWKES_MIXED) {
     // the float32 path must keep every scaled quantity finite and below the padding value
     const double span = (S->t_last32 - S->t_first32) * (double)R->beta;

@@ -70,6 +70,10 @@ struct Request {
   double mu0, tau_x, tau_t, theta, omega, h;
   double t_last;
   double tscale;  // scaled-to-raw time factor of the moments: 1/beta (mixed) or 1 (fp64)
+  // per-request float64 constants of the epilogue and compensator (no divisions per row)
+  double k_ab;    // A / mu0 = 1 / ((2 pi)^{3/2} tau_x^2 tau_t)
+  double k_cw;    // C / theta = omega / (2 pi h^2)
+  double inv_tx, inv_tt, inv_h, inv_om;
   // workspace (device)
   double *partials;    // nrt * slices * S * kRowTile
   double *comp;        // nrt * 8: per row tile, the sums of Lambda_n and d Lambda_n / d Theta
@@ -172,18 +176,18 @@ template <typename TT>
 __device__ void compensator_tile(const Request &R, const TT *t, int rt, bool grad) {
   __shared__ double red[32][8];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = (blockDim.x + 31) >> 5;
-  const double mu0 = R.mu0, tt = R.tau_t, th = R.theta, om = R.omega, tN = R.t_last;
+  const double mu0 = R.mu0, th = R.theta, om = R.omega, tN = R.t_last, inv_tt = R.inv_tt;
   double v[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   const int end = min((rt + 1) * kRowTile, R.set.n);
   for (int i = rt * kRowTile + tid; i < end; i += blockDim.x) {
     const double tn = (double)t[i];
-    const double a = (tN - tn) / tt, b = -tn / tt, D = tN - tn;
+    const double a = (tN - tn) * inv_tt, b = -tn * inv_tt, D = tN - tn;
     const double e = exp(-om * D);
     const double Pa = normcdf(a), Pb = normcdf(b);
     v[0] += mu0 * (Pa - Pb) + th * (1.0 - e);
     if (grad) {
       v[1] += Pa - Pb;
-      v[3] += mu0 / tt * (-a * std_normal_pdf(a) + b * std_normal_pdf(b));
+      v[3] += mu0 * inv_tt * (-a * std_normal_pdf(a) + b * std_normal_pdf(b));
       v[4] += 1.0 - e;
       v[5] += th * D * e;
     }

@@ -98,11 +98,9 @@ __global__ void __launch_bounds__(kEpiThreads) noalloc_epilogue(const __grid_con
         sb += src[0];
         ss += src[kRowTile];
       }
-      const double two_pi = 6.28318530717958647693;
-      const double A = R.mu0 / (two_pi * sqrt(two_pi) * R.tau_x * R.tau_x * R.tau_t);
-      const double C = R.theta * R.omega / (two_pi * R.h * R.h);
+      const double A = R.mu0 * R.k_ab, C = R.theta * R.k_cw;
       const double tn = (double)st[i];
-      const double Lam = R.mu0 * (normcdf((t_last - tn) / R.tau_t) - normcdf(-tn / R.tau_t)) +
+      const double Lam = R.mu0 * (normcdf((t_last - tn) * R.inv_tt) - normcdf(-tn * R.inv_tt)) +
                          R.theta * (1.0 - exp(-R.omega * (t_last - tn)));
       v = log(A * sb + C * ss) - Lam;
     }
@@ -216,6 +214,12 @@ extern "C" int hawkes_loglik_noalloc(const float *x, const float *y, const float
     return HAWKES_E_INVAL;
   R.mu0 = p->mu0; R.tau_x = p->tau_x; R.tau_t = p->tau_t;
   R.theta = p->theta; R.omega = p->omega; R.h = p->h;
+  {
+    const double two_pi = 6.28318530717958647693;
+    R.k_ab = 1.0 / (two_pi * std::sqrt(two_pi) * p->tau_x * p->tau_x * p->tau_t);
+    R.k_cw = p->omega / (two_pi * p->h * p->h);
+    R.inv_tx = 1.0 / p->tau_x; R.inv_tt = 1.0 / p->tau_t; R.inv_h = 1.0 / p->h; R.inv_om = 1.0 / p->omega;
+  }
   R.tscale = 1.0 / (double)R.beta;
   // the same exact-zero column window as the context path (see exact_zero_cutoffs there)
   const double bg = 1.01 * std::sqrt(130.0) / (double)R.beta, trig = 1.01 * 131.0 / (p->omega * log2e);

@@ -202,10 +202,9 @@ __global__ void __launch_bounds__(kEpiThreads) epilogue_kernel(const __grid_cons
 #pragma unroll
         for (int s = 0; s < NS; ++s) sums[s] += src[s * kRowTile];
       }
-      const double two_pi = 6.28318530717958647693;
-      const double mu0 = R.mu0, tx = R.tau_x, tt = R.tau_t, th = R.theta, om = R.omega, h = R.h;
-      const double Ab = 1.0 / (two_pi * sqrt(two_pi) * tx * tx * tt);  // A / mu0
-      const double Cw = om / (two_pi * h * h);                         // C / theta
+      const double mu0 = R.mu0, th = R.theta, om = R.omega;
+      const double itx = R.inv_tx, itt = R.inv_tt, ih = R.inv_h, iom = R.inv_om;
+      const double Ab = R.k_ab, Cw = R.k_cw;  // A / mu0, C / theta
       const double A = mu0 * Ab, C = th * Cw;
       const double mu = A * sums[0], xi = C * sums[1], lam = mu + xi;
       if (R.mu_out) R.mu_out[i] = mu;
@@ -218,21 +217,21 @@ __global__ void __launch_bounds__(kEpiThreads) epilogue_kernel(const __grid_cons
         const double Sb = sums[0], Ss = sums[1];
         const double inv = 1.0 / lam;
         v[1] = Ab * Sb * inv;
-        v[2] = A * (-2.0 * Sb / tx + Rb / (tx * tx * tx)) * inv;
-        v[3] = A * (-Sb / tt + Tb / (tt * tt * tt)) * inv;
+        v[2] = A * itx * (-2.0 * Sb + Rb * itx * itx) * inv;
+        v[3] = A * itt * (-Sb + Tb * itt * itt) * inv;
         v[4] = Cw * Ss * inv;
-        v[5] = C * (Ss / om - Us) * inv;
-        v[6] = C * (-2.0 * Ss / h + Rs / (h * h * h)) * inv;
+        v[5] = C * (Ss * iom - Us) * inv;
+        v[6] = C * ih * (-2.0 * Ss + Rs * ih * ih) * inv;
       }
       if (own_comp) {
         const double tn = B.mode == 1 ? (double)S.t32[i] : S.t64[i];
-        const double a = (R.t_last - tn) / tt, b = -tn / tt, D = R.t_last - tn;
+        const double a = (R.t_last - tn) * itt, b = -tn * itt, D = R.t_last - tn;
         const double e = exp(-om * D);
         const double Pa = normcdf(a), Pb = normcdf(b);
         v[0] -= mu0 * (Pa - Pb) + th * (1.0 - e);
         if (GRAD) {
           v[1] -= Pa - Pb;
-          v[3] -= mu0 / tt * (-a * std_normal_pdf(a) + b * std_normal_pdf(b));
+          v[3] -= mu0 * itt * (-a * std_normal_pdf(a) + b * std_normal_pdf(b));
           v[4] -= 1.0 - e;
           v[5] -= th * D * e;
         }
