@@ -239,36 +239,36 @@ int make_request(hawkes_ctx *ctx, const EventSetRec *S, const hawkes_params *p, 
   return HAWKES_OK;
 }
 
-int epi_blocks(int64_t n) { return (int)((n + kEpiThreads - 1) / kEpiThreads); }
-
-// Device bytes one request needs: partial sums, compensator sums, epilogue block partials.
+// Device bytes one request needs: partial sums, compensator sums, row-tile sums.
 size_t request_footprint(const EventSetRec *S, int mode, int grad) {
   const size_t items = (size_t)S->nrt * S->slices[kind_of(mode, grad)];
   size_t b = align_up(items * sums_of(grad) * kRowTile * sizeof(double), 256);
-  b += align_up((size_t)S->nrt * 8 * sizeof(double), 256);
-  b += align_up((size_t)epi_blocks(S->n) * 8 * sizeof(double), 256);
+  b += 2 * align_up((size_t)S->nrt * 8 * sizeof(double), 256);
   return b;
 }
 
-// Batch workspace header: the pair-kernel counter at byte 0, one epilogue ticket per
-// request at kTicketOff + 4 r, then the per-request outputs (8 doubles each). One
-// memset of the header clears the counter and every ticket.
-constexpr size_t kTicketOff = 256;
-constexpr size_t kHdrBytes = 1024;
+// Bytes of a request's completion counters (nrt + 1 unsigned), kept in one zeroed region per
+// batch (see batch_counter_bytes).
+size_t counter_bytes(const EventSetRec *S) { return align_up(((size_t)S->nrt + 1) * sizeof(unsigned), 64); }
+
+// Batch workspace header: the pair-kernel work counter at byte 0, then the per-request outputs
+// (8 doubles each), then every request's completion counters. One memset of the header and
+// the counters (kFixedBytes + the batch's counter bytes) zeroes everything that must start at 0.
+constexpr size_t kHdrBytes = 256;
 constexpr size_t kOutBytes = (size_t)kMaxBatch * 8 * sizeof(double);
 constexpr size_t kFixedBytes = kHdrBytes + kOutBytes;
 
 // Carve one request's workspace out of `base` (as sized by request_footprint).
 void bind_workspace(Request *R, const EventSetRec *S, int mode, int grad, char *base, double *out,
-                    unsigned *ticket) {
+                    unsigned *counters) {
   const size_t items = (size_t)S->nrt * S->slices[kind_of(mode, grad)];
   size_t off = 0;
   R->partials = (double *)(base + off);
   off += align_up(items * sums_of(grad) * kRowTile * sizeof(double), 256);
   R->comp = (double *)(base + off);
   off += align_up((size_t)S->nrt * 8 * sizeof(double), 256);
-  R->block_part = (double *)(base + off);
-  R->ticket = ticket;
+  R->rt_sum = (double *)(base + off);
+  R->rt_count = counters;
   R->out = out;
 }
 
@@ -277,24 +277,21 @@ int pair_grid(hawkes_ctx *ctx, int mode, int grad, int total_items) {
   return std::max(1, std::min(total_items, cap));
 }
 
-// Enqueue pair + epilogue kernels for a prepared batch on `s`. The counter and every
-// request's ticket must already be zero (the caller clears the batch header).
+// Enqueue the persistent pair kernel for a prepared batch on `s`; it finishes every row tile
+// and every request itself (fused epilogue). The work counter and every request's completion
+// counters must already be zero (the caller clears them with one memset).
 int launch_batch(hawkes_ctx *ctx, Batch &b, int mode, int grad, cudaStream_t s) {
   b.mode = mode == HAWKES_MIXED ? 1 : 0;
-  int items = 0, epi = 0;
+  b.fused = 1;
+  int items = 0;
   for (int r = 0; r < b.nreq; ++r) {
     b.req[r].item_begin = items;
-    b.req[r].epi_begin = epi;
     items += b.req[r].set.nrt * b.req[r].slices;
-    epi += epi_blocks(b.req[r].set.n);
   }
   b.total_items = items;
-  b.total_epi = epi;
   const int grid = pair_grid(ctx, mode, grad, items);
   if (mode == HAWKES_MIXED) HK_CUDA(ctx, launch_pair_mixed(b, grad != 0, grid, s));
   else HK_CUDA(ctx, launch_pair_fp64(b, grad != 0, grid, s));
-  const int egrid = std::max(1, std::min(epi, ctx->sms * 8));
-  HK_CUDA(ctx, launch_epilogue(b, grad != 0, egrid, s));
   return HAWKES_OK;
 }
 
@@ -345,7 +342,8 @@ int eval_sync(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_params *param
   if (!S) return HAWKES_E_NOSET;
   const size_t per = request_footprint(S, mode, grad);
   const size_t rows_bytes = (mu_out || xi_out) ? align_up((size_t)S->n * sizeof(double), 256) * 2 : 0;
-  const size_t need = kFixedBytes + rows_bytes + per * k;
+  const size_t cnt = align_up(counter_bytes(S) * k, 256);
+  const size_t need = kFixedBytes + cnt + rows_bytes + per * k;
   if (int rc = ensure_sync_ws(ctx, need)) return rc;
   char *base = (char *)ctx->sync_ws.dev;
   std::unique_ptr<Batch> b(new Batch());
@@ -353,18 +351,19 @@ int eval_sync(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_params *param
   b->nreq = k;
   b->counter = (unsigned *)base;
   double *outs = (double *)(base + kHdrBytes);
-  char *rows_base = base + kFixedBytes;
+  char *cnt_base = base + kFixedBytes;
+  char *rows_base = cnt_base + cnt;
   char *req_base = rows_base + rows_bytes;
   for (int r = 0; r < k; ++r) {
     if (int rc = make_request(ctx, S, &params[r], mode, grad, ctx->flags, &b->req[r])) return rc;
     bind_workspace(&b->req[r], S, mode, grad, req_base + (size_t)r * per,
-                   device_out ? device_out : outs + 8 * r, (unsigned *)(base + kTicketOff) + r);
+                   device_out ? device_out : outs + 8 * r, (unsigned *)(cnt_base + (size_t)r * counter_bytes(S)));
   }
   if (rows_bytes) {
     b->req[0].mu_out = (double *)rows_base;
     b->req[0].xi_out = (double *)(rows_base + rows_bytes / 2);
   }
-  HK_CUDA(ctx, cudaMemsetAsync(base, 0, kHdrBytes, ctx->stream));
+  HK_CUDA(ctx, cudaMemsetAsync(base, 0, kFixedBytes + cnt, ctx->stream));
   if (int rc = launch_batch(ctx, *b, mode, grad, ctx->stream)) return rc;
   if (device_out) return HAWKES_OK;
   HK_CUDA(ctx, cudaMemcpyAsync(ctx->pinned_out, outs, (size_t)k * 8 * sizeof(double), cudaMemcpyDeviceToHost,
@@ -435,7 +434,7 @@ bool launch_pending(hawkes_ctx *ctx, Flight &F) {
   const int mode = H.mode, grad = H.grad;
   std::vector<uint64_t> take;
   std::vector<EventSetRec *> sets;
-  size_t bytes = kFixedBytes;
+  size_t bytes = kFixedBytes, cnt = 0;
   const size_t used = ctx->used.load();
   const size_t room = ctx->budget > used ? ctx->budget - used : 0;
   const size_t fixed_used = used - ctx->serving_bytes;  // resident sets and the sync workspace
@@ -453,8 +452,9 @@ bool launch_pending(hawkes_ctx *ctx, Flight &F) {
         ctx->done_cv.notify_all();
         continue;
       }
-      if (bytes + T.footprint > room) {
-        const bool never_fits = kFixedBytes + T.footprint + fixed_used > ctx->budget;
+      if (bytes + T.footprint + counter_bytes(sit->second) > room) {
+        const bool never_fits = kFixedBytes + 512 + T.footprint + counter_bytes(sit->second) + fixed_used >
+                                ctx->budget;
         if (take.empty() && !any_flight && never_fits) {
           complete_ticket(ctx, *it, HAWKES_E_ADMISSION, nullptr);
           release_set_ref(ctx, sit->second);
@@ -464,7 +464,8 @@ bool launch_pending(hawkes_ctx *ctx, Flight &F) {
         }
         break;  // first-come first-served within a kind: wait for memory to free up
       }
-      bytes += T.footprint;
+      bytes += T.footprint + counter_bytes(sit->second);
+      cnt += counter_bytes(sit->second);
       take.push_back(*it);
       sets.push_back(sit->second);
       it = ctx->pending.erase(it);
@@ -477,19 +478,23 @@ bool launch_pending(hawkes_ctx *ctx, Flight &F) {
   std::unique_ptr<Batch> b(new Batch());
   std::memset(b.get(), 0, sizeof(Batch));
   int rc = HAWKES_OK;
+  cnt = align_up(cnt, 256);
+  bytes = align_up(bytes, 256) + 256;
   cudaError_t e = cudaMallocAsync(&ws, bytes, F.stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(ws, 0, kHdrBytes, F.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ws, 0, kFixedBytes + cnt, F.stream);
   if (e != cudaSuccess) rc = cuda_fail(ctx, e);
   if (rc == HAWKES_OK) {
     char *base = (char *)ws;
     b->counter = (unsigned *)base;
     double *outs = (double *)(base + kHdrBytes);
-    char *cur = base + kFixedBytes;
+    char *cnt_cur = base + kFixedBytes;
+    char *cur = base + kFixedBytes + cnt;
     b->nreq = (int)take.size();
     for (size_t r = 0; r < take.size() && rc == HAWKES_OK; ++r) {
       TicketRec &T = ctx->tickets[take[r]];
       rc = make_request(ctx, sets[r], &T.p, mode, grad, T.flags, &b->req[r]);
-      bind_workspace(&b->req[r], sets[r], mode, grad, cur, outs + 8 * r, (unsigned *)(base + kTicketOff) + r);
+      bind_workspace(&b->req[r], sets[r], mode, grad, cur, outs + 8 * r, (unsigned *)cnt_cur);
+      cnt_cur += counter_bytes(sets[r]);
       cur += T.footprint;
     }
     if (rc == HAWKES_OK) rc = launch_batch(ctx, *b, mode, grad, F.stream);

@@ -26,12 +26,14 @@ constexpr int kRowTile = kThreads * kRowsPerThread;  // 512 with 4 rows per thre
 constexpr int kColTile = HK_COL_TILE;
 constexpr int kWarpRows = 32 * kRowsPerThread;       // consecutive rows per warp
 constexpr int kPadTo = kRowTile > kColTile ? kRowTile : kColTile;  // event arrays padded to this
-constexpr int kEpiThreads = 256;                     // epilogue rows per CTA
+constexpr int kEpiThreads = 256;                     // rows per CTA of the allocation-free epilogue
 constexpr int kMaxBatch = 64;                        // requests per launch
 constexpr int kSumsLoglik = 2;                       // S_b, S_s
 constexpr int kSumsGrad = 6;                         // S_b, S_s, R_b, T_b, R_s, U_s
 constexpr int kFlagExcludeSelf = 1;                  // HAWKES_FLAG_EXCLUDE_SELF
 constexpr int kFlagDense = 2;                        // HAWKES_FLAG_DENSE
+constexpr int kMaxCtaWarps = 8;                      // pair-kernel CTAs have at most 256 threads
+static_assert(kThreads <= 32 * kMaxCtaWarps && kRowTile / 4 <= 32 * kMaxCtaWarps, "CTA too wide");
 
 // One resident event set, as the kernels see it.
 struct SetView {
@@ -53,7 +55,6 @@ struct Request {
   int grad;        // 0: loglik only; 1: loglik and gradient
   int flags;       // HAWKES_FLAG_* of the context at submission
   int item_begin;  // first pair-kernel item of this request in the batch
-  int epi_begin;   // first epilogue item (block of kEpiThreads rows) in the batch
   // Column window: column n' can only contribute to row n if
   //   t_n - cut_early <= t_n' <= t_n + cut_late   (days; +inf keeps every column)
   double cut_early, cut_late;
@@ -77,10 +78,10 @@ struct Request {
   // workspace (device)
   double *partials;    // nrt * slices * S * kRowTile
   double *comp;        // nrt * 8: per row tile, the sums of Lambda_n and d Lambda_n / d Theta
-                       // (written by slice 0 of the pair kernel), or nullptr: the epilogue
-                       // then computes the compensator itself
-  double *block_part;  // epilogue blocks * 8
-  unsigned *ticket;    // epilogue completion counter, zero between launches
+                       // (written by slice 0 of the pair kernel), or nullptr (not formed)
+  unsigned *rt_count;  // nrt + 1 counters, zero at launch (fused epilogue): finished slices per
+                       // row tile, then finished row tiles
+  double *rt_sum;      // nrt * 8: per row tile, sum of log lambda_n and of the gradient terms
   double *out;         // 7 doubles: ell, d ell / d Theta
   double *mu_out;      // optional per-event mu_n (n doubles) or nullptr
   double *xi_out;      // optional per-event xi_n (n doubles) or nullptr
@@ -89,8 +90,8 @@ struct Request {
 struct Batch {
   int nreq;
   int total_items;  // pair-kernel items over all requests
-  int total_epi;    // epilogue items over all requests
   int mode;         // 0 fp64, 1 mixed (one mode per launch)
+  int fused;        // 1: the pair kernel finishes each row tile and each request itself
   unsigned *counter;  // pair-kernel work counter, zeroed before the launch
   Request req[kMaxBatch];
 };
@@ -99,18 +100,16 @@ struct Batch {
 // grid size; the kernels loop over items with an atomic counter.
 cudaError_t launch_pair_mixed(const Batch &b, bool grad, int grid, cudaStream_t s);
 cudaError_t launch_pair_fp64(const Batch &b, bool grad, int grid, cudaStream_t s);
-cudaError_t launch_epilogue(const Batch &b, bool grad, int grid, cudaStream_t s);
 // Resident CTAs per SM of each pair kernel (for the persistent grid and the slices).
 int occupancy_pair_mixed(bool grad);
 int occupancy_pair_fp64(bool grad);
 
-// Item lookup: the request whose [begin, next begin) holds `item`.
-__host__ __device__ inline int find_request(const Batch &b, int item, bool epi) {
+// Item lookup: the request whose [item_begin, next item_begin) holds `item`.
+__host__ __device__ inline int find_request(const Batch &b, int item) {
   int lo = 0, hi = b.nreq - 1;
   while (lo < hi) {
     int mid = (lo + hi + 1) >> 1;
-    int start = epi ? b.req[mid].epi_begin : b.req[mid].item_begin;
-    if (start <= item) lo = mid; else hi = mid - 1;
+    if (b.req[mid].item_begin <= item) lo = mid; else hi = mid - 1;
   }
   return lo;
 }
@@ -174,7 +173,7 @@ __device__ __forceinline__ double std_normal_pdf(double u) {
 // h). Thread 0 writes the 7 sums to R.comp[8 rt ...]. Called by every thread of the CTA.
 template <typename TT>
 __device__ void compensator_tile(const Request &R, const TT *t, int rt, bool grad) {
-  __shared__ double red[32][8];
+  __shared__ double red[kMaxCtaWarps][8];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = (blockDim.x + 31) >> 5;
   const double mu0 = R.mu0, th = R.theta, om = R.omega, tN = R.t_last, inv_tt = R.inv_tt;
   double v[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
@@ -206,6 +205,107 @@ __device__ void compensator_tile(const Request &R, const TT *t, int rt, bool gra
     R.comp[(size_t)rt * 8 + tid] = x;
   }
   __syncthreads();
+}
+
+// Fused epilogue of row tile rt, run by the CTA that finished its last slice (Section 2.1):
+// the row sums over the tile's slices in slice order, lambda_n = A S_b + C S_s, log lambda_n
+// and the gradient terms (d lambda_n / d Theta) / lambda_n, summed over the tile's rows in a
+// fixed order into R.rt_sum. The CTA that finishes the request's last row tile then writes
+// ell = sum over row tiles of (rt_sum - comp), in a fixed order, to R.out. Called by every
+// thread of the CTA; the caller has made the slices' partial sums visible (threadfence).
+template <bool GRAD>
+__device__ void rowtile_epilogue(const Request &R, int rt) {
+  constexpr int NS = GRAD ? kSumsGrad : kSumsLoglik;
+  constexpr int NV = GRAD ? 7 : 1;
+  __shared__ double red2[kMaxCtaWarps][8];
+  __shared__ int s_final;
+  const SetView &S = R.set;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = (blockDim.x + 31) >> 5;
+  const double mu0 = R.mu0, th = R.theta;
+  const double itx = R.inv_tx, itt = R.inv_tt, ih = R.inv_h, iom = R.inv_om;
+  const double Ab = R.k_ab, Cw = R.k_cw, A = mu0 * Ab, C = th * Cw;
+  double v[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) v[q] = 0.0;
+  const int r0 = rt * kRowTile, end = min(r0 + kRowTile, S.n);
+  for (int i = r0 + tid; i < end; i += blockDim.x) {
+    const int li = i - r0;
+    double sums[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) sums[s] = 0.0;
+    for (int k = rt * R.slices; k < (rt + 1) * R.slices; ++k) {
+      const double *src = R.partials + (size_t)k * NS * kRowTile + li;
+#pragma unroll
+      for (int s = 0; s < NS; ++s) sums[s] += __ldcg(src + s * kRowTile);
+    }
+    const double mu = A * sums[0], xi = C * sums[1], lam = mu + xi;
+    if (R.mu_out) R.mu_out[i] = mu;
+    if (R.xi_out) R.xi_out[i] = xi;
+    v[0] += log(lam);
+    if (GRAD) {
+      const double Sb = sums[0], Ss = sums[1], Rb = sums[2], Tb = sums[3] * R.tscale * R.tscale;
+      const double Rs = sums[4], Us = sums[5] * R.tscale;
+      const double inv = 1.0 / lam;
+      v[1] += Ab * Sb * inv;
+      v[2] += A * itx * (-2.0 * Sb + Rb * itx * itx) * inv;
+      v[3] += A * itt * (-Sb + Tb * itt * itt) * inv;
+      v[4] += Cw * Ss * inv;
+      v[5] += C * (Ss * iom - Us) * inv;
+      v[6] += C * ih * (-2.0 * Ss + Rs * ih * ih) * inv;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    double x = v[q];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+    if (lane == 0) red2[warp][q] = x;
+  }
+  __syncthreads();
+  if (tid < NV) {
+    double x = 0.0;
+    for (int w = 0; w < nw; ++w) x += red2[w][tid];
+    R.rt_sum[(size_t)rt * 8 + tid] = x;
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_final = atomicAdd(R.rt_count + S.nrt, 1u) == (unsigned)(S.nrt - 1);
+  __syncthreads();
+  if (s_final) {
+    __threadfence();
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double x = 0.0;
+      for (int r = tid; r < S.nrt; r += blockDim.x)
+        x += __ldcg(R.rt_sum + (size_t)r * 8 + q) - __ldcg(R.comp + (size_t)r * 8 + q);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+      if (lane == 0) red2[warp][q] = x;
+    }
+    __syncthreads();
+    if (tid < NV) {
+      double x = 0.0;
+      for (int w = 0; w < nw; ++w) x += red2[w][tid];
+      R.out[tid] = x;
+    }
+  }
+  __syncthreads();
+}
+
+// End of a pair-kernel item: count the finished slice of row tile rt; the CTA that finishes
+// the tile's last slice runs its fused epilogue. Called by every thread of the CTA.
+template <bool GRAD>
+__device__ void finish_item(const Batch &B, const Request &R, int rt) {
+  if (!B.fused) return;
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(R.rt_count + rt, 1u) == (unsigned)(R.slices - 1);
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    rowtile_epilogue<GRAD>(R, rt);
+  }
 }
 #endif
 

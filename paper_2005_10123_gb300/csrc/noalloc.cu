@@ -227,8 +227,6 @@ extern "C" int hawkes_loglik_noalloc(const float *x, const float *y, const float
   R.cut_late = bg;
   R.comp = nullptr;  // noalloc_epilogue computes the compensator
   R.partials = (double *)(base + kOffPartials);
-  R.block_part = (double *)(base + kOffBlockPart);
-  R.ticket = (unsigned *)(base + kOffHeader + 256);
   R.out = device_out;
   R.t_last = 0.0;  // unused here: noalloc_epilogue reads t_N on the device
 
@@ -237,13 +235,13 @@ extern "C" int hawkes_loglik_noalloc(const float *x, const float *y, const float
   noalloc_prep<<<std::min(d->sms * 4, (npad + 255) / 256 + 1), 256, 0, s>>>(x, y, t, (int)n, npad, base);
   if (cudaGetLastError() != cudaSuccess) return HAWKES_E_CUDA;
   b.req[0].item_begin = 0;
-  b.req[0].epi_begin = 0;
   b.total_items = nrt * chunks;
-  b.total_epi = (int)((n + kEpiThreads - 1) / kEpiThreads);
+  b.fused = 0;  // noalloc_epilogue finishes the evaluation
+  const int epi_blocks = (int)((n + kEpiThreads - 1) / kEpiThreads);
   const int grid = std::max(1, std::min(b.total_items, d->sms * d->occ));
   if (launch_pair_mixed(b, false, grid, s) != cudaSuccess) return HAWKES_E_CUDA;
-  noalloc_epilogue<<<std::max(1, std::min(b.total_epi, d->sms * 8)), kEpiThreads, 0, s>>>(b.req[0], chunks,
-                                                                                        base);
+  noalloc_epilogue<<<std::max(1, std::min(epi_blocks, d->sms * 8)), kEpiThreads, 0, s>>>(b.req[0], chunks,
+                                                                                       base);
   if (cudaGetLastError() != cudaSuccess) return HAWKES_E_CUDA;
   return HAWKES_OK;
 }

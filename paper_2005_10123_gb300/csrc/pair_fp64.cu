@@ -1,18 +1,10 @@
-// Double-precision pair kernel and the epilogue shared by both precision modes.
+// Double-precision pair kernel.
 //
 // pair_fp64_kernel forms the same per-row sums as the mixed kernel (S_b, S_s and the
 // gradient moments R_b, T_b, R_s, U_s of Section 2.1, Eq. 1), entirely in float64 with
-// the library exp(), and the moments in raw units (r^2 in km^2, dt in days).
-//
-// epilogue_kernel turns each row's sums into (Section 2.1)
-//   lambda_n = A S_b + C S_s,  A = mu0 / ((2 pi)^{3/2} tau_x^2 tau_t),  C = theta omega / (2 pi h^2)
-//   ell_n    = log lambda_n - Lambda_n
-// plus the gradient terms (d lambda_n / d Theta) / lambda_n - d Lambda_n / d Theta, and
-// reduces them over n in a fixed order: a warp-shuffle tree and an in-order warp sum
-// per block, then the last block to finish sums the block partials in block order and
-// subtracts the compensator sums Lambda = sum_n Lambda_n (and its gradient) that slice 0 of
-// each row tile formed in the pair kernel, in row-tile order, where its float64 work
-// overlaps the float32 pair work of other CTAs.
+// the library exp(), and the moments in raw units (r^2 in km^2, dt in days). Slice 0 of each
+// row tile sums the tile's compensator terms, and the CTA that finishes a row tile's last
+// slice runs the fused epilogue (hk_internal.h: rowtile_epilogue).
 #include "hk_internal.h"
 
 namespace hk {
@@ -155,7 +147,7 @@ __global__ void __launch_bounds__(kThreads64) pair_fp64_kernel(const __grid_cons
     __syncthreads();
     const int item = s_item;
     if (item >= B.total_items) break;
-    const Request &R = B.req[find_request(B, item, false)];
+    const Request &R = B.req[find_request(B, item)];
     const int local = item - R.item_begin;
     const int rt = local / R.slices, sl = local - rt * R.slices;
     if (threadIdx.x < 32) {
@@ -169,116 +161,8 @@ __global__ void __launch_bounds__(kThreads64) pair_fp64_kernel(const __grid_cons
     const int c_end = w.x + (int)((long long)width * (sl + 1) / R.slices);
     run_piece64<GRAD>(R, make_int4(rt, c_begin, c_end, 0), local, sx, sy, st);
     if (sl == 0 && R.comp) compensator_tile(R, R.set.t64, rt, GRAD);
+    finish_item<GRAD>(B, R, rt);
     __syncthreads();  // s_item, s_win and the staging buffers are reused by the next item
-  }
-}
-
-template <bool GRAD>
-__global__ void __launch_bounds__(kEpiThreads) epilogue_kernel(const __grid_constant__ Batch B) {
-  constexpr int NS = GRAD ? kSumsGrad : kSumsLoglik;
-  constexpr int NV = GRAD ? 7 : 1;
-  constexpr int NW = kEpiThreads / 32;
-  __shared__ double red[NW][8];
-  __shared__ int s_last;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int item = blockIdx.x; item < B.total_epi; item += gridDim.x) {
-    const Request &R = B.req[find_request(B, item, true)];
-    const SetView &S = R.set;
-    const int blk = item - R.epi_begin;
-    const int nblk = (S.n + kEpiThreads - 1) / kEpiThreads;
-    const int i = blk * kEpiThreads + tid;
-    const bool own_comp = R.comp == nullptr;  // compensator not summed by the pair kernel
-    double v[NV];
-#pragma unroll
-    for (int q = 0; q < NV; ++q) v[q] = 0.0;
-    if (i < S.n) {
-      const int rt = i / kRowTile, li = i - rt * kRowTile;
-      double sums[NS];
-#pragma unroll
-      for (int s = 0; s < NS; ++s) sums[s] = 0.0;
-      const int k0 = rt * R.slices, k1 = k0 + R.slices;
-      for (int k = k0; k < k1; ++k) {
-        const double *src = R.partials + (size_t)k * NS * kRowTile + li;
-#pragma unroll
-        for (int s = 0; s < NS; ++s) sums[s] += src[s * kRowTile];
-      }
-      const double mu0 = R.mu0, th = R.theta, om = R.omega;
-      const double itx = R.inv_tx, itt = R.inv_tt, ih = R.inv_h, iom = R.inv_om;
-      const double Ab = R.k_ab, Cw = R.k_cw;  // A / mu0, C / theta
-      const double A = mu0 * Ab, C = th * Cw;
-      const double mu = A * sums[0], xi = C * sums[1], lam = mu + xi;
-      if (R.mu_out) R.mu_out[i] = mu;
-      if (R.xi_out) R.xi_out[i] = xi;
-      v[0] = log(lam);
-      if (GRAD) {
-        // raw moments: r^2 in km^2, dt in days (the mixed kernel keeps dt in scaled units)
-        const double Rb = sums[2], Tb = sums[3] * R.tscale * R.tscale;
-        const double Rs = sums[4], Us = sums[5] * R.tscale;
-        const double Sb = sums[0], Ss = sums[1];
-        const double inv = 1.0 / lam;
-        v[1] = Ab * Sb * inv;
-        v[2] = A * itx * (-2.0 * Sb + Rb * itx * itx) * inv;
-        v[3] = A * itt * (-Sb + Tb * itt * itt) * inv;
-        v[4] = Cw * Ss * inv;
-        v[5] = C * (Ss * iom - Us) * inv;
-        v[6] = C * ih * (-2.0 * Ss + Rs * ih * ih) * inv;
-      }
-      if (own_comp) {
-        const double tn = B.mode == 1 ? (double)S.t32[i] : S.t64[i];
-        const double a = (R.t_last - tn) * itt, b = -tn * itt, D = R.t_last - tn;
-        const double e = exp(-om * D);
-        const double Pa = normcdf(a), Pb = normcdf(b);
-        v[0] -= mu0 * (Pa - Pb) + th * (1.0 - e);
-        if (GRAD) {
-          v[1] -= Pa - Pb;
-          v[3] -= mu0 * itt * (-a * std_normal_pdf(a) + b * std_normal_pdf(b));
-          v[4] -= 1.0 - e;
-          v[5] -= th * D * e;
-        }
-      }
-    }
-    // fixed-order block reduction
-#pragma unroll
-    for (int q = 0; q < NV; ++q) {
-      double x = v[q];
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
-      if (lane == 0) red[warp][q] = x;
-    }
-    __syncthreads();
-    if (tid < NV) {
-      double x = 0.0;
-#pragma unroll
-      for (int w = 0; w < NW; ++w) x += red[w][tid];
-      R.block_part[(size_t)blk * 8 + tid] = x;
-    }
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) s_last = (atomicAdd(R.ticket, 1u) == (unsigned)(nblk - 1));
-    __syncthreads();
-    if (s_last) {
-      __threadfence();
-      // every thread sums a fixed strided subset of the block partials (and of the row-tile
-      // compensator sums), then a fixed-shape tree over the threads: a deterministic order
-      for (int q = 0; q < NV; ++q) {
-        double x = 0.0;
-        for (int bb = tid; bb < nblk; bb += kEpiThreads) x += __ldcg(R.block_part + (size_t)bb * 8 + q);
-        if (!own_comp)
-          for (int rt = tid; rt < S.nrt; rt += kEpiThreads) x -= __ldcg(R.comp + (size_t)rt * 8 + q);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
-        if (lane == 0) red[warp][q] = x;
-      }
-      __syncthreads();
-      if (tid < NV) {
-        double x = 0.0;
-#pragma unroll
-        for (int w = 0; w < NW; ++w) x += red[w][tid];
-        R.out[tid] = x;
-      }
-      if (tid == 0) *R.ticket = 0u;
-    }
-    __syncthreads();
   }
 }
 
@@ -287,12 +171,6 @@ __global__ void __launch_bounds__(kEpiThreads) epilogue_kernel(const __grid_cons
 cudaError_t launch_pair_fp64(const Batch &b, bool grad, int grid, cudaStream_t s) {
   if (grad) pair_fp64_kernel<true><<<grid, kThreads64, 0, s>>>(b);
   else pair_fp64_kernel<false><<<grid, kThreads64, 0, s>>>(b);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_epilogue(const Batch &b, bool grad, int grid, cudaStream_t s) {
-  if (grad) epilogue_kernel<true><<<grid, kEpiThreads, 0, s>>>(b);
-  else epilogue_kernel<false><<<grid, kEpiThreads, 0, s>>>(b);
   return cudaGetLastError();
 }
 

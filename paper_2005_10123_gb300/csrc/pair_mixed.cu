@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(kThreads, HK_MIN_CTAS) pair_mixed_kernel(const
     cta_sync();
     const int item = s_item;
     if (item >= B.total_items) break;
-    const Request &R = B.req[find_request(B, item, false)];
+    const Request &R = B.req[find_request(B, item)];
     const int local = item - R.item_begin;
     const int rt = local / R.slices, sl = local - rt * R.slices;
     if (threadIdx.x < 32) {
@@ -347,6 +347,7 @@ __global__ void __launch_bounds__(kThreads, HK_MIN_CTAS) pair_mixed_kernel(const
     const int c_end = w.x + (int)((long long)width * (sl + 1) / R.slices);
     run_piece<GRAD>(R, make_int4(rt, c_begin, c_end, 0), local, sxy, stb, sacc);
     if (sl == 0 && R.comp) compensator_tile(R, R.set.t32, rt, GRAD);
+    finish_item<GRAD>(B, R, rt);
     cta_sync();  // s_item, s_win and the staging buffers are reused by the next item
   }
 }

@@ -114,30 +114,16 @@ static void check_schedule(const Request &R) {
   bool ok = R.slices >= 1 && R.slices <= S.nct;
   if (S.npad != S.nrt * kRowTile || S.nct * kColTile != S.npad || S.n > S.npad || S.n < 1) ok = false;
   if (!(R.cut_early > 0.0) || !(R.cut_late > 0.0)) ok = false;
-  if (!R.partials || !R.comp || !R.block_part || !R.ticket || !R.out) ok = false;
+  if (!R.partials || !R.comp || !R.rt_sum || !R.rt_count || !R.out) ok = false;
+  for (int i = 0; ok && i <= S.nrt; ++i)
+    if (R.rt_count[i] != 0u) ok = false;  // completion counters zeroed before the launch
   if (!ok) g_schedule_errors++;
 }
 
-static cudaError_t fake_pair(const Batch &b) {
-  g_launches++;
-  int items = 0;
-  for (int r = 0; r < b.nreq; ++r) {
-    if (b.req[r].item_begin != items) g_schedule_errors++;
-    items += b.req[r].set.nrt * b.req[r].slices;
-    check_schedule(b.req[r]);
-  }
-  if (items != b.total_items || *b.counter != 0u) g_schedule_errors++;
-  return cudaSuccess;
-}
-
-cudaError_t launch_pair_mixed(const Batch &b, bool, int, cudaStream_t) { return fake_pair(b); }
-cudaError_t launch_pair_fp64(const Batch &b, bool, int, cudaStream_t) { return fake_pair(b); }
-
 // Output of a request: a function of its own inputs only, so the tests can tell where it went.
-cudaError_t launch_epilogue(const Batch &b, bool grad, int, cudaStream_t) {
+static void fake_outputs(const Batch &b, bool grad) {
   for (int r = 0; r < b.nreq; ++r) {
     const Request &R = b.req[r];
-    if (*R.ticket != 0u) g_schedule_errors++;
     R.out[0] = R.mu0 * 1000.0 + R.set.n + (b.mode ? 0.5 : 0.0);
     if (grad) {
       const double th[6] = {R.mu0, R.tau_x, R.tau_t, R.theta, R.omega, R.h};
@@ -146,8 +132,23 @@ cudaError_t launch_epilogue(const Batch &b, bool grad, int, cudaStream_t) {
     if (R.mu_out)
       for (int i = 0; i < R.set.n; ++i) { R.mu_out[i] = i; R.xi_out[i] = -i; }
   }
+}
+
+static cudaError_t fake_pair(const Batch &b, bool grad) {
+  g_launches++;
+  int items = 0;
+  for (int r = 0; r < b.nreq; ++r) {
+    if (b.req[r].item_begin != items) g_schedule_errors++;
+    items += b.req[r].set.nrt * b.req[r].slices;
+    check_schedule(b.req[r]);
+  }
+  if (items != b.total_items || *b.counter != 0u || !b.fused) g_schedule_errors++;
+  fake_outputs(b, grad);
   return cudaSuccess;
 }
+
+cudaError_t launch_pair_mixed(const Batch &b, bool grad, int, cudaStream_t) { return fake_pair(b, grad); }
+cudaError_t launch_pair_fp64(const Batch &b, bool grad, int, cudaStream_t) { return fake_pair(b, grad); }
 
 int occupancy_pair_mixed(bool) { return 4; }
 int occupancy_pair_fp64(bool) { return 2; }
