@@ -49,6 +49,8 @@ struct EventSetRec {
   double t_first32 = 0, t_last32 = 0, t_first64 = 0, t_last64 = 0;
   std::vector<float> t32h;   // host copies of the stored times (for hawkes_pair_work)
   std::vector<double> t64h;
+  WinTable win32{}, win64{};  // column-tile lookups (device pointers)
+  std::vector<int> win32h, win64h;  // host copies: first[nb] then last[nb]
   int slices[kKinds] = {1, 1, 1};  // slices per row tile, per kernel kind
   int refs = 0;  // queued or running serving requests
   bool released = false;
@@ -159,6 +161,35 @@ std::vector<int> tie_starts(const std::vector<F> &t, int64_t n, int64_t npad) {
   return lo;
 }
 
+// Column-tile lookup table of a set's stored times (see WinTable): host copy in `h` (first[nb]
+// then last[nb]) and the table's parameters in W (device pointers are set after upload). No
+// table (nb = 0) when the times span too little for buckets wider than their rounding.
+template <typename TT>
+void build_win_table(const TT *t, int64_t n, int nct, WinTable *W, std::vector<int> *h) {
+  *W = WinTable{};
+  h->clear();
+  const double t0 = (double)t[0], t1 = (double)t[n - 1], span = t1 - t0;
+  const double scale = std::max({std::fabs(t0), std::fabs(t1), 1.0});
+  if (!(span > 1e-9 * scale)) return;
+  const int nb = kWinBuckets, real = (int)((n + kColTile - 1) / kColTile);
+  const double width = span / nb;
+  std::vector<double> tile_first((size_t)real), tile_last((size_t)real);
+  for (int c = 0; c < real; ++c) {
+    tile_first[(size_t)c] = (double)t[(int64_t)c * kColTile];
+    tile_last[(size_t)c] = (double)t[std::min<int64_t>((int64_t)(c + 1) * kColTile, n) - 1];
+  }
+  h->resize((size_t)2 * nb);
+  for (int b = 0; b < nb; ++b) {
+    const double lo = t0 + b * width, hi = t0 + (b + 1) * width;
+    (*h)[(size_t)b] = (int)(std::lower_bound(tile_last.begin(), tile_last.end(), lo) - tile_last.begin());
+    (*h)[(size_t)nb + b] = (int)(std::upper_bound(tile_first.begin(), tile_first.end(), hi) - tile_first.begin());
+  }
+  (void)nct;
+  W->t0 = t0;
+  W->inv = 1.0 / width;
+  W->nb = nb;
+}
+
 // Slices per row tile for a kernel kind: enough items for about kItemsPerSlot items per
 // resident CTA, at most one column tile per slice.
 #ifndef HK_ITEMS_PER_SLOT
@@ -207,6 +238,7 @@ int make_request(hawkes_ctx *ctx, const EventSetRec *S, const hawkes_params *p, 
   R->set.x32 = S->x32; R->set.y32 = S->y32; R->set.t32 = S->t32;
   R->set.x64 = S->x64; R->set.y64 = S->y64; R->set.t64 = S->t64;
   R->set.lo32 = S->lo32; R->set.lo64 = S->lo64;
+  R->set.win32 = S->win32; R->set.win64 = S->win64;
   R->set.n = (int)S->n; R->set.npad = (int)S->npad; R->set.nrt = S->nrt; R->set.nct = S->nct;
   R->slices = S->slices[kind_of(mode, grad)];
   R->grad = grad;
@@ -240,20 +272,27 @@ int make_request(hawkes_ctx *ctx, const EventSetRec *S, const hawkes_params *p, 
 }
 
 // Device bytes one request needs: partial sums, compensator sums, row-tile sums.
+// Pair items (= partial-sum slots) of one request on S (see Request).
+size_t set_slots(const EventSetRec *S, int mode, int grad) {
+  return (size_t)S->nrt * S->slices[kind_of(mode, grad)];
+}
+
 size_t request_footprint(const EventSetRec *S, int mode, int grad) {
-  const size_t items = (size_t)S->nrt * S->slices[kind_of(mode, grad)];
+  const size_t items = set_slots(S, mode, grad);
   size_t b = align_up(items * sums_of(grad) * kRowTile * sizeof(double), 256);
   b += 2 * align_up((size_t)S->nrt * 8 * sizeof(double), 256);
   return b;
 }
 
-// Bytes of a request's completion counters (nrt + 1 unsigned), kept in one zeroed region per
-// batch (see batch_counter_bytes).
-size_t counter_bytes(const EventSetRec *S) { return align_up(((size_t)S->nrt + 1) * sizeof(unsigned), 64); }
+// Bytes of a request's completion counters (the merge-tree nodes of its row tiles and one
+// final counter, see Request::rt_count), kept in one zeroed region per batch.
+size_t counter_bytes(const EventSetRec *S, int mode, int grad) {
+  return align_up((2 * set_slots(S, mode, grad) + 1) * sizeof(unsigned), 64);
+}
 
-// Batch workspace header: the pair-kernel work counter at byte 0, then the per-request outputs
-// (8 doubles each), then every request's completion counters. One memset of the header and
-// the counters (kFixedBytes + the batch's counter bytes) zeroes everything that must start at 0.
+// Batch workspace: a 256-byte header (unused, keeps the outputs aligned), the per-request
+// outputs (8 doubles each), then every request's completion counters. One memset of these
+// (kFixedBytes + the batch's counter bytes) zeroes everything that must start at 0.
 constexpr size_t kHdrBytes = 256;
 constexpr size_t kOutBytes = (size_t)kMaxBatch * 8 * sizeof(double);
 constexpr size_t kFixedBytes = kHdrBytes + kOutBytes;
@@ -261,7 +300,7 @@ constexpr size_t kFixedBytes = kHdrBytes + kOutBytes;
 // Carve one request's workspace out of `base` (as sized by request_footprint).
 void bind_workspace(Request *R, const EventSetRec *S, int mode, int grad, char *base, double *out,
                     unsigned *counters) {
-  const size_t items = (size_t)S->nrt * S->slices[kind_of(mode, grad)];
+  const size_t items = set_slots(S, mode, grad);
   size_t off = 0;
   R->partials = (double *)(base + off);
   off += align_up(items * sums_of(grad) * kRowTile * sizeof(double), 256);
@@ -272,26 +311,21 @@ void bind_workspace(Request *R, const EventSetRec *S, int mode, int grad, char *
   R->out = out;
 }
 
-int pair_grid(hawkes_ctx *ctx, int mode, int grad, int total_items) {
-  const int cap = ctx->sms * std::max(1, ctx->occ_launch[mode == HAWKES_MIXED ? 1 : 0][grad]);
-  return std::max(1, std::min(total_items, cap));
-}
-
-// Enqueue the persistent pair kernel for a prepared batch on `s`; it finishes every row tile
-// and every request itself (fused epilogue). The work counter and every request's completion
-// counters must already be zero (the caller clears them with one memset).
+// Enqueue the pair kernel (one CTA per item) for a prepared batch on `s`; it finishes every
+// row tile and every request itself (fused epilogue). Every request's completion counters
+// must already be zero (the caller clears them with one memset).
 int launch_batch(hawkes_ctx *ctx, Batch &b, int mode, int grad, cudaStream_t s) {
   b.mode = mode == HAWKES_MIXED ? 1 : 0;
   b.fused = 1;
-  int items = 0;
+  long long items = 0;
   for (int r = 0; r < b.nreq; ++r) {
-    b.req[r].item_begin = items;
-    items += b.req[r].set.nrt * b.req[r].slices;
+    b.req[r].item_begin = (int)items;
+    items += request_items(b.req[r]);
   }
-  b.total_items = items;
-  const int grid = pair_grid(ctx, mode, grad, items);
-  if (mode == HAWKES_MIXED) HK_CUDA(ctx, launch_pair_mixed(b, grad != 0, grid, s));
-  else HK_CUDA(ctx, launch_pair_fp64(b, grad != 0, grid, s));
+  if (items > 0x7fffffffLL) return HAWKES_E_INVAL;
+  b.total_items = (int)items;
+  if (mode == HAWKES_MIXED) HK_CUDA(ctx, launch_pair_mixed(b, grad != 0, s));
+  else HK_CUDA(ctx, launch_pair_fp64(b, grad != 0, s));
   return HAWKES_OK;
 }
 
@@ -342,14 +376,13 @@ int eval_sync(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_params *param
   if (!S) return HAWKES_E_NOSET;
   const size_t per = request_footprint(S, mode, grad);
   const size_t rows_bytes = (mu_out || xi_out) ? align_up((size_t)S->n * sizeof(double), 256) * 2 : 0;
-  const size_t cnt = align_up(counter_bytes(S) * k, 256);
+  const size_t cnt = align_up(counter_bytes(S, mode, grad) * k, 256);
   const size_t need = kFixedBytes + cnt + rows_bytes + per * k;
   if (int rc = ensure_sync_ws(ctx, need)) return rc;
   char *base = (char *)ctx->sync_ws.dev;
   std::unique_ptr<Batch> b(new Batch());
   std::memset(b.get(), 0, sizeof(Batch));
   b->nreq = k;
-  b->counter = (unsigned *)base;
   double *outs = (double *)(base + kHdrBytes);
   char *cnt_base = base + kFixedBytes;
   char *rows_base = cnt_base + cnt;
@@ -357,7 +390,7 @@ int eval_sync(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_params *param
   for (int r = 0; r < k; ++r) {
     if (int rc = make_request(ctx, S, &params[r], mode, grad, ctx->flags, &b->req[r])) return rc;
     bind_workspace(&b->req[r], S, mode, grad, req_base + (size_t)r * per,
-                   device_out ? device_out : outs + 8 * r, (unsigned *)(cnt_base + (size_t)r * counter_bytes(S)));
+                   device_out ? device_out : outs + 8 * r, (unsigned *)(cnt_base + (size_t)r * counter_bytes(S, mode, grad)));
   }
   if (rows_bytes) {
     b->req[0].mu_out = (double *)rows_base;
@@ -452,8 +485,8 @@ bool launch_pending(hawkes_ctx *ctx, Flight &F) {
         ctx->done_cv.notify_all();
         continue;
       }
-      if (bytes + T.footprint + counter_bytes(sit->second) > room) {
-        const bool never_fits = kFixedBytes + 512 + T.footprint + counter_bytes(sit->second) + fixed_used >
+      if (bytes + T.footprint + counter_bytes(sit->second, mode, grad) > room) {
+        const bool never_fits = kFixedBytes + 512 + T.footprint + counter_bytes(sit->second, mode, grad) + fixed_used >
                                 ctx->budget;
         if (take.empty() && !any_flight && never_fits) {
           complete_ticket(ctx, *it, HAWKES_E_ADMISSION, nullptr);
@@ -464,8 +497,8 @@ bool launch_pending(hawkes_ctx *ctx, Flight &F) {
         }
         break;  // first-come first-served within a kind: wait for memory to free up
       }
-      bytes += T.footprint + counter_bytes(sit->second);
-      cnt += counter_bytes(sit->second);
+      bytes += T.footprint + counter_bytes(sit->second, mode, grad);
+      cnt += counter_bytes(sit->second, mode, grad);
       take.push_back(*it);
       sets.push_back(sit->second);
       it = ctx->pending.erase(it);
@@ -485,7 +518,6 @@ bool launch_pending(hawkes_ctx *ctx, Flight &F) {
   if (e != cudaSuccess) rc = cuda_fail(ctx, e);
   if (rc == HAWKES_OK) {
     char *base = (char *)ws;
-    b->counter = (unsigned *)base;
     double *outs = (double *)(base + kHdrBytes);
     char *cnt_cur = base + kFixedBytes;
     char *cur = base + kFixedBytes + cnt;
@@ -494,7 +526,7 @@ bool launch_pending(hawkes_ctx *ctx, Flight &F) {
       TicketRec &T = ctx->tickets[take[r]];
       rc = make_request(ctx, sets[r], &T.p, mode, grad, T.flags, &b->req[r]);
       bind_workspace(&b->req[r], sets[r], mode, grad, cur, outs + 8 * r, (unsigned *)cnt_cur);
-      cnt_cur += counter_bytes(sets[r]);
+      cnt_cur += counter_bytes(sets[r], mode, grad);
       cur += T.footprint;
     }
     if (rc == HAWKES_OK) rc = launch_batch(ctx, *b, mode, grad, F.stream);
@@ -696,6 +728,8 @@ int hawkes_upload_events(hawkes_ctx *ctx, const double *x, const double *y, cons
   S->t64h.assign(T64.begin(), T64.begin() + n);
   S->t_first32 = T32[0]; S->t_last32 = T32[(size_t)n - 1];
   S->t_first64 = T64[0]; S->t_last64 = T64[(size_t)n - 1];
+  build_win_table(T32.data(), n, S->nct, &S->win32, &S->win32h);
+  build_win_table(T64.data(), n, S->nct, &S->win64, &S->win64h);
   for (int k = 0; k < kKinds; ++k) S->slices[k] = slices_for(S->nrt, S->nct, ctx->sms * ctx->occ[k]);
   // one device allocation
   size_t off = 0;
@@ -703,6 +737,7 @@ int hawkes_upload_events(hawkes_ctx *ctx, const double *x, const double *y, cons
   const size_t o_x32 = take(npad * 4), o_y32 = take(npad * 4), o_t32 = take(npad * 4);
   const size_t o_x64 = take(npad * 8), o_y64 = take(npad * 8), o_t64 = take(npad * 8);
   const size_t o_lo32 = take(npad * 4), o_lo64 = take(npad * 4);
+  const size_t o_w32 = take(S->win32h.size() * 4), o_w64 = take(S->win64h.size() * 4);
   const size_t bytes = off;
   std::lock_guard<std::mutex> lock(ctx->mu);
   if (ctx->used.load() + bytes > ctx->budget) return HAWKES_E_ADMISSION;
@@ -715,6 +750,8 @@ int hawkes_upload_events(hawkes_ctx *ctx, const double *x, const double *y, cons
   put(o_x32, X32.data(), npad * 4); put(o_y32, Y32.data(), npad * 4); put(o_t32, T32.data(), npad * 4);
   put(o_x64, X64.data(), npad * 8); put(o_y64, Y64.data(), npad * 8); put(o_t64, T64.data(), npad * 8);
   put(o_lo32, lo32.data(), npad * 4); put(o_lo64, lo64.data(), npad * 4);
+  if (!S->win32h.empty()) put(o_w32, S->win32h.data(), S->win32h.size() * 4);
+  if (!S->win64h.empty()) put(o_w64, S->win64h.data(), S->win64h.size() * 4);
   e = cudaMemcpyAsync(dev, host.data(), bytes, cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) { cudaFree(dev); return cuda_fail(ctx, e); }
@@ -723,6 +760,8 @@ int hawkes_upload_events(hawkes_ctx *ctx, const double *x, const double *y, cons
   S->x32 = (float *)(d + o_x32); S->y32 = (float *)(d + o_y32); S->t32 = (float *)(d + o_t32);
   S->x64 = (double *)(d + o_x64); S->y64 = (double *)(d + o_y64); S->t64 = (double *)(d + o_t64);
   S->lo32 = (int *)(d + o_lo32); S->lo64 = (int *)(d + o_lo64);
+  if (S->win32.nb) { S->win32.first = (int *)(d + o_w32); S->win32.last = S->win32.first + S->win32.nb; }
+  if (S->win64.nb) { S->win64.first = (int *)(d + o_w64); S->win64.last = S->win64.first + S->win64.nb; }
   ctx->used += bytes;
   const int32_t id = ctx->next_set++;
   S->id = id;
@@ -779,10 +818,17 @@ int hawkes_pair_work(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *param
     trig_reach = 805.0 / params->omega;
   }
   int64_t visited = 0, bg_pairs = 0, trig_pairs = 0;
-  for (int rt = 0; rt < S->nrt; ++rt) {  // the window of column_window() in the kernels
+  WinTable W = mode == HAWKES_MIXED ? S->win32 : S->win64;  // host copy of the kernels' table
+  const std::vector<int> &wh = mode == HAWKES_MIXED ? S->win32h : S->win64h;
+  if (W.nb) { W.first = wh.data(); W.last = wh.data() + W.nb; }
+  for (int rt = 0; rt < S->nrt; ++rt) {  // the window the kernels use (table_window_rt)
     const int64_t r0 = (int64_t)rt * kRowTile, r1 = std::min<int64_t>(r0 + kRowTile, n) - 1;
     int c0 = 0, c1 = S->nct;
-    if (!(ctx->flags & HAWKES_FLAG_DENSE)) {
+    if (!(ctx->flags & HAWKES_FLAG_DENSE) && W.nb) {
+      const int2 w = table_window(W, (int)n, S->nct, t[(size_t)r0] - R.cut_early, t[(size_t)r1] + R.cut_late);
+      c0 = w.x;
+      c1 = w.y;
+    } else if (!(ctx->flags & HAWKES_FLAG_DENSE)) {
       const int64_t j0 = std::lower_bound(t.begin(), t.end(), t[(size_t)r0] - R.cut_early) - t.begin();
       const int64_t j1 = std::upper_bound(t.begin(), t.end(), t[(size_t)r1] + R.cut_late) - t.begin();
       c0 = (int)(j0 / kColTile);

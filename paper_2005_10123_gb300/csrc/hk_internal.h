@@ -2,6 +2,7 @@
 // Not part of the public ABI (include/hawkes.h is).
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -35,20 +36,50 @@ constexpr int kFlagDense = 2;                        // HAWKES_FLAG_DENSE
 constexpr int kMaxCtaWarps = 8;                      // pair-kernel CTAs have at most 256 threads
 static_assert(kThreads <= 32 * kMaxCtaWarps && kRowTile / 4 <= 32 * kMaxCtaWarps, "CTA too wide");
 
+// Column-tile lookup by time, built once per event set and precision: time is cut into nb
+// equal buckets, bucket b = [t0 + b / inv, t0 + (b + 1) / inv). first[b] counts the column
+// tiles whose latest time lies below the start of bucket b, last[b] the column tiles whose
+// earliest time is at most the end of bucket b. A column window [tau0, tau1] in time then maps
+// to a superset of its column tiles with two table reads (see table_window).
+struct WinTable {
+  const int *first, *last;
+  double t0, inv;
+  int nb;  // 0: no table
+};
+constexpr int kWinBuckets = 4096;
+
 // One resident event set, as the kernels see it.
 struct SetView {
   const float *x32, *y32, *t32;
   const double *x64, *y64, *t64;
   const int *lo32, *lo64;  // lo[i] = first index with the same stored time as event i
+  WinTable win32, win64;   // column-tile lookups over the float32 and float64 times
   int n, npad, nrt, nct;   // events, padded length, row tiles, column tiles
 };
 
-// Work decomposition: item = (row tile rt, slice s), s < slices. For each request the
-// pair kernel finds the window of column tiles of rt that can hold a nonzero pair term
-// (every other pair term is exactly zero at the working precision, see cut_early and
-// cut_late) and gives slice s the s-th of `slices` near-equal parts of that window. The
-// item index rt * slices + s is also the partial-sum slot, so results do not depend on
-// which CTA ran which item.
+// Column tiles [x, y) that hold every column with time in [tau0, tau1] (a superset by at most
+// the columns of two buckets on each side; columns outside the exact range only add exact
+// zeros). One bucket of margin on each side absorbs the rounding of the bucket index.
+__host__ __device__ inline int2 table_window(const WinTable &W, int n, int nct, double tau0, double tau1) {
+  const int real = (n + kColTile - 1) / kColTile;  // column tiles holding real events
+  int c0 = 0, c1 = real;
+  const double u0 = (tau0 - W.t0) * W.inv, u1 = (tau1 - W.t0) * W.inv;
+  if (u0 >= 1.0) {
+    const double b = floor(u0) - 1.0;
+    c0 = W.first[b >= (double)(W.nb - 1) ? W.nb - 1 : (int)b];
+  }
+  if (u1 < (double)(W.nb - 1)) c1 = W.last[u1 < 0.0 ? 0 : (int)floor(u1) + 1];
+  c1 = c1 < nct ? c1 : nct;
+  return make_int2(c0, c1 > c0 + 1 ? c1 : c0 + 1);
+}
+
+// Work decomposition: the pair kernels run one CTA per item. A request's items are first
+// one compensator item per row tile (when comp is set), then the pair items (row tile rt,
+// slice s), s < slices, numbered rt * slices + s. For a pair item the kernel finds the window
+// of column tiles of rt that can hold a nonzero pair term (every other pair term is exactly
+// zero at the working precision, see cut_early and cut_late) and gives slice s the s-th of
+// `slices` near-equal parts of that window. The pair item's number is also its partial-sum
+// slot, so results do not depend on which CTA ran which item or when.
 struct Request {
   SetView set;
   int slices;      // slices per row tile (fixed per set and kernel kind)
@@ -76,11 +107,12 @@ struct Request {
   double k_cw;    // C / theta = omega / (2 pi h^2)
   double inv_tx, inv_tt, inv_h, inv_om;
   // workspace (device)
-  double *partials;    // nrt * slices * S * kRowTile
+  double *partials;    // one slot of S * kRowTile float64 row sums per pair item
   double *comp;        // nrt * 8: per row tile, the sums of Lambda_n and d Lambda_n / d Theta
-                       // (written by slice 0 of the pair kernel), or nullptr (not formed)
-  unsigned *rt_count;  // nrt + 1 counters, zero at launch (fused epilogue): finished slices per
-                       // row tile, then finished row tiles
+                       // (written by the compensator items), or nullptr (not formed)
+  unsigned *rt_count;  // request_counters(R) counters, zero at launch (fused epilogue): the
+                       // merge-tree nodes of every row tile (2 slices from 2 rt slices), then
+                       // the finished row-tile epilogues and compensator items
   double *rt_sum;      // nrt * 8: per row tile, sum of log lambda_n and of the gradient terms
   double *out;         // 7 doubles: ell, d ell / d Theta
   double *mu_out;      // optional per-event mu_n (n doubles) or nullptr
@@ -89,18 +121,27 @@ struct Request {
 
 struct Batch {
   int nreq;
-  int total_items;  // pair-kernel items over all requests
+  int total_items;  // pair-kernel items (= CTAs) over all requests
   int mode;         // 0 fp64, 1 mixed (one mode per launch)
   int fused;        // 1: the pair kernel finishes each row tile and each request itself
-  unsigned *counter;  // pair-kernel work counter, zeroed before the launch
   Request req[kMaxBatch];
 };
 
-// Launchers (defined in the kernel translation units). grid is the persistent
-// grid size; the kernels loop over items with an atomic counter.
-cudaError_t launch_pair_mixed(const Batch &b, bool grad, int grid, cudaStream_t s);
-cudaError_t launch_pair_fp64(const Batch &b, bool grad, int grid, cudaStream_t s);
-// Resident CTAs per SM of each pair kernel (for the persistent grid and the slices).
+// Items of one request (see Request): compensator items first, then pair items.
+__host__ __device__ inline int comp_items(const Request &R) { return R.comp ? R.set.nrt : 0; }
+__host__ __device__ inline int pair_items(const Request &R) { return R.set.nrt * R.slices; }
+__host__ __device__ inline int request_items(const Request &R) { return comp_items(R) + pair_items(R); }
+__host__ __device__ inline int request_counters(const Request &R) { return 2 * pair_items(R) + 1; }
+// Row tile and slice of pair item `slot`.
+__host__ __device__ inline int2 slot_tile(const Request &R, int slot) {
+  return make_int2(slot / R.slices, slot % R.slices);
+}
+
+// Launchers (defined in the kernel translation units): one CTA per item, grid =
+// b.total_items.
+cudaError_t launch_pair_mixed(const Batch &b, bool grad, cudaStream_t s);
+cudaError_t launch_pair_fp64(const Batch &b, bool grad, cudaStream_t s);
+// Resident CTAs per SM of each pair kernel (sets the number of slices).
 int occupancy_pair_mixed(bool grad);
 int occupancy_pair_fp64(bool grad);
 
@@ -163,6 +204,18 @@ __device__ inline int2 column_window(const Request &R, const TT *t, int rt) {
   return make_int2(c0, max(c1, c0 + 1));
 }
 
+// Column window of row tile rt from the set's lookup table W over times t: every thread of
+// the CTA gets the same window without a search or a barrier. (-1, -1) when the set has no
+// table (the caller then runs column_window).
+template <typename TT>
+__device__ inline int2 table_window_rt(const Request &R, const WinTable &W, const TT *t, int rt) {
+  const SetView &S = R.set;
+  if (R.flags & kFlagDense) return make_int2(0, S.nct);
+  if (W.nb == 0) return make_int2(-1, -1);
+  const int r0 = rt * kRowTile, r1 = min(r0 + kRowTile, S.n) - 1;
+  return table_window(W, S.n, S.nct, (double)__ldg(t + r0) - R.cut_early, (double)__ldg(t + r1) + R.cut_late);
+}
+
 __device__ __forceinline__ double std_normal_pdf(double u) {
   return exp(-0.5 * u * u) * 0.39894228040143267794;  // 1 / sqrt(2 pi)
 }
@@ -170,7 +223,9 @@ __device__ __forceinline__ double std_normal_pdf(double u) {
 // Compensator of Section 2.1 for the rows of row tile rt, summed in a fixed order over the
 // CTA: Lambda_n = mu0 (Phi((t_N - t_n)/tau_t) - Phi(-t_n/tau_t)) + theta (1 - e^{-omega (t_N -
 // t_n)}) and, with `grad`, its derivatives with respect to (mu0, tau_x, tau_t, theta, omega,
-// h). Thread 0 writes the 7 sums to R.comp[8 rt ...]. Called by every thread of the CTA.
+// h). Thread 0 writes the 7 sums to R.comp[8 rt ...]. Called by every thread of the CTA of a
+// compensator item; these items come first in a request, so their float64 work overlaps the
+// pair items instead of ending the launch.
 template <typename TT>
 __device__ void compensator_tile(const Request &R, const TT *t, int rt, bool grad) {
   __shared__ double red[kMaxCtaWarps][8];
@@ -207,53 +262,111 @@ __device__ void compensator_tile(const Request &R, const TT *t, int rt, bool gra
   __syncthreads();
 }
 
-// Fused epilogue of row tile rt, run by the CTA that finished its last slice (Section 2.1):
-// the row sums over the tile's slices in slice order, lambda_n = A S_b + C S_s, log lambda_n
-// and the gradient terms (d lambda_n / d Theta) / lambda_n, summed over the tile's rows in a
-// fixed order into R.rt_sum. The CTA that finishes the request's last row tile then writes
-// ell = sum over row tiles of (rt_sum - comp), in a fixed order, to R.out. Called by every
-// thread of the CTA; the caller has made the slices' partial sums visible (threadfence).
+// Count one finished row-tile epilogue or compensator item of request R; the CTA that
+// finishes the last of them writes ell = sum over row tiles of (rt_sum - comp) and the
+// gradient, in a fixed order, to R.out. Called by every thread of the CTA after its results
+// are written.
 template <bool GRAD>
-__device__ void rowtile_epilogue(const Request &R, int rt) {
-  constexpr int NS = GRAD ? kSumsGrad : kSumsLoglik;
+__device__ void finish_request(const Request &R) {
   constexpr int NV = GRAD ? 7 : 1;
-  __shared__ double red2[kMaxCtaWarps][8];
+  __shared__ double red3[kMaxCtaWarps][8];
   __shared__ int s_final;
   const SetView &S = R.set;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = (blockDim.x + 31) >> 5;
-  const double mu0 = R.mu0, th = R.theta;
-  const double itx = R.inv_tx, itt = R.inv_tt, ih = R.inv_h, iom = R.inv_om;
-  const double Ab = R.k_ab, Cw = R.k_cw, A = mu0 * Ab, C = th * Cw;
-  double v[NV];
+  const unsigned parts = (unsigned)(S.nrt + comp_items(R));
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_final = atomicAdd(R.rt_count + 2 * pair_items(R), 1u) == parts - 1u;
+  __syncthreads();
+  if (s_final) {
+    __threadfence();
 #pragma unroll
-  for (int q = 0; q < NV; ++q) v[q] = 0.0;
-  const int r0 = rt * kRowTile, end = min(r0 + kRowTile, S.n);
-  for (int i = r0 + tid; i < end; i += blockDim.x) {
-    const int li = i - r0;
-    double sums[NS];
+    for (int q = 0; q < NV; ++q) {
+      double x = 0.0;
+      for (int r = tid; r < S.nrt; r += blockDim.x) {
+        x += __ldcg(R.rt_sum + (size_t)r * 8 + q);
+        if (R.comp) x -= __ldcg(R.comp + (size_t)r * 8 + q);
+      }
 #pragma unroll
-    for (int s = 0; s < NS; ++s) sums[s] = 0.0;
-    for (int k = rt * R.slices; k < (rt + 1) * R.slices; ++k) {
-      const double *src = R.partials + (size_t)k * NS * kRowTile + li;
-#pragma unroll
-      for (int s = 0; s < NS; ++s) sums[s] += __ldcg(src + s * kRowTile);
+      for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+      if (lane == 0) red3[warp][q] = x;
     }
-    const double mu = A * sums[0], xi = C * sums[1], lam = mu + xi;
-    if (R.mu_out) R.mu_out[i] = mu;
-    if (R.xi_out) R.xi_out[i] = xi;
-    v[0] += log(lam);
-    if (GRAD) {
-      const double Sb = sums[0], Ss = sums[1], Rb = sums[2], Tb = sums[3] * R.tscale * R.tscale;
-      const double Rs = sums[4], Us = sums[5] * R.tscale;
-      const double inv = 1.0 / lam;
-      v[1] += Ab * Sb * inv;
-      v[2] += A * itx * (-2.0 * Sb + Rb * itx * itx) * inv;
-      v[3] += A * itt * (-Sb + Tb * itt * itt) * inv;
-      v[4] += Cw * Ss * inv;
-      v[5] += C * (Ss * iom - Us) * inv;
-      v[6] += C * ih * (-2.0 * Ss + Rs * ih * ih) * inv;
+    __syncthreads();
+    if (tid < NV) {
+      double x = 0.0;
+      for (int w = 0; w < nw; ++w) x += red3[w][tid];
+      R.out[tid] = x;
     }
   }
+  __syncthreads();
+}
+
+// Merge tree of row tile rt's slices (fused epilogue). Slice sl stores its partial row sums
+// in its slot and climbs a binary tree over the tile's K slices: at each node whose sibling
+// subtree exists, the CTA stores its current sums, counts its arrival, and stops if it is
+// first; the second to arrive adds the sibling's stored sums to its own and climbs on. A node's
+// value is left + right whichever side arrives second (floating-point addition commutes), so
+// the sums do not depend on the order in which slices finish. Returns true in the one CTA that
+// completes the root: it then holds the tile's full row sums. store(slot) writes the CTA's
+// current sums to a slot, merge(slot) adds a slot's sums to them (reading through L2). Called
+// by every thread of the CTA.
+template <class Store, class Merge>
+__device__ bool merge_tree(const Request &R, int rt, int sl, Store store, Merge merge) {
+  __shared__ int s_go;
+  const int K = R.slices, first = rt * R.slices;
+  unsigned *cnt = R.rt_count + 2 * first;
+  int node = sl, width = 1, off = 0;
+  while (width < K) {
+    const int parent = node >> 1, sib = node ^ 1;
+    if (sib * width < K) {  // the sibling subtree exists
+      store(first + node * width);
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) s_go = atomicAdd(cnt + off + parent, 1u) == 1u;
+      __syncthreads();
+      if (!s_go) return false;
+      __threadfence();
+      merge(first + sib * width);
+      __syncthreads();
+    }
+    off += (K + 2 * width - 1) / (2 * width);  // nodes at the parent's level
+    node = parent;
+    width <<= 1;
+  }
+  return true;
+}
+
+// Log-intensity and gradient terms of event i from its row sums (Section 2.1, Eq. 1):
+// lambda_i = A S_b + C S_s, v[0] += log lambda_i and, with GRAD, v[1..6] += (d lambda_i / d
+// Theta) / lambda_i; also mu_i and xi_i of Eq. 2 when the request asks for them.
+template <bool GRAD>
+__device__ __forceinline__ void row_terms(const Request &R, int i, const double *sums, double *v) {
+  const double Ab = R.k_ab, Cw = R.k_cw, A = R.mu0 * Ab, C = R.theta * Cw;
+  const double mu = A * sums[0], xi = C * sums[1], lam = mu + xi;
+  if (R.mu_out) R.mu_out[i] = mu;
+  if (R.xi_out) R.xi_out[i] = xi;
+  v[0] += log(lam);
+  if (GRAD) {
+    const double itx = R.inv_tx, itt = R.inv_tt, ih = R.inv_h, iom = R.inv_om;
+    const double Sb = sums[0], Ss = sums[1], Rb = sums[2], Tb = sums[3] * R.tscale * R.tscale;
+    const double Rs = sums[4], Us = sums[5] * R.tscale;
+    const double inv = 1.0 / lam;
+    v[1] += Ab * Sb * inv;
+    v[2] += A * itx * (-2.0 * Sb + Rb * itx * itx) * inv;
+    v[3] += A * itt * (-Sb + Tb * itt * itt) * inv;
+    v[4] += Cw * Ss * inv;
+    v[5] += C * (Ss * iom - Us) * inv;
+    v[6] += C * ih * (-2.0 * Ss + Rs * ih * ih) * inv;
+  }
+}
+
+// End of row tile rt's epilogue: sum every thread's row terms v in a fixed order (warp tree,
+// warps in order) into R.rt_sum, then finish_request. Called by every thread of the CTA.
+template <bool GRAD>
+__device__ void rowtile_reduce(const Request &R, int rt, const double *v) {
+  constexpr int NV = GRAD ? 7 : 1;
+  __shared__ double red2[kMaxCtaWarps][8];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
   for (int q = 0; q < NV; ++q) {
     double x = v[q];
@@ -267,45 +380,7 @@ __device__ void rowtile_epilogue(const Request &R, int rt) {
     for (int w = 0; w < nw; ++w) x += red2[w][tid];
     R.rt_sum[(size_t)rt * 8 + tid] = x;
   }
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) s_final = atomicAdd(R.rt_count + S.nrt, 1u) == (unsigned)(S.nrt - 1);
-  __syncthreads();
-  if (s_final) {
-    __threadfence();
-#pragma unroll
-    for (int q = 0; q < NV; ++q) {
-      double x = 0.0;
-      for (int r = tid; r < S.nrt; r += blockDim.x)
-        x += __ldcg(R.rt_sum + (size_t)r * 8 + q) - __ldcg(R.comp + (size_t)r * 8 + q);
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
-      if (lane == 0) red2[warp][q] = x;
-    }
-    __syncthreads();
-    if (tid < NV) {
-      double x = 0.0;
-      for (int w = 0; w < nw; ++w) x += red2[w][tid];
-      R.out[tid] = x;
-    }
-  }
-  __syncthreads();
-}
-
-// End of a pair-kernel item: count the finished slice of row tile rt; the CTA that finishes
-// the tile's last slice runs its fused epilogue. Called by every thread of the CTA.
-template <bool GRAD>
-__device__ void finish_item(const Batch &B, const Request &R, int rt) {
-  if (!B.fused) return;
-  __shared__ int s_last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) s_last = atomicAdd(R.rt_count + rt, 1u) == (unsigned)(R.slices - 1);
-  __syncthreads();
-  if (s_last) {
-    __threadfence();
-    rowtile_epilogue<GRAD>(R, rt);
-  }
+  finish_request<GRAD>(R);
 }
 #endif
 

@@ -30,7 +30,7 @@ constexpr int kMaxRowTiles = kNoallocMax / kRowTile;     // 128
 constexpr int kMaxItems = kMaxRowTiles * kChunks;        // 512
 
 // Layout of g_scratch (byte offsets, all 256-aligned).
-constexpr size_t kOffHeader = 0;                                              // counter, ticket
+constexpr size_t kOffHeader = 0;                                              // epilogue ticket
 constexpr size_t kOffX = 1024;
 constexpr size_t kOffY = kOffX + (size_t)kNoallocMax * 4;
 constexpr size_t kOffT = kOffY + (size_t)kNoallocMax * 4;
@@ -194,7 +194,6 @@ extern "C" int hawkes_loglik_noalloc(const float *x, const float *y, const float
   std::memset(&b, 0, sizeof(b));
   b.nreq = 1;
   b.mode = 1;
-  b.counter = (unsigned *)(base + kOffHeader);
   Request &R = b.req[0];
   R.set.x32 = (const float *)(base + kOffX);
   R.set.y32 = (const float *)(base + kOffY);
@@ -238,8 +237,7 @@ extern "C" int hawkes_loglik_noalloc(const float *x, const float *y, const float
   b.total_items = nrt * chunks;
   b.fused = 0;  // noalloc_epilogue finishes the evaluation
   const int epi_blocks = (int)((n + kEpiThreads - 1) / kEpiThreads);
-  const int grid = std::max(1, std::min(b.total_items, d->sms * d->occ));
-  if (launch_pair_mixed(b, false, grid, s) != cudaSuccess) return HAWKES_E_CUDA;
+  if (launch_pair_mixed(b, false, s) != cudaSuccess) return HAWKES_E_CUDA;
   noalloc_epilogue<<<std::max(1, std::min(epi_blocks, d->sms * 8)), kEpiThreads, 0, s>>>(b.req[0], chunks,
                                                                                        base);
   if (cudaGetLastError() != cudaSuccess) return HAWKES_E_CUDA;

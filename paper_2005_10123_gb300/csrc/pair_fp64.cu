@@ -2,9 +2,9 @@
 //
 // pair_fp64_kernel forms the same per-row sums as the mixed kernel (S_b, S_s and the
 // gradient moments R_b, T_b, R_s, U_s of Section 2.1, Eq. 1), entirely in float64 with
-// the library exp(), and the moments in raw units (r^2 in km^2, dt in days). Slice 0 of each
-// row tile sums the tile's compensator terms, and the CTA that finishes a row tile's last
-// slice runs the fused epilogue (hk_internal.h: rowtile_epilogue).
+// the library exp(), and the moments in raw units (r^2 in km^2, dt in days). Compensator
+// items sum each row tile's compensator terms, and the CTA that completes a row tile's merge
+// tree runs its fused epilogue (hk_internal.h: merge_tree, row_terms, rowtile_reduce).
 #include "hk_internal.h"
 
 namespace hk {
@@ -55,7 +55,7 @@ __device__ __forceinline__ void tile_pass64(const double *__restrict__ sx, const
 }
 
 template <bool GRAD>
-__device__ void run_piece64(const Request &R, int4 piece, int slot, double (*sx)[kColTile],
+__device__ void run_piece64(const Batch &B, const Request &R, int4 piece, int slot, double (*sx)[kColTile],
                             double (*sy)[kColTile], double (*st)[kColTile]) {
   constexpr int NS = GRAD ? kSumsGrad : kSumsLoglik;
   const SetView &S = R.set;
@@ -128,49 +128,76 @@ __device__ void run_piece64(const Request &R, int4 piece, int slot, double (*sx)
     if (ct + 1 < piece.z) stage(ct + 1, buf ^ 1);
     __syncthreads();
   }
-  double *dst = R.partials + (size_t)slot * NS * kRowTile;
+  // this thread's rows: li = warp * kWarpRows64 + lane + 32 k, sums in acc[s][k]
+  auto store = [&](int to) {
+    double *dst = R.partials + (size_t)to * NS * kRowTile;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int s = 0; s < NS; ++s) dst[s * kRowTile + warp * kWarpRows64 + lane + 32 * k] = acc[s][k];
+  };
+  if (!B.fused) {
+    store(slot);
+    return;
+  }
+  auto merge = [&](int from) {
+    const double *src = R.partials + (size_t)from * NS * kRowTile;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int s = 0; s < NS; ++s) acc[s][k] += __ldcg(src + s * kRowTile + warp * kWarpRows64 + lane + 32 * k);
+  };
+  if (!merge_tree(R, piece.x, slot - piece.x * R.slices, store, merge)) return;
+  double v[GRAD ? 7 : 1] = {};
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    const int li = warp * kWarpRows64 + lane + 32 * k;
+    const int i = row0 + warp * kWarpRows64 + lane + 32 * k;
+    if (i < n) {
+      double sums[NS];
 #pragma unroll
-    for (int s = 0; s < NS; ++s) dst[s * kRowTile + li] = acc[s][k];
+      for (int s = 0; s < NS; ++s) sums[s] = acc[s][k];
+      row_terms<GRAD>(R, i, sums, v);
+    }
   }
+  rowtile_reduce<GRAD>(R, piece.x, v);
 }
 
 template <bool GRAD>
 __global__ void __launch_bounds__(kThreads64) pair_fp64_kernel(const __grid_constant__ Batch B) {
   __shared__ double sx[2][kColTile], sy[2][kColTile], st[2][kColTile];
-  __shared__ int s_item;
   __shared__ int2 s_win;
-  for (;;) {
-    if (threadIdx.x == 0) s_item = (int)atomicAdd(B.counter, 1u);
-    __syncthreads();
-    const int item = s_item;
-    if (item >= B.total_items) break;
-    const Request &R = B.req[find_request(B, item)];
-    const int local = item - R.item_begin;
-    const int rt = local / R.slices, sl = local - rt * R.slices;
+  const int item = blockIdx.x;
+  const Request &R = B.req[find_request(B, item)];
+  const int local = item - R.item_begin, nc = comp_items(R);
+  if (local < nc) {  // compensator item of row tile `local`
+    compensator_tile(R, R.set.t64, local, GRAD);
+    if (B.fused) finish_request<GRAD>(R);
+    return;
+  }
+  const int slot = local - nc;
+  const int2 tile = slot_tile(R, slot);
+  const int rt = tile.x, sl = tile.y, ns = R.slices;
+  int2 w = table_window_rt(R, R.set.win64, R.set.t64, rt);
+  if (w.x < 0) {  // no lookup table: one warp searches the times
     if (threadIdx.x < 32) {
-      const int2 w = column_window(R, R.set.t64, rt);
-      if (threadIdx.x == 0) s_win = w;
+      const int2 v = column_window(R, R.set.t64, rt);
+      if (threadIdx.x == 0) s_win = v;
     }
     __syncthreads();
-    const int2 w = s_win;
-    const int width = w.y - w.x;
-    const int c_begin = w.x + (int)((long long)width * sl / R.slices);
-    const int c_end = w.x + (int)((long long)width * (sl + 1) / R.slices);
-    run_piece64<GRAD>(R, make_int4(rt, c_begin, c_end, 0), local, sx, sy, st);
-    if (sl == 0 && R.comp) compensator_tile(R, R.set.t64, rt, GRAD);
-    finish_item<GRAD>(B, R, rt);
-    __syncthreads();  // s_item, s_win and the staging buffers are reused by the next item
+    w = s_win;
   }
+  const int width = w.y - w.x;
+  const int c_begin = w.x + (int)((long long)width * sl / ns);
+  const int c_end = w.x + (int)((long long)width * (sl + 1) / ns);
+  run_piece64<GRAD>(B, R, make_int4(rt, c_begin, c_end, 0), slot, sx, sy, st);
 }
 
 }  // namespace
 
-cudaError_t launch_pair_fp64(const Batch &b, bool grad, int grid, cudaStream_t s) {
-  if (grad) pair_fp64_kernel<true><<<grid, kThreads64, 0, s>>>(b);
-  else pair_fp64_kernel<false><<<grid, kThreads64, 0, s>>>(b);
+cudaError_t launch_pair_fp64(const Batch &b, bool grad, cudaStream_t s) {
+  if (b.total_items < 1) return cudaErrorInvalidValue;
+  if (grad) pair_fp64_kernel<true><<<b.total_items, kThreads64, 0, s>>>(b);
+  else pair_fp64_kernel<false><<<b.total_items, kThreads64, 0, s>>>(b);
   return cudaGetLastError();
 }
 

@@ -1,5 +1,5 @@
 // Mixed-precision pair kernel: float32 pair terms, float32 accumulation over one
-// 256-column tile, float64 accumulation across tiles.
+// 256-column tile, float64 accumulation across tiles and slices.
 //
 // For every row (event n) of its row tile the kernel forms, over the columns n' of its
 // work range (Section 2.1, Eq. 1 inner sum; the gradient moments are added here):
@@ -9,7 +9,8 @@
 // with r^2 = |x_n - x_n'|^2 from exact float32 differences of the stored coordinates, and
 // dt' = beta (t_n - t_n'), beta^2 = log2(e)/(2 tau_t^2); times enter relative to the first
 // row of the tile before scaling, so nearby time differences keep full relative precision.
-// The epilogue kernel turns the row sums into lambda_n, log lambda_n and the gradient.
+// The CTA that completes a row tile's merge tree turns its row sums into lambda_n,
+// log lambda_n and the gradient in float64 (fused epilogue).
 //
 // Arithmetic per (row, column) pair, two rows per packed f32x2 value:
 //   e_b = 2^-q with q = a2 r^2 + dt'^2, a2 = log2(e)/(2 tau_x^2);
@@ -212,8 +213,11 @@ __device__ __forceinline__ void cta_sync() {
   else __syncthreads();
 }
 
+// One pair item: the row sums of row tile piece.x over column tiles [piece.y, piece.z), then
+// (fused) the row tile's merge tree and, in the CTA that completes it, the tile's epilogue;
+// otherwise the sums go to the item's partial-sum slot.
 template <bool GRAD>
-__device__ void run_piece(const Request &R, int4 piece, int slot, float4 (*sxy)[kColTile],
+__device__ void run_piece(const Batch &B, const Request &R, int4 piece, int slot, float4 (*sxy)[kColTile],
                           float4 (*stb)[kColTile], double *sacc) {
   constexpr int NS = GRAD ? kSumsGrad : kSumsLoglik;
   const SetView &S = R.set;
@@ -308,16 +312,40 @@ __device__ void run_piece(const Request &R, int4 piece, int slot, float4 (*sxy)[
     if (has_next) store_cols(nxt, ct + 1, tid, n, t_origin, beta, wn, sxy[buf ^ 1], stb[buf ^ 1]);
     cta_sync();
   }
-  double *dst = R.partials + (size_t)slot * NS * kRowTile;
+  // this thread's rows: la = warp * kWarpRows + lane + 32 k, sums at sacc[(s R + k) T + tid]
+  auto store = [&](int to) {
+    double *dst = R.partials + (size_t)to * NS * kRowTile;
 #pragma unroll
-  for (int p = 0; p < kPairs; ++p) {
-    const int la = warp * kWarpRows + lane + 64 * p;
+    for (int k = 0; k < kRowsPerThread; ++k)
 #pragma unroll
-    for (int s = 0; s < NS; ++s) {
-      dst[s * kRowTile + la] = sacc[(s * kRowsPerThread + 2 * p) * kThreads + tid];
-      dst[s * kRowTile + la + 32] = sacc[(s * kRowsPerThread + 2 * p + 1) * kThreads + tid];
+      for (int s = 0; s < NS; ++s)
+        dst[s * kRowTile + warp * kWarpRows + lane + 32 * k] = sacc[(s * kRowsPerThread + k) * kThreads + tid];
+  };
+  if (!B.fused) {
+    store(slot);
+    return;
+  }
+  auto merge = [&](int from) {
+    const double *src = R.partials + (size_t)from * NS * kRowTile;
+#pragma unroll
+    for (int k = 0; k < kRowsPerThread; ++k)
+#pragma unroll
+      for (int s = 0; s < NS; ++s)
+        sacc[(s * kRowsPerThread + k) * kThreads + tid] += __ldcg(src + s * kRowTile + warp * kWarpRows + lane + 32 * k);
+  };
+  if (!merge_tree(R, piece.x, slot - piece.x * R.slices, store, merge)) return;
+  double v[GRAD ? 7 : 1] = {};
+#pragma unroll
+  for (int k = 0; k < kRowsPerThread; ++k) {
+    const int i = row0 + warp * kWarpRows + lane + 32 * k;
+    if (i < n) {
+      double sums[NS];
+#pragma unroll
+      for (int s = 0; s < NS; ++s) sums[s] = sacc[(s * kRowsPerThread + k) * kThreads + tid];
+      row_terms<GRAD>(R, i, sums, v);
     }
   }
+  rowtile_reduce<GRAD>(R, piece.x, v);
 }
 
 template <bool GRAD>
@@ -326,37 +354,39 @@ __global__ void __launch_bounds__(kThreads, HK_MIN_CTAS) pair_mixed_kernel(const
   __shared__ __align__(16) float4 sxy[2][kColTile];
   __shared__ __align__(16) float4 stb[2][kColTile];
   __shared__ double sacc[NS * kRowsPerThread * kThreads];
-  __shared__ int s_item;
   __shared__ int2 s_win;
-  for (;;) {
-    if (threadIdx.x == 0) s_item = (int)atomicAdd(B.counter, 1u);
-    cta_sync();
-    const int item = s_item;
-    if (item >= B.total_items) break;
-    const Request &R = B.req[find_request(B, item)];
-    const int local = item - R.item_begin;
-    const int rt = local / R.slices, sl = local - rt * R.slices;
+  const int item = blockIdx.x;
+  const Request &R = B.req[find_request(B, item)];
+  const int local = item - R.item_begin, nc = comp_items(R);
+  if (local < nc) {  // compensator item of row tile `local`
+    compensator_tile(R, R.set.t32, local, GRAD);
+    if (B.fused) finish_request<GRAD>(R);
+    return;
+  }
+  const int slot = local - nc;
+  const int2 tile = slot_tile(R, slot);
+  const int rt = tile.x, sl = tile.y, ns = R.slices;
+  int2 w = table_window_rt(R, R.set.win32, R.set.t32, rt);
+  if (w.x < 0) {  // no lookup table: one warp searches the times
     if (threadIdx.x < 32) {
-      const int2 w = column_window(R, R.set.t32, rt);
-      if (threadIdx.x == 0) s_win = w;
+      const int2 v = column_window(R, R.set.t32, rt);
+      if (threadIdx.x == 0) s_win = v;
     }
     cta_sync();
-    const int2 w = s_win;
-    const int width = w.y - w.x;
-    const int c_begin = w.x + (int)((long long)width * sl / R.slices);
-    const int c_end = w.x + (int)((long long)width * (sl + 1) / R.slices);
-    run_piece<GRAD>(R, make_int4(rt, c_begin, c_end, 0), local, sxy, stb, sacc);
-    if (sl == 0 && R.comp) compensator_tile(R, R.set.t32, rt, GRAD);
-    finish_item<GRAD>(B, R, rt);
-    cta_sync();  // s_item, s_win and the staging buffers are reused by the next item
+    w = s_win;
   }
+  const int width = w.y - w.x;
+  const int c_begin = w.x + (int)((long long)width * sl / ns);
+  const int c_end = w.x + (int)((long long)width * (sl + 1) / ns);
+  run_piece<GRAD>(B, R, make_int4(rt, c_begin, c_end, 0), slot, sxy, stb, sacc);
 }
 
 }  // namespace
 
-cudaError_t launch_pair_mixed(const Batch &b, bool grad, int grid, cudaStream_t s) {
-  if (grad) pair_mixed_kernel<true><<<grid, kThreads, 0, s>>>(b);
-  else pair_mixed_kernel<false><<<grid, kThreads, 0, s>>>(b);
+cudaError_t launch_pair_mixed(const Batch &b, bool grad, cudaStream_t s) {
+  if (b.total_items < 1) return cudaErrorInvalidValue;
+  if (grad) pair_mixed_kernel<true><<<b.total_items, kThreads, 0, s>>>(b);
+  else pair_mixed_kernel<false><<<b.total_items, kThreads, 0, s>>>(b);
   return cudaGetLastError();
 }
 

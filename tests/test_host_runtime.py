@@ -26,8 +26,10 @@ def test_host_runtime_checks():
         sys.path.pop(0)
     try:
         build_fake.build()
-    except (OSError, subprocess.CalledProcessError) as e:
-        pytest.skip(f"cannot build the host-test library: {e}")
+    except OSError as e:  # no host compiler: nothing to test with
+        pytest.skip(f"cannot run the host compiler: {e}")
+    except subprocess.CalledProcessError as e:  # the library's host code no longer compiles
+        pytest.fail(f"the host-test library does not build: {e}")
     env = dict(os.environ)
     asan = _asan_runtime()
     if asan:
