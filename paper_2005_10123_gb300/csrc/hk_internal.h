@@ -132,9 +132,22 @@ __host__ __device__ inline int comp_items(const Request &R) { return R.comp ? R.
 __host__ __device__ inline int pair_items(const Request &R) { return R.set.nrt * R.slices; }
 __host__ __device__ inline int request_items(const Request &R) { return comp_items(R) + pair_items(R); }
 __host__ __device__ inline int request_counters(const Request &R) { return 2 * pair_items(R) + 1; }
-// Row tile and slice of pair item `slot`.
-__host__ __device__ inline int2 slot_tile(const Request &R, int slot) {
-  return make_int2(slot / R.slices, slot % R.slices);
+// Row tile and slice of the request's p-th pair item in launch order. Row tiles go out from
+// the middle of the time range outwards (m, m - 1, m + 1, m - 2, ...): the first and last row
+// tiles, whose column windows are cut off by t = 0 and t = t_N, launch last, so the launch
+// ends on short items. The item's partial-sum slot is rt * slices + slice, whatever the order.
+#ifndef HK_MIDDLE_OUT
+#define HK_MIDDLE_OUT 1
+#endif
+__host__ __device__ inline int2 slot_tile(const Request &R, int p) {
+  const int k = p / R.slices, sl = p % R.slices;
+#if HK_MIDDLE_OUT
+  const int m = R.set.nrt / 2;
+  const int rt = k == 0 ? m : (k & 1) ? m - (k + 1) / 2 : m + k / 2;
+#else
+  const int rt = k;
+#endif
+  return make_int2(rt, sl);
 }
 
 // Launchers (defined in the kernel translation units): one CTA per item, grid =

@@ -174,9 +174,8 @@ __global__ void __launch_bounds__(kThreads64) pair_fp64_kernel(const __grid_cons
     if (B.fused) finish_request<GRAD>(R);
     return;
   }
-  const int slot = local - nc;
-  const int2 tile = slot_tile(R, slot);
-  const int rt = tile.x, sl = tile.y, ns = R.slices;
+  const int2 tile = slot_tile(R, local - nc);
+  const int rt = tile.x, sl = tile.y, ns = R.slices, slot = rt * ns + sl;
   int2 w = table_window_rt(R, R.set.win64, R.set.t64, rt);
   if (w.x < 0) {  // no lookup table: one warp searches the times
     if (threadIdx.x < 32) {

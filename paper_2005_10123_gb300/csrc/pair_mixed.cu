@@ -363,9 +363,8 @@ __global__ void __launch_bounds__(kThreads, HK_MIN_CTAS) pair_mixed_kernel(const
     if (B.fused) finish_request<GRAD>(R);
     return;
   }
-  const int slot = local - nc;
-  const int2 tile = slot_tile(R, slot);
-  const int rt = tile.x, sl = tile.y, ns = R.slices;
+  const int2 tile = slot_tile(R, local - nc);
+  const int rt = tile.x, sl = tile.y, ns = R.slices, slot = rt * ns + sl;
   int2 w = table_window_rt(R, R.set.win32, R.set.t32, rt);
   if (w.x < 0) {  // no lookup table: one warp searches the times
     if (threadIdx.x < 32) {

@@ -112,6 +112,13 @@ namespace hk {
 static void check_schedule(const Request &R) {
   const SetView &S = R.set;
   bool ok = R.slices >= 1 && R.slices <= S.nct;
+  // the launch order visits every (row tile, slice) exactly once
+  std::vector<char> seen((size_t)S.nrt * R.slices, 0);
+  for (int p = 0; ok && p < pair_items(R); ++p) {
+    const int2 tile = slot_tile(R, p);
+    if (tile.x < 0 || tile.x >= S.nrt || tile.y < 0 || tile.y >= R.slices || seen[(size_t)tile.x * R.slices + tile.y]++)
+      ok = false;
+  }
   if (S.npad != S.nrt * kRowTile || S.nct * kColTile != S.npad || S.n > S.npad || S.n < 1) ok = false;
   if (!(R.cut_early > 0.0) || !(R.cut_late > 0.0)) ok = false;
   if (!R.partials || !R.comp || !R.rt_sum || !R.rt_count || !R.out) ok = false;
