@@ -182,6 +182,21 @@ def batched_chains(ctx, sid, n, stream):
             "pairs_visited_per_launch": visited, "note": "host-timed, results copied back each launch"}
 
 
+def pi_posterior(ctx, sid, n, k: int = 256):
+    """Eq. 2 over a sample of k parameter vectors (the posterior-probability workload of
+    Section 3.2, there 1,000 vectors on 55,000 events): one hawkes_pi_batch call, k x N
+    probabilities copied back to the host."""
+    from paper_2005_10123_gb300 import binding
+    ths = synth.theta_batch(k, seed=20055)
+    ctx.hawkes_pi_batch(sid, ths[:64], binding.HAWKES_MIXED)
+    t0 = time.perf_counter()
+    pi, _ = ctx.hawkes_pi_batch(sid, ths, binding.HAWKES_MIXED)
+    dt = time.perf_counter() - t0
+    return {"thetas": k, "events": int(n), "s": dt, "value": k * float(n) ** 2 / dt, "unit": "pair-evals/s",
+            "d2h_bytes": int(pi.nbytes), "mean_pi": float(pi.mean()),
+            "note": "host-timed, includes the copy of k x N doubles to the host"}
+
+
 def mh_chain(ctx, sid, iters):
     """Algorithm 1 over all six parameters with log-normal proposals, mixed-precision likelihood.
     With tau_x and tau_t free the background sum must leave out n' = n: with the self term,
@@ -368,6 +383,7 @@ def run_ours(args):
         }
         if not args.no_extras:
             extra["batched_chains"] = batched_chains(ctx, sid, n, stream)
+            extra["pi_posterior"] = pi_posterior(ctx, sid, n)
             extra["mh_chain"] = mh_chain(ctx, sid, args.mh_iters)
             extra["serving"] = serving_runs(ctx, args.serving_requests)
 

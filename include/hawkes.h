@@ -157,6 +157,16 @@ int hawkes_pair_work(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *param
 int hawkes_event_terms(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *params,
                        hawkes_mode mode, double *mu_out, double *xi_out, double *loglik_out);
 
+/* Eq. 2 for k parameter vectors on one set, the posterior form of Section 3.2 (a sample
+ * Theta^(1..k) gives k vectors of N probabilities): pi_out[r * n + i] = xi_i / lambda_i at
+ * params[r], for events in stored (time) order. pi_out is a host array of k * n doubles and
+ * loglik_out (k doubles, may be NULL) receives ell at each params[r]; both owned by the
+ * caller. The call blocks; it launches up to 64 parameter vectors at a time and needs device
+ * workspace for 64 * n doubles of output besides the evaluation's own. k = 0 does nothing.
+ * Errors as hawkes_loglik; on an error the entries of pi_out not yet written are undefined. */
+int hawkes_pi_batch(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_params *params,
+                    hawkes_mode mode, double *pi_out, double *loglik_out);
+
 /* ---- serving: continuous batching of requests from many chains ----------------------
  * hawkes_submit queues one request (set, Theta, gradient flag, mode) and returns a
  * ticket at once. A scheduler thread admits queued requests while their device

@@ -31,7 +31,7 @@ EXPORTS = (
     "hawkes_release_events", "hawkes_set_info", "hawkes_loglik", "hawkes_loglik_grad",
     "hawkes_loglik_async", "hawkes_loglik_batch", "hawkes_event_terms", "hawkes_submit",
     "hawkes_poll", "hawkes_wait", "hawkes_stats", "hawkes_strerror", "hawkes_last_cuda_error",
-    "hawkes_loglik_noalloc", "hawkes_pair_work", "hawkes_poll_timed",
+    "hawkes_loglik_noalloc", "hawkes_pair_work", "hawkes_poll_timed", "hawkes_pi_batch",
 )
 HAWKES_NOALLOC_MAX_EVENTS = 65536
 
@@ -83,6 +83,7 @@ def load(build_if_missing: bool = False, path: str | None = None):
         "hawkes_loglik_async": [vp, i32, P, ctypes.c_int, ctypes.c_int, vp],
         "hawkes_loglik_batch": [vp, i32, ctypes.c_int, P, ctypes.c_int, ctypes.c_int, _D, _D],
         "hawkes_event_terms": [vp, i32, P, ctypes.c_int, _D, _D, _D],
+        "hawkes_pi_batch": [vp, i32, ctypes.c_int, P, ctypes.c_int, _D, _D],
         "hawkes_submit": [vp, i32, P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(u64)],
         "hawkes_poll": [vp, u64, ctypes.POINTER(ctypes.c_int), _D, _D],
         "hawkes_wait": [vp, u64, ctypes.c_int, _D, _D],
@@ -222,6 +223,18 @@ class Context:
                                                 mu.ctypes.data_as(_D), xi.ctypes.data_as(_D),
                                                 ctypes.byref(ll)), "hawkes_event_terms")
         return mu, xi, ll.value
+
+    def hawkes_pi_batch(self, set_id: int, thetas, mode: int = HAWKES_MIXED):
+        """pi_n of Eq. 2 at each of k parameter vectors: returns (pi of shape (k, n), ell of shape (k,))."""
+        n, _ = self.hawkes_set_info(set_id)
+        th = np.ascontiguousarray(thetas, dtype=np.float64).reshape(-1, 6)
+        k = th.shape[0]
+        arr = (hawkes_params * max(k, 1))(*[hawkes_params(*row) for row in th])
+        pi = np.zeros((k, n))
+        ll = np.zeros(k)
+        self._check(self.lib.hawkes_pi_batch(self.h, int(set_id), k, arr, int(mode), pi.ctypes.data_as(_D),
+                                             ll.ctypes.data_as(_D)), "hawkes_pi_batch")
+        return pi, ll
 
     def hawkes_pair_work(self, set_id: int, theta, mode: int = HAWKES_MIXED) -> dict:
         """Pair counts of an evaluation at theta: visited (inside the windows), all (N^2),

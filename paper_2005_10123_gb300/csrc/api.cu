@@ -365,8 +365,10 @@ void free_set(hawkes_ctx *ctx, EventSetRec *S) {
 // Synchronous evaluation of k requests on one set (k = 1 for the single calls).
 // Results (7 doubles per request) land in host_out[8 * r]; device_out, if given
 // (k = 1 only), receives them on the device instead and the call does not block.
+// mu_out / xi_out (k = 1) receive the per-event mu_n and xi_n of Eq. 2, pi_out (k rows of n)
+// the per-event pi_n of every request.
 int eval_sync(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_params *params, int mode, int grad,
-              double *host_out, double *device_out, double *mu_out, double *xi_out) {
+              double *host_out, double *device_out, double *mu_out, double *xi_out, double *pi_out) {
   if (mode != HAWKES_FP64 && mode != HAWKES_MIXED) return HAWKES_E_INVAL;
   if (k < 1 || k > kMaxBatch) return HAWKES_E_INVAL;
   for (int r = 0; r < k; ++r)
@@ -375,7 +377,8 @@ int eval_sync(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_params *param
   EventSetRec *S = find_set(ctx, set_id);
   if (!S) return HAWKES_E_NOSET;
   const size_t per = request_footprint(S, mode, grad);
-  const size_t rows_bytes = (mu_out || xi_out) ? align_up((size_t)S->n * sizeof(double), 256) * 2 : 0;
+  const size_t row_bytes = align_up((size_t)S->n * sizeof(double), 256);
+  const size_t rows_bytes = (mu_out || xi_out ? 2 * row_bytes : 0) + (pi_out ? (size_t)k * row_bytes : 0);
   const size_t cnt = align_up(counter_bytes(S, mode, grad) * k, 256);
   const size_t need = kFixedBytes + cnt + rows_bytes + per * k;
   if (int rc = ensure_sync_ws(ctx, need)) return rc;
@@ -390,21 +393,29 @@ int eval_sync(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_params *param
   for (int r = 0; r < k; ++r) {
     if (int rc = make_request(ctx, S, &params[r], mode, grad, ctx->flags, &b->req[r])) return rc;
     bind_workspace(&b->req[r], S, mode, grad, req_base + (size_t)r * per,
-                   device_out ? device_out : outs + 8 * r, (unsigned *)(cnt_base + (size_t)r * counter_bytes(S, mode, grad)));
+                   device_out ? device_out : outs + 8 * r,
+                   (unsigned *)(cnt_base + (size_t)r * counter_bytes(S, mode, grad)));
   }
-  if (rows_bytes) {
-    b->req[0].mu_out = (double *)rows_base;
-    b->req[0].xi_out = (double *)(rows_base + rows_bytes / 2);
+  char *rows_cur = rows_base;
+  if (mu_out || xi_out) {
+    b->req[0].mu_out = (double *)rows_cur;
+    b->req[0].xi_out = (double *)(rows_cur + row_bytes);
+    rows_cur += 2 * row_bytes;
   }
+  if (pi_out)
+    for (int r = 0; r < k; ++r) b->req[r].pi_out = (double *)(rows_cur + (size_t)r * row_bytes);
   HK_CUDA(ctx, cudaMemsetAsync(base, 0, kFixedBytes + cnt, ctx->stream));
   if (int rc = launch_batch(ctx, *b, mode, grad, ctx->stream)) return rc;
   if (device_out) return HAWKES_OK;
   HK_CUDA(ctx, cudaMemcpyAsync(ctx->pinned_out, outs, (size_t)k * 8 * sizeof(double), cudaMemcpyDeviceToHost,
                                ctx->stream));
-  if (mu_out) HK_CUDA(ctx, cudaMemcpyAsync(mu_out, b->req[0].mu_out, (size_t)S->n * sizeof(double),
-                                           cudaMemcpyDeviceToHost, ctx->stream));
-  if (xi_out) HK_CUDA(ctx, cudaMemcpyAsync(xi_out, b->req[0].xi_out, (size_t)S->n * sizeof(double),
-                                           cudaMemcpyDeviceToHost, ctx->stream));
+  const size_t nb = (size_t)S->n * sizeof(double);
+  if (mu_out) HK_CUDA(ctx, cudaMemcpyAsync(mu_out, b->req[0].mu_out, nb, cudaMemcpyDeviceToHost, ctx->stream));
+  if (xi_out) HK_CUDA(ctx, cudaMemcpyAsync(xi_out, b->req[0].xi_out, nb, cudaMemcpyDeviceToHost, ctx->stream));
+  if (pi_out)
+    for (int r = 0; r < k; ++r)
+      HK_CUDA(ctx, cudaMemcpyAsync(pi_out + (size_t)r * S->n, b->req[r].pi_out, nb, cudaMemcpyDeviceToHost,
+                                   ctx->stream));
   HK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   std::memcpy(host_out, ctx->pinned_out, (size_t)k * 8 * sizeof(double));
   return HAWKES_OK;
@@ -856,7 +867,7 @@ int hawkes_loglik(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *params, 
   if (!ctx || !params || !loglik_out) return HAWKES_E_INVAL;
   cudaSetDevice(ctx->device);
   double out[8];
-  int rc = eval_sync(ctx, set_id, 1, params, mode, 0, out, nullptr, nullptr, nullptr);
+  int rc = eval_sync(ctx, set_id, 1, params, mode, 0, out, nullptr, nullptr, nullptr, nullptr);
   if (rc == HAWKES_OK) *loglik_out = out[0];
   return rc;
 }
@@ -866,7 +877,7 @@ int hawkes_loglik_grad(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *par
   if (!ctx || !params || !loglik_out || !grad_out) return HAWKES_E_INVAL;
   cudaSetDevice(ctx->device);
   double out[8];
-  int rc = eval_sync(ctx, set_id, 1, params, mode, 1, out, nullptr, nullptr, nullptr);
+  int rc = eval_sync(ctx, set_id, 1, params, mode, 1, out, nullptr, nullptr, nullptr, nullptr);
   if (rc == HAWKES_OK) {
     *loglik_out = out[0];
     for (int q = 0; q < 6; ++q) grad_out[q] = out[1 + q];
@@ -878,7 +889,7 @@ int hawkes_loglik_async(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *pa
                         int want_grad, double *device_out) {
   if (!ctx || !params || !device_out) return HAWKES_E_INVAL;
   cudaSetDevice(ctx->device);
-  return eval_sync(ctx, set_id, 1, params, mode, want_grad ? 1 : 0, nullptr, device_out, nullptr, nullptr);
+  return eval_sync(ctx, set_id, 1, params, mode, want_grad ? 1 : 0, nullptr, device_out, nullptr, nullptr, nullptr);
 }
 
 int hawkes_loglik_batch(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_params *params, hawkes_mode mode,
@@ -887,7 +898,7 @@ int hawkes_loglik_batch(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_par
     return HAWKES_E_INVAL;
   cudaSetDevice(ctx->device);
   std::vector<double> out((size_t)k * 8);
-  int rc = eval_sync(ctx, set_id, k, params, mode, want_grad ? 1 : 0, out.data(), nullptr, nullptr, nullptr);
+  int rc = eval_sync(ctx, set_id, k, params, mode, want_grad ? 1 : 0, out.data(), nullptr, nullptr, nullptr, nullptr);
   if (rc != HAWKES_OK) return rc;
   for (int r = 0; r < k; ++r) {
     loglik_out[r] = out[(size_t)r * 8];
@@ -902,9 +913,32 @@ int hawkes_event_terms(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *par
   if (!ctx || !params || !mu_out || !xi_out) return HAWKES_E_INVAL;
   cudaSetDevice(ctx->device);
   double out[8];
-  int rc = eval_sync(ctx, set_id, 1, params, mode, 0, out, nullptr, mu_out, xi_out);
+  int rc = eval_sync(ctx, set_id, 1, params, mode, 0, out, nullptr, mu_out, xi_out, nullptr);
   if (rc == HAWKES_OK && loglik_out) *loglik_out = out[0];
   return rc;
+}
+
+int hawkes_pi_batch(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_params *params, hawkes_mode mode,
+                    double *pi_out, double *loglik_out) {
+  if (!ctx || !params || !pi_out || k < 0) return HAWKES_E_INVAL;
+  cudaSetDevice(ctx->device);
+  int64_t n = 0;
+  {
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    EventSetRec *S = find_set(ctx, set_id);
+    if (!S) return HAWKES_E_NOSET;
+    n = S->n;
+  }
+  std::vector<double> out((size_t)kMaxBatch * 8);
+  for (int r0 = 0; r0 < k; r0 += kMaxBatch) {  // up to kMaxBatch parameter vectors per launch
+    const int m = std::min(kMaxBatch, k - r0);
+    int rc = eval_sync(ctx, set_id, m, params + r0, mode, 0, out.data(), nullptr, nullptr, nullptr,
+                       pi_out + (size_t)r0 * n);
+    if (rc != HAWKES_OK) return rc;
+    if (loglik_out)
+      for (int r = 0; r < m; ++r) loglik_out[r0 + r] = out[(size_t)8 * r];
+  }
+  return HAWKES_OK;
 }
 
 int hawkes_submit(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *params, int want_grad, hawkes_mode mode,

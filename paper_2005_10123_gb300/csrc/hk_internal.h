@@ -117,6 +117,7 @@ struct Request {
   double *out;         // 7 doubles: ell, d ell / d Theta
   double *mu_out;      // optional per-event mu_n (n doubles) or nullptr
   double *xi_out;      // optional per-event xi_n (n doubles) or nullptr
+  double *pi_out;      // optional per-event pi_n = xi_n / lambda_n (n doubles) or nullptr
 };
 
 struct Batch {
@@ -351,13 +352,15 @@ __device__ bool merge_tree(const Request &R, int rt, int sl, Store store, Merge 
 
 // Log-intensity and gradient terms of event i from its row sums (Section 2.1, Eq. 1):
 // lambda_i = A S_b + C S_s, v[0] += log lambda_i and, with GRAD, v[1..6] += (d lambda_i / d
-// Theta) / lambda_i; also mu_i and xi_i of Eq. 2 when the request asks for them.
+// Theta) / lambda_i; also mu_i, xi_i and pi_i = xi_i / lambda_i of Eq. 2 when the request
+// asks for them.
 template <bool GRAD>
 __device__ __forceinline__ void row_terms(const Request &R, int i, const double *sums, double *v) {
   const double Ab = R.k_ab, Cw = R.k_cw, A = R.mu0 * Ab, C = R.theta * Cw;
   const double mu = A * sums[0], xi = C * sums[1], lam = mu + xi;
   if (R.mu_out) R.mu_out[i] = mu;
   if (R.xi_out) R.xi_out[i] = xi;
+  if (R.pi_out) R.pi_out[i] = xi / lam;
   v[0] += log(lam);
   if (GRAD) {
     const double itx = R.inv_tx, itt = R.inv_tt, ih = R.inv_h, iom = R.inv_om;

@@ -29,10 +29,16 @@
 #include "hk_internal.h"
 
 #ifndef HK_MIN_CTAS
-#define HK_MIN_CTAS 5
+#define HK_MIN_CTAS 5  // resident CTAs per SM, loglik + gradient (shared memory allows 5)
+#endif
+#ifndef HK_MIN_CTAS_LL
+#define HK_MIN_CTAS_LL 6  // resident CTAs per SM, loglik only (80 registers, no spills)
 #endif
 #ifndef HK_COL_UNROLL
-#define HK_COL_UNROLL 4
+#define HK_COL_UNROLL 4  // columns unrolled per step of the tile loop, loglik + gradient
+#endif
+#ifndef HK_COL_UNROLL_LL
+#define HK_COL_UNROLL_LL 8  // loglik only
 #endif
 #ifndef HK_PACK_ADD
 #define HK_PACK_ADD 1  // differences dx, dy, dt
@@ -95,7 +101,7 @@ __device__ __forceinline__ float2 accfma2(float2 a, float2 e, float2 s) {
 }
 
 constexpr int kPairs = kRowsPerThread / 2;  // packed row pairs per thread
-constexpr int kColUnroll = HK_COL_UNROLL;
+constexpr int kColUnroll = HK_COL_UNROLL, kColUnrollLL = HK_COL_UNROLL_LL;
 
 template <int NS>
 struct Acc32 {
@@ -115,7 +121,8 @@ __device__ __forceinline__ void tile_pass(const float4 *__restrict__ sxy, const 
   constexpr bool kBg = KIND != 3;
   constexpr bool kTrig = KIND != 0;
   constexpr bool kNeedDt = kBg || KIND == 2 || GRAD;
-#pragma unroll kColUnroll
+  constexpr int kUnroll = GRAD ? kColUnroll : kColUnrollLL;
+#pragma unroll kUnroll
   for (int j = 0; j < kColTile; ++j) {
     const float4 c = sxy[j];  // {-x, -x, -y, -y}
     const float4 d = stb[j];  // {-t', -t', b, b}, b = wn (t'_ref - t')
@@ -349,7 +356,7 @@ __device__ void run_piece(const Batch &B, const Request &R, int4 piece, int slot
 }
 
 template <bool GRAD>
-__global__ void __launch_bounds__(kThreads, HK_MIN_CTAS) pair_mixed_kernel(const __grid_constant__ Batch B) {
+__global__ void __launch_bounds__(kThreads, GRAD ? HK_MIN_CTAS : HK_MIN_CTAS_LL) pair_mixed_kernel(const __grid_constant__ Batch B) {
   constexpr int NS = GRAD ? kSumsGrad : kSumsLoglik;
   __shared__ __align__(16) float4 sxy[2][kColTile];
   __shared__ __align__(16) float4 stb[2][kColTile];

@@ -138,6 +138,8 @@ static void fake_outputs(const Batch &b, bool grad) {
     }
     if (R.mu_out)
       for (int i = 0; i < R.set.n; ++i) { R.mu_out[i] = i; R.xi_out[i] = -i; }
+    if (R.pi_out)
+      for (int i = 0; i < R.set.n; ++i) R.pi_out[i] = R.mu0 + i;
   }
 }
 

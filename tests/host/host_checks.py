@@ -80,6 +80,15 @@ def main():
     ctx.hawkes_set_flags(0)
     mu, xi, _ = ctx.hawkes_event_terms(sids[1000], TH, 1)
     assert np.array_equal(mu, np.arange(1000)) and np.array_equal(xi, -np.arange(1000))
+    # pi for 70 parameter vectors: two launches (64 + 6), every row lands at its own offset
+    ths = np.array([[0.001 * (r + 1), 1, 30, 0.5, 1, 0.1] for r in range(70)])
+    pi, ll = ctx.hawkes_pi_batch(sids[1000], ths, 1)
+    assert pi.shape == (70, 1000)
+    assert np.array_equal(pi, ths[:, :1] + np.arange(1000)[None, :])
+    assert np.array_equal(ll, ths[:, 0] * 1000.0 + 1000 + 0.5)
+    pi0, ll0 = ctx.hawkes_pi_batch(sids[1000], np.zeros((0, 6)), 1)
+    assert pi0.shape == (0, 1000) and ll0.shape == (0,)
+    expect_status(lambda: ctx.hawkes_pi_batch(999, ths, 1), -3)
     # invalid parameters, unknown set
     for bad in [(0, 1, 1, 0.5, 1, 1), (1, 1, -1, 0.5, 1, 1), (1, 1, 1, -1, 1, 1), (1, 1, 1, 0.5, 1, np.nan)]:
         expect_status(lambda: ctx.hawkes_loglik(sids[2], bad, 1), -1)

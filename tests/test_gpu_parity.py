@@ -110,6 +110,29 @@ def test_event_terms_rows(ctx, mode):
 
 
 @pytest.mark.parametrize("mode", [0, 1], ids=["fp64", "mixed"])
+def test_pi_batch(ctx, mode):
+    """Eq. 2 at 70 parameter vectors (two launches): each row against the oracle's per-event
+    terms, and the log-likelihoods bitwise equal to single evaluations."""
+    ev = synth.simulate(3000, 1000.0, seed=22)
+    ths = synth.theta_batch(70, seed=23)
+    sid = ctx.hawkes_upload_events(ev.x, ev.y, ev.t)
+    try:
+        pi, ll = ctx.hawkes_pi_batch(sid, ths, mode)
+        singles = [ctx.hawkes_loglik(sid, ths[k], mode) for k in (0, 63, 64, 69)]
+    finally:
+        ctx.hawkes_release_events(sid)
+    assert pi.shape == (70, ev.n)
+    assert [ll[k] for k in (0, 63, 64, 69)] == singles
+    ref = ev.rounded32() if mode == 1 else ev
+    tol = 5e-6 if mode == 1 else 1e-12
+    for k in (0, 64, 69):
+        r = oracle.rows(ref.x, ref.y, ref.t, ths[k], np.arange(ev.n))
+        want = r["xi"] / (r["mu"] + r["xi"])
+        np.testing.assert_allclose(pi[k], want, rtol=tol, atol=tol)
+    assert np.all((pi >= 0) & (pi <= 1))
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["fp64", "mixed"])
 def test_exact_zero_window_matches_dense(ctx, mode):
     """Skipping the columns whose pair terms are exactly zero at the working precision changes
     nothing but the grouping of the float64 partial sums."""
