@@ -109,6 +109,32 @@ def test_event_terms_rows(ctx, mode):
     assert np.all((pi >= 0) & (pi <= 1))
 
 
+def _golden_cases():
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "small_cases.json")) as fh:
+        return json.load(fh)["cases"]
+
+
+@pytest.mark.parametrize("case", _golden_cases(), ids=lambda c: c["name"])
+@pytest.mark.parametrize("mode", [0, 1], ids=["fp64", "mixed"])
+def test_golden_cases(ctx, case, mode):
+    """The stored oracle values of tests/golden/small_cases.json: FP64 path against the values for
+    the float64 inputs, mixed path against those for the float32-rounded inputs."""
+    x, y, t = (np.asarray(case[k], dtype=np.float64) for k in ("x", "y", "t"))
+    ctx.hawkes_set_flags(case["flags"])
+    sid = ctx.hawkes_upload_events(x, y, t)
+    try:
+        ll, g = ctx.hawkes_loglik_grad(sid, case["theta"], mode)
+    finally:
+        ctx.hawkes_release_events(sid)
+        ctx.hawkes_set_flags(0)
+    want = case["f64" if mode == 0 else "f32in"]
+    tol_ll, tol_g = (TOL_FP64_LL, TOL_FP64_G) if mode == 0 else (TOL_MIXED_LL, TOL_MIXED_G)
+    assert rel(ll, want["loglik"]) <= tol_ll, (ll, want["loglik"])
+    assert grad_err(g, np.asarray(want["grad"])) <= tol_g, (g, want["grad"])
+
+
 @pytest.mark.parametrize("mode", [0, 1], ids=["fp64", "mixed"])
 def test_pi_batch(ctx, mode):
     """Eq. 2 at 70 parameter vectors (two launches): each row against the oracle's per-event
