@@ -182,6 +182,30 @@ def batched_chains(ctx, sid, n, stream):
             "pairs_visited_per_launch": visited, "note": "host-timed, results copied back each launch"}
 
 
+def small_fp64_loglik(ctx, stream):
+    """The plain FP64 log-likelihood on the small workload (N=2,000 over 1,000 days, float64
+    coordinates, Theta0), device-timed over 50 evaluations."""
+    import torch
+    from paper_2005_10123_gb300 import binding
+    ev = synth.small_workload()
+    sid = ctx.hawkes_upload_events(ev.x, ev.y, ev.t)
+    out = torch.zeros(7, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        ctx.hawkes_loglik_async(sid, THETA0, binding.HAWKES_FP64, False, out.data_ptr())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(50):
+        ctx.hawkes_loglik_async(sid, THETA0, binding.HAWKES_FP64, False, out.data_ptr())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 50
+    ll = float(out[0].item())
+    ctx.hawkes_release_events(sid)
+    return {"events": int(ev.n), "ms_per_eval": ms, "value": float(ev.n) ** 2 / (ms * 1e-3), "unit": "pair-evals/s",
+            "loglik": ll}
+
+
 def pi_posterior(ctx, sid, n, k: int = 256):
     """Eq. 2 over a sample of k parameter vectors (the posterior-probability workload of
     Section 3.2, there 1,000 vectors on 55,000 events): one hawkes_pi_batch call, k x N
@@ -308,6 +332,16 @@ def run_ours(args):
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
+    if args.profile_batch:
+        # the grouped-kernel profiling case: K loglik+grad requests on the set per launch
+        from paper_2005_10123_gb300 import binding
+        ths = synth.theta_batch(args.profile_batch, seed=20053)
+        for _ in range(args.warmup + args.steps):
+            ll, _ = ctx.hawkes_loglik_batch(sid, ths, binding.HAWKES_MIXED, want_grad=True)
+        print(json.dumps({"profile_case": f"{args.profile_batch} x " + WORKLOAD, "launches": args.warmup + args.steps,
+                          "loglik0": float(ll[0])}))
+        ctx.close()
+        return 0
     if args.profile:
         # the profiling case: only the timed kernel sequence, nothing else
         for _ in range(args.steps):
@@ -384,6 +418,7 @@ def run_ours(args):
         if not args.no_extras:
             extra["batched_chains"] = batched_chains(ctx, sid, n, stream)
             extra["pi_posterior"] = pi_posterior(ctx, sid, n)
+            extra["small_fp64_loglik"] = small_fp64_loglik(ctx, stream)
             extra["mh_chain"] = mh_chain(ctx, sid, args.mh_iters)
             extra["serving"] = serving_runs(ctx, args.serving_requests)
 
@@ -461,6 +496,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip batched chains, MH chain and serving")
     ap.add_argument("--mh-iters", type=int, default=10000)
     ap.add_argument("--serving-requests", type=int, default=1000)
+    ap.add_argument("--profile-batch", type=int, default=0, metavar="K",
+                    help="run only warm-up + steps launches of K batched loglik+grad requests (grouped kernel)")
     ap.add_argument("--profile", action="store_true",
                     help="run only warm-up + steps of the mixed loglik+grad call (the case profiled with ncu)")
     args = ap.parse_args()

@@ -318,13 +318,21 @@ int launch_batch(hawkes_ctx *ctx, Batch &b, int mode, int grad, cudaStream_t s) 
   b.mode = mode == HAWKES_MIXED ? 1 : 0;
   b.fused = 1;
   long long items = 0;
-  for (int r = 0; r < b.nreq; ++r) {
-    b.req[r].item_begin = (int)items;
-    items += request_items(b.req[r]);
+  if (b.group) {  // grouped kernel: every request's compensator items, then the groups' pair items
+    const int G = b.group;
+    for (int r = 0; r < b.nreq; ++r) items += comp_items(b.req[r]);
+    b.comp_total = (int)items;
+    items += (long long)((b.nreq + G - 1) / G) * pair_items(b.req[0]);
+  } else {
+    for (int r = 0; r < b.nreq; ++r) {
+      b.req[r].item_begin = (int)items;
+      items += request_items(b.req[r]);
+    }
   }
   if (items > 0x7fffffffLL) return HAWKES_E_INVAL;
   b.total_items = (int)items;
-  if (mode == HAWKES_MIXED) HK_CUDA(ctx, launch_pair_mixed(b, grad != 0, s));
+  if (b.group) HK_CUDA(ctx, launch_pair_group(b, grad != 0, s));
+  else if (mode == HAWKES_MIXED) HK_CUDA(ctx, launch_pair_mixed(b, grad != 0, s));
   else HK_CUDA(ctx, launch_pair_fp64(b, grad != 0, s));
   return HAWKES_OK;
 }
@@ -390,20 +398,33 @@ int eval_sync(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_params *param
   char *cnt_base = base + kFixedBytes;
   char *rows_base = cnt_base + cnt;
   char *req_base = rows_base + rows_bytes;
+  // Two or more mixed-precision requests on this set share each pair's geometry (grouped
+  // kernel, moments in raw units). Groups are consecutive requests in order of tau_t, so a
+  // group's members have similar column windows; request r of the launch is params[order[r]]
+  // and writes its results to that parameter vector's place.
+  const bool grouped = k >= 2 && mode == HAWKES_MIXED && group_size(grad != 0) > 1;
+  int order[kMaxBatch];
+  for (int r = 0; r < k; ++r) order[r] = r;
+  if (grouped)
+    std::stable_sort(order, order + k, [&](int a, int c) { return params[a].tau_t < params[c].tau_t; });
   for (int r = 0; r < k; ++r) {
-    if (int rc = make_request(ctx, S, &params[r], mode, grad, ctx->flags, &b->req[r])) return rc;
+    const int q = order[r];
+    if (int rc = make_request(ctx, S, &params[q], mode, grad, ctx->flags, &b->req[r])) return rc;
     bind_workspace(&b->req[r], S, mode, grad, req_base + (size_t)r * per,
-                   device_out ? device_out : outs + 8 * r,
+                   device_out ? device_out : outs + 8 * q,
                    (unsigned *)(cnt_base + (size_t)r * counter_bytes(S, mode, grad)));
+    if (grouped) b->req[r].tscale = 1.0;
   }
+  if (grouped) b->group = group_size(grad != 0);
   char *rows_cur = rows_base;
   if (mu_out || xi_out) {
     b->req[0].mu_out = (double *)rows_cur;
     b->req[0].xi_out = (double *)(rows_cur + row_bytes);
     rows_cur += 2 * row_bytes;
   }
+  char *pi_rows = rows_cur;  // row q holds pi for params[q]
   if (pi_out)
-    for (int r = 0; r < k; ++r) b->req[r].pi_out = (double *)(rows_cur + (size_t)r * row_bytes);
+    for (int r = 0; r < k; ++r) b->req[r].pi_out = (double *)(pi_rows + (size_t)order[r] * row_bytes);
   HK_CUDA(ctx, cudaMemsetAsync(base, 0, kFixedBytes + cnt, ctx->stream));
   if (int rc = launch_batch(ctx, *b, mode, grad, ctx->stream)) return rc;
   if (device_out) return HAWKES_OK;
@@ -413,9 +434,9 @@ int eval_sync(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_params *param
   if (mu_out) HK_CUDA(ctx, cudaMemcpyAsync(mu_out, b->req[0].mu_out, nb, cudaMemcpyDeviceToHost, ctx->stream));
   if (xi_out) HK_CUDA(ctx, cudaMemcpyAsync(xi_out, b->req[0].xi_out, nb, cudaMemcpyDeviceToHost, ctx->stream));
   if (pi_out)
-    for (int r = 0; r < k; ++r)
-      HK_CUDA(ctx, cudaMemcpyAsync(pi_out + (size_t)r * S->n, b->req[r].pi_out, nb, cudaMemcpyDeviceToHost,
-                                   ctx->stream));
+    for (int q = 0; q < k; ++q)
+      HK_CUDA(ctx, cudaMemcpyAsync(pi_out + (size_t)q * S->n, pi_rows + (size_t)q * row_bytes, nb,
+                                   cudaMemcpyDeviceToHost, ctx->stream));
   HK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   std::memcpy(host_out, ctx->pinned_out, (size_t)k * 8 * sizeof(double));
   return HAWKES_OK;

@@ -125,6 +125,8 @@ struct Batch {
   int total_items;  // pair-kernel items (= CTAs) over all requests
   int mode;         // 0 fp64, 1 mixed (one mode per launch)
   int fused;        // 1: the pair kernel finishes each row tile and each request itself
+  int group;        // 0, or the grouped kernel's group size (every request on one set)
+  int comp_total;   // grouped kernel: compensator items, first in the launch
   Request req[kMaxBatch];
 };
 
@@ -155,6 +157,11 @@ __host__ __device__ inline int2 slot_tile(const Request &R, int p) {
 // b.total_items.
 cudaError_t launch_pair_mixed(const Batch &b, bool grad, cudaStream_t s);
 cudaError_t launch_pair_fp64(const Batch &b, bool grad, cudaStream_t s);
+// Grouped mixed kernel (pair_group.cu): requests on one set in groups of group_size(grad), each
+// pair's geometry shared by the group. Items: nreq * nrt compensator items, then
+// ceil(nreq / group_size(grad)) * nrt * slices pair items. b.group must equal group_size(grad).
+cudaError_t launch_pair_group(const Batch &b, bool grad, cudaStream_t s);
+int group_size(bool grad);
 // Resident CTAs per SM of each pair kernel (sets the number of slices).
 int occupancy_pair_mixed(bool grad);
 int occupancy_pair_fp64(bool grad);

@@ -146,10 +146,22 @@ static void fake_outputs(const Batch &b, bool grad) {
 static cudaError_t fake_pair(const Batch &b, bool grad) {
   g_launches++;
   int items = 0;
-  for (int r = 0; r < b.nreq; ++r) {
-    if (b.req[r].item_begin != items) g_schedule_errors++;
-    items += request_items(b.req[r]);
-    check_schedule(b.req[r]);
+  if (b.group) {  // grouped kernel: compensator items, then one item per (group, row tile, slice)
+    for (int r = 0; r < b.nreq; ++r) {
+      items += comp_items(b.req[r]);
+      check_schedule(b.req[r]);
+      const Request &R = b.req[r], &L = b.req[0];
+      if (R.set.x32 != L.set.x32 || R.slices != L.slices || R.flags != L.flags || R.tscale != 1.0)
+        g_schedule_errors++;  // one set, one decomposition, raw-unit moments
+    }
+    if (items != b.comp_total || b.mode != 1) g_schedule_errors++;
+    items += (b.nreq + b.group - 1) / b.group * pair_items(b.req[0]);
+  } else {
+    for (int r = 0; r < b.nreq; ++r) {
+      if (b.req[r].item_begin != items) g_schedule_errors++;
+      items += request_items(b.req[r]);
+      check_schedule(b.req[r]);
+    }
   }
   if (items != b.total_items || !b.fused) g_schedule_errors++;
   fake_outputs(b, grad);
@@ -158,6 +170,11 @@ static cudaError_t fake_pair(const Batch &b, bool grad) {
 
 cudaError_t launch_pair_mixed(const Batch &b, bool grad, cudaStream_t) { return fake_pair(b, grad); }
 cudaError_t launch_pair_fp64(const Batch &b, bool grad, cudaStream_t) { return fake_pair(b, grad); }
+cudaError_t launch_pair_group(const Batch &b, bool grad, cudaStream_t) {
+  if (!b.group) g_schedule_errors++;
+  return fake_pair(b, grad);
+}
+int group_size(bool grad) { return grad ? 4 : 8; }
 
 int occupancy_pair_mixed(bool) { return 4; }
 int occupancy_pair_fp64(bool) { return 2; }

@@ -81,7 +81,8 @@ def main():
     mu, xi, _ = ctx.hawkes_event_terms(sids[1000], TH, 1)
     assert np.array_equal(mu, np.arange(1000)) and np.array_equal(xi, -np.arange(1000))
     # pi for 70 parameter vectors: two launches (64 + 6), every row lands at its own offset
-    ths = np.array([[0.001 * (r + 1), 1, 30, 0.5, 1, 0.1] for r in range(70)])
+    # tau_t falls with r, so the grouped launch (ordered by tau_t) reverses the requests
+    ths = np.array([[0.001 * (r + 1), 1, 100.0 - r, 0.5, 1, 0.1] for r in range(70)])
     pi, ll = ctx.hawkes_pi_batch(sids[1000], ths, 1)
     assert pi.shape == (70, 1000)
     assert np.array_equal(pi, ths[:, :1] + np.arange(1000)[None, :])
