@@ -457,7 +457,8 @@ def run_ours(args):
                        "pairs_visited_per_step": visited,
                        "l2": "flushed between timed steps (256 MB write); the 1 MB event set is re-read from HBM",
                        "replicas": world},
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": args.steps,  # one pair_mixed_kernel per step (fused epilogue)
+            "memsets_per_step": 1,  # cudaMemsetAsync of the step's completion counters
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
                          "unit": "T FP32-pipe ops/s", "frac": achieved / peak,
                          "traffic": _profiled_traffic(kernel_hash),

@@ -762,7 +762,11 @@ int hawkes_upload_events(hawkes_ctx *ctx, const double *x, const double *y, cons
   S->t_first64 = T64[0]; S->t_last64 = T64[(size_t)n - 1];
   build_win_table(T32.data(), n, S->nct, &S->win32, &S->win32h);
   build_win_table(T64.data(), n, S->nct, &S->win64, &S->win64h);
-  for (int k = 0; k < kKinds; ++k) S->slices[k] = slices_for(S->nrt, S->nct, ctx->sms * ctx->occ[k]);
+  for (int k = 0; k < kKinds; ++k) {
+    // the float64 kernel can cut a column tile into chunks, the mixed kernels cannot
+    const int units = k == kind_of(HAWKES_FP64, 0) ? S->nct * fp64_chunks_per_tile() : S->nct;
+    S->slices[k] = slices_for(S->nrt, units, ctx->sms * ctx->occ[k]);
+  }
   // one device allocation
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off += align_up(bytes, 256); return o; };

@@ -165,6 +165,9 @@ int group_size(bool grad);
 // Resident CTAs per SM of each pair kernel (sets the number of slices).
 int occupancy_pair_mixed(bool grad);
 int occupancy_pair_fp64(bool grad);
+// Column chunks per column tile in the float64 kernel's slices (a slice may be shorter than a
+// column tile there).
+int fp64_chunks_per_tile();
 
 // Item lookup: the request whose [item_begin, next item_begin) holds `item`.
 __host__ __device__ inline int find_request(const Batch &b, int item) {

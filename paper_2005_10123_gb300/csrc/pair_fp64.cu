@@ -16,15 +16,21 @@ constexpr double kPadTime = 1.0e150;  // time of a padded event: dt^2 = 1e300 st
 constexpr int kRows64 = 4;
 constexpr int kThreads64 = kRowTile / kRows64;
 constexpr int kWarpRows64 = 32 * kRows64;
+// Slices cut the column window at kChunk64-column granularity (float64 pair work is slow
+// enough that a small set needs items smaller than a column tile to fill the GPU).
+constexpr int kChunk64 = 32;
+constexpr int kChunksPerTile64 = kColTile / kChunk64;
+static_assert(kColTile % kChunk64 == 0, "column chunks must tile a column tile");
 
 template <int KIND, bool GRAD>
 __device__ __forceinline__ void tile_pass64(const double *__restrict__ sx, const double *__restrict__ sy,
                                             const double *__restrict__ st, const double (&X)[4],
                                             const double (&Y)[4], const double (&T)[4], const int (&LO)[4],
-                                            int row_a0, int c0, bool excl, double da, double db, double dc,
-                                            double omega, double (&acc)[GRAD ? kSumsGrad : kSumsLoglik][4]) {
+                                            int row_a0, int c0, int j0, int j1, bool excl, double da, double db,
+                                            double dc, double omega,
+                                            double (&acc)[GRAD ? kSumsGrad : kSumsLoglik][4]) {
 #pragma unroll 2
-  for (int j = 0; j < kColTile; ++j) {
+  for (int j = j0; j < j1; ++j) {
     const double cx = sx[j], cy = sy[j], ctj = st[j];
     const int col = c0 + j;
 #pragma unroll
@@ -97,14 +103,18 @@ __device__ void run_piece64(const Batch &B, const Request &R, int4 piece, int sl
       st[buf][jj] = j < n ? S.t64[j] : kPadTime;
     }
   };
-  int ct = piece.y;
-  if (ct < piece.z) {  // an empty slice of the window writes zero partial sums
+  // piece.y, piece.z: the item's column range in kChunk64-column chunks
+  const int col_begin = piece.y * kChunk64, col_end = piece.z * kChunk64;
+  int ct = piece.y / kChunksPerTile64;
+  const int ct_end = piece.y < piece.z ? (piece.z - 1) / kChunksPerTile64 + 1 : ct;
+  if (ct < ct_end) {  // an empty slice of the window writes zero partial sums
     stage(ct, 0);
     __syncthreads();
   }
-  for (int k = 0; ct < piece.z; ++ct, ++k) {
+  for (int k = 0; ct < ct_end; ++ct, ++k) {
     const int buf = k & 1;
     const int c0 = ct * kColTile, c1 = c0 + kColTile;
+    const int j0 = max(col_begin - c0, 0), j1 = min(col_end - c0, kColTile);
     int kind;
     if (c1 <= lo_wa) {  // every pair causal: which of the two terms can be nonzero?
       const double gap = t_first - st[buf][kColTile - 1];
@@ -118,14 +128,14 @@ __device__ void run_piece64(const Batch &B, const Request &R, int4 piece, int sl
     if (excl && c0 <= wb && c1 > wa) kind = 2;
     const int row_a0 = wa + lane;
     if (kind == 0)
-      tile_pass64<0, GRAD>(sx[buf], sy[buf], st[buf], X, Y, T, LO, row_a0, c0, excl, da, db, dc, omega, acc);
+      tile_pass64<0, GRAD>(sx[buf], sy[buf], st[buf], X, Y, T, LO, row_a0, c0, j0, j1, excl, da, db, dc, omega, acc);
     else if (kind == 1)
-      tile_pass64<1, GRAD>(sx[buf], sy[buf], st[buf], X, Y, T, LO, row_a0, c0, excl, da, db, dc, omega, acc);
+      tile_pass64<1, GRAD>(sx[buf], sy[buf], st[buf], X, Y, T, LO, row_a0, c0, j0, j1, excl, da, db, dc, omega, acc);
     else if (kind == 2)
-      tile_pass64<2, GRAD>(sx[buf], sy[buf], st[buf], X, Y, T, LO, row_a0, c0, excl, da, db, dc, omega, acc);
+      tile_pass64<2, GRAD>(sx[buf], sy[buf], st[buf], X, Y, T, LO, row_a0, c0, j0, j1, excl, da, db, dc, omega, acc);
     else if (kind == 3)
-      tile_pass64<3, GRAD>(sx[buf], sy[buf], st[buf], X, Y, T, LO, row_a0, c0, excl, da, db, dc, omega, acc);
-    if (ct + 1 < piece.z) stage(ct + 1, buf ^ 1);
+      tile_pass64<3, GRAD>(sx[buf], sy[buf], st[buf], X, Y, T, LO, row_a0, c0, j0, j1, excl, da, db, dc, omega, acc);
+    if (ct + 1 < ct_end) stage(ct + 1, buf ^ 1);
     __syncthreads();
   }
   // this thread's rows: li = warp * kWarpRows64 + lane + 32 k, sums in acc[s][k]
@@ -185,9 +195,10 @@ __global__ void __launch_bounds__(kThreads64) pair_fp64_kernel(const __grid_cons
     __syncthreads();
     w = s_win;
   }
-  const int width = w.y - w.x;
-  const int c_begin = w.x + (int)((long long)width * sl / ns);
-  const int c_end = w.x + (int)((long long)width * (sl + 1) / ns);
+  // the window in column chunks, cut into `ns` near-equal slices
+  const int cw0 = w.x * kChunksPerTile64, width = (w.y - w.x) * kChunksPerTile64;
+  const int c_begin = cw0 + (int)((long long)width * sl / ns);
+  const int c_end = cw0 + (int)((long long)width * (sl + 1) / ns);
   run_piece64<GRAD>(B, R, make_int4(rt, c_begin, c_end, 0), slot, sx, sy, st);
 }
 
@@ -199,6 +210,8 @@ cudaError_t launch_pair_fp64(const Batch &b, bool grad, cudaStream_t s) {
   else pair_fp64_kernel<false><<<b.total_items, kThreads64, 0, s>>>(b);
   return cudaGetLastError();
 }
+
+int fp64_chunks_per_tile() { return kChunksPerTile64; }
 
 int occupancy_pair_fp64(bool grad) {
   int n = 0;

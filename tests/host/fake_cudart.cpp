@@ -109,9 +109,10 @@ cudaError_t cudaEventQuery(cudaEvent_t e) {
 namespace hk {
 
 // Check one request's work decomposition against its set.
-static void check_schedule(const Request &R) {
+static void check_schedule(const Request &R, int mode) {
   const SetView &S = R.set;
-  bool ok = R.slices >= 1 && R.slices <= S.nct;
+  // the float64 kernel's slices may cut column tiles into chunks
+  bool ok = R.slices >= 1 && R.slices <= S.nct * (mode == 0 ? fp64_chunks_per_tile() : 1);
   // the launch order visits every (row tile, slice) exactly once
   std::vector<char> seen((size_t)S.nrt * R.slices, 0);
   for (int p = 0; ok && p < pair_items(R); ++p) {
@@ -149,7 +150,7 @@ static cudaError_t fake_pair(const Batch &b, bool grad) {
   if (b.group) {  // grouped kernel: compensator items, then one item per (group, row tile, slice)
     for (int r = 0; r < b.nreq; ++r) {
       items += comp_items(b.req[r]);
-      check_schedule(b.req[r]);
+      check_schedule(b.req[r], b.mode);
       const Request &R = b.req[r], &L = b.req[0];
       if (R.set.x32 != L.set.x32 || R.slices != L.slices || R.flags != L.flags || R.tscale != 1.0)
         g_schedule_errors++;  // one set, one decomposition, raw-unit moments
@@ -160,7 +161,7 @@ static cudaError_t fake_pair(const Batch &b, bool grad) {
     for (int r = 0; r < b.nreq; ++r) {
       if (b.req[r].item_begin != items) g_schedule_errors++;
       items += request_items(b.req[r]);
-      check_schedule(b.req[r]);
+      check_schedule(b.req[r], b.mode);
     }
   }
   if (items != b.total_items || !b.fused) g_schedule_errors++;
@@ -175,6 +176,7 @@ cudaError_t launch_pair_group(const Batch &b, bool grad, cudaStream_t) {
   return fake_pair(b, grad);
 }
 int group_size(bool grad) { return grad ? 4 : 8; }
+int fp64_chunks_per_tile() { return 8; }
 
 int occupancy_pair_mixed(bool) { return 4; }
 int occupancy_pair_fp64(bool) { return 2; }
