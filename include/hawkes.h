@@ -170,7 +170,7 @@ int hawkes_pi_batch(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_params 
 /* ---- serving: continuous batching of requests from many chains ----------------------
  * hawkes_submit queues one request (set, Theta, gradient flag, mode) and returns a
  * ticket at once. A scheduler thread admits queued requests while their device
- * footprint fits the budget, groups them into persistent launches (up to 64
+ * footprint fits the budget, groups them into kernel launches (up to 64
  * requests each, several launches in flight on separate streams) and completes
  * tickets as launches finish. A request's result does not depend on what it was
  * batched with. */

@@ -1,11 +1,12 @@
 // Host runtime behind include/hawkes.h: contexts, resident event sets, synchronous and
 // batched evaluation, and the serving queue.
 //
-// Every evaluation is one "batch" launch pair on a stream: the persistent pair kernel
-// (mixed or fp64) fills per-row partial sums, then the epilogue kernel turns them into
-// log lambda_n - Lambda_n and the gradient terms and reduces them per request in a
-// fixed order. A request's arithmetic depends only on its own set, parameters and
-// work decomposition, never on the other requests of its batch.
+// Every evaluation is one "batch" launch on a stream (after one memset of its counters): the
+// pair kernel (mixed, fp64, or the grouped mixed kernel for several parameter vectors on one
+// set) runs one CTA per work item, merges each row tile's partial sums in a fixed tree and
+// finishes every row tile and request itself (log lambda_n - Lambda_n, gradient terms, fixed-
+// order reductions). Outside the grouped kernel a request's arithmetic depends only on its own
+// set, parameters and work decomposition, never on the other requests of its batch.
 #include <algorithm>
 #include <atomic>
 #include <chrono>

@@ -33,7 +33,8 @@ constexpr int kSumsLoglik = 2;                       // S_b, S_s
 constexpr int kSumsGrad = 6;                         // S_b, S_s, R_b, T_b, R_s, U_s
 constexpr int kFlagExcludeSelf = 1;                  // HAWKES_FLAG_EXCLUDE_SELF
 constexpr int kFlagDense = 2;                        // HAWKES_FLAG_DENSE
-constexpr int kMaxCtaWarps = 8;                      // pair-kernel CTAs have at most 256 threads
+// widest pair-kernel CTA: the grouped kernel's, two rows per thread
+constexpr int kMaxCtaWarps = (kRowTile / 2 > kThreads ? kRowTile / 2 : kThreads) / 32;
 static_assert(kThreads <= 32 * kMaxCtaWarps && kRowTile / 4 <= 32 * kMaxCtaWarps, "CTA too wide");
 
 // Column-tile lookup by time, built once per event set and precision: time is cut into nb

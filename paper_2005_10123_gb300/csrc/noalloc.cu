@@ -26,7 +26,7 @@ namespace {
 
 constexpr int kNoallocMax = HAWKES_NOALLOC_MAX_EVENTS;  // 65,536 events
 constexpr int kChunks = 4;                               // most column chunks per row tile
-constexpr int kMaxRowTiles = kNoallocMax / kRowTile;     // 128
+constexpr int kMaxRowTiles = (kNoallocMax + kRowTile - 1) / kRowTile;  // 128
 constexpr int kMaxItems = kMaxRowTiles * kChunks;        // 512
 
 // Layout of g_scratch (byte offsets, all 256-aligned).
@@ -229,7 +229,7 @@ extern "C" int hawkes_loglik_noalloc(const float *x, const float *y, const float
   R.out = device_out;
   R.t_last = 0.0;  // unused here: noalloc_epilogue reads t_N on the device
 
-  // the work counter and the epilogue ticket must start at zero on every call
+  // the epilogue ticket must start at zero on every call
   if (cudaMemsetAsync(base + kOffHeader, 0, 1024, s) != cudaSuccess) return HAWKES_E_CUDA;
   noalloc_prep<<<std::min(d->sms * 4, (npad + 255) / 256 + 1), 256, 0, s>>>(x, y, t, (int)n, npad, base);
   if (cudaGetLastError() != cudaSuccess) return HAWKES_E_CUDA;
