@@ -47,6 +47,24 @@ WORKLOAD = ("loglik+grad of Eq. 1, N=85,000 events over T=5,000 days (seeded bra
             "float32 coordinates), Theta0=(0.01,1.0,30,0.5,1.0,0.1), mixed precision")
 
 
+def max_over_ranks(x: float) -> float:
+    """The largest x over all ranks of the process group (x itself without one): a replicated
+    job's step takes as long as its slowest replica."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(pairs_per_step: float, world: int, step_ms: float) -> float:
+    """Whole-job pair-evals/s: every replica evaluates the full workload once per step."""
+    return world * pairs_per_step / (step_ms * 1e-3)
+
+
 def _dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -368,13 +386,10 @@ def run_ours(args):
     wall = time.perf_counter() - wall0
     clocks = sampler.stop()
     ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    step_ms = sum(ms) / len(ms)
+    step_ms = max_over_ranks(sum(ms) / len(ms))
     if world > 1:
-        t = torch.tensor([step_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        step_ms = float(t.item())
         torch.distributed.barrier()
-    value = world * pairs / (step_ms * 1e-3)
+    value = replica_value(pairs, world, step_ms)
     ll_mixed = float(out[0].item())
     work = ctx.hawkes_pair_work(sid, THETA0, binding.HAWKES_MIXED)
     visited = work["visited"]
@@ -435,11 +450,7 @@ def run_ours(args):
         ctx.hawkes_release_events(sid2)
         if k > 0:
             t_e2e.append(t1 - t0)
-    e2e_s = sum(t_e2e) / len(t_e2e)
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(sum(t_e2e) / len(t_e2e))
 
     kernel_hash = _kernel_source_hash()
     if rank == 0:
