@@ -311,3 +311,23 @@ def test_full_size_gradient_finite_differences(ctx, big):
         up[k] += h; dn[k] -= h
         fd = (ctx.hawkes_loglik(sid, up, 0) - ctx.hawkes_loglik(sid, dn, 0)) / (2 * h)
         assert abs(fd - g[k]) <= 1e-6 * max(abs(g[k]), 1e-3 * np.max(np.abs(g))), (k, fd, g[k])
+
+
+def test_largest_serving_size_sampled_rows(ctx):
+    """N = 300,000 over 5,000 days (the largest set of the serving workload): per-event terms of
+    the mixed path at sampled rows (tile edges, ties, both ends) against the oracle, and the
+    mixed log-likelihood and gradient against the FP64 path."""
+    from paper_2005_10123_gb300 import binding
+    ev = synth.simulate(300000, 5000.0, seed=30000, theta=0.6, omega=2.0).rounded32()
+    sid = ctx.hawkes_upload_events(ev.x, ev.y, ev.t)
+    try:
+        mu, xi, _ = ctx.hawkes_event_terms(sid, TH0, binding.HAWKES_MIXED)
+        llm, gm = ctx.hawkes_loglik_grad(sid, TH0, binding.HAWKES_MIXED)
+        ll64, g64 = ctx.hawkes_loglik_grad(sid, TH0, binding.HAWKES_FP64)
+    finally:
+        ctx.hawkes_release_events(sid)
+    idx = _sample_rows(ev)
+    r = oracle.rows(ev.x, ev.y, ev.t, TH0, idx)
+    np.testing.assert_allclose(mu[idx], r["mu"], rtol=1e-5)
+    np.testing.assert_allclose(xi[idx], r["xi"], rtol=1e-5, atol=1e-5 * np.max(r["xi"]))
+    assert rel(llm, ll64) <= TOL_MIXED_LL and grad_err(gm, g64) <= TOL_MIXED_G
