@@ -139,7 +139,8 @@ int hawkes_loglik_async(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *pa
 int hawkes_loglik_batch(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_params *params,
                         hawkes_mode mode, int want_grad, double *loglik_out, double *grad_out);
 
-/* Work accounting for an evaluation at Theta (host computation only, no GPU work):
+/* Work accounting for an evaluation at Theta (host computation on the set's stored times, read
+ * back from the device; no kernel launch):
  *   out[0] (row, column) pairs inside the exact-zero windows the kernels visit (see
  *          HAWKES_FLAG_DENSE), counted over real events;
  *   out[1] N^2, the pairs of Eq. 1's double sum;

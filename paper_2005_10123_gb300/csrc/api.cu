@@ -48,8 +48,6 @@ struct EventSetRec {
   double *x64 = nullptr, *y64 = nullptr, *t64 = nullptr;
   int *lo32 = nullptr, *lo64 = nullptr;
   double t_first32 = 0, t_last32 = 0, t_first64 = 0, t_last64 = 0;
-  std::vector<float> t32h;   // host copies of the stored times (for hawkes_pair_work)
-  std::vector<double> t64h;
   WinTable win32{}, win64{};  // column-tile lookups (device pointers)
   std::vector<int> win32h, win64h;  // host copies: first[nb] then last[nb]
   int slices[kKinds] = {1, 1, 1};  // slices per row tile, per kernel kind
@@ -106,6 +104,9 @@ struct hawkes_ctx {
   int32_t next_set = 1;
   Workspace sync_ws;
   double *pinned_out = nullptr;  // kMaxBatch * 8 doubles
+  cudaMemPool_t pool = nullptr;   // device memory of event sets and serving workspaces (stream-ordered)
+  char *stage = nullptr;          // pinned host staging for uploads (grows; guarded by mu)
+  size_t stage_bytes = 0;
   std::string last_cuda;
   // serving
   std::mutex smu;
@@ -152,14 +153,13 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // lo[i] = first index whose stored time equals t[i] (times sorted); padded entries get n.
 template <typename F>
-std::vector<int> tie_starts(const std::vector<F> &t, int64_t n, int64_t npad) {
-  std::vector<int> lo((size_t)npad, (int)n);
+void tie_starts(const F *t, int64_t n, int64_t npad, int *lo) {
   int64_t start = 0;
   for (int64_t i = 0; i < n; ++i) {
-    if (i > 0 && t[(size_t)i] != t[(size_t)(i - 1)]) start = i;
-    lo[(size_t)i] = (int)start;
+    if (i > 0 && t[i] != t[i - 1]) start = i;
+    lo[i] = (int)start;
   }
-  return lo;
+  for (int64_t i = n; i < npad; ++i) lo[i] = (int)n;
 }
 
 // Column-tile lookup table of a set's stored times (see WinTable): host copy in `h` (first[nb]
@@ -180,10 +180,18 @@ void build_win_table(const TT *t, int64_t n, int nct, WinTable *W, std::vector<i
     tile_last[(size_t)c] = (double)t[std::min<int64_t>((int64_t)(c + 1) * kColTile, n) - 1];
   }
   h->resize((size_t)2 * nb);
+  // both bucket edges and tile times ascend: one sweep each (lower / upper bound per bucket)
+  int c = 0;
   for (int b = 0; b < nb; ++b) {
-    const double lo = t0 + b * width, hi = t0 + (b + 1) * width;
-    (*h)[(size_t)b] = (int)(std::lower_bound(tile_last.begin(), tile_last.end(), lo) - tile_last.begin());
-    (*h)[(size_t)nb + b] = (int)(std::upper_bound(tile_first.begin(), tile_first.end(), hi) - tile_first.begin());
+    const double lo = t0 + b * width;
+    while (c < real && tile_last[(size_t)c] < lo) ++c;
+    (*h)[(size_t)b] = c;
+  }
+  c = 0;
+  for (int b = 0; b < nb; ++b) {
+    const double hi = t0 + (b + 1) * width;
+    while (c < real && tile_first[(size_t)c] <= hi) ++c;
+    (*h)[(size_t)nb + b] = c;
   }
   (void)nct;
   W->t0 = t0;
@@ -366,7 +374,9 @@ EventSetRec *find_set(hawkes_ctx *ctx, int32_t id) {
 }
 
 void free_set(hawkes_ctx *ctx, EventSetRec *S) {
-  if (S->dev) cudaFree(S->dev);
+  // stream-ordered: after the work already queued on the context's stream, the last user of a
+  // set outside serving (serving requests hold a reference until their launch has finished)
+  if (S->dev) cudaFreeAsync(S->dev, ctx->stream);
   ctx->used -= S->bytes;
   delete S;
 }
@@ -546,7 +556,7 @@ bool launch_pending(hawkes_ctx *ctx, Flight &F) {
   int rc = HAWKES_OK;
   cnt = align_up(cnt, 256);
   bytes = align_up(bytes, 256) + 256;
-  cudaError_t e = cudaMallocAsync(&ws, bytes, F.stream);
+  cudaError_t e = cudaMallocFromPoolAsync(&ws, bytes, ctx->pool, F.stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(ws, 0, kFixedBytes + cnt, F.stream);
   if (e != cudaSuccess) rc = cuda_fail(ctx, e);
   if (rc == HAWKES_OK) {
@@ -682,6 +692,20 @@ int hawkes_create(hawkes_ctx **out, int device, size_t hbm_budget_bytes, void *c
   ctx->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.9 * (double)free_b);
   e = cudaMallocHost((void **)&ctx->pinned_out, kMaxBatch * 8 * sizeof(double));
   if (e != cudaSuccess) return cuda_fail(nullptr, e);
+  // the context's own device memory pool; it keeps freed memory for reuse (the HBM budget
+  // bounds what the context holds) and returns it when the context is destroyed
+  cudaMemPoolProps props;
+  std::memset(&props, 0, sizeof(props));
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = device;
+  e = cudaMemPoolCreate(&ctx->pool, &props);
+  if (e != cudaSuccess) {
+    cudaFreeHost(ctx->pinned_out);
+    return cuda_fail(nullptr, e);
+  }
+  uint64_t keep = ~(uint64_t)0;
+  cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep);
   *out = ctx.release();
   return HAWKES_OK;
 }
@@ -712,12 +736,15 @@ int hawkes_destroy(hawkes_ctx *ctx) {
     if (F.host_out) cudaFreeHost(F.host_out);
   }
   for (auto &kv : ctx->sets) {
-    if (kv.second->dev) cudaFree(kv.second->dev);
+    if (kv.second->dev) cudaFreeAsync(kv.second->dev, ctx->stream);
     delete kv.second;
   }
   ctx->sets.clear();
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
   if (ctx->sync_ws.dev) cudaFree(ctx->sync_ws.dev);
   if (ctx->pinned_out) cudaFreeHost(ctx->pinned_out);
+  if (ctx->stage) cudaFreeHost(ctx->stage);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return HAWKES_OK;
@@ -734,12 +761,6 @@ int hawkes_upload_events(hawkes_ctx *ctx, const double *x, const double *y, cons
                          int32_t *set_id_out) {
   if (!ctx || !x || !y || !t || !set_id_out || n < 1) return HAWKES_E_INVAL;
   if (n > (int64_t)1 << 30) return HAWKES_E_INVAL;
-  for (int64_t i = 0; i < n; ++i) {
-    if (!std::isfinite(x[i]) || !std::isfinite(y[i]) || !std::isfinite(t[i]) || t[i] < 0.0) return HAWKES_E_INVAL;
-    if (std::fabs(x[i]) > 1e30 || std::fabs(y[i]) > 1e30 || t[i] > 1e30) return HAWKES_E_INVAL;
-  }
-  for (int64_t i = 1; i < n; ++i)
-    if (!(t[i] >= t[i - 1])) return HAWKES_E_UNSORTED;
   cudaSetDevice(ctx->device);
   const int64_t npad = (int64_t)align_up((size_t)n, kPadTo);
   std::unique_ptr<EventSetRec> S(new EventSetRec());
@@ -747,51 +768,83 @@ int hawkes_upload_events(hawkes_ctx *ctx, const double *x, const double *y, cons
   S->npad = npad;
   S->nrt = (int)(npad / kRowTile);
   S->nct = (int)(npad / kColTile);
-  // host staging: float64 and float32 SoA, padded with zeros (the kernels substitute
-  // a sentinel time for padded events)
-  std::vector<double> X64((size_t)npad, 0.0), Y64((size_t)npad, 0.0), T64((size_t)npad, 0.0);
-  std::vector<float> X32((size_t)npad, 0.f), Y32((size_t)npad, 0.f), T32((size_t)npad, 0.f);
-  for (int64_t i = 0; i < n; ++i) {
-    X64[(size_t)i] = x[i]; Y64[(size_t)i] = y[i]; T64[(size_t)i] = t[i];
-    X32[(size_t)i] = (float)x[i]; Y32[(size_t)i] = (float)y[i]; T32[(size_t)i] = (float)t[i];
-  }
-  for (int64_t i = n; i < npad; ++i) { T64[(size_t)i] = t[n - 1]; T32[(size_t)i] = (float)t[n - 1]; }
-  std::vector<int> lo32 = tie_starts(T32, n, npad), lo64 = tie_starts(T64, n, npad);
-  S->t32h.assign(T32.begin(), T32.begin() + n);
-  S->t64h.assign(T64.begin(), T64.begin() + n);
-  S->t_first32 = T32[0]; S->t_last32 = T32[(size_t)n - 1];
-  S->t_first64 = T64[0]; S->t_last64 = T64[(size_t)n - 1];
-  build_win_table(T32.data(), n, S->nct, &S->win32, &S->win32h);
-  build_win_table(T64.data(), n, S->nct, &S->win64, &S->win64h);
   for (int k = 0; k < kKinds; ++k) {
     // the float64 kernel can cut a column tile into chunks, the mixed kernels cannot
     const int units = k == kind_of(HAWKES_FP64, 0) ? S->nct * fp64_chunks_per_tile() : S->nct;
     S->slices[k] = slices_for(S->nrt, units, ctx->sms * ctx->occ[k]);
   }
-  // one device allocation
+  // one device allocation: float32 and float64 SoA, tie indices, the two window tables
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off += align_up(bytes, 256); return o; };
   const size_t o_x32 = take(npad * 4), o_y32 = take(npad * 4), o_t32 = take(npad * 4);
   const size_t o_x64 = take(npad * 8), o_y64 = take(npad * 8), o_t64 = take(npad * 8);
   const size_t o_lo32 = take(npad * 4), o_lo64 = take(npad * 4);
-  const size_t o_w32 = take(S->win32h.size() * 4), o_w64 = take(S->win64h.size() * 4);
+  const size_t o_w32 = take((size_t)2 * kWinBuckets * 4), o_w64 = take((size_t)2 * kWinBuckets * 4);
   const size_t bytes = off;
   std::lock_guard<std::mutex> lock(ctx->mu);
   if (ctx->used.load() + bytes > ctx->budget) return HAWKES_E_ADMISSION;
+  if (ctx->stage_bytes < bytes) {  // pinned staging, kept for later uploads
+    if (ctx->stage) cudaFreeHost(ctx->stage);
+    ctx->stage = nullptr;
+    ctx->stage_bytes = 0;
+    cudaError_t es = cudaMallocHost((void **)&ctx->stage, bytes);
+    if (es != cudaSuccess) {
+      ctx->stage = nullptr;
+      return cuda_fail(ctx, es);
+    }
+    ctx->stage_bytes = bytes;
+  }
+  // staging, written in place in pinned memory: coordinates padded with zeros and times with
+  // t_N (the kernels substitute a sentinel time for padded events)
+  // (the inputs are checked in the same passes: finite coordinates within 1e30, times in
+  // [0, 1e30] and non-decreasing; a comparison with NaN is false)
+  char *host = ctx->stage;
+  float *X32 = (float *)(host + o_x32), *Y32 = (float *)(host + o_y32), *T32 = (float *)(host + o_t32);
+  double *X64 = (double *)(host + o_x64), *Y64 = (double *)(host + o_y64), *T64 = (double *)(host + o_t64);
+  bool bad = false, unsorted = false;
+  for (int64_t i = 0; i < n; ++i) {
+    const double v = x[i];
+    X64[i] = v;
+    X32[i] = (float)v;
+    bad |= !(std::fabs(v) <= 1e30);
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    const double v = y[i];
+    Y64[i] = v;
+    Y32[i] = (float)v;
+    bad |= !(std::fabs(v) <= 1e30);
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    const double v = t[i];
+    T64[i] = v;
+    T32[i] = (float)v;
+    bad |= !(v >= 0.0 && v <= 1e30);
+  }
+  for (int64_t i = 1; i < n; ++i) unsorted |= !(t[i] >= t[i - 1]);
+  if (bad) return HAWKES_E_INVAL;
+  if (unsorted) return HAWKES_E_UNSORTED;
+  for (int64_t i = n; i < npad; ++i) {
+    X64[i] = 0.0; Y64[i] = 0.0; T64[i] = t[n - 1];
+    X32[i] = 0.f; Y32[i] = 0.f; T32[i] = (float)t[n - 1];
+  }
+  tie_starts(T32, n, npad, (int *)(host + o_lo32));
+  tie_starts(T64, n, npad, (int *)(host + o_lo64));
+  S->t_first32 = T32[0]; S->t_last32 = T32[n - 1];
+  S->t_first64 = T64[0]; S->t_last64 = T64[n - 1];
+  build_win_table(T32, n, S->nct, &S->win32, &S->win32h);
+  build_win_table(T64, n, S->nct, &S->win64, &S->win64h);
+  if (!S->win32h.empty()) std::memcpy(host + o_w32, S->win32h.data(), S->win32h.size() * 4);
+  if (!S->win64h.empty()) std::memcpy(host + o_w64, S->win64h.data(), S->win64h.size() * 4);
   void *dev = nullptr;
-  cudaError_t e = cudaMalloc(&dev, bytes);
+  cudaError_t e = cudaMallocFromPoolAsync(&dev, bytes, ctx->pool, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e);
   char *d = (char *)dev;
-  std::vector<char> host(bytes, 0);
-  auto put = [&](size_t o, const void *src, size_t nb) { std::memcpy(host.data() + o, src, nb); };
-  put(o_x32, X32.data(), npad * 4); put(o_y32, Y32.data(), npad * 4); put(o_t32, T32.data(), npad * 4);
-  put(o_x64, X64.data(), npad * 8); put(o_y64, Y64.data(), npad * 8); put(o_t64, T64.data(), npad * 8);
-  put(o_lo32, lo32.data(), npad * 4); put(o_lo64, lo64.data(), npad * 4);
-  if (!S->win32h.empty()) put(o_w32, S->win32h.data(), S->win32h.size() * 4);
-  if (!S->win64h.empty()) put(o_w64, S->win64h.data(), S->win64h.size() * 4);
-  e = cudaMemcpyAsync(dev, host.data(), bytes, cudaMemcpyHostToDevice, ctx->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-  if (e != cudaSuccess) { cudaFree(dev); return cuda_fail(ctx, e); }
+  e = cudaMemcpyAsync(dev, host, bytes, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);  // the staging buffer is reused
+  if (e != cudaSuccess) {
+    cudaFreeAsync(dev, ctx->stream);
+    return cuda_fail(ctx, e);
+  }
   S->dev = dev;
   S->bytes = bytes;
   S->x32 = (float *)(d + o_x32); S->y32 = (float *)(d + o_y32); S->t32 = (float *)(d + o_t32);
@@ -844,7 +897,15 @@ int hawkes_pair_work(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *param
   const int64_t n = S->n;
   // stored times of the mode, as doubles
   std::vector<double> t((size_t)n);
-  for (int64_t i = 0; i < n; ++i) t[(size_t)i] = mode == HAWKES_MIXED ? (double)S->t32h[(size_t)i] : S->t64h[(size_t)i];
+  if (mode == HAWKES_MIXED) {
+    std::vector<float> t32((size_t)n);
+    HK_CUDA(ctx, cudaMemcpyAsync(t32.data(), S->t32, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    HK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int64_t i = 0; i < n; ++i) t[(size_t)i] = (double)t32[(size_t)i];
+  } else {
+    HK_CUDA(ctx, cudaMemcpyAsync(t.data(), S->t64, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    HK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  }
   // exact-zero reach (days) of each term on its own (the window uses the larger on the early side)
   double bg_reach, trig_reach;
   if (mode == HAWKES_MIXED) {

@@ -66,6 +66,15 @@ cudaError_t cudaMalloc(void **p, size_t n) {
   return cudaSuccess;
 }
 cudaError_t cudaMallocAsync(void **p, size_t n, cudaStream_t) { return cudaMalloc(p, n); }
+cudaError_t cudaMallocFromPoolAsync(void **p, size_t n, cudaMemPool_t, cudaStream_t) { return cudaMalloc(p, n); }
+cudaError_t cudaMemPoolCreate(cudaMemPool_t *pool, const cudaMemPoolProps *) {
+  static int token;
+  *pool = reinterpret_cast<cudaMemPool_t>(&token);
+  g_live_allocs++;
+  return cudaSuccess;
+}
+cudaError_t cudaMemPoolDestroy(cudaMemPool_t) { g_live_allocs--; return cudaSuccess; }
+cudaError_t cudaMemPoolSetAttribute(cudaMemPool_t, cudaMemPoolAttr, void *) { return cudaSuccess; }
 cudaError_t cudaFree(void *p) { if (p) { std::free(p); g_live_allocs--; } return cudaSuccess; }
 cudaError_t cudaFreeAsync(void *p, cudaStream_t) { return cudaFree(p); }
 cudaError_t cudaMallocHost(void **p, size_t n) {
