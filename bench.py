@@ -36,12 +36,12 @@ METRIC = "pair-evals/s (loglik+grad, N=85k) mixed vs FP64 on GB300 at <=1e-6 rel
 N_EVENTS = 85000
 THETA0 = synth.THETA0
 # Algorithmic FP32 operations per term (loglik + gradient): a background term costs the three
-# differences (dx, dy, dt), r^2 (a multiply and an FMA), the exponent (dt^2 and an FMA), the
-# accumulation and two moments = 10; a trigger term its exponent (1, or 2 where the causal
-# test runs per pair), the accumulation, two moments and the indicator or row factor = 5 (it
-# shares the differences and r^2). Only terms that can be nonzero at the working precision are
-# algorithmic work.
-FP32_OPS_BG_GRAD, FP32_OPS_TRIG_GRAD = 10.0, 5.0
+# differences (dx, dy, dt of coordinates pre-scaled to the kernel's bandwidths), dt^2, the
+# quadratic form (two FMAs onto dt^2), the accumulation and two moments = 9; a trigger term
+# its exponent (1, or 2 where the causal test runs per pair), the accumulation, two moments
+# and the indicator or row factor = 5 (it shares the differences and r^2). Only terms that
+# can be nonzero at the working precision are algorithmic work.
+FP32_OPS_BG_GRAD, FP32_OPS_TRIG_GRAD = 9.0, 5.0
 SMS, FP32_LANES, EX2_LANES, MAX_MHZ = 152, 128, 32, 2070.0
 WORKLOAD = ("loglik+grad of Eq. 1, N=85,000 events over T=5,000 days (seeded branching simulation, "
             "float32 coordinates), Theta0=(0.01,1.0,30,0.5,1.0,0.1), mixed precision")

@@ -6,17 +6,20 @@
 //   S_b = sum_n'           e_b,   e_b = exp(-r^2/(2 tau_x^2) - dt^2/(2 tau_t^2))
 //   S_s = sum_{t_n' < t_n} e_s,   e_s = exp(-omega dt - r^2/(2 h^2))
 //   R_b = sum r^2 e_b,  T_b = sum dt'^2 e_b,  R_s = sum r^2 e_s,  U_s = sum dt' e_s
-// with r^2 = |x_n - x_n'|^2 from exact float32 differences of the stored coordinates, and
-// dt' = beta (t_n - t_n'), beta^2 = log2(e)/(2 tau_t^2); times enter relative to the first
-// row of the tile before scaling, so nearby time differences keep full relative precision.
-// The CTA that completes a row tile's merge tree turns its row sums into lambda_n,
-// log lambda_n and the gradient in float64 (fused epilogue).
+// with r^2 = |x_n - x_n'|^2 and dt' = beta (t_n - t_n'), beta^2 = log2(e)/(2 tau_t^2); times
+// enter relative to the first row of the tile before scaling, so nearby time differences
+// keep full relative precision. The CTA that completes a row tile's merge tree turns its row
+// sums into lambda_n, log lambda_n and the gradient in float64 (fused epilogue).
 //
 // Arithmetic per (row, column) pair, two rows per packed f32x2 value:
-//   e_b = 2^-q with q = a2 r^2 + dt'^2, a2 = log2(e)/(2 tau_x^2);
+//   e_b = 2^-q with q = a2 r^2 + dt'^2, a2 = s^2 = log2(e)/(2 tau_x^2);
 //   e_s = 2^(cn r^2 + wn dt'), cn = -log2(e)/(2 h^2), wn = -omega log2(e)/beta.
+// Tiles with background terms only (most of the window) take the differences of coordinates
+// pre-scaled by s, q = (s dx)^2 + (s dy)^2 + dt'^2; tiles with trigger terms take r^2 from
+// exact float32 differences of the stored coordinates. Sum 2 accumulates Q = sum q e_b, and
+// the epilogue forms R_b = (Q - T_b) / s^2 in float64.
 // In tiles where every pair is causal the trigger factor 2^(wn dt') splits into a column
-// factor 2^(wn (t'_ref - t'_n')) folded into the exponent at staging and a row factor
+// factor 2^(wn (t'_ref - t'_n')) folded into the exponent and a row factor
 // 2^(wn (t'_n - t'_ref)) applied to the tile's trigger sums, with t'_ref the tile's latest
 // column time (both factors <= 1).
 // The causal indicator t_n' < t_n is tested on stored times through lo[n] (the first
@@ -112,30 +115,56 @@ struct Acc32 {
 // every trigger term of the tile is exactly zero); 1: every pair causal (separable trigger
 // factor); 2: test each pair (and mask n' = n when excluding self); 3: every pair causal and
 // every background term exactly zero (trigger only, separable).
+// KIND 0 reads the scaled coordinates (X, Y and sxs hold s x, s y with s^2 = a2), so that
+// q = (s dx)^2 + (s dy)^2 + dt'^2 takes two FMAs after dt'^2. The other kinds read the stored
+// coordinates, because the trigger term's Gaussian is narrow (h) and needs r^2 from exact
+// differences: there q = a2 r^2 + dt'^2 with a2 = s*s rounded. Every kind accumulates the
+// background moment Q = sum q e_b in sum 2; the epilogue recovers R_b = (Q - T_b) / s^2.
+// The separable column factor b = wn (t'_ref - t') is formed per column from the staged
+// time: one rounded difference, then one rounded product.
 template <int KIND, bool GRAD>
-__device__ __forceinline__ void tile_pass(const float4 *__restrict__ sxy, const float4 *__restrict__ stb,
+__device__ __forceinline__ void tile_pass(const float4 *__restrict__ sxs, const float4 *__restrict__ stx,
                                           const float2 (&X)[kPairs], const float2 (&Y)[kPairs],
-                                          const float2 (&T)[kPairs], const int (&LO)[kRowsPerThread], int row_a0,
-                                          int c0, bool excl, float2 A2, float2 CN,
-                                          float2 WN, Acc32<GRAD ? kSumsGrad : kSumsLoglik> &acc) {
+                                          const float2 (&T)[kPairs], const int (&LO)[kRowsPerThread],
+                                          int row_a0, int c0, bool excl, float2 A2, float2 CN, float2 WN,
+                                          float2 SREF, Acc32<GRAD ? kSumsGrad : kSumsLoglik> &acc) {
   constexpr bool kBg = KIND != 3;
   constexpr bool kTrig = KIND != 0;
   constexpr bool kNeedDt = kBg || KIND == 2 || GRAD;
   constexpr int kUnroll = GRAD ? kColUnroll : kColUnrollLL;
 #pragma unroll kUnroll
   for (int j = 0; j < kColTile; ++j) {
-    const float4 c = sxy[j];  // {-x, -x, -y, -y}
-    const float4 d = stb[j];  // {-t', -t', b, b}, b = wn (t'_ref - t')
-    const float2 cx = make_float2(c.x, c.y), cy = make_float2(c.z, c.w);
-    const float2 ct = make_float2(d.x, d.y), bj = make_float2(d.z, d.w);
+    const float4 d = stx[j];  // {-t', -t', -x, -y}
+    const float2 ct = make_float2(d.x, d.y);
     const int col = c0 + j;
+    float2 cx, cy, bj;
+    if (KIND == 0) {
+      const float4 c = sxs[j];  // {-s x, -s x, -s y, -s y}
+      cx = make_float2(c.x, c.y);
+      cy = make_float2(c.z, c.w);
+    } else {
+      cx = make_float2(d.z, d.z);
+      cy = make_float2(d.w, d.w);
+    }
+    if (KIND == 1 || KIND == 3) bj = mul2(add2(SREF, ct), WN);
 #pragma unroll
     for (int p = 0; p < kPairs; ++p) {
       const float2 dx = add2(X[p], cx);
       const float2 dy = add2(Y[p], cy);
-      const float2 rho = fma2(dy, dy, mul2(dx, dx));
       float2 dt = make_float2(0.f, 0.f);
       if (kNeedDt) dt = add2(T[p], ct);
+      if (KIND == 0) {
+        const float2 u = mul2(dt, dt);
+        const float2 q = fma2(dy, dy, fma2(dx, dx, u));
+        const float2 eb = make_float2(ex2(-q.x), ex2(-q.y));
+        acc.v[0][p] = acc2(acc.v[0][p], eb);
+        if (GRAD) {
+          acc.v[2][p] = accfma2(q, eb, acc.v[2][p]);
+          acc.v[3][p] = accfma2(u, eb, acc.v[3][p]);
+        }
+        continue;
+      }
+      const float2 rho = fma2(dy, dy, mul2(dx, dx));
       if (kBg) {
         const float2 u = mul2(dt, dt);
         const float2 q = fma2(rho, A2, u);
@@ -147,7 +176,7 @@ __device__ __forceinline__ void tile_pass(const float4 *__restrict__ sxy, const 
         }
         acc.v[0][p] = acc2(acc.v[0][p], eb);
         if (GRAD) {
-          acc.v[2][p] = accfma2(rho, eb, acc.v[2][p]);
+          acc.v[2][p] = accfma2(q, eb, acc.v[2][p]);
           acc.v[3][p] = accfma2(u, eb, acc.v[3][p]);
         }
       }
@@ -178,17 +207,15 @@ constexpr float kBgZeroGap = 11.5157f;    // 1.01 * sqrt(130)
 constexpr float kTrigZeroExp = 132.31f;   // 1.01 * 131
 
 // Each thread stages kStage columns of a tile: raw values are loaded into registers one
-// tile ahead, then scaled, negated and duplicated into shared memory.
+// tile ahead, then scaled, negated and (for packed operands) duplicated into shared memory.
 constexpr int kStage = kColTile / kThreads;
 static_assert(kColTile % kThreads == 0, "column tile must be a multiple of the CTA width");
 
 struct RawCols {
   float x[kStage], y[kStage], t[kStage];
-  float tref;
 };
 
 __device__ __forceinline__ RawCols load_cols(const SetView &S, int ct, int tid) {
-  const int last = min((ct + 1) * kColTile, S.n) - 1;  // latest real column of the tile
   RawCols r;
 #pragma unroll
   for (int h = 0; h < kStage; ++h) {
@@ -197,20 +224,36 @@ __device__ __forceinline__ RawCols load_cols(const SetView &S, int ct, int tid) 
     r.y[h] = __ldg(S.y32 + j);
     r.t[h] = __ldg(S.t32 + j);
   }
-  r.tref = __ldg(S.t32 + max(last, 0));
   return r;
 }
 
 __device__ __forceinline__ void store_cols(const RawCols &r, int ct, int tid, int n, float t_origin, float beta,
-                                           float wn, float4 *sxy, float4 *stb) {
-  const float sref = (r.tref - t_origin) * beta;
+                                           float sc, float4 *sxs, float4 *stx) {
 #pragma unroll
   for (int h = 0; h < kStage; ++h) {
     const int jj = tid + h * kThreads, j = ct * kColTile + jj;
     const float sj = j < n ? (r.t[h] - t_origin) * beta : kPadScaled;
-    const float bj = wn * (sref - sj);
-    sxy[jj] = make_float4(-r.x[h], -r.x[h], -r.y[h], -r.y[h]);
-    stb[jj] = make_float4(-sj, -sj, bj, bj);
+    const float xs = __fmul_rn(r.x[h], sc), ys = __fmul_rn(r.y[h], sc);
+    sxs[jj] = make_float4(-xs, -xs, -ys, -ys);
+    stx[jj] = make_float4(-sj, -sj, -r.x[h], -r.y[h]);
+  }
+}
+
+// This thread's row coordinates (rows ra = wa + lane + 32 k, packed in pairs k, k + 1),
+// stored values or scaled by sc with the columns' rounding, so that dx = 0 on the diagonal.
+template <bool SCALED>
+__device__ __forceinline__ void row_coords(const SetView &S, int ra0, float sc, float2 (&X)[kPairs],
+                                           float2 (&Y)[kPairs]) {
+#pragma unroll
+  for (int p = 0; p < kPairs; ++p) {
+    const int ra = ra0 + 64 * p, rb = ra + 32;
+    float xa = __ldg(S.x32 + ra), xb = __ldg(S.x32 + rb), ya = __ldg(S.y32 + ra), yb = __ldg(S.y32 + rb);
+    if (SCALED) {
+      xa = __fmul_rn(xa, sc); xb = __fmul_rn(xb, sc);
+      ya = __fmul_rn(ya, sc); yb = __fmul_rn(yb, sc);
+    }
+    X[p] = make_float2(xa, xb);
+    Y[p] = make_float2(ya, yb);
   }
 }
 
@@ -224,32 +267,37 @@ __device__ __forceinline__ void cta_sync() {
 // (fused) the row tile's merge tree and, in the CTA that completes it, the tile's epilogue;
 // otherwise the sums go to the item's partial-sum slot.
 template <bool GRAD>
-__device__ void run_piece(const Batch &B, const Request &R, int4 piece, int slot, float4 (*sxy)[kColTile],
-                          float4 (*stb)[kColTile], double *sacc) {
+__device__ void run_piece(const Batch &B, const Request &R, int4 piece, int slot, float4 (*sxs)[kColTile],
+                          float4 (*stx)[kColTile], double *sacc) {
   constexpr int NS = GRAD ? kSumsGrad : kSumsLoglik;
   const SetView &S = R.set;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int row0 = piece.x * kRowTile;
   const float t_origin = S.t32[row0];
   const float beta = R.beta, wn = R.wn;
+  const float sc = sqrtf(R.a2);  // spatial scale s of background-only tiles, s^2 ~ a2
   const int n = S.n;
   const int wa = row0 + warp * kWarpRows, wb = wa + kWarpRows - 1;
   const int lo_wa = S.lo32[wa], lo_wb = S.lo32[wb];
   const bool excl = (R.flags & 1) != 0;
+  const int row_a0 = wa + lane;
 
-  float2 X[kPairs], Y[kPairs], T[kPairs];
+  float2 T[kPairs];
   int LO[kRowsPerThread];
 #pragma unroll
   for (int p = 0; p < kPairs; ++p) {
-    const int ra = wa + lane + 64 * p, rb = ra + 32;
-    X[p] = make_float2(S.x32[ra], S.x32[rb]);
-    Y[p] = make_float2(S.y32[ra], S.y32[rb]);
+    const int ra = row_a0 + 64 * p, rb = ra + 32;
     T[p] = make_float2(ra < n ? (S.t32[ra] - t_origin) * beta : kPadScaled,
                        rb < n ? (S.t32[rb] - t_origin) * beta : kPadScaled);
     LO[2 * p] = S.lo32[ra];
     LO[2 * p + 1] = S.lo32[rb];
   }
-  const float2 A2 = make_float2(R.a2, R.a2), CN = make_float2(R.cn, R.cn), WN = make_float2(wn, wn);
+  // scaled row coordinates stay in registers; the stored ones are reloaded (L1) for the
+  // few tiles with trigger terms
+  float2 XS[kPairs], YS[kPairs];
+  row_coords<true>(S, row_a0, sc, XS, YS);
+  const float a2 = sc * sc;
+  const float2 A2 = make_float2(a2, a2), CN = make_float2(R.cn, R.cn), WN = make_float2(wn, wn);
   const float s_first = __shfl_sync(0xffffffffu, T[0].x, 0);            // scaled time of the warp's
   const float s_last = __shfl_sync(0xffffffffu, T[kPairs - 1].y, 31);  // first and last rows
 
@@ -261,7 +309,7 @@ __device__ void run_piece(const Batch &B, const Request &R, int4 piece, int slot
 
   int ct = piece.y;
   if (ct < piece.z) {  // an empty slice of the window writes zero partial sums
-    store_cols(load_cols(S, ct, tid), ct, tid, n, t_origin, beta, wn, sxy[0], stb[0]);
+    store_cols(load_cols(S, ct, tid), ct, tid, n, t_origin, beta, sc, sxs[0], stx[0]);
     cta_sync();
   }
   for (int k = 0; ct < piece.z; ++ct, ++k) {
@@ -272,11 +320,11 @@ __device__ void run_piece(const Batch &B, const Request &R, int4 piece, int slot
     const int c0 = ct * kColTile, c1 = c0 + kColTile;
     int kind;
     if (c1 <= lo_wa) {  // every pair causal: which of the two terms can be nonzero?
-      const float gap = s_first + stb[buf][kColTile - 1].x;  // t'(first row) - t'(latest column)
+      const float gap = s_first + stx[buf][kColTile - 1].x;  // t'(first row) - t'(latest column)
       const bool bg_zero = gap >= kBgZeroGap, trig_zero = wn * gap <= -kTrigZeroExp;
       kind = bg_zero ? (trig_zero ? -1 : 3) : (trig_zero ? 0 : 1);
     } else if (c0 >= lo_wb) {  // no causal pair: background only, zero past its reach
-      const float gap = -stb[buf][0].x - s_last;  // t'(earliest column) - t'(last row)
+      const float gap = -stx[buf][0].x - s_last;  // t'(earliest column) - t'(last row)
       kind = gap >= kBgZeroGap ? -1 : 0;
     } else {
       kind = 2;
@@ -287,14 +335,16 @@ __device__ void run_piece(const Batch &B, const Request &R, int4 piece, int slot
     for (int s = 0; s < NS; ++s)
 #pragma unroll
       for (int p = 0; p < kPairs; ++p) acc.v[s][p] = make_float2(0.f, 0.f);
-    const int row_a0 = wa + lane;
+    float2 X[kPairs], Y[kPairs];  // stored row coordinates, tiles with trigger terms
     if (kind == 0) {
-      tile_pass<0, GRAD>(sxy[buf], stb[buf], X, Y, T, LO, row_a0, c0, excl, A2, CN, WN, acc);
+      tile_pass<0, GRAD>(sxs[buf], stx[buf], XS, YS, T, LO, row_a0, c0, excl, A2, CN, WN, WN, acc);
     } else if (kind == 1 || kind == 3) {
-      if (kind == 1) tile_pass<1, GRAD>(sxy[buf], stb[buf], X, Y, T, LO, row_a0, c0, excl, A2, CN, WN, acc);
-      else tile_pass<3, GRAD>(sxy[buf], stb[buf], X, Y, T, LO, row_a0, c0, excl, A2, CN, WN, acc);
+      row_coords<false>(S, row_a0, sc, X, Y);
+      const float sref = -stx[buf][kColTile - 1].x;  // t'_ref: the tile's latest column
+      const float2 SREF = make_float2(sref, sref);
+      if (kind == 1) tile_pass<1, GRAD>(sxs[buf], stx[buf], X, Y, T, LO, row_a0, c0, excl, A2, CN, WN, SREF, acc);
+      else tile_pass<3, GRAD>(sxs[buf], stx[buf], X, Y, T, LO, row_a0, c0, excl, A2, CN, WN, SREF, acc);
       // row factor 2^(wn (t'_n - t'_ref)) of the separable trigger term
-      const float sref = -stb[buf][kColTile - 1].x;
       const float2 sr = make_float2(-sref, -sref);
 #pragma unroll
       for (int p = 0; p < kPairs; ++p) {
@@ -307,7 +357,8 @@ __device__ void run_piece(const Batch &B, const Request &R, int4 piece, int slot
         }
       }
     } else if (kind == 2) {
-      tile_pass<2, GRAD>(sxy[buf], stb[buf], X, Y, T, LO, row_a0, c0, excl, A2, CN, WN, acc);
+      row_coords<false>(S, row_a0, sc, X, Y);
+      tile_pass<2, GRAD>(sxs[buf], stx[buf], X, Y, T, LO, row_a0, c0, excl, A2, CN, WN, WN, acc);
     }  // kind -1: every term of the tile is exactly zero for this warp
 #pragma unroll
     for (int s = 0; s < NS; ++s)
@@ -316,7 +367,7 @@ __device__ void run_piece(const Batch &B, const Request &R, int4 piece, int slot
         sacc[(s * kRowsPerThread + 2 * p) * kThreads + tid] += (double)acc.v[s][p].x;
         sacc[(s * kRowsPerThread + 2 * p + 1) * kThreads + tid] += (double)acc.v[s][p].y;
       }
-    if (has_next) store_cols(nxt, ct + 1, tid, n, t_origin, beta, wn, sxy[buf ^ 1], stb[buf ^ 1]);
+    if (has_next) store_cols(nxt, ct + 1, tid, n, t_origin, beta, sc, sxs[buf ^ 1], stx[buf ^ 1]);
     cta_sync();
   }
   // this thread's rows: la = warp * kWarpRows + lane + 32 k, sums at sacc[(s R + k) T + tid]
@@ -349,6 +400,7 @@ __device__ void run_piece(const Batch &B, const Request &R, int4 piece, int slot
       double sums[NS];
 #pragma unroll
       for (int s = 0; s < NS; ++s) sums[s] = sacc[(s * kRowsPerThread + k) * kThreads + tid];
+      if (GRAD) sums[2] = (sums[2] - sums[3]) / ((double)sc * (double)sc);  // R_b from Q and T_b
       row_terms<GRAD>(R, i, sums, v);
     }
   }
@@ -358,8 +410,8 @@ __device__ void run_piece(const Batch &B, const Request &R, int4 piece, int slot
 template <bool GRAD>
 __global__ void __launch_bounds__(kThreads, GRAD ? HK_MIN_CTAS : HK_MIN_CTAS_LL) pair_mixed_kernel(const __grid_constant__ Batch B) {
   constexpr int NS = GRAD ? kSumsGrad : kSumsLoglik;
-  __shared__ __align__(16) float4 sxy[2][kColTile];
-  __shared__ __align__(16) float4 stb[2][kColTile];
+  __shared__ __align__(16) float4 sxs[2][kColTile];
+  __shared__ __align__(16) float4 stx[2][kColTile];
   __shared__ double sacc[NS * kRowsPerThread * kThreads];
   __shared__ int2 s_win;
   const int item = blockIdx.x;
@@ -384,7 +436,7 @@ __global__ void __launch_bounds__(kThreads, GRAD ? HK_MIN_CTAS : HK_MIN_CTAS_LL)
   const int width = w.y - w.x;
   const int c_begin = w.x + (int)((long long)width * sl / ns);
   const int c_end = w.x + (int)((long long)width * (sl + 1) / ns);
-  run_piece<GRAD>(B, R, make_int4(rt, c_begin, c_end, 0), slot, sxy, stb, sacc);
+  run_piece<GRAD>(B, R, make_int4(rt, c_begin, c_end, 0), slot, sxs, stx, sacc);
 }
 
 }  // namespace

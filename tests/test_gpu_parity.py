@@ -300,6 +300,24 @@ def test_full_size_mixed_vs_fp64(ctx, big):
     assert grad_err(gm, g64) <= TOL_MIXED_G
 
 
+@pytest.mark.parametrize("theta", [(0.01, 0.25, 30.0, 0.5, 1.0, 0.1), (0.01, 4.0, 30.0, 0.5, 1.0, 0.1),
+                                   (0.01, 1.0, 3.0, 0.5, 1.0, 0.1)], ids=["tau_x_0.25", "tau_x_4", "tau_t_3"])
+def test_full_size_mixed_vs_fp64_bandwidths(ctx, big, theta):
+    """Mixed against FP64 at N = 85,000 for narrow and wide background kernels. Tiles with
+    background terms only take differences of coordinates pre-scaled by s = sqrt(a2), each
+    rounded once to float32, so the per-event error grows with the region's extent over
+    tau_x; ell and its gradient stay within the mixed tolerance."""
+    ev, sid = big
+    ll64, g64 = ctx.hawkes_loglik_grad(sid, theta, 0)
+    llm, gm = ctx.hawkes_loglik_grad(sid, theta, 1)
+    assert rel(llm, ll64) <= TOL_MIXED_LL
+    assert grad_err(gm, g64) <= TOL_MIXED_G
+    mu64, xi64, _ = ctx.hawkes_event_terms(sid, theta, 0)
+    mum, xim, _ = ctx.hawkes_event_terms(sid, theta, 1)
+    assert np.max(np.abs(mum - mu64) / mu64) <= 1e-5
+    assert np.max(np.abs(xim - xi64)) <= 1e-5 * np.max(xi64)
+
+
 def test_full_size_gradient_finite_differences(ctx, big):
     """The FP64 GPU gradient at N = 85,000 against central differences of the FP64 GPU
     log-likelihood (step 1e-6 relative)."""
