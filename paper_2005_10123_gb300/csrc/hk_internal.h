@@ -361,38 +361,55 @@ __device__ bool merge_tree(const Request &R, int rt, int sl, Store store, Merge 
   return true;
 }
 
-// Log-intensity and gradient terms of event i from its row sums (Section 2.1, Eq. 1):
-// lambda_i = A S_b + C S_s, v[0] += log lambda_i and, with GRAD, v[1..6] += (d lambda_i / d
-// Theta) / lambda_i; also mu_i, xi_i and pi_i = xi_i / lambda_i of Eq. 2 when the request
-// asks for them.
+// Log-intensity and gradient moments of event i from its row sums (Section 2.1, Eq. 1):
+// lambda_i = A S_b + C S_s, v[0] += log lambda_i and, with GRAD, v[1..6] += (S_b, S_s, R_b,
+// T_b, R_s, U_s) / lambda_i in stored units; also mu_i, xi_i and pi_i = xi_i / lambda_i of
+// Eq. 2 when the request asks for them. Every gradient term (d lambda_i / d Theta) / lambda_i
+// is a fixed linear combination of these six ratios, so rowtile_reduce applies the Theta
+// factors once per row tile (grad_from_moments).
 template <bool GRAD>
 __device__ __forceinline__ void row_terms(const Request &R, int i, const double *sums, double *v) {
-  const double Ab = R.k_ab, Cw = R.k_cw, A = R.mu0 * Ab, C = R.theta * Cw;
+  const double A = R.mu0 * R.k_ab, C = R.theta * R.k_cw;
   const double mu = A * sums[0], xi = C * sums[1], lam = mu + xi;
   if (R.mu_out) R.mu_out[i] = mu;
   if (R.xi_out) R.xi_out[i] = xi;
   if (R.pi_out) R.pi_out[i] = xi / lam;
   v[0] += log(lam);
   if (GRAD) {
-    const double itx = R.inv_tx, itt = R.inv_tt, ih = R.inv_h, iom = R.inv_om;
-    const double Sb = sums[0], Ss = sums[1], Rb = sums[2], Tb = sums[3] * R.tscale * R.tscale;
-    const double Rs = sums[4], Us = sums[5] * R.tscale;
     const double inv = 1.0 / lam;
-    v[1] += Ab * Sb * inv;
-    v[2] += A * itx * (-2.0 * Sb + Rb * itx * itx) * inv;
-    v[3] += A * itt * (-Sb + Tb * itt * itt) * inv;
-    v[4] += Cw * Ss * inv;
-    v[5] += C * (Ss * iom - Us) * inv;
-    v[6] += C * ih * (-2.0 * Ss + Rs * ih * ih) * inv;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) v[1 + k] = fma(sums[k], inv, v[1 + k]);
   }
 }
 
+// The six gradient terms of Eq. 1's log-intensity sum from the moment ratios m = (sum_i
+// S_b/lambda_i, S_s/lambda, R_b/lambda, T_b/lambda, R_s/lambda, U_s/lambda) of row_terms:
+//   d/d mu0    = k_ab m_Sb
+//   d/d tau_x  = A/tau_x (-2 m_Sb + m_Rb / tau_x^2)
+//   d/d tau_t  = A/tau_t (-m_Sb + m_Tb / tau_t^2)        (m_Tb, m_Us rescaled by tscale)
+//   d/d theta  = k_cw m_Ss
+//   d/d omega  = C (m_Ss / omega - m_Us)
+//   d/d h      = C/h (-2 m_Ss + m_Rs / h^2)
+__device__ __forceinline__ void grad_from_moments(const Request &R, const double *m, double *g) {
+  const double A = R.mu0 * R.k_ab, C = R.theta * R.k_cw;
+  const double itx = R.inv_tx, itt = R.inv_tt, ih = R.inv_h, iom = R.inv_om;
+  const double Sb = m[0], Ss = m[1], Rb = m[2], Tb = m[3] * R.tscale * R.tscale, Rs = m[4], Us = m[5] * R.tscale;
+  g[0] = R.k_ab * Sb;
+  g[1] = A * itx * (-2.0 * Sb + Rb * itx * itx);
+  g[2] = A * itt * (-Sb + Tb * itt * itt);
+  g[3] = R.k_cw * Ss;
+  g[4] = C * (Ss * iom - Us);
+  g[5] = C * ih * (-2.0 * Ss + Rs * ih * ih);
+}
+
 // End of row tile rt's epilogue: sum every thread's row terms v in a fixed order (warp tree,
-// warps in order) into R.rt_sum, then finish_request. Called by every thread of the CTA.
+// warps in order), turn the moment ratios into gradient terms (grad_from_moments), store
+// them in R.rt_sum, then finish_request. Called by every thread of the CTA.
 template <bool GRAD>
 __device__ void rowtile_reduce(const Request &R, int rt, const double *v) {
   constexpr int NV = GRAD ? 7 : 1;
   __shared__ double red2[kMaxCtaWarps][8];
+  __shared__ double tot[8];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
   for (int q = 0; q < NV; ++q) {
@@ -405,7 +422,17 @@ __device__ void rowtile_reduce(const Request &R, int rt, const double *v) {
   if (tid < NV) {
     double x = 0.0;
     for (int w = 0; w < nw; ++w) x += red2[w][tid];
-    R.rt_sum[(size_t)rt * 8 + tid] = x;
+    tot[tid] = x;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    R.rt_sum[(size_t)rt * 8] = tot[0];
+    if (GRAD) {
+      double g[6];
+      grad_from_moments(R, tot + 1, g);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) R.rt_sum[(size_t)rt * 8 + 1 + k] = g[k];
+    }
   }
   finish_request<GRAD>(R);
 }

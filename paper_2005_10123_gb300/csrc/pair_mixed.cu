@@ -360,13 +360,19 @@ __device__ void run_piece(const Batch &B, const Request &R, int4 piece, int slot
       row_coords<false>(S, row_a0, sc, X, Y);
       tile_pass<2, GRAD>(sxs[buf], stx[buf], X, Y, T, LO, row_a0, c0, excl, A2, CN, WN, WN, acc);
     }  // kind -1: every term of the tile is exactly zero for this warp
+    // fold the tile's sums into float64; a tile without trigger (background) terms leaves
+    // those sums at zero, so they are skipped
+    const bool fold_bg = kind == 0 || kind == 1 || kind == 2, fold_trig = kind >= 1;
 #pragma unroll
-    for (int s = 0; s < NS; ++s)
+    for (int s = 0; s < NS; ++s) {
+      const bool trig_sum = s == 1 || s == 4 || s == 5;  // S_s, R_s, U_s
+      if (trig_sum ? !fold_trig : !fold_bg) continue;
 #pragma unroll
       for (int p = 0; p < kPairs; ++p) {
         sacc[(s * kRowsPerThread + 2 * p) * kThreads + tid] += (double)acc.v[s][p].x;
         sacc[(s * kRowsPerThread + 2 * p + 1) * kThreads + tid] += (double)acc.v[s][p].y;
       }
+    }
     if (has_next) store_cols(nxt, ct + 1, tid, n, t_origin, beta, sc, sxs[buf ^ 1], stx[buf ^ 1]);
     cta_sync();
   }
@@ -393,6 +399,7 @@ __device__ void run_piece(const Batch &B, const Request &R, int4 piece, int slot
   };
   if (!merge_tree(R, piece.x, slot - piece.x * R.slices, store, merge)) return;
   double v[GRAD ? 7 : 1] = {};
+  const double inv_s2 = 1.0 / ((double)sc * (double)sc);
 #pragma unroll
   for (int k = 0; k < kRowsPerThread; ++k) {
     const int i = row0 + warp * kWarpRows + lane + 32 * k;
@@ -400,7 +407,7 @@ __device__ void run_piece(const Batch &B, const Request &R, int4 piece, int slot
       double sums[NS];
 #pragma unroll
       for (int s = 0; s < NS; ++s) sums[s] = sacc[(s * kRowsPerThread + k) * kThreads + tid];
-      if (GRAD) sums[2] = (sums[2] - sums[3]) / ((double)sc * (double)sc);  // R_b from Q and T_b
+      if (GRAD) sums[2] = (sums[2] - sums[3]) * inv_s2;  // R_b from Q and T_b
       row_terms<GRAD>(R, i, sums, v);
     }
   }
