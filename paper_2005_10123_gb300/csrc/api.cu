@@ -199,15 +199,28 @@ void build_win_table(const TT *t, int64_t n, int nct, WinTable *W, std::vector<i
   W->nb = nb;
 }
 
-// Slices per row tile for a kernel kind: enough items for about kItemsPerSlot items per
-// resident CTA, at most one column tile per slice.
+// Leaves per row tile for a kernel kind: about kItemsPerSlot items per resident CTA, at most
+// one column tile per leaf. The mixed kernels cut twice as fine: their items span 4, 2 or 1
+// leaves along the launch order (launch_tiers).
 #ifndef HK_ITEMS_PER_SLOT
 #define HK_ITEMS_PER_SLOT 4
 #endif
 constexpr int kItemsPerSlot = HK_ITEMS_PER_SLOT;
-int slices_for(int nrt, int nct, int resident_ctas) {
-  const int want = (kItemsPerSlot * resident_ctas + nrt - 1) / nrt;
+int slices_for(int nrt, int nct, int resident_ctas, bool tiered) {
+  const int want = (kItemsPerSlot * resident_ctas + nrt - 1) / nrt * (tiered ? 2 : 1);
   return std::max(1, std::min(want, nct));
+}
+
+// Item spans of the mixed kernels along the launch order (see Request): the first half of the
+// row tiles take 4-leaf items, the next quarter 2-leaf items and the last quarter 1-leaf items,
+// so the launch ends on short items. The float64 kernel takes 1-leaf items throughout.
+void launch_tiers(int nrt, int mode, int *wide, int *coarse) {
+  if (mode == HAWKES_MIXED) {
+    *wide = nrt / 2;
+    *coarse = nrt - nrt / 4;
+  } else {
+    *wide = *coarse = 0;
+  }
 }
 
 // Exact-zero cut-offs (days) of Section 2.1's pair terms at the working precision:
@@ -250,6 +263,7 @@ int make_request(hawkes_ctx *ctx, const EventSetRec *S, const hawkes_params *p, 
   R->set.win32 = S->win32; R->set.win64 = S->win64;
   R->set.n = (int)S->n; R->set.npad = (int)S->npad; R->set.nrt = S->nrt; R->set.nct = S->nct;
   R->slices = S->slices[kind_of(mode, grad)];
+  launch_tiers(S->nrt, mode, &R->wide, &R->coarse);
   R->grad = grad;
   R->flags = flags;
   const double beta = std::sqrt(kLog2e / (2.0 * p->tau_t * p->tau_t));
@@ -283,7 +297,12 @@ int make_request(hawkes_ctx *ctx, const EventSetRec *S, const hawkes_params *p, 
 // Device bytes one request needs: partial sums, compensator sums, row-tile sums.
 // Pair items (= partial-sum slots) of one request on S (see Request).
 size_t set_slots(const EventSetRec *S, int mode, int grad) {
-  return (size_t)S->nrt * S->slices[kind_of(mode, grad)];
+  Request R;
+  std::memset(&R, 0, sizeof(R));
+  R.set.nrt = S->nrt;
+  R.slices = S->slices[kind_of(mode, grad)];
+  launch_tiers(S->nrt, mode, &R.wide, &R.coarse);
+  return (size_t)pair_items(R);
 }
 
 size_t request_footprint(const EventSetRec *S, int mode, int grad) {
@@ -296,7 +315,7 @@ size_t request_footprint(const EventSetRec *S, int mode, int grad) {
 // Bytes of a request's completion counters (the merge-tree nodes of its row tiles and one
 // final counter, see Request::rt_count), kept in one zeroed region per batch.
 size_t counter_bytes(const EventSetRec *S, int mode, int grad) {
-  return align_up((2 * set_slots(S, mode, grad) + 1) * sizeof(unsigned), 64);
+  return align_up((2 * (size_t)S->nrt * S->slices[kind_of(mode, grad)] + 1) * sizeof(unsigned), 64);
 }
 
 // Batch workspace: a 256-byte header (unused, keeps the outputs aligned), the per-request
@@ -771,7 +790,7 @@ int hawkes_upload_events(hawkes_ctx *ctx, const double *x, const double *y, cons
   for (int k = 0; k < kKinds; ++k) {
     // the float64 kernel can cut a column tile into chunks, the mixed kernels cannot
     const int units = k == kind_of(HAWKES_FP64, 0) ? S->nct * fp64_chunks_per_tile() : S->nct;
-    S->slices[k] = slices_for(S->nrt, units, ctx->sms * ctx->occ[k]);
+    S->slices[k] = slices_for(S->nrt, units, ctx->sms * ctx->occ[k], k != kind_of(HAWKES_FP64, 0));
   }
   // one device allocation: float32 and float64 SoA, tie indices, the two window tables
   size_t off = 0;

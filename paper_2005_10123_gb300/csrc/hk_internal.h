@@ -75,15 +75,21 @@ __host__ __device__ inline int2 table_window(const WinTable &W, int n, int nct, 
 }
 
 // Work decomposition: the pair kernels run one CTA per item. A request's items are first
-// one compensator item per row tile (when comp is set), then the pair items (row tile rt,
-// slice s), s < slices, numbered rt * slices + s. For a pair item the kernel finds the window
-// of column tiles of rt that can hold a nonzero pair term (every other pair term is exactly
-// zero at the working precision, see cut_early and cut_late) and gives slice s the s-th of
-// `slices` near-equal parts of that window. The pair item's number is also its partial-sum
-// slot, so results do not depend on which CTA ran which item or when.
+// one compensator item per row tile (when comp is set), then the pair items. For a pair item
+// the kernel finds the window of column tiles of its row tile rt that can hold a nonzero pair
+// term (every other pair term is exactly zero at the working precision, see cut_early and
+// cut_late) and cuts it into `slices` near-equal leaves. Row tiles are launched from the
+// middle of the time range outwards; one item covers `span` consecutive leaves of its row
+// tile, with span 4 for the first `wide` row tiles launched, 2 up to `coarse` and 1 for the
+// rest, so that the launch starts on long items and ends on short ones. Items are numbered in
+// launch order; the item's number is its partial-sum slot, so results do not depend on which
+// CTA ran which item or when. An unfused launch (Batch::fused = 0, 1-leaf items only) leaves
+// each item's sums in the row-tile-major slot rt * slices + leaf for a separate epilogue.
 struct Request {
   SetView set;
-  int slices;      // slices per row tile (fixed per set and kernel kind)
+  int slices;      // leaves per row tile (fixed per set and kernel kind)
+  int wide;        // row tiles launched first whose items span 4 leaves
+  int coarse;      // row tiles launched before the 1-leaf items (span 4 or 2)
   int grad;        // 0: loglik only; 1: loglik and gradient
   int flags;       // HAWKES_FLAG_* of the context at submission
   int item_begin;  // first pair-kernel item of this request in the batch
@@ -133,25 +139,34 @@ struct Batch {
 
 // Items of one request (see Request): compensator items first, then pair items.
 __host__ __device__ inline int comp_items(const Request &R) { return R.comp ? R.set.nrt : 0; }
-__host__ __device__ inline int pair_items(const Request &R) { return R.set.nrt * R.slices; }
+// Leaves per item of the row tile launched k-th (see Request).
+__host__ __device__ inline int span_at(const Request &R, int k) { return k < R.wide ? 4 : k < R.coarse ? 2 : 1; }
+__host__ __device__ inline int pair_items(const Request &R) {
+  const int K = R.slices;
+  return R.wide * ((K + 3) / 4) + (R.coarse - R.wide) * ((K + 1) / 2) + (R.set.nrt - R.coarse) * K;
+}
 __host__ __device__ inline int request_items(const Request &R) { return comp_items(R) + pair_items(R); }
-__host__ __device__ inline int request_counters(const Request &R) { return 2 * pair_items(R) + 1; }
-// Row tile and slice of the request's p-th pair item in launch order. Row tiles go out from
-// the middle of the time range outwards (m, m - 1, m + 1, m - 2, ...): the first and last row
-// tiles, whose column windows are cut off by t = 0 and t = t_N, launch last, so the launch
-// ends on short items. The item's partial-sum slot is rt * slices + slice, whatever the order.
-#ifndef HK_MIDDLE_OUT
-#define HK_MIDDLE_OUT 1
-#endif
-__host__ __device__ inline int2 slot_tile(const Request &R, int p) {
-  const int k = p / R.slices, sl = p % R.slices;
-#if HK_MIDDLE_OUT
+// Merge-tree nodes (fewer than 2 per leaf) of every row tile, then the final counter.
+__host__ __device__ inline int request_counters(const Request &R) { return 2 * R.set.nrt * R.slices + 1; }
+
+// The request's p-th pair item in launch order: row tile rt, index `node` among the row tile's
+// items, leaves [node * span, min(node * span + span, slices)), and `base`, the slot of the row
+// tile's first item (the item's own slot is base + node = p). Row tiles go out from the middle
+// of the time range (m, m - 1, m + 1, m - 2, ...): the first and last row tiles, whose column
+// windows are cut off by t = 0 and t = t_N, launch last.
+struct PairItem {
+  int rt, node, span, base;
+};
+__host__ __device__ inline PairItem item_at(const Request &R, int p) {
+  const int K = R.slices, n4 = (K + 3) / 4, n2 = (K + 1) / 2;
+  const int p2 = R.wide * n4, p1 = p2 + (R.coarse - R.wide) * n2;  // first 2-leaf and 1-leaf items
+  int k, node, span;
+  if (p < p2) { k = p / n4; node = p - k * n4; span = 4; }
+  else if (p < p1) { k = (p - p2) / n2; node = p - p2 - k * n2; k += R.wide; span = 2; }
+  else { k = (p - p1) / K; node = p - p1 - k * K; k += R.coarse; span = 1; }
   const int m = R.set.nrt / 2;
   const int rt = k == 0 ? m : (k & 1) ? m - (k + 1) / 2 : m + k / 2;
-#else
-  const int rt = k;
-#endif
-  return make_int2(rt, sl);
+  return PairItem{rt, node, span, p - node};
 }
 
 // Launchers (defined in the kernel translation units): one CTA per item, grid =
@@ -301,7 +316,7 @@ __device__ void finish_request(const Request &R) {
   const unsigned parts = (unsigned)(S.nrt + comp_items(R));
   __threadfence();
   __syncthreads();
-  if (tid == 0) s_final = atomicAdd(R.rt_count + 2 * pair_items(R), 1u) == parts - 1u;
+  if (tid == 0) s_final = atomicAdd(R.rt_count + request_counters(R) - 1, 1u) == parts - 1u;
   __syncthreads();
   if (s_final) {
     __threadfence();
@@ -326,32 +341,34 @@ __device__ void finish_request(const Request &R) {
   __syncthreads();
 }
 
-// Merge tree of row tile rt's slices (fused epilogue). Slice sl stores its partial row sums
-// in its slot and climbs a binary tree over the tile's K slices: at each node whose sibling
-// subtree exists, the CTA stores its current sums, counts its arrival, and stops if it is
-// first; the second to arrive adds the sibling's stored sums to its own and climbs on. A node's
-// value is left + right whichever side arrives second (floating-point addition commutes), so
-// the sums do not depend on the order in which slices finish. Returns true in the one CTA that
-// completes the root: it then holds the tile's full row sums. store(slot) writes the CTA's
-// current sums to a slot, merge(slot) adds a slot's sums to them (reading through L2). Called
-// by every thread of the CTA.
+// Merge tree of a row tile's leaves (fused epilogue). An item enters at the node of its own
+// leaves, stores its partial row sums in its slot and climbs a binary tree over the tile's K
+// leaves: at each node whose sibling subtree exists, the CTA stores its current sums in the
+// slot of the node's first leaf, counts its arrival, and stops if it is first; the second to
+// arrive adds the sibling's stored sums to its own and climbs on. A node's value is left +
+// right whichever side arrives second (floating-point addition commutes), so the sums do not
+// depend on the order in which items finish. Returns true in the one CTA that completes the
+// root: it then holds the tile's full row sums. store(slot) writes the CTA's current sums to a
+// slot, merge(slot) adds a slot's sums to them (reading through L2). Called by every thread
+// of the CTA.
 template <class Store, class Merge>
-__device__ bool merge_tree(const Request &R, int rt, int sl, Store store, Merge merge) {
+__device__ bool merge_tree(const Request &R, const PairItem &it, Store store, Merge merge) {
   __shared__ int s_go;
-  const int K = R.slices, first = rt * R.slices;
-  unsigned *cnt = R.rt_count + 2 * first;
-  int node = sl, width = 1, off = 0;
+  const int K = R.slices;
+  unsigned *cnt = R.rt_count + 2 * (size_t)it.rt * K;
+  int node = it.node, width = it.span, off = 0;
+  for (int w = 1; w < width; w <<= 1) off += (K + 2 * w - 1) / (2 * w);  // levels below the item
   while (width < K) {
     const int parent = node >> 1, sib = node ^ 1;
     if (sib * width < K) {  // the sibling subtree exists
-      store(first + node * width);
+      store(it.base + node * width / it.span);
       __threadfence();
       __syncthreads();
       if (threadIdx.x == 0) s_go = atomicAdd(cnt + off + parent, 1u) == 1u;
       __syncthreads();
       if (!s_go) return false;
       __threadfence();
-      merge(first + sib * width);
+      merge(it.base + sib * width / it.span);
       __syncthreads();
     }
     off += (K + 2 * width - 1) / (2 * width);  // nodes at the parent's level

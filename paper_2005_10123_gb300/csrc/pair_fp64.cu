@@ -61,7 +61,7 @@ __device__ __forceinline__ void tile_pass64(const double *__restrict__ sx, const
 }
 
 template <bool GRAD>
-__device__ void run_piece64(const Batch &B, const Request &R, int4 piece, int slot, double (*sx)[kColTile],
+__device__ void run_piece64(const Batch &B, const Request &R, const PairItem &it, int4 piece, double (*sx)[kColTile],
                             double (*sy)[kColTile], double (*st)[kColTile]) {
   constexpr int NS = GRAD ? kSumsGrad : kSumsLoglik;
   const SetView &S = R.set;
@@ -146,8 +146,8 @@ __device__ void run_piece64(const Batch &B, const Request &R, int4 piece, int sl
 #pragma unroll
       for (int s = 0; s < NS; ++s) dst[s * kRowTile + warp * kWarpRows64 + lane + 32 * k] = acc[s][k];
   };
-  if (!B.fused) {
-    store(slot);
+  if (!B.fused) {  // row-tile-major slot of the item's first leaf (unfused launches use 1-leaf items)
+    store(it.rt * R.slices + it.node * it.span);
     return;
   }
   auto merge = [&](int from) {
@@ -157,7 +157,7 @@ __device__ void run_piece64(const Batch &B, const Request &R, int4 piece, int sl
 #pragma unroll
       for (int s = 0; s < NS; ++s) acc[s][k] += __ldcg(src + s * kRowTile + warp * kWarpRows64 + lane + 32 * k);
   };
-  if (!merge_tree(R, piece.x, slot - piece.x * R.slices, store, merge)) return;
+  if (!merge_tree(R, it, store, merge)) return;
   double v[GRAD ? 7 : 1] = {};
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
@@ -184,8 +184,8 @@ __global__ void __launch_bounds__(kThreads64) pair_fp64_kernel(const __grid_cons
     if (B.fused) finish_request<GRAD>(R);
     return;
   }
-  const int2 tile = slot_tile(R, local - nc);
-  const int rt = tile.x, sl = tile.y, ns = R.slices, slot = rt * ns + sl;
+  const PairItem it = item_at(R, local - nc);
+  const int rt = it.rt, ns = R.slices, l0 = it.node * it.span, l1 = min(l0 + it.span, ns);
   int2 w = table_window_rt(R, R.set.win64, R.set.t64, rt);
   if (w.x < 0) {  // no lookup table: one warp searches the times
     if (threadIdx.x < 32) {
@@ -195,11 +195,11 @@ __global__ void __launch_bounds__(kThreads64) pair_fp64_kernel(const __grid_cons
     __syncthreads();
     w = s_win;
   }
-  // the window in column chunks, cut into `ns` near-equal slices
+  // the window in column chunks, cut into `ns` near-equal leaves
   const int cw0 = w.x * kChunksPerTile64, width = (w.y - w.x) * kChunksPerTile64;
-  const int c_begin = cw0 + (int)((long long)width * sl / ns);
-  const int c_end = cw0 + (int)((long long)width * (sl + 1) / ns);
-  run_piece64<GRAD>(B, R, make_int4(rt, c_begin, c_end, 0), slot, sx, sy, st);
+  const int c_begin = cw0 + (int)((long long)width * l0 / ns);
+  const int c_end = cw0 + (int)((long long)width * l1 / ns);
+  run_piece64<GRAD>(B, R, it, make_int4(rt, c_begin, c_end, 0), sx, sy, st);
 }
 
 }  // namespace

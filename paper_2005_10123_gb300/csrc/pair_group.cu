@@ -128,12 +128,12 @@ __device__ __forceinline__ void gstage(const SetView &S, int ct, float t0, float
 }
 
 template <int G, bool GRAD>
-__device__ void group_item(const Batch &B, int leader, int gsize, int rt, int sl, unsigned char *smem) {
+__device__ void group_item(const Batch &B, int leader, int gsize, const PairItem &it, unsigned char *smem) {
   constexpr int NS = GRAD ? kSumsGrad : kSumsLoglik;
   const Request &R0 = B.req[leader];
   const SetView &S = R0.set;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int row0 = rt * kRowTile, n = S.n;
+  const int rt = it.rt, row0 = rt * kRowTile, n = S.n;
   const float t0 = S.t32[row0];
   const int wa = row0 + warp * kGWarpRows, wb = wa + kGWarpRows - 1;
   const int lo_wa = S.lo32[wa], lo_wb = S.lo32[wb];
@@ -172,8 +172,8 @@ __device__ void group_item(const Batch &B, int leader, int gsize, int rt, int sl
     }
   }
   const int width = c_hi - c_lo;
-  const int ns = R0.slices;
-  const int c_begin = c_lo + (int)((long long)width * sl / ns), c_end = c_lo + (int)((long long)width * (sl + 1) / ns);
+  const int ns = R0.slices, l0 = it.node * it.span, l1 = min(l0 + it.span, ns);
+  const int c_begin = c_lo + (int)((long long)width * l0 / ns), c_end = c_lo + (int)((long long)width * l1 / ns);
 
   GStage &sg = *reinterpret_cast<GStage *>(smem);
   GAcc<G, NS> acc;
@@ -224,7 +224,6 @@ __device__ void group_item(const Batch &B, int leader, int gsize, int rt, int sl
       gsum[(k * NS + s) * kRowTile + la] = (double)acc.v[k][s].x;
       gsum[(k * NS + s) * kRowTile + lb] = (double)acc.v[k][s].y;
     }
-  const int slot = rt * ns + sl;
   auto store = [&](int to) {
     for (int k = 0; k < gsize; ++k) {
       double *dst = B.req[leader + k].partials + (size_t)to * NS * kRowTile;
@@ -235,8 +234,8 @@ __device__ void group_item(const Batch &B, int leader, int gsize, int rt, int sl
       }
     }
   };
-  if (!B.fused) {
-    store(slot);
+  if (!B.fused) {  // row-tile-major slot of the item's first leaf (unfused launches use 1-leaf items)
+    store(rt * ns + l0);
     return;
   }
   auto merge = [&](int from) {
@@ -249,7 +248,7 @@ __device__ void group_item(const Batch &B, int leader, int gsize, int rt, int sl
       }
     }
   };
-  if (!merge_tree(R0, rt, sl, store, merge)) return;
+  if (!merge_tree(R0, it, store, merge)) return;
   for (int k = 0; k < gsize; ++k) {
     const Request &R = B.req[leader + k];
     double v[GRAD ? 7 : 1] = {};
@@ -279,11 +278,10 @@ __global__ void __launch_bounds__(kGThreads, 2) pair_group_kernel(const __grid_c
     if (B.fused) finish_request<GRAD>(R);
     return;
   }
-  const int per_group = nrt * B.req[0].slices;
+  const int per_group = pair_items(B.req[0]);
   const int p = item - B.comp_total, g = p / per_group, local = p - g * per_group;
   const int leader = g * G, gsize = min(G, B.nreq - leader);
-  const int2 tile = slot_tile(B.req[leader], local);
-  group_item<G, GRAD>(B, leader, gsize, tile.x, tile.y, gsmem);
+  group_item<G, GRAD>(B, leader, gsize, item_at(B.req[leader], local), gsmem);
 }
 
 template <int G, bool GRAD>

@@ -263,16 +263,16 @@ __device__ __forceinline__ void cta_sync() {
   else __syncthreads();
 }
 
-// One pair item: the row sums of row tile piece.x over column tiles [piece.y, piece.z), then
+// One pair item: the row sums of row tile it.rt over column tiles [c_begin, c_end), then
 // (fused) the row tile's merge tree and, in the CTA that completes it, the tile's epilogue;
 // otherwise the sums go to the item's partial-sum slot.
 template <bool GRAD>
-__device__ void run_piece(const Batch &B, const Request &R, int4 piece, int slot, float4 (*sxs)[kColTile],
-                          float4 (*stx)[kColTile], double *sacc) {
+__device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, int c_begin, int c_end,
+                          float4 (*sxs)[kColTile], float4 (*stx)[kColTile], double *sacc) {
   constexpr int NS = GRAD ? kSumsGrad : kSumsLoglik;
   const SetView &S = R.set;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int row0 = piece.x * kRowTile;
+  const int row0 = it.rt * kRowTile;
   const float t_origin = S.t32[row0];
   const float beta = R.beta, wn = R.wn;
   const float sc = sqrtf(R.a2);  // spatial scale s of background-only tiles, s^2 ~ a2
@@ -307,14 +307,14 @@ __device__ void run_piece(const Batch &B, const Request &R, int4 piece, int slot
 #pragma unroll
     for (int k = 0; k < kRowsPerThread; ++k) sacc[(s * kRowsPerThread + k) * kThreads + tid] = 0.0;
 
-  int ct = piece.y;
-  if (ct < piece.z) {  // an empty slice of the window writes zero partial sums
+  int ct = c_begin;
+  if (ct < c_end) {  // an empty slice of the window writes zero partial sums
     store_cols(load_cols(S, ct, tid), ct, tid, n, t_origin, beta, sc, sxs[0], stx[0]);
     cta_sync();
   }
-  for (int k = 0; ct < piece.z; ++ct, ++k) {
+  for (int k = 0; ct < c_end; ++ct, ++k) {
     const int buf = k & 1;
-    const bool has_next = ct + 1 < piece.z;
+    const bool has_next = ct + 1 < c_end;
     RawCols nxt;
     if (has_next) nxt = load_cols(S, ct + 1, tid);
     const int c0 = ct * kColTile, c1 = c0 + kColTile;
@@ -385,8 +385,8 @@ __device__ void run_piece(const Batch &B, const Request &R, int4 piece, int slot
       for (int s = 0; s < NS; ++s)
         dst[s * kRowTile + warp * kWarpRows + lane + 32 * k] = sacc[(s * kRowsPerThread + k) * kThreads + tid];
   };
-  if (!B.fused) {
-    store(slot);
+  if (!B.fused) {  // row-tile-major slot of the item's first leaf (unfused launches use 1-leaf items)
+    store(it.rt * R.slices + it.node * it.span);
     return;
   }
   auto merge = [&](int from) {
@@ -397,7 +397,7 @@ __device__ void run_piece(const Batch &B, const Request &R, int4 piece, int slot
       for (int s = 0; s < NS; ++s)
         sacc[(s * kRowsPerThread + k) * kThreads + tid] += __ldcg(src + s * kRowTile + warp * kWarpRows + lane + 32 * k);
   };
-  if (!merge_tree(R, piece.x, slot - piece.x * R.slices, store, merge)) return;
+  if (!merge_tree(R, it, store, merge)) return;
   double v[GRAD ? 7 : 1] = {};
   const double inv_s2 = 1.0 / ((double)sc * (double)sc);
 #pragma unroll
@@ -411,7 +411,7 @@ __device__ void run_piece(const Batch &B, const Request &R, int4 piece, int slot
       row_terms<GRAD>(R, i, sums, v);
     }
   }
-  rowtile_reduce<GRAD>(R, piece.x, v);
+  rowtile_reduce<GRAD>(R, it.rt, v);
 }
 
 template <bool GRAD>
@@ -429,8 +429,8 @@ __global__ void __launch_bounds__(kThreads, GRAD ? HK_MIN_CTAS : HK_MIN_CTAS_LL)
     if (B.fused) finish_request<GRAD>(R);
     return;
   }
-  const int2 tile = slot_tile(R, local - nc);
-  const int rt = tile.x, sl = tile.y, ns = R.slices, slot = rt * ns + sl;
+  const PairItem it = item_at(R, local - nc);
+  const int rt = it.rt, ns = R.slices, l0 = it.node * it.span, l1 = min(l0 + it.span, ns);
   int2 w = table_window_rt(R, R.set.win32, R.set.t32, rt);
   if (w.x < 0) {  // no lookup table: one warp searches the times
     if (threadIdx.x < 32) {
@@ -441,9 +441,9 @@ __global__ void __launch_bounds__(kThreads, GRAD ? HK_MIN_CTAS : HK_MIN_CTAS_LL)
     w = s_win;
   }
   const int width = w.y - w.x;
-  const int c_begin = w.x + (int)((long long)width * sl / ns);
-  const int c_end = w.x + (int)((long long)width * (sl + 1) / ns);
-  run_piece<GRAD>(B, R, make_int4(rt, c_begin, c_end, 0), slot, sxs, stx, sacc);
+  const int c_begin = w.x + (int)((long long)width * l0 / ns);
+  const int c_end = w.x + (int)((long long)width * l1 / ns);
+  run_piece<GRAD>(B, R, it, c_begin, c_end, sxs, stx, sacc);
 }
 
 }  // namespace

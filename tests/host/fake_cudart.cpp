@@ -13,6 +13,7 @@
 // fake_release_events() completes every event recorded so far.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cstdio>
 #include <cstdlib>
@@ -122,13 +123,22 @@ static void check_schedule(const Request &R, int mode) {
   const SetView &S = R.set;
   // the float64 kernel's slices may cut column tiles into chunks
   bool ok = R.slices >= 1 && R.slices <= S.nct * (mode == 0 ? fp64_chunks_per_tile() : 1);
-  // the launch order visits every (row tile, slice) exactly once
+  // the launch tiers: 4-leaf items, then 2-leaf, then 1-leaf (mixed); 1-leaf only (float64)
+  if (R.wide < 0 || R.wide > R.coarse || R.coarse > S.nrt || (mode == 0 && R.coarse != 0)) ok = false;
+  // the launch order covers every (row tile, leaf) exactly once; an item's slot is its number,
+  // and a row tile's items are consecutive, so base + node = p
   std::vector<char> seen((size_t)S.nrt * R.slices, 0);
   for (int p = 0; ok && p < pair_items(R); ++p) {
-    const int2 tile = slot_tile(R, p);
-    if (tile.x < 0 || tile.x >= S.nrt || tile.y < 0 || tile.y >= R.slices || seen[(size_t)tile.x * R.slices + tile.y]++)
-      ok = false;
+    const PairItem it = item_at(R, p);
+    if (it.rt < 0 || it.rt >= S.nrt || it.node < 0 || it.base + it.node != p || it.base < 0) { ok = false; break; }
+    if (it.span != 1 && it.span != 2 && it.span != 4) { ok = false; break; }
+    const int l0 = it.node * it.span, l1 = std::min(l0 + it.span, R.slices);
+    if (l0 >= R.slices) { ok = false; break; }
+    for (int l = l0; l < l1; ++l)
+      if (seen[(size_t)it.rt * R.slices + l]++) ok = false;
   }
+  for (size_t i = 0; ok && i < seen.size(); ++i)
+    if (seen[i] != 1) ok = false;
   if (S.npad != S.nrt * kRowTile || S.nct * kColTile != S.npad || S.n > S.npad || S.n < 1) ok = false;
   if (!(R.cut_early > 0.0) || !(R.cut_late > 0.0)) ok = false;
   if (!R.partials || !R.comp || !R.rt_sum || !R.rt_count || !R.out) ok = false;
