@@ -211,15 +211,19 @@ int slices_for(int nrt, int nct, int resident_ctas, bool tiered) {
   return std::max(1, std::min(want, nct));
 }
 
-// Item spans of the mixed kernels along the launch order (see Request): the first half of the
+// Item spans along the launch order (see Request). The mixed kernel: the first half of the
 // row tiles take 4-leaf items, the next quarter 2-leaf items and the last quarter 1-leaf items,
-// so the launch ends on short items. The float64 kernel takes 1-leaf items throughout.
-void launch_tiers(int nrt, int mode, int *wide, int *coarse) {
-  if (mode == HAWKES_MIXED) {
+// so the launch ends on short items. The grouped kernel, whose items already carry several
+// requests, runs 2-leaf items throughout (measured faster for it); the float64 kernel 1-leaf.
+void launch_tiers(int nrt, int mode, bool grouped, int *wide, int *coarse) {
+  if (mode != HAWKES_MIXED) {
+    *wide = *coarse = 0;
+  } else if (grouped) {
+    *wide = 0;
+    *coarse = nrt;
+  } else {
     *wide = nrt / 2;
     *coarse = nrt - nrt / 4;
-  } else {
-    *wide = *coarse = 0;
   }
 }
 
@@ -263,7 +267,7 @@ int make_request(hawkes_ctx *ctx, const EventSetRec *S, const hawkes_params *p, 
   R->set.win32 = S->win32; R->set.win64 = S->win64;
   R->set.n = (int)S->n; R->set.npad = (int)S->npad; R->set.nrt = S->nrt; R->set.nct = S->nct;
   R->slices = S->slices[kind_of(mode, grad)];
-  launch_tiers(S->nrt, mode, &R->wide, &R->coarse);
+  launch_tiers(S->nrt, mode, false, &R->wide, &R->coarse);
   R->grad = grad;
   R->flags = flags;
   const double beta = std::sqrt(kLog2e / (2.0 * p->tau_t * p->tau_t));
@@ -295,14 +299,16 @@ int make_request(hawkes_ctx *ctx, const EventSetRec *S, const hawkes_params *p, 
 }
 
 // Device bytes one request needs: partial sums, compensator sums, row-tile sums.
-// Pair items (= partial-sum slots) of one request on S (see Request).
+// Partial-sum slots of one request on S: its pair items, alone or grouped (see Request).
 size_t set_slots(const EventSetRec *S, int mode, int grad) {
   Request R;
   std::memset(&R, 0, sizeof(R));
   R.set.nrt = S->nrt;
   R.slices = S->slices[kind_of(mode, grad)];
-  launch_tiers(S->nrt, mode, &R.wide, &R.coarse);
-  return (size_t)pair_items(R);
+  launch_tiers(S->nrt, mode, false, &R.wide, &R.coarse);
+  const int alone = pair_items(R);
+  launch_tiers(S->nrt, mode, true, &R.wide, &R.coarse);
+  return (size_t)std::max(alone, pair_items(R));
 }
 
 size_t request_footprint(const EventSetRec *S, int mode, int grad) {
@@ -443,7 +449,10 @@ int eval_sync(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_params *param
     bind_workspace(&b->req[r], S, mode, grad, req_base + (size_t)r * per,
                    device_out ? device_out : outs + 8 * q,
                    (unsigned *)(cnt_base + (size_t)r * counter_bytes(S, mode, grad)));
-    if (grouped) b->req[r].tscale = 1.0;
+    if (grouped) {
+      b->req[r].tscale = 1.0;
+      launch_tiers(S->nrt, mode, true, &b->req[r].wide, &b->req[r].coarse);
+    }
   }
   if (grouped) b->group = group_size(grad != 0);
   char *rows_cur = rows_base;
