@@ -96,10 +96,12 @@ int hawkes_set_flags(hawkes_ctx *ctx, int flags);
 /* Copy an event set to the device (Section 2.1: events (x_n, t_n), x_n in R^2).
  * x, y (km) and t (days) are host arrays of n doubles; the caller keeps ownership
  * and may free them when the call returns. t must be non-decreasing and >= 0
- * (the compensator integrates from 0 to t_N, the last event). The library stores
- * float64 and float32 copies in structure-of-arrays layout, padded to a multiple
- * of 512 with sentinel events that contribute exactly zero. The set stays resident
- * until hawkes_release_events or hawkes_destroy.
+ * (the compensator integrates from 0 to t_N, the last event). The library copies
+ * the float64 arrays to the device and forms there, in one launch, the float32
+ * copies, the tie indices and the time tables, and checks the inputs; all in
+ * structure-of-arrays layout, padded to a multiple of 512 with sentinel events that
+ * contribute exactly zero. The call returns when the set is ready (or rejected). The
+ * set stays resident until hawkes_release_events or hawkes_destroy.
  * Errors: E_INVAL (NULL, n < 1, non-finite, t < 0), E_UNSORTED, E_ADMISSION
  * (set does not fit the budget), E_NOMEM, E_CUDA. */
 int hawkes_upload_events(hawkes_ctx *ctx, const double *x, const double *y, const double *t,

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libhawkes_gb300.so")
-SOURCES = ["api.cu", "pair_mixed.cu", "pair_group.cu", "pair_fp64.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "pair_mixed.cu", "pair_group.cu", "pair_fp64.cu", "noalloc.cu", "upload.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

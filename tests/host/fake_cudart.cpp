@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <cstdio>
 #include <cstdlib>
@@ -185,6 +186,51 @@ static cudaError_t fake_pair(const Batch &b, bool grad) {
   }
   if (items != b.total_items || !b.fused) g_schedule_errors++;
   fake_outputs(b, grad);
+  return cudaSuccess;
+}
+
+// CPU model of the upload preparation launch (upload.cu): float32 copies, padding, tie
+// indices, window tables and the input checks, on the fake runtime's host memory.
+cudaError_t launch_upload_prep(const UploadPrep &u, cudaStream_t) {
+  if (u.n < 1 || u.npad < u.n) return cudaErrorInvalidValue;
+  unsigned flag = 0;
+  const double tn = u.t64[u.n - 1];
+  int64_t s64 = 0, s32 = 0;
+  for (int64_t i = 0; i < u.npad; ++i) {
+    if (i < u.n) {
+      const double x = u.x64[i], y = u.y64[i], t = u.t64[i];
+      if (!(std::fabs(x) <= 1e30) || !(std::fabs(y) <= 1e30) || !(t >= 0.0 && t <= 1e30)) flag |= 1u;
+      if (i > 0 && !(t >= u.t64[i - 1])) flag |= 2u;
+      u.x32[i] = (float)x; u.y32[i] = (float)y; u.t32[i] = (float)t;
+      if (i > 0 && u.t64[i] != u.t64[i - 1]) s64 = i;
+      if (i > 0 && (float)u.t64[i] != (float)u.t64[i - 1]) s32 = i;
+      u.lo64[i] = (int)s64; u.lo32[i] = (int)s32;
+    } else {
+      u.x64[i] = 0.0; u.y64[i] = 0.0; u.t64[i] = tn;
+      u.x32[i] = 0.f; u.y32[i] = 0.f; u.t32[i] = (float)tn;
+      u.lo64[i] = u.lo32[i] = (int)u.n;
+    }
+  }
+  const int nb = kWinBuckets, real = (int)((u.n + kColTile - 1) / kColTile);
+  for (int f64 = 0; f64 < 2; ++f64) {
+    int *w = f64 ? u.w64 : u.w32;
+    if (!w) continue;
+    const double t0 = f64 ? u.t0_64 : u.t0_32, width = f64 ? u.width_64 : u.width_32;
+    auto tm = [&](int64_t j) { return f64 ? u.t64[j] : (double)(float)u.t64[j]; };
+    int c = 0;
+    for (int b = 0; b < nb; ++b) {
+      const double lo = t0 + (double)b * width;
+      while (c < real && tm(std::min<int64_t>((int64_t)(c + 1) * kColTile, u.n) - 1) < lo) ++c;
+      w[b] = c;
+    }
+    c = 0;
+    for (int b = 0; b < nb; ++b) {
+      const double hi = t0 + (double)(b + 1) * width;
+      while (c < real && tm((int64_t)c * kColTile) <= hi) ++c;
+      w[nb + b] = c;
+    }
+  }
+  *u.flags |= flag;
   return cudaSuccess;
 }
 

@@ -42,6 +42,31 @@ def test_invalid_inputs(binding):
         assert e.value.status == -9
 
 
+def test_upload_checks_deep_in_a_large_set(binding):
+    """The checks run on the device over every event: a decrease or a bad value far from the
+    ends is found, and the context stays usable."""
+    ev = synth.simulate(100_000, 6000.0, seed=5)
+    with binding.Context(device=0) as ctx:
+        t = ev.t.copy()
+        t[61_234], t[61_235] = t[61_235] + 1.0, t[61_234]
+        with pytest.raises(binding.HawkesError) as e:
+            ctx.hawkes_upload_events(ev.x, ev.y, t)
+        assert e.value.status == -2
+        for arr, k, v in [(0, 99_999, np.inf), (1, 77_777, np.nan), (2, 88_888, -1.0)]:
+            cols = [ev.x.copy(), ev.y.copy(), ev.t.copy()]
+            cols[arr][k] = v
+            if arr == 2:
+                cols[2][:k + 1] = np.minimum(cols[2][:k + 1], v)  # still sorted: only the sign is wrong
+            with pytest.raises(binding.HawkesError) as e:
+                ctx.hawkes_upload_events(*cols)
+            assert e.value.status == -1
+        sid = ctx.hawkes_upload_events(ev.x, ev.y, ev.t)
+        ll = ctx.hawkes_loglik(sid, synth.THETA0, 1)
+    with binding.Context(device=0) as fresh:
+        sid = fresh.hawkes_upload_events(ev.x, ev.y, ev.t)
+        assert fresh.hawkes_loglik(sid, synth.THETA0, 1) == ll
+
+
 def test_admission_budget(binding):
     ev = synth.simulate(20000, 2000.0, seed=2)
     with binding.Context(device=0, hbm_budget_bytes=1 << 18) as ctx:
