@@ -132,67 +132,93 @@ __device__ __forceinline__ void tile_pass(const float4 *__restrict__ sxs, const 
   constexpr bool kTrig = KIND != 0;
   constexpr bool kNeedDt = kBg || KIND == 2 || GRAD;
   constexpr int kUnroll = GRAD ? kColUnroll : kColUnrollLL;
-#pragma unroll kUnroll
-  for (int j = 0; j < kColTile; ++j) {
-    const float4 d = stx[j];  // {-t', -t', -x, -y}
-    const float2 ct = make_float2(d.x, d.y);
-    const int col = c0 + j;
-    float2 cx, cy, bj;
-    if (KIND == 0) {
-      const float4 c = sxs[j];  // {-s x, -s x, -s y, -s y}
-      cx = make_float2(c.x, c.y);
-      cy = make_float2(c.z, c.w);
-    } else {
-      cx = make_float2(d.z, d.z);
-      cy = make_float2(d.w, d.w);
+  if constexpr (KIND == 0 && !GRAD) {
+    // background only, loglik: the unused trigger sum holds the odd columns' background sum,
+    // halving the dependent chain of the accumulation (1.4% faster loglik; no gain with the
+    // gradient, whose three chains already interleave)
+#pragma unroll kUnroll / 2
+    for (int j = 0; j < kColTile; j += 2) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float4 d = stx[j + h], c = sxs[j + h];
+        const float2 ct = make_float2(d.x, d.y), cx = make_float2(c.x, c.y), cy = make_float2(c.z, c.w);
+#pragma unroll
+        for (int p = 0; p < kPairs; ++p) {
+          const float2 dx = add2(X[p], cx), dy = add2(Y[p], cy), dt = add2(T[p], ct);
+          const float2 q = fma2(dy, dy, fma2(dx, dx, mul2(dt, dt)));
+          acc.v[h][p] = acc2(acc.v[h][p], make_float2(ex2(-q.x), ex2(-q.y)));
+        }
+      }
     }
-    if (KIND == 1 || KIND == 3) bj = mul2(add2(SREF, ct), WN);
 #pragma unroll
     for (int p = 0; p < kPairs; ++p) {
-      const float2 dx = add2(X[p], cx);
-      const float2 dy = add2(Y[p], cy);
-      float2 dt = make_float2(0.f, 0.f);
-      if (kNeedDt) dt = add2(T[p], ct);
+      acc.v[0][p] = acc2(acc.v[0][p], acc.v[1][p]);
+      acc.v[1][p] = make_float2(0.f, 0.f);
+    }
+    return;
+  } else {
+#pragma unroll kUnroll
+    for (int j = 0; j < kColTile; ++j) {
+      const float4 d = stx[j];  // {-t', -t', -x, -y}
+      const float2 ct = make_float2(d.x, d.y);
+      const int col = c0 + j;
+      float2 cx, cy, bj;
       if (KIND == 0) {
-        const float2 u = mul2(dt, dt);
-        const float2 q = fma2(dy, dy, fma2(dx, dx, u));
-        const float2 eb = make_float2(ex2(-q.x), ex2(-q.y));
-        acc.v[0][p] = acc2(acc.v[0][p], eb);
-        if (GRAD) {
-          acc.v[2][p] = accfma2(q, eb, acc.v[2][p]);
-          acc.v[3][p] = accfma2(u, eb, acc.v[3][p]);
-        }
-        continue;
+        const float4 c = sxs[j];  // {-s x, -s x, -s y, -s y}
+        cx = make_float2(c.x, c.y);
+        cy = make_float2(c.z, c.w);
+      } else {
+        cx = make_float2(d.z, d.z);
+        cy = make_float2(d.w, d.w);
       }
-      const float2 rho = fma2(dy, dy, mul2(dx, dx));
-      if (kBg) {
-        const float2 u = mul2(dt, dt);
-        const float2 q = fma2(rho, A2, u);
-        float2 eb = make_float2(ex2(-q.x), ex2(-q.y));
-        if (KIND == 2 && excl) {
-          const int ra = row_a0 + 64 * p;
-          if (col == ra) eb.x = 0.f;
-          if (col == ra + 32) eb.y = 0.f;
+      if (KIND == 1 || KIND == 3) bj = mul2(add2(SREF, ct), WN);
+#pragma unroll
+      for (int p = 0; p < kPairs; ++p) {
+        const float2 dx = add2(X[p], cx);
+        const float2 dy = add2(Y[p], cy);
+        float2 dt = make_float2(0.f, 0.f);
+        if (kNeedDt) dt = add2(T[p], ct);
+        if (KIND == 0) {
+          const float2 u = mul2(dt, dt);
+          const float2 q = fma2(dy, dy, fma2(dx, dx, u));
+          const float2 eb = make_float2(ex2(-q.x), ex2(-q.y));
+          acc.v[0][p] = acc2(acc.v[0][p], eb);
+          if (GRAD) {
+            acc.v[2][p] = accfma2(q, eb, acc.v[2][p]);
+            acc.v[3][p] = accfma2(u, eb, acc.v[3][p]);
+          }
+          continue;
         }
-        acc.v[0][p] = acc2(acc.v[0][p], eb);
-        if (GRAD) {
-          acc.v[2][p] = accfma2(q, eb, acc.v[2][p]);
-          acc.v[3][p] = accfma2(u, eb, acc.v[3][p]);
+        const float2 rho = fma2(dy, dy, mul2(dx, dx));
+        if (kBg) {
+          const float2 u = mul2(dt, dt);
+          const float2 q = fma2(rho, A2, u);
+          float2 eb = make_float2(ex2(-q.x), ex2(-q.y));
+          if (KIND == 2 && excl) {
+            const int ra = row_a0 + 64 * p;
+            if (col == ra) eb.x = 0.f;
+            if (col == ra + 32) eb.y = 0.f;
+          }
+          acc.v[0][p] = acc2(acc.v[0][p], eb);
+          if (GRAD) {
+            acc.v[2][p] = accfma2(q, eb, acc.v[2][p]);
+            acc.v[3][p] = accfma2(u, eb, acc.v[3][p]);
+          }
         }
-      }
-      if (kTrig) {
-        float2 arg;
-        if (KIND == 2) arg = fma2(rho, CN, mul2(dt, WN));
-        else arg = fma2(rho, CN, bj);
-        float2 es = make_float2(ex2(arg.x), ex2(arg.y));
-        if (KIND == 2) {
-          es.x = (col < LO[2 * p]) ? es.x : 0.f;
-          es.y = (col < LO[2 * p + 1]) ? es.y : 0.f;
-        }
-        acc.v[1][p] = acc2(acc.v[1][p], es);
-        if (GRAD) {
-          acc.v[4][p] = accfma2(rho, es, acc.v[4][p]);
-          acc.v[5][p] = accfma2(dt, es, acc.v[5][p]);
+        if (kTrig) {
+          float2 arg;
+          if (KIND == 2) arg = fma2(rho, CN, mul2(dt, WN));
+          else arg = fma2(rho, CN, bj);
+          float2 es = make_float2(ex2(arg.x), ex2(arg.y));
+          if (KIND == 2) {
+            es.x = (col < LO[2 * p]) ? es.x : 0.f;
+            es.y = (col < LO[2 * p + 1]) ? es.y : 0.f;
+          }
+          acc.v[1][p] = acc2(acc.v[1][p], es);
+          if (GRAD) {
+            acc.v[4][p] = accfma2(rho, es, acc.v[4][p]);
+            acc.v[5][p] = accfma2(dt, es, acc.v[5][p]);
+          }
         }
       }
     }
