@@ -105,6 +105,8 @@ struct hawkes_ctx {
   double *pinned_out = nullptr;  // kMaxBatch * 8 doubles
   cudaMemPool_t pool = nullptr;   // device memory of event sets and serving workspaces (stream-ordered)
   char *stage = nullptr;          // pinned host word for the upload checks (guarded by mu)
+  char *bounce = nullptr;         // pinned bounce buffer for per-event rows (guarded by mu)
+  cudaEvent_t bounce_ev[2] = {nullptr, nullptr};
   std::string last_cuda;
   // serving
   std::mutex smu;
@@ -356,6 +358,50 @@ void free_set(hawkes_ctx *ctx, EventSetRec *S) {
   delete S;
 }
 
+// Device rows (n doubles each) to caller-owned host memory through a pinned bounce buffer
+// in two halves: the device-to-host copy into one half overlaps the host copy out of the
+// other. Direct copies into pageable memory ran at about 2 GB/s on the Grace host. Called
+// with ctx->mu held; the copies are issued on ctx->stream after the work that writes `src`.
+constexpr size_t kBounceHalf = (size_t)4 << 20;
+int rows_to_host(hawkes_ctx *ctx, double *const *dst, const char *const *src, int rows, size_t nb) {
+  if (!ctx->bounce) {
+    HK_CUDA(ctx, cudaMallocHost((void **)&ctx->bounce, 2 * kBounceHalf));
+    for (cudaEvent_t &ev : ctx->bounce_ev) HK_CUDA(ctx, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  }
+  struct Piece { char *dst; size_t len; };
+  std::vector<Piece> pend[2];
+  size_t fill[2] = {0, 0};
+  int h = 0;
+  auto drain = [&](int w) -> int {
+    if (pend[w].empty()) return HAWKES_OK;
+    HK_CUDA(ctx, cudaEventSynchronize(ctx->bounce_ev[w]));
+    size_t off = 0;
+    for (const Piece &p : pend[w]) {
+      std::memcpy(p.dst, ctx->bounce + (size_t)w * kBounceHalf + off, p.len);
+      off += p.len;
+    }
+    pend[w].clear();
+    fill[w] = 0;
+    return HAWKES_OK;
+  };
+  for (int r = 0; r < rows; ++r)
+    for (size_t o = 0; o < nb; o += kBounceHalf) {
+      const size_t len = std::min(kBounceHalf, nb - o);
+      if (fill[h] + len > kBounceHalf) {  // this half is full: hand it over, take the other
+        HK_CUDA(ctx, cudaEventRecord(ctx->bounce_ev[h], ctx->stream));
+        h ^= 1;
+        if (int rc = drain(h)) return rc;
+      }
+      HK_CUDA(ctx, cudaMemcpyAsync(ctx->bounce + (size_t)h * kBounceHalf + fill[h], src[r] + o, len,
+                                   cudaMemcpyDeviceToHost, ctx->stream));
+      pend[h].push_back(Piece{(char *)dst[r] + o, len});
+      fill[h] += len;
+    }
+  HK_CUDA(ctx, cudaEventRecord(ctx->bounce_ev[h], ctx->stream));
+  if (int rc = drain(h ^ 1)) return rc;
+  return drain(h);
+}
+
 // Synchronous evaluation of k requests on one set (k = 1 for the single calls).
 // Results (7 doubles per request) land in host_out[8 * r]; device_out, if given
 // (k = 1 only), receives them on the device instead and the call does not block.
@@ -420,12 +466,17 @@ int eval_sync(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_params *param
   HK_CUDA(ctx, cudaMemcpyAsync(ctx->pinned_out, outs, (size_t)k * 8 * sizeof(double), cudaMemcpyDeviceToHost,
                                ctx->stream));
   const size_t nb = (size_t)S->n * sizeof(double);
-  if (mu_out) HK_CUDA(ctx, cudaMemcpyAsync(mu_out, b->req[0].mu_out, nb, cudaMemcpyDeviceToHost, ctx->stream));
-  if (xi_out) HK_CUDA(ctx, cudaMemcpyAsync(xi_out, b->req[0].xi_out, nb, cudaMemcpyDeviceToHost, ctx->stream));
+  std::vector<double *> dst;
+  std::vector<const char *> src;
+  if (mu_out) { dst.push_back(mu_out); src.push_back((const char *)b->req[0].mu_out); }
+  if (xi_out) { dst.push_back(xi_out); src.push_back((const char *)b->req[0].xi_out); }
   if (pi_out)
-    for (int q = 0; q < k; ++q)
-      HK_CUDA(ctx, cudaMemcpyAsync(pi_out + (size_t)q * S->n, pi_rows + (size_t)q * row_bytes, nb,
-                                   cudaMemcpyDeviceToHost, ctx->stream));
+    for (int q = 0; q < k; ++q) {
+      dst.push_back(pi_out + (size_t)q * S->n);
+      src.push_back(pi_rows + (size_t)q * row_bytes);
+    }
+  if (!dst.empty())
+    if (int rc = rows_to_host(ctx, dst.data(), src.data(), (int)dst.size(), nb)) return rc;
   HK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   std::memcpy(host_out, ctx->pinned_out, (size_t)k * 8 * sizeof(double));
   return HAWKES_OK;
@@ -723,6 +774,9 @@ int hawkes_destroy(hawkes_ctx *ctx) {
   if (ctx->sync_ws.dev) cudaFree(ctx->sync_ws.dev);
   if (ctx->pinned_out) cudaFreeHost(ctx->pinned_out);
   if (ctx->stage) cudaFreeHost(ctx->stage);
+  if (ctx->bounce) cudaFreeHost(ctx->bounce);
+  for (cudaEvent_t ev : ctx->bounce_ev)
+    if (ev) cudaEventDestroy(ev);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return HAWKES_OK;

@@ -108,6 +108,7 @@ cudaError_t cudaEventRecord(cudaEvent_t e, cudaStream_t) {
   reinterpret_cast<FakeEvent *>(e)->epoch = g_epoch.load();
   return cudaSuccess;
 }
+cudaError_t cudaEventSynchronize(cudaEvent_t) { return cudaSuccess; }
 cudaError_t cudaEventQuery(cudaEvent_t e) {
   auto *f = reinterpret_cast<FakeEvent *>(e);
   std::lock_guard<std::mutex> lk(g_mu);

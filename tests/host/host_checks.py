@@ -87,6 +87,14 @@ def main():
     assert pi.shape == (70, 1000)
     assert np.array_equal(pi, ths[:, :1] + np.arange(1000)[None, :])
     assert np.array_equal(ll, ths[:, 0] * 1000.0 + 1000 + 0.5)
+    # rows larger than half of the pinned bounce buffer (4 MB) are copied out in pieces
+    big_t = np.arange(600_001, dtype=np.float64) * 0.01
+    sbig = ctx.hawkes_upload_events(np.zeros(600_001), np.zeros(600_001), big_t)
+    pib, _ = ctx.hawkes_pi_batch(sbig, ths[:3], 1)
+    assert np.array_equal(pib, ths[:3, :1] + np.arange(600_001)[None, :])
+    mub, xib, _ = ctx.hawkes_event_terms(sbig, TH, 1)
+    assert np.array_equal(mub, np.arange(600_001)) and np.array_equal(xib, -np.arange(600_001))
+    ctx.hawkes_release_events(sbig)
     pi0, ll0 = ctx.hawkes_pi_batch(sids[1000], np.zeros((0, 6)), 1)
     assert pi0.shape == (0, 1000) and ll0.shape == (0,)
     expect_status(lambda: ctx.hawkes_pi_batch(999, ths, 1), -3)
