@@ -364,18 +364,35 @@ __device__ void finish_request(const Request &R) {
 }
 
 // Merge tree of a row tile's leaves (fused epilogue). An item enters at the node of its own
-// leaves, stores its partial row sums in its slot and climbs a binary tree over the tile's K
-// leaves: at each node whose sibling subtree exists, the CTA stores its current sums in the
-// slot of the node's first leaf, counts its arrival, and stops if it is first; the second to
-// arrive adds the sibling's stored sums to its own and climbs on. A node's value is left +
-// right whichever side arrives second (floating-point addition commutes), so the sums do not
-// depend on the order in which items finish. Returns true in the one CTA that completes the
-// root: it then holds the tile's full row sums. store(slot) writes the CTA's current sums to a
-// slot, merge(slot) adds a slot's sums to them (reading through L2). Called by every thread
-// of the CTA.
-template <class Store, class Merge>
+// leaves and climbs a binary tree over the tile's K leaves; at each node whose sibling subtree
+// exists, the first CTA to arrive leaves its current sums in the slot of the node's first leaf
+// and stops, and the second adds the sibling's sums to its own and climbs on. A node's value
+// is left + right whichever side arrives second (floating-point addition commutes), so the
+// sums do not depend on the order in which items finish. Returns true in the one CTA that
+// completes the root: it then holds the tile's full row sums. store(slot) writes the CTA's
+// current sums to a slot, merge(slot) adds a slot's sums to them (reading through L2). Called
+// by every thread of the CTA. Two protocols, same sums:
+//  - PUBLISH_FIRST: a CTA counts its arrival first; only the first stores (then adds a ready
+//    mark), and the second waits for the mark if it is not there yet. The climbing CTA never
+//    stores, which shortens the path of the last items (loglik + gradient: 24.6 KB slots).
+//  - otherwise every arriving CTA stores before counting, so the second never waits (faster
+//    for the 8 KB loglik slots, whose siblings tend to arrive close together).
+// The wait is for a CTA that has already arrived and has nothing left to wait for, so it ends;
+// it is still bounded (kMergeSpin polls), and a CTA that gives up writes NaN to the request's
+// results instead of hanging.
+// a node's counter: arrivals add 1 (at most 2, bits 0-1), the publisher's ready mark adds 4
+constexpr unsigned kMergeArrived = 1u, kMergeReady = 4u;
+constexpr int kMergeSpin = 1 << 22;
+
+__device__ __forceinline__ unsigned load_acquire(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+template <bool PUBLISH_FIRST, class Store, class Merge>
 __device__ bool merge_tree(const Request &R, const PairItem &it, Store store, Merge merge) {
-  __shared__ int s_go;
+  __shared__ unsigned s_old, s_ok;
   const int K = R.slices;
   unsigned *cnt = R.rt_count + 2 * (size_t)it.rt * K;
   int node = it.node, width = it.span, off = 0;
@@ -383,12 +400,44 @@ __device__ bool merge_tree(const Request &R, const PairItem &it, Store store, Me
   while (width < K) {
     const int parent = node >> 1, sib = node ^ 1;
     if (sib * width < K) {  // the sibling subtree exists
-      store(it.base + node * width / it.span);
-      __threadfence();
+      unsigned *c = cnt + off + parent;
+      if (!PUBLISH_FIRST) {
+        store(it.base + node * width / it.span);
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) s_old = atomicAdd(c, kMergeArrived);
+        __syncthreads();
+        if (s_old == 0u) return false;
+        __threadfence();
+        merge(it.base + sib * width / it.span);
+        __syncthreads();
+        off += (K + 2 * width - 1) / (2 * width);
+        node = parent;
+        width <<= 1;
+        continue;
+      }
       __syncthreads();
-      if (threadIdx.x == 0) s_go = atomicAdd(cnt + off + parent, 1u) == 1u;
+      if (threadIdx.x == 0) s_old = atomicAdd(c, kMergeArrived);
       __syncthreads();
-      if (!s_go) return false;
+      const unsigned old = s_old;
+      if (old == 0u) {  // first: publish, then stop
+        store(it.base + node * width / it.span);
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) atomicAdd(c, kMergeReady);
+        return false;
+      }
+      if (threadIdx.x == 0) {  // second: wait for the sibling's sums if they are not out yet
+        int k = 0;
+        if (!(old & kMergeReady))
+          while (!(load_acquire(c) & kMergeReady) && ++k < kMergeSpin) __nanosleep(64);
+        s_ok = k < kMergeSpin;
+      }
+      __syncthreads();
+      if (!s_ok) {  // gave up waiting (never expected): mark the results invalid
+        if (threadIdx.x < 7) R.out[threadIdx.x] = __longlong_as_double(0x7ff8000000000000ll);
+        return false;
+      }
       __threadfence();
       merge(it.base + sib * width / it.span);
       __syncthreads();

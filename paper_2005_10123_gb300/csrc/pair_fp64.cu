@@ -157,7 +157,7 @@ __device__ void run_piece64(const Batch &B, const Request &R, const PairItem &it
 #pragma unroll
       for (int s = 0; s < NS; ++s) acc[s][k] += __ldcg(src + s * kRowTile + warp * kWarpRows64 + lane + 32 * k);
   };
-  if (!merge_tree(R, it, store, merge)) return;
+  if (!merge_tree<true>(R, it, store, merge)) return;
   double v[GRAD ? 7 : 1] = {};
 #pragma unroll
   for (int k = 0; k < 4; ++k) {

@@ -248,7 +248,7 @@ __device__ void group_item(const Batch &B, int leader, int gsize, const PairItem
       }
     }
   };
-  if (!merge_tree(R0, it, store, merge)) return;
+  if (!merge_tree<GRAD>(R0, it, store, merge)) return;
   for (int k = 0; k < gsize; ++k) {
     const Request &R = B.req[leader + k];
     double v[GRAD ? 7 : 1] = {};

@@ -423,7 +423,7 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
       for (int s = 0; s < NS; ++s)
         sacc[(s * kRowsPerThread + k) * kThreads + tid] += __ldcg(src + s * kRowTile + warp * kWarpRows + lane + 32 * k);
   };
-  if (!merge_tree(R, it, store, merge)) return;
+  if (!merge_tree<GRAD>(R, it, store, merge)) return;
   double v[GRAD ? 7 : 1] = {};
   const double inv_s2 = 1.0 / ((double)sc * (double)sc);
 #pragma unroll
