@@ -68,6 +68,17 @@ def test_tied_times(ctx, mode):
 
 
 @pytest.mark.parametrize("mode", [0, 1], ids=["fp64", "mixed"])
+def test_ties_from_float32_rounding(ctx, mode):
+    """Times distinct in float64 that coincide after rounding to float32 (ulp 2.4e-4 days near
+    t = 4,000): the mixed path's causal indicator and tie indices follow the stored float32
+    values, the float64 path the doubles."""
+    ev = synth.simulate(2500, 200.0, seed=91)
+    ev.t = 4000.0 + np.cumsum(np.where(np.arange(ev.n) % 3 == 0, 0.05, 3e-5))
+    _check(ctx, ev, (0.05, 0.7, 5.0, 0.5, 2.0, 0.2), mode)
+    assert len(np.unique(ev.t.astype(np.float32))) < 0.5 * ev.n  # the case is exercised
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["fp64", "mixed"])
 def test_exclude_self(ctx, mode):
     from paper_2005_10123_gb300 import binding
     ev = synth.simulate(1500, 600.0, seed=5)
