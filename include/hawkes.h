@@ -24,7 +24,7 @@
  * Precision modes. HAWKES_FP64 runs every step in double precision. HAWKES_MIXED
  * stores coordinates as float32 (rounded from the uploaded doubles), computes pair
  * distances and kernel values in float32, accumulates each row in float32 over
- * 256-column tiles and folds every tile into float64; the log, the compensator and
+ * 128-column tiles and folds every tile into float64; the log, the compensator and
  * all reductions are float64. All reductions run in a fixed order: the same call on
  * the same inputs returns bit-identical results, alone or batched with others.
  *

@@ -16,14 +16,14 @@ namespace hk {
 #define HK_ROWS_PER_THREAD 4
 #endif
 #ifndef HK_THREADS
-#define HK_THREADS 128
+#define HK_THREADS 64  // two warps: the per-tile barrier waits on one other warp only
 #endif
 #ifndef HK_COL_TILE
-#define HK_COL_TILE 256
+#define HK_COL_TILE 128
 #endif
 constexpr int kThreads = HK_THREADS;
 constexpr int kRowsPerThread = HK_ROWS_PER_THREAD;  // even: rows are processed in packed pairs
-constexpr int kRowTile = kThreads * kRowsPerThread;  // 512 with 4 rows per thread
+constexpr int kRowTile = kThreads * kRowsPerThread;  // 256: 64 threads x 4 rows
 constexpr int kColTile = HK_COL_TILE;
 constexpr int kWarpRows = 32 * kRowsPerThread;       // consecutive rows per warp
 constexpr int kPadTo = kRowTile > kColTile ? kRowTile : kColTile;  // event arrays padded to this

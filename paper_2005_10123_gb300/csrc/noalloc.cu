@@ -26,8 +26,8 @@ namespace {
 
 constexpr int kNoallocMax = HAWKES_NOALLOC_MAX_EVENTS;  // 65,536 events
 constexpr int kChunks = 4;                               // most column chunks per row tile
-constexpr int kMaxRowTiles = (kNoallocMax + kRowTile - 1) / kRowTile;  // 128
-constexpr int kMaxItems = kMaxRowTiles * kChunks;        // 512
+constexpr int kMaxRowTiles = (kNoallocMax + kRowTile - 1) / kRowTile;
+constexpr int kMaxItems = kMaxRowTiles * kChunks;
 
 // Layout of g_scratch (byte offsets, all 256-aligned).
 constexpr size_t kOffHeader = 0;                                              // epilogue ticket

@@ -1,5 +1,5 @@
 // Mixed-precision pair kernel: float32 pair terms, float32 accumulation over one
-// 256-column tile, float64 accumulation across tiles and slices.
+// kColTile-column tile, float64 accumulation across tiles and items.
 //
 // For every row (event n) of its row tile the kernel forms, over the columns n' of its
 // work range (Section 2.1, Eq. 1 inner sum; the gradient moments are added here):
@@ -32,10 +32,10 @@
 #include "hk_internal.h"
 
 #ifndef HK_MIN_CTAS
-#define HK_MIN_CTAS 5  // resident CTAs per SM, loglik + gradient (shared memory allows 5)
+#define HK_MIN_CTAS 10  // resident CTAs per SM, loglik + gradient (shared memory allows 10)
 #endif
 #ifndef HK_MIN_CTAS_LL
-#define HK_MIN_CTAS_LL 6  // resident CTAs per SM, loglik only (80 registers, no spills)
+#define HK_MIN_CTAS_LL 12  // resident CTAs per SM, loglik only (80 registers, no spills)
 #endif
 #ifndef HK_COL_UNROLL
 #define HK_COL_UNROLL 4  // columns unrolled per step of the tile loop, loglik + gradient
