@@ -158,6 +158,12 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 #define HK_ITEMS_PER_SLOT 4
 #endif
 constexpr int kItemsPerSlot = HK_ITEMS_PER_SLOT;
+#ifndef HK_TIER_WIDE_PCT
+#define HK_TIER_WIDE_PCT 50  // percent of the row tiles (launched first) with 4-leaf items
+#endif
+#ifndef HK_TIER_FINE_PCT
+#define HK_TIER_FINE_PCT 25  // percent of the row tiles (launched last) with 1-leaf items
+#endif
 int slices_for(int nrt, int nct, int resident_ctas, bool tiered) {
   const int want = (kItemsPerSlot * resident_ctas + nrt - 1) / nrt * (tiered ? 2 : 1);
   return std::max(1, std::min(want, nct));
@@ -174,8 +180,8 @@ void launch_tiers(int nrt, int mode, bool grouped, int *wide, int *coarse) {
     *wide = 0;
     *coarse = nrt;
   } else {
-    *wide = nrt / 2;
-    *coarse = nrt - nrt / 4;
+    *wide = nrt * HK_TIER_WIDE_PCT / 100;
+    *coarse = nrt - nrt * HK_TIER_FINE_PCT / 100;
   }
 }
 

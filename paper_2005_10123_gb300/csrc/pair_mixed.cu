@@ -38,7 +38,7 @@
 #define HK_MIN_CTAS_LL 12  // resident CTAs per SM, loglik only (80 registers, no spills)
 #endif
 #ifndef HK_COL_UNROLL
-#define HK_COL_UNROLL 4  // columns unrolled per step of the tile loop, loglik + gradient
+#define HK_COL_UNROLL 8  // columns unrolled per step of the tile loop, loglik + gradient
 #endif
 #ifndef HK_COL_UNROLL_LL
 #define HK_COL_UNROLL_LL 8  // loglik only
