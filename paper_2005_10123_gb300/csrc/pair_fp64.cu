@@ -10,6 +10,10 @@
 namespace hk {
 namespace {
 
+#ifndef HK_FP64_MIN_CTAS
+#define HK_FP64_MIN_CTAS 1  // resident CTAs per SM the register budget must allow
+#endif
+
 constexpr double kPadTime = 1.0e150;  // time of a padded event: dt^2 = 1e300 stays finite
 // Each thread holds 4 rows; a CTA covers the row tile with kRowTile / 4 threads and each
 // warp owns 128 consecutive rows.
@@ -173,7 +177,7 @@ __device__ void run_piece64(const Batch &B, const Request &R, const PairItem &it
 }
 
 template <bool GRAD>
-__global__ void __launch_bounds__(kThreads64) pair_fp64_kernel(const __grid_constant__ Batch B) {
+__global__ void __launch_bounds__(kThreads64, HK_FP64_MIN_CTAS) pair_fp64_kernel(const __grid_constant__ Batch B) {
   __shared__ double sx[2][kColTile], sy[2][kColTile], st[2][kColTile];
   __shared__ int2 s_win;
   const int item = blockIdx.x;
