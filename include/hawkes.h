@@ -99,7 +99,7 @@ int hawkes_set_flags(hawkes_ctx *ctx, int flags);
  * (the compensator integrates from 0 to t_N, the last event). The library copies
  * the float64 arrays to the device and forms there, in one launch, the float32
  * copies, the tie indices and the time tables, and checks the inputs; all in
- * structure-of-arrays layout, padded to a multiple of 512 with sentinel events that
+ * structure-of-arrays layout, padded to a multiple of 256 with sentinel events that
  * contribute exactly zero. The call returns when the set is ready (or rejected). The
  * set stays resident until hawkes_release_events or hawkes_destroy.
  * Errors: E_INVAL (NULL, n < 1, non-finite, t < 0), E_UNSORTED, E_ADMISSION
