@@ -91,6 +91,7 @@ struct Flight {
 struct hawkes_ctx {
   int device = 0;
   int sms = 0;
+  int host_direct = 0;  // the device reads pageable host memory (uploads skip the copy)
   int occ[kKinds] = {1, 1, 1};
   int occ_launch[2][2] = {{1, 1}, {1, 1}};  // [mode][grad]
   cudaStream_t stream = nullptr;
@@ -706,6 +707,8 @@ int hawkes_create(hawkes_ctx **out, int device, size_t hbm_budget_bytes, void *c
   if (!ctx) return HAWKES_E_NOMEM;
   ctx->device = device;
   cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device);
+  if (cudaDeviceGetAttribute(&ctx->host_direct, cudaDevAttrPageableMemoryAccess, device) != cudaSuccess)
+    ctx->host_direct = 0;
   ctx->occ_launch[1][0] = occupancy_pair_mixed(false);
   ctx->occ_launch[1][1] = occupancy_pair_mixed(true);
   ctx->occ_launch[0][0] = occupancy_pair_fp64(false);
@@ -862,11 +865,14 @@ int hawkes_upload_events(hawkes_ctx *ctx, const double *x, const double *y, cons
   u.n = n;
   u.npad = npad;
   u.sms = ctx->sms;
-  // straight from the caller's (pageable) arrays: on this platform that measured faster
-  // than a copy through pinned staging (0.08 against 0.15 ms for 85,000 events)
-  e = cudaMemcpyAsync(u.x64, x, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(u.y64, y, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(u.t64, t, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+  if (ctx->host_direct) {  // the launch reads the caller's arrays in place (coherent host memory)
+    u.sx = x; u.sy = y; u.st = t;
+  } else {  // copied straight from the caller's (pageable) arrays, then read on the device
+    u.sx = u.x64; u.sy = u.y64; u.st = u.t64;
+    e = cudaMemcpyAsync(u.x64, x, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(u.y64, y, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(u.t64, t, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(u.flags, 0, sizeof(unsigned), ctx->stream);
   if (e == cudaSuccess) e = launch_upload_prep(u, ctx->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(hflag, u.flags, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream);

@@ -1,7 +1,9 @@
-// Upload preparation on the device: one launch turns the float64 coordinates that
-// hawkes_upload_events copied into a set's allocation into everything the pair kernels read
-// (SetView): the float32 copies, the padding, the tie indices lo and the two column-tile time
-// tables (WinTable), and checks the inputs on the way.
+// Upload preparation on the device: one launch turns the caller's float64 coordinates into
+// everything the pair kernels read (SetView): the float64 and float32 copies, the padding,
+// the tie indices lo and the two column-tile time tables (WinTable), and checks the inputs on
+// the way. The coordinates are read from sx, sy, st: the caller's host arrays themselves where
+// the device can read pageable host memory, else the set's own x64, y64, t64 after a copy.
+// Every read goes to the source arrays, never to what this launch writes.
 //
 // Events (blocks [0, event_blocks)), grid-stride over the padded length:
 //   i < n:  x32, y32, t32 = the float64 values rounded to nearest; flag 1 if a coordinate is
@@ -42,15 +44,18 @@ __device__ __forceinline__ int tie_start(F get, int64_t i) {
 __global__ void __launch_bounds__(kPrepThreads) upload_prep_kernel(const UploadPrep u, int event_blocks) {
   if ((int)blockIdx.x < event_blocks) {
     unsigned flag = 0;
-    const double tn = u.t64[u.n - 1];
-    auto t64 = [&](int64_t j) { return u.t64[j]; };
-    auto t32 = [&](int64_t j) { return __double2float_rn(u.t64[j]); };
+    const double tn = u.st[u.n - 1];
+    auto t64 = [&](int64_t j) { return u.st[j]; };
+    auto t32 = [&](int64_t j) { return __double2float_rn(u.st[j]); };
     const int64_t stride = (int64_t)event_blocks * kPrepThreads;
     for (int64_t i = (int64_t)blockIdx.x * kPrepThreads + threadIdx.x; i < u.npad; i += stride) {
       if (i < u.n) {
-        const double x = u.x64[i], y = u.y64[i], t = u.t64[i];
+        const double x = u.sx[i], y = u.sy[i], t = u.st[i];
         if (!(fabs(x) <= 1e30) || !(fabs(y) <= 1e30) || !(t >= 0.0 && t <= 1e30)) flag |= 1u;
-        if (i > 0 && !(t >= u.t64[i - 1])) flag |= 2u;
+        if (i > 0 && !(t >= u.st[i - 1])) flag |= 2u;
+        u.x64[i] = x;
+        u.y64[i] = y;
+        u.t64[i] = t;
         u.x32[i] = __double2float_rn(x);
         u.y32[i] = __double2float_rn(y);
         u.t32[i] = __double2float_rn(t);
@@ -79,7 +84,7 @@ __global__ void __launch_bounds__(kPrepThreads) upload_prep_kernel(const UploadP
   int *w = f64 ? u.w64 : u.w32;
   if (!w) return;  // no table for these times
   const double t0 = f64 ? u.t0_64 : u.t0_32, width = f64 ? u.width_64 : u.width_32;
-  auto tm = [&](int64_t j) { return f64 ? u.t64[j] : (double)__double2float_rn(u.t64[j]); };
+  auto tm = [&](int64_t j) { return f64 ? u.st[j] : (double)__double2float_rn(u.st[j]); };
   const int real = (int)((u.n + kColTile - 1) / kColTile);  // column tiles holding real events
   int a = 0, e = real;
   if (!upper) {  // first tile whose latest time is >= the bucket's start

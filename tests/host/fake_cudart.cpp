@@ -54,7 +54,14 @@ long fake_live_allocs() { return g_live_allocs.load(); }
 cudaError_t cudaGetDeviceCount(int *c) { *c = 1; return cudaSuccess; }
 cudaError_t cudaSetDevice(int) { return cudaSuccess; }
 cudaError_t cudaDeviceGetAttribute(int *v, cudaDeviceAttr a, int) {
-  *v = a == cudaDevAttrMultiProcessorCount ? 152 : 0;
+  *v = 0;
+  if (a == cudaDevAttrMultiProcessorCount) *v = 152;
+  // host memory is the fake's device memory: a device that reads pageable host memory, or
+  // not, as the test asks (FAKE_HOST_DIRECT=1)
+  if (a == cudaDevAttrPageableMemoryAccess) {
+    const char *e = std::getenv("FAKE_HOST_DIRECT");
+    *v = e && e[0] == '1';
+  }
   return cudaSuccess;
 }
 cudaError_t cudaMemGetInfo(size_t *f, size_t *t) { *f = (size_t)64 << 30; *t = (size_t)80 << 30; return cudaSuccess; }
@@ -195,16 +202,17 @@ static cudaError_t fake_pair(const Batch &b, bool grad) {
 cudaError_t launch_upload_prep(const UploadPrep &u, cudaStream_t) {
   if (u.n < 1 || u.npad < u.n) return cudaErrorInvalidValue;
   unsigned flag = 0;
-  const double tn = u.t64[u.n - 1];
+  const double tn = u.st[u.n - 1];
   int64_t s64 = 0, s32 = 0;
   for (int64_t i = 0; i < u.npad; ++i) {
     if (i < u.n) {
-      const double x = u.x64[i], y = u.y64[i], t = u.t64[i];
+      const double x = u.sx[i], y = u.sy[i], t = u.st[i];
       if (!(std::fabs(x) <= 1e30) || !(std::fabs(y) <= 1e30) || !(t >= 0.0 && t <= 1e30)) flag |= 1u;
-      if (i > 0 && !(t >= u.t64[i - 1])) flag |= 2u;
+      if (i > 0 && !(t >= u.st[i - 1])) flag |= 2u;
+      u.x64[i] = x; u.y64[i] = y; u.t64[i] = t;
       u.x32[i] = (float)x; u.y32[i] = (float)y; u.t32[i] = (float)t;
-      if (i > 0 && u.t64[i] != u.t64[i - 1]) s64 = i;
-      if (i > 0 && (float)u.t64[i] != (float)u.t64[i - 1]) s32 = i;
+      if (i > 0 && u.st[i] != u.st[i - 1]) s64 = i;
+      if (i > 0 && (float)u.st[i] != (float)u.st[i - 1]) s32 = i;
       u.lo64[i] = (int)s64; u.lo32[i] = (int)s32;
     } else {
       u.x64[i] = 0.0; u.y64[i] = 0.0; u.t64[i] = tn;
@@ -217,7 +225,7 @@ cudaError_t launch_upload_prep(const UploadPrep &u, cudaStream_t) {
     int *w = f64 ? u.w64 : u.w32;
     if (!w) continue;
     const double t0 = f64 ? u.t0_64 : u.t0_32, width = f64 ? u.width_64 : u.width_32;
-    auto tm = [&](int64_t j) { return f64 ? u.t64[j] : (double)(float)u.t64[j]; };
+    auto tm = [&](int64_t j) { return f64 ? u.st[j] : (double)(float)u.st[j]; };
     int c = 0;
     for (int b = 0; b < nb; ++b) {
       const double lo = t0 + (double)b * width;

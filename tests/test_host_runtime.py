@@ -35,6 +35,9 @@ def test_host_runtime_checks():
     if asan:
         env["LD_PRELOAD"] = asan
         env["ASAN_OPTIONS"] = "detect_leaks=0:abort_on_error=1"
-    r = subprocess.run([sys.executable, os.path.join(HERE, "host", "host_checks.py")], env=env,
-                       capture_output=True, text=True, timeout=600)
-    assert r.returncode == 0 and "ALL OK" in r.stdout, r.stdout[-3000:] + r.stderr[-6000:]
+    # uploads both ways: a copy of the caller's arrays, and a device that reads them in place
+    for direct in ("0", "1"):
+        env["FAKE_HOST_DIRECT"] = direct
+        r = subprocess.run([sys.executable, os.path.join(HERE, "host", "host_checks.py")], env=env,
+                           capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0 and "ALL OK" in r.stdout, r.stdout[-3000:] + r.stderr[-6000:]
