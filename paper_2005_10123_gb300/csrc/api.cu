@@ -25,7 +25,7 @@
 #include <vector>
 
 #include "../../include/hawkes.h"
-#include "hk_internal.h"
+#include "upload.h"
 
 using namespace hk;
 

@@ -20,7 +20,7 @@
 // multiply-add so that they are the same on every build.
 // For decreasing or non-finite times the indices and tables are meaningless, and the host
 // rejects the set from the flags.
-#include "hk_internal.h"
+#include "upload.h"
 
 namespace hk {
 namespace {

@@ -12,6 +12,7 @@ CUDA_INC = os.environ.get("CUDA_INC", "/usr/local/cuda/include")
 def build() -> str:
     srcs = [os.path.join(ROOT, "paper_2005_10123_gb300", "csrc", "api.cu"), os.path.join(HERE, "fake_cudart.cpp")]
     deps = srcs + [os.path.join(ROOT, "paper_2005_10123_gb300", "csrc", "hk_internal.h"),
+                   os.path.join(ROOT, "paper_2005_10123_gb300", "csrc", "upload.h"),
                    os.path.join(ROOT, "include", "hawkes.h")]
     if os.path.exists(OUT) and all(os.path.getmtime(OUT) >= os.path.getmtime(d) for d in deps):
         return OUT

@@ -22,7 +22,7 @@
 #include <mutex>
 #include <vector>
 
-#include "../../paper_2005_10123_gb300/csrc/hk_internal.h"
+#include "../../paper_2005_10123_gb300/csrc/upload.h"
 
 namespace {
 std::atomic<long> g_fail_after{-1};
