@@ -108,6 +108,8 @@ struct hawkes_ctx {
   char *stage = nullptr;          // pinned host word for the upload checks (guarded by mu)
   char *bounce = nullptr;         // pinned bounce buffer for per-event rows (guarded by mu)
   cudaEvent_t bounce_ev[2] = {nullptr, nullptr};
+  cudaStream_t copy_stream = nullptr;  // copies out of pi batches, beside the launches
+  std::vector<cudaEvent_t> chunk_ev;   // one per launch of a pi batch
   std::string last_cuda;
   // serving
   std::mutex smu;
@@ -370,7 +372,8 @@ void free_set(hawkes_ctx *ctx, EventSetRec *S) {
 // other. Direct copies into pageable memory ran at about 2 GB/s on the Grace host. Called
 // with ctx->mu held; the copies are issued on ctx->stream after the work that writes `src`.
 constexpr size_t kBounceHalf = (size_t)4 << 20;
-int rows_to_host(hawkes_ctx *ctx, double *const *dst, const char *const *src, int rows, size_t nb) {
+int rows_to_host(hawkes_ctx *ctx, double *const *dst, const char *const *src, int rows, size_t nb,
+                 cudaStream_t stream) {
   if (!ctx->bounce) {
     HK_CUDA(ctx, cudaMallocHost((void **)&ctx->bounce, 2 * kBounceHalf));
     for (cudaEvent_t &ev : ctx->bounce_ev) HK_CUDA(ctx, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
@@ -395,16 +398,16 @@ int rows_to_host(hawkes_ctx *ctx, double *const *dst, const char *const *src, in
     for (size_t o = 0; o < nb; o += kBounceHalf) {
       const size_t len = std::min(kBounceHalf, nb - o);
       if (fill[h] + len > kBounceHalf) {  // this half is full: hand it over, take the other
-        HK_CUDA(ctx, cudaEventRecord(ctx->bounce_ev[h], ctx->stream));
+        HK_CUDA(ctx, cudaEventRecord(ctx->bounce_ev[h], stream));
         h ^= 1;
         if (int rc = drain(h)) return rc;
       }
       HK_CUDA(ctx, cudaMemcpyAsync(ctx->bounce + (size_t)h * kBounceHalf + fill[h], src[r] + o, len,
-                                   cudaMemcpyDeviceToHost, ctx->stream));
+                                   cudaMemcpyDeviceToHost, stream));
       pend[h].push_back(Piece{(char *)dst[r] + o, len});
       fill[h] += len;
     }
-  HK_CUDA(ctx, cudaEventRecord(ctx->bounce_ev[h], ctx->stream));
+  HK_CUDA(ctx, cudaEventRecord(ctx->bounce_ev[h], stream));
   if (int rc = drain(h ^ 1)) return rc;
   return drain(h);
 }
@@ -414,6 +417,13 @@ int rows_to_host(hawkes_ctx *ctx, double *const *dst, const char *const *src, in
 // (k = 1 only), receives them on the device instead and the call does not block.
 // mu_out / xi_out (k = 1) receive the per-event mu_n and xi_n of Eq. 2, pi_out (k rows of n)
 // the per-event pi_n of every request.
+// eval_sync with ctx->mu held and the set found. pi_dev (device, rows of row_bytes for each
+// parameter vector) receives pi instead of pi_out when given; with device_out the call
+// returns once the launch is enqueued.
+int eval_locked(hawkes_ctx *ctx, EventSetRec *S, int k, const hawkes_params *params, int mode, int grad,
+                double *host_out, double *device_out, double *mu_out, double *xi_out, double *pi_out,
+                char *pi_dev);
+
 int eval_sync(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_params *params, int mode, int grad,
               double *host_out, double *device_out, double *mu_out, double *xi_out, double *pi_out) {
   if (mode != HAWKES_FP64 && mode != HAWKES_MIXED) return HAWKES_E_INVAL;
@@ -423,6 +433,12 @@ int eval_sync(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_params *param
   std::lock_guard<std::mutex> lock(ctx->mu);
   EventSetRec *S = find_set(ctx, set_id);
   if (!S) return HAWKES_E_NOSET;
+  return eval_locked(ctx, S, k, params, mode, grad, host_out, device_out, mu_out, xi_out, pi_out, nullptr);
+}
+
+int eval_locked(hawkes_ctx *ctx, EventSetRec *S, int k, const hawkes_params *params, int mode, int grad,
+                double *host_out, double *device_out, double *mu_out, double *xi_out, double *pi_out,
+                char *pi_dev) {
   const size_t per = request_footprint(S, mode, grad);
   // per-event rows. mu and xi (one request) are written by the kernel straight into the
   // caller's host arrays where the device writes pageable host memory (0.50 -> 0.40 ms at
@@ -432,7 +448,7 @@ int eval_sync(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_params *param
   const bool direct_rows = ctx->host_direct != 0;
   const size_t row_bytes = align_up((size_t)S->n * sizeof(double), 256);
   const size_t rows_bytes =
-      ((mu_out || xi_out) && !direct_rows ? 2 * row_bytes : 0) + (pi_out ? (size_t)k * row_bytes : 0);
+      ((mu_out || xi_out) && !direct_rows ? 2 * row_bytes : 0) + (pi_out && !pi_dev ? (size_t)k * row_bytes : 0);
   const size_t cnt = align_up(counter_bytes(S, mode, grad) * k, 256);
   const size_t need = kFixedBytes + cnt + rows_bytes + per * k;
   if (int rc = ensure_sync_ws(ctx, need)) return rc;
@@ -457,7 +473,7 @@ int eval_sync(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_params *param
     const int q = order[r];
     if (int rc = make_request(ctx, S, &params[q], mode, grad, ctx->flags, &b->req[r])) return rc;
     bind_workspace(&b->req[r], S, mode, grad, req_base + (size_t)r * per,
-                   device_out ? device_out : outs + 8 * q,
+                   device_out ? device_out + 8 * q : outs + 8 * q,
                    (unsigned *)(cnt_base + (size_t)r * counter_bytes(S, mode, grad)));
     if (grouped) {
       b->req[r].tscale = 1.0;
@@ -474,8 +490,8 @@ int eval_sync(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_params *param
     b->req[0].xi_out = (double *)(rows_cur + row_bytes);
     rows_cur += 2 * row_bytes;
   }
-  char *pi_rows = rows_cur;  // row q holds pi for params[q]
-  if (pi_out)
+  char *pi_rows = pi_dev ? pi_dev : rows_cur;  // row q holds pi for params[q]
+  if (pi_out || pi_dev)
     for (int r = 0; r < k; ++r) b->req[r].pi_out = (double *)(pi_rows + (size_t)order[r] * row_bytes);
   HK_CUDA(ctx, cudaMemsetAsync(base, 0, kFixedBytes + cnt, ctx->stream));
   if (int rc = launch_batch(ctx, *b, mode, grad, ctx->stream)) return rc;
@@ -493,7 +509,7 @@ int eval_sync(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_params *param
       src.push_back(pi_rows + (size_t)q * row_bytes);
     }
   if (!dst.empty())
-    if (int rc = rows_to_host(ctx, dst.data(), src.data(), (int)dst.size(), nb)) return rc;
+    if (int rc = rows_to_host(ctx, dst.data(), src.data(), (int)dst.size(), nb, ctx->stream)) return rc;
   HK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   std::memcpy(host_out, ctx->pinned_out, (size_t)k * 8 * sizeof(double));
   return HAWKES_OK;
@@ -796,6 +812,8 @@ int hawkes_destroy(hawkes_ctx *ctx) {
   if (ctx->bounce) cudaFreeHost(ctx->bounce);
   for (cudaEvent_t ev : ctx->bounce_ev)
     if (ev) cudaEventDestroy(ev);
+  for (cudaEvent_t ev : ctx->chunk_ev) cudaEventDestroy(ev);
+  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return HAWKES_OK;
@@ -1063,23 +1081,66 @@ int hawkes_event_terms(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *par
 int hawkes_pi_batch(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_params *params, hawkes_mode mode,
                     double *pi_out, double *loglik_out) {
   if (!ctx || !params || !pi_out || k < 0) return HAWKES_E_INVAL;
+  if (mode != HAWKES_FP64 && mode != HAWKES_MIXED) return HAWKES_E_INVAL;
+  for (int r = 0; r < k; ++r)
+    if (int rc = check_params(&params[r])) return rc;
+  if (k == 0) return HAWKES_OK;
   cudaSetDevice(ctx->device);
-  int64_t n = 0;
-  {
-    std::lock_guard<std::mutex> lock(ctx->mu);
-    EventSetRec *S = find_set(ctx, set_id);
-    if (!S) return HAWKES_E_NOSET;
-    n = S->n;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  EventSetRec *S = find_set(ctx, set_id);
+  if (!S) return HAWKES_E_NOSET;
+  // Every launch of up to kMaxBatch parameter vectors is enqueued first, with its pi rows in
+  // one device buffer; the rows of launch c leave through the bounce buffer on a second
+  // stream as soon as launch c is done, while the later launches run.
+  const size_t row_bytes = align_up((size_t)S->n * sizeof(double), 256);
+  const size_t outs_off = align_up((size_t)k * row_bytes, 256);
+  const int chunks = (k + kMaxBatch - 1) / kMaxBatch;
+  if (!ctx->copy_stream) HK_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+  while ((int)ctx->chunk_ev.size() < chunks) {
+    cudaEvent_t ev = nullptr;
+    HK_CUDA(ctx, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    ctx->chunk_ev.push_back(ev);
   }
-  std::vector<double> out((size_t)kMaxBatch * 8);
-  for (int r0 = 0; r0 < k; r0 += kMaxBatch) {  // up to kMaxBatch parameter vectors per launch
-    const int m = std::min(kMaxBatch, k - r0);
-    int rc = eval_sync(ctx, set_id, m, params + r0, mode, 0, out.data(), nullptr, nullptr, nullptr,
-                       pi_out + (size_t)r0 * n);
-    if (rc != HAWKES_OK) return rc;
-    if (loglik_out)
-      for (int r = 0; r < m; ++r) loglik_out[r0 + r] = out[(size_t)8 * r];
+  if (ctx->used.load() + outs_off + (size_t)k * 8 * sizeof(double) > ctx->budget) return HAWKES_E_ADMISSION;
+  const size_t dev_bytes = outs_off + (size_t)k * 8 * sizeof(double);
+  void *dev = nullptr;
+  HK_CUDA(ctx, cudaMallocFromPoolAsync(&dev, dev_bytes, ctx->pool, ctx->stream));
+  ctx->used += dev_bytes;
+  char *rows = (char *)dev;
+  double *outs = (double *)(rows + outs_off);
+  int rc = HAWKES_OK;
+  int launched = 0;
+  for (int c = 0; c < chunks && rc == HAWKES_OK; ++c, ++launched) {
+    const int r0 = c * kMaxBatch, m = std::min(kMaxBatch, k - r0);
+    rc = eval_locked(ctx, S, m, params + r0, mode, 0, nullptr, outs + (size_t)8 * r0, nullptr, nullptr, nullptr,
+                     rows + (size_t)r0 * row_bytes);
+    if (rc == HAWKES_OK && cudaEventRecord(ctx->chunk_ev[c], ctx->stream) != cudaSuccess) rc = HAWKES_E_CUDA;
   }
+  std::vector<double *> dst;
+  std::vector<const char *> src;
+  for (int c = 0; c < launched && rc == HAWKES_OK; ++c) {
+    const int r0 = c * kMaxBatch, m = std::min(kMaxBatch, k - r0);
+    if (cudaStreamWaitEvent(ctx->copy_stream, ctx->chunk_ev[c], 0) != cudaSuccess) { rc = HAWKES_E_CUDA; break; }
+    dst.clear();
+    src.clear();
+    for (int r = r0; r < r0 + m; ++r) {
+      dst.push_back(pi_out + (size_t)r * S->n);
+      src.push_back(rows + (size_t)r * row_bytes);
+    }
+    rc = rows_to_host(ctx, dst.data(), src.data(), m, (size_t)S->n * sizeof(double), ctx->copy_stream);
+  }
+  std::vector<double> host((size_t)k * 8);
+  if (rc == HAWKES_OK && cudaMemcpyAsync(host.data(), outs, host.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                         ctx->stream) != cudaSuccess)
+    rc = HAWKES_E_CUDA;
+  const cudaError_t e1 = cudaStreamSynchronize(ctx->copy_stream), e2 = cudaStreamSynchronize(ctx->stream);
+  cudaFreeAsync(dev, ctx->stream);
+  ctx->used -= dev_bytes;
+  if (rc != HAWKES_OK) return rc;
+  if (e1 != cudaSuccess) return cuda_fail(ctx, e1);
+  if (e2 != cudaSuccess) return cuda_fail(ctx, e2);
+  if (loglik_out)
+    for (int r = 0; r < k; ++r) loglik_out[r] = host[(size_t)8 * r];
   return HAWKES_OK;
 }
 

@@ -116,6 +116,7 @@ cudaError_t cudaEventRecord(cudaEvent_t e, cudaStream_t) {
   return cudaSuccess;
 }
 cudaError_t cudaEventSynchronize(cudaEvent_t) { return cudaSuccess; }
+cudaError_t cudaStreamWaitEvent(cudaStream_t, cudaEvent_t, unsigned) { return cudaSuccess; }
 cudaError_t cudaEventQuery(cudaEvent_t e) {
   auto *f = reinterpret_cast<FakeEvent *>(e);
   std::lock_guard<std::mutex> lk(g_mu);
