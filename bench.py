@@ -365,6 +365,17 @@ def run_ours(args):
                           "loglik0": float(ll[0])}))
         ctx.close()
         return 0
+    if args.profile_fp64_small:
+        # the float64 profiling case: the plain FP64 loglik on the N=2,000 workload
+        sm = synth.small_workload()
+        sid2 = ctx.hawkes_upload_events(sm.x, sm.y, sm.t)
+        for _ in range(args.warmup + args.steps):
+            ctx.hawkes_loglik_async(sid2, THETA0, binding.HAWKES_FP64, False, out.data_ptr())
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "FP64 loglik, N=2,000 over 1,000 days, Theta0",
+                          "launches": args.warmup + args.steps, "loglik": float(out[0].item())}))
+        ctx.close()
+        return 0
     if args.profile:
         # the profiling case: only the timed kernel sequence, nothing else
         for _ in range(args.steps):
@@ -515,6 +526,8 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=1000)
     ap.add_argument("--profile-batch", type=int, default=0, metavar="K",
                     help="run only warm-up + steps launches of K batched loglik+grad requests (grouped kernel)")
+    ap.add_argument("--profile-fp64-small", action="store_true",
+                    help="run only the float64 loglik of the N=2,000 workload (the FP64 kernel's ncu case)")
     ap.add_argument("--profile", action="store_true",
                     help="run only warm-up + steps of the mixed loglik+grad call (the case profiled with ncu)")
     args = ap.parse_args()
