@@ -22,7 +22,10 @@ constexpr int kThreads64 = kRowTile / kRows64;
 constexpr int kWarpRows64 = 32 * kRows64;
 // Slices cut the column window at kChunk64-column granularity (float64 pair work is slow
 // enough that a small set needs items smaller than a column tile to fill the GPU).
-constexpr int kChunk64 = 32;
+#ifndef HK_CHUNK64
+#define HK_CHUNK64 8  // N = 2,000 loglik: 0.43 ms with 32-column chunks, 0.36 with 8
+#endif
+constexpr int kChunk64 = HK_CHUNK64;
 constexpr int kChunksPerTile64 = kColTile / kChunk64;
 static_assert(kColTile % kChunk64 == 0, "column chunks must tile a column tile");
 
