@@ -1084,11 +1084,11 @@ int hawkes_pi_batch(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_params 
   if (mode != HAWKES_FP64 && mode != HAWKES_MIXED) return HAWKES_E_INVAL;
   for (int r = 0; r < k; ++r)
     if (int rc = check_params(&params[r])) return rc;
-  if (k == 0) return HAWKES_OK;
   cudaSetDevice(ctx->device);
   std::lock_guard<std::mutex> lock(ctx->mu);
   EventSetRec *S = find_set(ctx, set_id);
   if (!S) return HAWKES_E_NOSET;
+  if (k == 0) return HAWKES_OK;
   // Every launch of up to kMaxBatch parameter vectors is enqueued first, with its pi rows in
   // one device buffer; the rows of launch c leave through the bounce buffer on a second
   // stream as soon as launch c is done, while the later launches run.
