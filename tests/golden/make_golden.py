@@ -1,17 +1,31 @@
-"""Writes tests/golden/small_cases.json: log-likelihood and gradient of Eq. 1 (Section 2.1) for
-small seeded event sets, as computed by the FP64 CPU oracle (oracle/, the only code this
-script calls besides the seeded input generator).
+"""Writes the stored oracle values the tests compare with (Section 2.1, Eq. 1 and its gradient),
+as computed by the FP64 CPU oracle (oracle/, the only code this script calls besides the seeded
+input generator):
 
-Each case stores its inputs (x, y, t as float64), Theta, the flags, and the oracle's
+  tests/golden/small_cases.json   ell and gradient for small seeded event sets;
+  tests/golden/full_85k.json      ell and gradient for the N = 85,000 workload (--full).
+
+Each small case stores its inputs (x, y, t as float64), Theta, the flags, and the oracle's
 ell and gradient both for the inputs as given ("f64") and for the same inputs rounded to
-float32 ("f32in", the values the mixed-precision path stores). Re-run with
-    python tests/golden/make_golden.py
-only when a change to the oracle's arithmetic is justified by the paper; the tests compare the
-oracle and the CUDA path against these stored values.
+float32 ("f32in", the values the mixed-precision path stores).
+
+The full-size file stores the generator's arguments and a SHA-256 digest of the float32-rounded
+event arrays instead of the events (1 MB of floats), and the parameter vectors themselves, so that
+a test can check that it regenerated the same inputs before it compares. Beside ell and the gradient
+it stores sum_n |ell_n| and, per component, sum_n |d ell_n / d Theta_k|: the scales against which
+the error of a sum that nearly cancels is stated. The N = 85,000 events
+are float32-representable, so one oracle evaluation serves the float64 and the mixed paths.
+It takes a few minutes on 8 to 16 cores (about 70 s per parameter vector on 8 x86 cores).
+
+Re-run with
+    python tests/golden/make_golden.py [--full]
+only when a change to the oracle's arithmetic is justified by the paper.
 """
+import hashlib
 import json
 import os
 import sys
+import time
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(os.path.dirname(HERE))
@@ -32,8 +46,22 @@ CASES = [  # (name, n, T, seed, Theta, flags)
     ("n777_ragged", 777, 500.0, 106, synth.THETA0, 0),
 ]
 
+# The N = 85,000 workload: Theta0, a second vector at which no gradient component is near zero,
+# and four of the 64 vectors of the batched-chains workload (log-uniform within +-50% of Theta0,
+# seed 20053), which the grouped kernel evaluates.
+THETA_B = (0.012, 1.3, 20.0, 0.4, 1.5, 0.12)
+BATCH_SEED, BATCH_K, BATCH_PICK = 20053, 64, (0, 21, 42, 63)
 
-def main():
+
+def events_digest(ev) -> str:
+    """SHA-256 of the float32-rounded x, y, t arrays (held as float64, little-endian)."""
+    h = hashlib.sha256()
+    for a in (ev.x, ev.y, ev.t):
+        h.update(np.ascontiguousarray(a, dtype="<f8").tobytes())
+    return h.hexdigest()
+
+
+def write_small():
     out = {"source": "oracle/ (FP64, Section 2.1 Eq. 1), written by tests/golden/make_golden.py",
            "param_order": list(oracle.PARAM_NAMES), "cases": []}
     for name, n, T, seed, th, flags in CASES:
@@ -50,6 +78,45 @@ def main():
         fh.write("{\n" + ",\n".join(f" {json.dumps(k)}: {json.dumps(v)}" for k, v in head.items()))
         fh.write(',\n "cases": [\n' + ",\n".join("  " + json.dumps(c) for c in out["cases"]) + "\n ]\n}\n")
     print("wrote", path, len(out["cases"]), "cases")
+
+
+def write_full():
+    ev = synth.large_workload()
+    batch = synth.theta_batch(BATCH_K, seed=BATCH_SEED)
+    thetas = [("theta0", tuple(synth.THETA0)), ("theta_b", THETA_B)]
+    thetas += [(f"batch{BATCH_SEED}_{k}", tuple(float(v) for v in batch[k])) for k in BATCH_PICK]
+    out = {"source": "oracle/ (FP64, Section 2.1 Eq. 1 and its gradient), written by "
+                     "tests/golden/make_golden.py --full",
+           "param_order": list(oracle.PARAM_NAMES),
+           "workload": {"generator": "synth.large_workload", "n": int(ev.n), "T": 5000.0, "seed": 20051,
+                        "rounded32": True, "sha256_xyt_f64le": events_digest(ev)},
+           "threads": oracle.default_threads(), "cases": []}
+    rows = np.arange(ev.n, dtype=np.int64)
+    for name, th in thetas:
+        t0 = time.time()
+        r = oracle.rows(ev.x, ev.y, ev.t, th, rows, grad=True)
+        # per-event gradient terms d ell_n / d Theta = (d lambda_n / d Theta) / lambda_n - d Lambda_n / d Theta;
+        # their absolute sums are the scale against which a nearly cancelling component's error is stated
+        terms = r["dlam"] / r["lam"][:, None] - r["dLambda"]
+        case = {"name": name, "theta": [float(v) for v in th], "loglik": float(r["ell_sum"]),
+                "grad": [float(v) for v in r["grad_sum"]],
+                "grad_abs_sum": [float(v) for v in np.sum(np.abs(terms), axis=0)],
+                "loglik_abs_sum": float(np.sum(np.abs(r["ell_n"])))}
+        out["cases"].append(case)
+        print(name, case["loglik"], f"{time.time() - t0:.1f} s", flush=True)
+    path = os.path.join(HERE, "full_85k.json")
+    with open(path, "w") as fh:
+        head = {k: v for k, v in out.items() if k != "cases"}
+        fh.write("{\n" + ",\n".join(f" {json.dumps(k)}: {json.dumps(v)}" for k, v in head.items()))
+        fh.write(',\n "cases": [\n' + ",\n".join("  " + json.dumps(c) for c in out["cases"]) + "\n ]\n}\n")
+    print("wrote", path, len(out["cases"]), "cases")
+
+
+def main():
+    if "--full" in sys.argv:
+        write_full()
+    else:
+        write_small()
 
 
 if __name__ == "__main__":
