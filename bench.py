@@ -133,11 +133,37 @@ def _accuracy(theta, ll_m, g_m, ll_d, g_d) -> dict:
             "grad_fp64": [float(b) for b in g_d]}
 
 
+GOLDEN_FULL = os.path.join(ROOT, "tests", "golden", "full_85k.json")
+
+
+def _vs_oracle(name, ll, g):
+    """Against the stored FP64 oracle values of this workload (tests/golden/full_85k.json, written
+    by tests/golden/make_golden.py --full from oracle/ alone): relative error of ell, of the
+    gradient in the infinity norm and per component, and each component's error over
+    sum_n |d ell_n / d Theta_k| (the scale of a sum that cancels)."""
+    try:
+        with open(GOLDEN_FULL) as fh:
+            cases = {c["name"]: c for c in json.load(fh)["cases"]}
+    except (OSError, ValueError):
+        return None
+    c = cases.get(name)
+    if c is None:
+        return None
+    g, ref, absum = np.asarray(g), np.asarray(c["grad"]), np.asarray(c["grad_abs_sum"])
+    return {"rel_err_loglik": abs(ll - c["loglik"]) / abs(c["loglik"]),
+            "rel_err_grad_inf": float(np.max(np.abs(g - ref)) / np.max(np.abs(ref))),
+            "rel_err_grad_each": [float(v) for v in np.abs(g - ref) / np.abs(ref)],
+            "err_grad_each_over_abs_sum": [float(v) for v in np.abs(g - ref) / absum]}
+
+
 def _accuracy_at(ctx, sid, theta) -> dict:
     from paper_2005_10123_gb300 import binding
     ll_m, g_m = ctx.hawkes_loglik_grad(sid, theta, binding.HAWKES_MIXED)
     ll_d, g_d = ctx.hawkes_loglik_grad(sid, theta, binding.HAWKES_FP64)
-    return _accuracy(theta, ll_m, g_m, ll_d, g_d)
+    out = _accuracy(theta, ll_m, g_m, ll_d, g_d)
+    out["mixed_vs_oracle"] = _vs_oracle("theta_b", ll_m, g_m)
+    out["fp64_vs_oracle"] = _vs_oracle("theta_b", ll_d, g_d)
+    return out
 
 
 # The sources the timed pair kernel is compiled from (its translation unit and the shared
@@ -443,6 +469,8 @@ def run_ours(args):
                           "pair_work": ctx.hawkes_pair_work(sid, THETA0, binding.HAWKES_FP64)},
             "loglik_only_mixed": {"value": pairs / (ll_ms * 1e-3), "unit": "pair-evals/s", "ms_per_step": ll_ms},
             "mixed_vs_fp64": _accuracy(THETA0, ll_mixed, gm, ll64, g64),
+            "mixed_vs_oracle": _vs_oracle("theta0", ll_mixed, gm),
+            "fp64_vs_oracle": _vs_oracle("theta0", ll64, g64),
             "mixed_vs_fp64_theta_b": _accuracy_at(ctx, sid, THETA_B),
             "speedup_mixed_over_fp64": fp64_ms / step_ms,
         }
@@ -480,6 +508,8 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "pair-evals/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "fp32-pair/fp64-accumulate", "data": "synthetic",
+            "visited_pair_evals_per_s": world * visited / (step_ms * 1e-3),
+            "nonzero_term_evals_per_s": world * (work["bg"] + work["trig"]) / (step_ms * 1e-3),
             "config": {"workload": WORKLOAD, "n_events": n, "pairs_per_step": pairs,
                        "pairs_visited_per_step": visited,
                        "l2": "flushed between timed steps (256 MB write); the 1 MB event set is re-read from HBM",

@@ -26,7 +26,23 @@
  * distances and kernel values in float32, accumulates each row in float32 over
  * 128-column tiles and folds every tile into float64; the log, the compensator and
  * all reductions are float64. All reductions run in a fixed order: the same call on
- * the same inputs returns bit-identical results, alone or batched with others.
+ * the same inputs returns bit-identical results. A request served through
+ * hawkes_submit returns the same bits whatever it is batched with. hawkes_loglik_batch
+ * returns bit-identical results to single calls in HAWKES_FP64; in HAWKES_MIXED with
+ * two or more parameter vectors it runs a kernel that shares each pair's geometry
+ * across requests, and its results agree with single calls within the mixed-precision
+ * accuracy below, not bitwise.
+ *
+ * Mixed-precision accuracy (against float64 on the same float32-rounded inputs, measured
+ * on the N = 85,000 workload): ell to about 1e-7 relative and the gradient to about 1e-7
+ * of max|grad|. Scaled times and coordinates are rounded once from the exact float64
+ * scales, so the float32 path carries no systematic bandwidth error; a gradient component
+ * that nearly cancels (d ell / d tau_t cancels to about 1e-3 per event on that workload) has
+ * an absolute error of about 1e-7 of sum_n |d ell_n / d Theta_k|, not of its own size.
+ * Per-event values (hawkes_event_terms, hawkes_pi_batch) are held to about 1e-6 relative
+ * for tau_x >= 1 km; background-only tiles difference coordinates pre-scaled by 1/tau_x, so
+ * the error grows with the region's extent over tau_x (about 4e-6 at tau_x = 0.25 km and
+ * 8e-6 at tau_x = 0.1 km on a 20 km square). HAWKES_FP64 holds them to 1e-11.
  *
  * Threading. A context may be used from several host threads; calls on one
  * context are serialised internally, except hawkes_poll/hawkes_wait, which only
@@ -55,10 +71,18 @@ extern "C" {
 #define HAWKES_E_CUDA -8      /* a CUDA runtime call failed (see hawkes_last_cuda_error) */
 #define HAWKES_E_TICKET -9    /* unknown ticket, or its result was already collected   */
 #define HAWKES_E_SHUTDOWN -10 /* the context is being destroyed                        */
+#define HAWKES_E_DEVICE -11   /* a bounded wait inside a kernel ran out; the results of  */
+                              /* the request are discarded (the context stays usable)  */
 
 /* ---- flags (hawkes_set_flags) ----------------------------------------------------- */
 #define HAWKES_FLAG_EXCLUDE_SELF 1 /* drop n' = n from the background sum of lambda_n    */
 #define HAWKES_FLAG_DENSE 2        /* visit all N^2 pairs (see below)                      */
+/* For testing the failure path only: in loglik + gradient evaluations the first work item to
+ * reach each merge node of row tile 0 publishes its partial sums without marking them ready,
+ * so the bounded device wait of its sibling runs out (after at most 0.5 s) and the call
+ * returns HAWKES_E_DEVICE. Nothing faults or hangs; later calls without the flag are
+ * unaffected. */
+#define HAWKES_FLAG_TEST_WITHHOLD_READY (1 << 30)
 /* By default each row only visits the columns whose pair terms can be nonzero at the working
  * precision: a pair term whose exponent is so negative that float32 ex2 (flushing subnormals
  * to zero) or float64 exp returns exactly +0 cannot change a sum. Every term computed is the
@@ -115,8 +139,8 @@ int hawkes_release_events(hawkes_ctx *ctx, int32_t set_id);
 int hawkes_set_info(hawkes_ctx *ctx, int32_t set_id, int64_t *n_out, size_t *device_bytes_out);
 
 /* ell(Theta) of Eq. 1 for a resident set. Blocks until the result is on the host.
- * Errors: E_INVAL, E_NOSET, E_ADMISSION, E_NOMEM, E_CUDA. If some lambda_n is zero
- * (possible only with HAWKES_FLAG_EXCLUDE_SELF) the result is -inf with status OK. */
+ * Errors: E_INVAL, E_NOSET, E_ADMISSION, E_NOMEM, E_CUDA, E_DEVICE. If some lambda_n is
+ * zero (possible only with HAWKES_FLAG_EXCLUDE_SELF) the result is -inf with status OK. */
 int hawkes_loglik(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *params,
                   hawkes_mode mode, double *loglik_out);
 
@@ -130,14 +154,18 @@ int hawkes_loglik_grad(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *par
  * evaluation on the context's stream and return at once. `device_out` is a device
  * pointer to 7 doubles (ell, then the gradient if want_grad; the gradient entries
  * are left unchanged otherwise). The caller synchronises the stream before reading
- * it. Calls on one context share its workspace and therefore run in stream order. */
+ * it. Calls on one context share its workspace and therefore run in stream order. A device
+ * wait that ran out (HAWKES_E_DEVICE for the blocking calls) leaves NaN in device_out. */
 int hawkes_loglik_async(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *params,
                         hawkes_mode mode, int want_grad, double *device_out);
 
 /* K parameter vectors on one resident set in one launch (K <= 64): the batched
  * evaluation of many MCMC chains that share a data set. loglik_out has K entries;
- * grad_out (K x 6, row-major) may be NULL when want_grad is 0. Each result is
- * bit-identical to the same request evaluated alone. */
+ * grad_out (K x 6, row-major) may be NULL when want_grad is 0. Results are deterministic
+ * for a given batch. In HAWKES_FP64 each is bit-identical to the same request evaluated
+ * alone. In HAWKES_MIXED with K >= 2 groups of requests share each pair's geometry (time
+ * differences in days, float32 sums over a work item rather than a tile), so the results
+ * agree with single calls within the mixed-precision accuracy stated above, not bitwise. */
 int hawkes_loglik_batch(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_params *params,
                         hawkes_mode mode, int want_grad, double *loglik_out, double *grad_out);
 
@@ -156,7 +184,10 @@ int hawkes_pair_work(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *param
 /* Per-event terms of Eq. 2: mu_out[n] = mu(x_n, t_n) (background rate at event n)
  * and xi_out[n] = lambda_n - mu_n (the self-excitation part), so lambda_n =
  * mu_n + xi_n and pi_n = xi_n / lambda_n. Host arrays of n doubles each, owned by
- * the caller. The log-likelihood of the same pass goes to loglik_out if not NULL. */
+ * the caller. The log-likelihood of the same pass goes to loglik_out if not NULL.
+ * Accuracy in HAWKES_MIXED: mu_n to about 1e-6 relative for tau_x >= 1 km, growing as the
+ * region's extent over tau_x grows (about 4e-6 at tau_x = 0.25 km and 8e-6 at 0.1 km on a
+ * 20 km square); xi_n to about 1e-6 of max xi. HAWKES_FP64: 1e-11. */
 int hawkes_event_terms(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *params,
                        hawkes_mode mode, double *mu_out, double *xi_out, double *loglik_out);
 
@@ -166,6 +197,8 @@ int hawkes_event_terms(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *par
  * loglik_out (k doubles, may be NULL) receives ell at each params[r]; both owned by the
  * caller. The call blocks; it launches up to 64 parameter vectors at a time and needs device
  * workspace for 64 * n doubles of output besides the evaluation's own. k = 0 does nothing.
+ * Accuracy as hawkes_event_terms (pi_n = xi_n / lambda_n: about 1e-6 absolute in HAWKES_MIXED
+ * for tau_x >= 1 km, up to about 8e-6 at tau_x = 0.1 km; 1e-11 in HAWKES_FP64).
  * Errors as hawkes_loglik; on an error the entries of pi_out not yet written are undefined. */
 int hawkes_pi_batch(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_params *params,
                     hawkes_mode mode, double *pi_out, double *loglik_out);
@@ -211,15 +244,20 @@ int hawkes_stats(hawkes_ctx *ctx, int64_t out[7]);
  * the library (about 5.3 MB, reserved on every GPU that loads the library, until exit).
  *
  * x, y, t: device pointers to n float32 values each (km, km, days), t non-decreasing and
- * >= 0 (not checked: the values are never read on the host); 1 <= n <=
- * HAWKES_NOALLOC_MAX_EVENTS, larger n returns HAWKES_E_INVAL. flags: HAWKES_FLAG_*.
+ * >= 0, coordinates finite; 1 <= n <= HAWKES_NOALLOC_MAX_EVENTS, larger n returns
+ * HAWKES_E_INVAL. The event values are never read on the host: they are checked on the
+ * device, and inputs that hawkes_upload_events would reject (unsorted, negative or
+ * non-finite times, non-finite coordinates), or a time span too long for the float32 path at
+ * this tau_t, make device_out NaN. flags: HAWKES_FLAG_EXCLUDE_SELF and HAWKES_FLAG_DENSE.
  * device_out: device pointer to one double that receives ell. cuda_stream: the stream to
  * enqueue on (NULL = the legacy default stream). The call is asynchronous: the caller
  * synchronises the stream before reading device_out.
  * The first call on each device sets up the array's device address (cudaGetSymbolAddress),
- * so make that first call before any stream capture. Every call reuses the same array:
- * calls that may overlap on the GPU (on different streams, or from several threads) race
- * and must be serialised by the caller. Errors: E_INVAL, E_CUDA. */
+ * so make that first call before any stream capture; a device reset (cudaDeviceReset) makes
+ * the next call set it up again. Every call reuses the same array, which keeps the previous
+ * call's contents (each call clears what must start at zero): calls that may overlap on the
+ * GPU (on different streams, or from several threads) race and must be serialised by the
+ * caller. Errors: E_INVAL, E_CUDA. */
 #define HAWKES_NOALLOC_MAX_EVENTS 65536
 int hawkes_loglik_noalloc(const float *x, const float *y, const float *t, int64_t n,
                           const hawkes_params *params, int flags, double *device_out, void *cuda_stream);

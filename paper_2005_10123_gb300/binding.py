@@ -18,11 +18,12 @@ HAWKES_FP64 = 0
 HAWKES_MIXED = 1
 HAWKES_FLAG_EXCLUDE_SELF = 1
 HAWKES_FLAG_DENSE = 2
+HAWKES_FLAG_TEST_WITHHOLD_READY = 1 << 30  # tests of the device-wait failure path only
 
 STATUS = {
     0: "HAWKES_OK", -1: "HAWKES_E_INVAL", -2: "HAWKES_E_UNSORTED", -3: "HAWKES_E_NOSET",
     -4: "HAWKES_E_ADMISSION", -5: "HAWKES_E_NOMEM", -6: "HAWKES_E_TIMEOUT", -7: "HAWKES_E_PENDING",
-    -8: "HAWKES_E_CUDA", -9: "HAWKES_E_TICKET", -10: "HAWKES_E_SHUTDOWN",
+    -8: "HAWKES_E_CUDA", -9: "HAWKES_E_TICKET", -10: "HAWKES_E_SHUTDOWN", -11: "HAWKES_E_DEVICE",
 }
 
 # Every symbol include/hawkes.h declares (checked by the CPU test suite).

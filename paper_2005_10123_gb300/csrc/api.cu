@@ -82,7 +82,7 @@ struct Flight {
   std::vector<uint64_t> ids;
   void *ws = nullptr;
   size_t ws_bytes = 0;
-  double *host_out = nullptr;  // pinned, kMaxBatch * 8
+  double *host_out = nullptr;  // pinned, kFixedBytes: status words, then kMaxBatch * 8 results
   std::vector<EventSetRec *> sets;
 };
 
@@ -103,7 +103,7 @@ struct hawkes_ctx {
   std::map<int32_t, EventSetRec *> sets;
   int32_t next_set = 1;
   Workspace sync_ws;
-  double *pinned_out = nullptr;  // kMaxBatch * 8 doubles
+  double *pinned_out = nullptr;  // kFixedBytes: status words, then kMaxBatch * 8 results
   cudaMemPool_t pool = nullptr;   // device memory of event sets and serving workspaces (stream-ordered)
   char *stage = nullptr;          // pinned host word for the upload checks (guarded by mu)
   char *bounce = nullptr;         // pinned bounce buffer for per-event rows (guarded by mu)
@@ -231,11 +231,7 @@ int make_request(hawkes_ctx *ctx, const EventSetRec *S, const hawkes_params *p, 
   launch_tiers(S->nrt, mode, false, &R->wide, &R->coarse);
   R->grad = grad;
   R->flags = flags;
-  const double beta = std::sqrt(kLog2e / (2.0 * p->tau_t * p->tau_t));
-  R->a2 = (float)(kLog2e / (2.0 * p->tau_x * p->tau_x));
-  R->beta = (float)beta;
-  R->wn = (float)(-p->omega * kLog2e / (double)R->beta);
-  R->cn = (float)(-kLog2e / (2.0 * p->h * p->h));
+  set_mixed_constants(R, p->tau_x, p->tau_t, p->omega, p->h);
   R->da = 1.0 / (2.0 * p->tau_x * p->tau_x);
   R->db = 1.0 / (2.0 * p->tau_t * p->tau_t);
   R->dc = 1.0 / (2.0 * p->h * p->h);
@@ -245,11 +241,10 @@ int make_request(hawkes_ctx *ctx, const EventSetRec *S, const hawkes_params *p, 
   if (mode == HAWKES_MIXED) {
     // the float32 path must keep every scaled quantity finite and below the padding value
     const double span = (S->t_last32 - S->t_first32) * (double)R->beta;
-    if (!(R->a2 > 0.f) || !(R->beta > 0.f) || !std::isfinite(R->wn) || !(R->cn < 0.f) ||
-        !std::isfinite(R->a2) || !std::isfinite(R->cn) || span > 1.0e15)
+    if (!(R->a2 > 0.f) || !(R->beta > 0.f) || !(R->b2 > 0.f) || !(R->s_hi > 0.f) || !std::isfinite(R->wn) ||
+        !(R->cn < 0.f) || !std::isfinite(R->a2) || !std::isfinite(R->b2) || !std::isfinite(R->cn) || span > 1.0e15)
       return HAWKES_E_INVAL;
     R->t_last = S->t_last32;
-    R->tscale = 1.0 / (double)R->beta;
   } else {
     R->t_last = S->t_last64;
     R->tscale = 1.0;
@@ -285,12 +280,21 @@ size_t counter_bytes(const EventSetRec *S, int mode, int grad) {
   return align_up((2 * (size_t)S->nrt * S->slices[kind_of(mode, grad)] + 1) * sizeof(unsigned), 64);
 }
 
-// Batch workspace: a 256-byte header (unused, keeps the outputs aligned), the per-request
-// outputs (8 doubles each), then every request's completion counters. One memset of these
-// (kFixedBytes + the batch's counter bytes) zeroes everything that must start at 0.
+// Batch workspace: a 256-byte header holding one device status word per request (see
+// Request::status), the per-request outputs (8 doubles each), then every request's completion
+// counters. One memset of these (kFixedBytes + the batch's counter bytes) zeroes everything
+// that must start at 0; one copy of the first kHdrBytes + 64 k bytes brings the status words
+// and results back.
 constexpr size_t kHdrBytes = 256;
 constexpr size_t kOutBytes = (size_t)kMaxBatch * 8 * sizeof(double);
 constexpr size_t kFixedBytes = kHdrBytes + kOutBytes;
+static_assert(kHdrBytes >= kMaxBatch * sizeof(unsigned), "one status word per request");
+
+// The status of request r from the copied-back header: HAWKES_E_DEVICE if one of its device
+// waits ran out (its results are NaN), else HAWKES_OK.
+int device_status(const void *header, int r) {
+  return ((const unsigned *)header)[r] ? HAWKES_E_DEVICE : HAWKES_OK;
+}
 
 // Carve one request's workspace out of `base` (as sized by request_footprint).
 void bind_workspace(Request *R, const EventSetRec *S, int mode, int grad, char *base, double *out,
@@ -475,6 +479,7 @@ int eval_locked(hawkes_ctx *ctx, EventSetRec *S, int k, const hawkes_params *par
     bind_workspace(&b->req[r], S, mode, grad, req_base + (size_t)r * per,
                    device_out ? device_out + 8 * q : outs + 8 * q,
                    (unsigned *)(cnt_base + (size_t)r * counter_bytes(S, mode, grad)));
+    b->req[r].status = (unsigned *)base + q;
     if (grouped) {
       b->req[r].tscale = 1.0;
       launch_tiers(S->nrt, mode, true, &b->req[r].wide, &b->req[r].coarse);
@@ -496,8 +501,8 @@ int eval_locked(hawkes_ctx *ctx, EventSetRec *S, int k, const hawkes_params *par
   HK_CUDA(ctx, cudaMemsetAsync(base, 0, kFixedBytes + cnt, ctx->stream));
   if (int rc = launch_batch(ctx, *b, mode, grad, ctx->stream)) return rc;
   if (device_out) return HAWKES_OK;
-  HK_CUDA(ctx, cudaMemcpyAsync(ctx->pinned_out, outs, (size_t)k * 8 * sizeof(double), cudaMemcpyDeviceToHost,
-                               ctx->stream));
+  HK_CUDA(ctx, cudaMemcpyAsync(ctx->pinned_out, base, kHdrBytes + (size_t)k * 8 * sizeof(double),
+                               cudaMemcpyDeviceToHost, ctx->stream));
   const size_t nb = (size_t)S->n * sizeof(double);
   std::vector<double *> dst;
   std::vector<const char *> src;
@@ -511,7 +516,9 @@ int eval_locked(hawkes_ctx *ctx, EventSetRec *S, int k, const hawkes_params *par
   if (!dst.empty())
     if (int rc = rows_to_host(ctx, dst.data(), src.data(), (int)dst.size(), nb, ctx->stream)) return rc;
   HK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  std::memcpy(host_out, ctx->pinned_out, (size_t)k * 8 * sizeof(double));
+  for (int q = 0; q < k; ++q)
+    if (int rc = device_status(ctx->pinned_out, q)) return rc;
+  std::memcpy(host_out, (const char *)ctx->pinned_out + kHdrBytes, (size_t)k * 8 * sizeof(double));
   return HAWKES_OK;
 }
 
@@ -548,7 +555,11 @@ void reap_flights(hawkes_ctx *ctx) {
     if (q == cudaErrorNotReady) continue;
     const int status = q == cudaSuccess ? HAWKES_OK : HAWKES_E_CUDA;
     if (q != cudaSuccess) ctx->last_cuda = cudaGetErrorString(q);
-    for (size_t r = 0; r < F.ids.size(); ++r) complete_ticket(ctx, F.ids[r], status, F.host_out + 8 * r);
+    const double *vals = (const double *)((const char *)F.host_out + kHdrBytes);
+    for (size_t r = 0; r < F.ids.size(); ++r) {
+      const int st = status == HAWKES_OK ? device_status(F.host_out, (int)r) : status;
+      complete_ticket(ctx, F.ids[r], st, vals + 8 * r);
+    }
     {
       std::lock_guard<std::mutex> lock(ctx->mu);
       for (auto *S : F.sets) release_set_ref(ctx, S);
@@ -631,12 +642,14 @@ bool launch_pending(hawkes_ctx *ctx, Flight &F) {
       TicketRec &T = ctx->tickets[take[r]];
       rc = make_request(ctx, sets[r], &T.p, mode, grad, T.flags, &b->req[r]);
       bind_workspace(&b->req[r], sets[r], mode, grad, cur, outs + 8 * r, (unsigned *)cnt_cur);
+      b->req[r].status = (unsigned *)base + r;
       cnt_cur += counter_bytes(sets[r], mode, grad);
       cur += T.footprint;
     }
     if (rc == HAWKES_OK) rc = launch_batch(ctx, *b, mode, grad, F.stream);
     if (rc == HAWKES_OK) {
-      e = cudaMemcpyAsync(F.host_out, outs, take.size() * 8 * sizeof(double), cudaMemcpyDeviceToHost, F.stream);
+      e = cudaMemcpyAsync(F.host_out, base, kHdrBytes + take.size() * 8 * sizeof(double), cudaMemcpyDeviceToHost,
+                          F.stream);
       if (e != cudaSuccess) rc = cuda_fail(ctx, e);
     }
     cudaFreeAsync(ws, F.stream);
@@ -689,7 +702,7 @@ int init_flights(hawkes_ctx *ctx) {
   for (auto &F : ctx->flights) {  // resumable: members created by an earlier failed call are kept
     if (!F.stream) HK_CUDA(ctx, cudaStreamCreateWithFlags(&F.stream, cudaStreamNonBlocking));
     if (!F.done) HK_CUDA(ctx, cudaEventCreateWithFlags(&F.done, cudaEventDisableTiming));
-    if (!F.host_out) HK_CUDA(ctx, cudaMallocHost((void **)&F.host_out, kMaxBatch * 8 * sizeof(double)));
+    if (!F.host_out) HK_CUDA(ctx, cudaMallocHost((void **)&F.host_out, kFixedBytes));
   }
   ctx->flights_ready = true;
   return HAWKES_OK;
@@ -714,6 +727,7 @@ const char *hawkes_strerror(int status) {
     case HAWKES_E_CUDA: return "CUDA error";
     case HAWKES_E_TICKET: return "unknown or consumed ticket";
     case HAWKES_E_SHUTDOWN: return "context shut down";
+    case HAWKES_E_DEVICE: return "a bounded device wait ran out (results discarded)";
     default: return "unknown status";
   }
 }
@@ -754,7 +768,7 @@ int hawkes_create(hawkes_ctx **out, int device, size_t hbm_budget_bytes, void *c
   e = cudaMemGetInfo(&free_b, &total_b);
   if (e != cudaSuccess) return cuda_fail(nullptr, e);
   ctx->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.9 * (double)free_b);
-  e = cudaMallocHost((void **)&ctx->pinned_out, kMaxBatch * 8 * sizeof(double));
+  e = cudaMallocHost((void **)&ctx->pinned_out, kFixedBytes);
   if (e != cudaSuccess) return cuda_fail(nullptr, e);
   // the context's own device memory pool; it keeps freed memory for reuse (the HBM budget
   // bounds what the context holds) and returns it when the context is destroyed
@@ -820,7 +834,8 @@ int hawkes_destroy(hawkes_ctx *ctx) {
 }
 
 int hawkes_set_flags(hawkes_ctx *ctx, int flags) {
-  if (!ctx || (flags & ~(HAWKES_FLAG_EXCLUDE_SELF | HAWKES_FLAG_DENSE))) return HAWKES_E_INVAL;
+  if (!ctx || (flags & ~(HAWKES_FLAG_EXCLUDE_SELF | HAWKES_FLAG_DENSE | HAWKES_FLAG_TEST_WITHHOLD_READY)))
+    return HAWKES_E_INVAL;
   std::lock_guard<std::mutex> lock(ctx->mu);
   ctx->flags = flags;
   return HAWKES_OK;
@@ -1139,6 +1154,8 @@ int hawkes_pi_batch(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_params 
   if (rc != HAWKES_OK) return rc;
   if (e1 != cudaSuccess) return cuda_fail(ctx, e1);
   if (e2 != cudaSuccess) return cuda_fail(ctx, e2);
+  for (int r = 0; r < k; ++r)  // the status words of earlier launches are cleared by later ones:
+    if (std::isnan(host[(size_t)8 * r])) return HAWKES_E_DEVICE;  // a NaN ell is a device wait that ran out
   if (loglik_out)
     for (int r = 0; r < k; ++r) loglik_out[r] = host[(size_t)8 * r];
   return HAWKES_OK;

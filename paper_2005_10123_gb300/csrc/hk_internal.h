@@ -33,6 +33,8 @@ constexpr int kSumsLoglik = 2;                       // S_b, S_s
 constexpr int kSumsGrad = 6;                         // S_b, S_s, R_b, T_b, R_s, U_s
 constexpr int kFlagExcludeSelf = 1;                  // HAWKES_FLAG_EXCLUDE_SELF
 constexpr int kFlagDense = 2;                        // HAWKES_FLAG_DENSE
+constexpr int kFlagTestWithholdReady = 1 << 30;      // HAWKES_FLAG_TEST_WITHHOLD_READY (tests only)
+constexpr unsigned kStatusMergeTimeout = 1u;         // Request::status: a merge-tree wait ran out
 // widest pair-kernel CTA: the grouped kernel's, two rows per thread
 constexpr int kMaxCtaWarps = (kRowTile / 2 > kThreads ? kRowTile / 2 : kThreads) / 32;
 static_assert(kThreads <= 32 * kMaxCtaWarps && kRowTile / 4 <= 32 * kMaxCtaWarps, "CTA too wide");
@@ -96,11 +98,18 @@ struct Request {
   // Column window: column n' can only contribute to row n if
   //   t_n - cut_early <= t_n' <= t_n + cut_late   (days; +inf keeps every column)
   double cut_early, cut_late;
-  // float32 pair constants (mixed mode)
-  float a2;    // log2(e) / (2 tau_x^2)                  multiplies r^2
-  float beta;  // sqrt(log2(e) / (2 tau_t^2))            scales (t - t0)
-  float wn;    // -omega log2(e) / beta                  multiplies scaled dt
-  float cn;    // -log2(e) / (2 h^2)                     multiplies r^2
+  // float32 pair constants (mixed mode). The two scales applied to stored values (s to the
+  // coordinates of background-only tiles, beta to times) are each held as a float32 head and
+  // tail, v = hi + lo to about 2^-48 relative, so that a scaled value is the correctly rounded
+  // product with the float64 scale (scale_split): a float32-rounded bandwidth would shift every
+  // pair term the same way, and where a gradient component nearly cancels (d ell / d tau_t on the
+  // N = 85,000 workload cancels to about 2e-3 per row) that shift dominates its error.
+  float a2;              // log2(e) / (2 tau_x^2), rounded       multiplies r^2 (tiles with trigger terms)
+  float s_hi, s_lo;      // s = sqrt(a2)                         scales x, y (background-only tiles)
+  float beta, beta_lo;   // beta = sqrt(log2(e) / (2 tau_t^2))   scales (t - t0)
+  float b2, b2_lo;       // beta^2 = b2 + b2_lo                  multiplies dt^2 (grouped kernel)
+  float wn;              // -omega log2(e) / beta                multiplies scaled dt
+  float cn;              // -log2(e) / (2 h^2)                   multiplies r^2
   // float64 pair constants (fp64 mode)
   double da;   // 1 / (2 tau_x^2)
   double db;   // 1 / (2 tau_t^2)
@@ -109,6 +118,7 @@ struct Request {
   double mu0, tau_x, tau_t, theta, omega, h;
   double t_last;
   double tscale;  // scaled-to-raw time factor of the moments: 1/beta (mixed) or 1 (fp64)
+  double inv_a2;  // 1 / a2 in float64: R_b = (Q - T_b) / a2 from the background moment Q (mixed)
   // per-request float64 constants of the epilogue and compensator (no divisions per row)
   double k_ab;    // A / mu0 = 1 / ((2 pi)^{3/2} tau_x^2 tau_t)
   double k_cw;    // C / theta = omega / (2 pi h^2)
@@ -122,6 +132,8 @@ struct Request {
                        // the finished row-tile epilogues and compensator items
   double *rt_sum;      // nrt * 8: per row tile, sum of log lambda_n and of the gradient terms
   double *out;         // 7 doubles: ell, d ell / d Theta
+  unsigned *status;    // device word, zero at launch: kStatusMergeTimeout if a device wait of
+                       // this request ran out (its results are then NaN), or nullptr
   double *mu_out;      // optional per-event mu_n (n doubles) or nullptr
   double *xi_out;      // optional per-event xi_n (n doubles) or nullptr
   double *pi_out;      // optional per-event pi_n = xi_n / lambda_n (n doubles) or nullptr
@@ -136,6 +148,25 @@ struct Batch {
   int comp_total;   // grouped kernel: compensator items, first in the launch
   Request req[kMaxBatch];
 };
+
+// The mixed-precision constants of a request from Theta (Section 2.1, d = 2; base-2 exponents):
+// e_b = 2^-(a2 r^2 + beta^2 dt^2), e_s = 2^(cn r^2 + wn beta dt). Host code.
+inline void set_mixed_constants(Request *R, double tau_x, double tau_t, double omega, double h) {
+  const double log2e = 1.4426950408889634074;
+  const double a2 = log2e / (2.0 * tau_x * tau_x), s = std::sqrt(a2);
+  const double beta = std::sqrt(log2e / (2.0 * tau_t * tau_t));
+  R->a2 = (float)a2;
+  R->s_hi = (float)s;
+  R->s_lo = (float)(s - (double)R->s_hi);
+  R->beta = (float)beta;
+  R->beta_lo = (float)(beta - (double)R->beta);
+  R->b2 = (float)(beta * beta);
+  R->b2_lo = (float)(beta * beta - (double)R->b2);
+  R->wn = (float)(-omega * log2e / beta);
+  R->cn = (float)(-log2e / (2.0 * h * h));
+  R->inv_a2 = 1.0 / a2;
+  R->tscale = 1.0 / beta;
+}
 
 // Items of one request (see Request): compensator items first, then pair items.
 __host__ __device__ inline int comp_items(const Request &R) { return R.comp ? R.set.nrt : 0; }
@@ -239,7 +270,7 @@ __device__ inline int2 column_window(const Request &R, const TT *t, int rt) {
   const int r0 = rt * kRowTile, r1 = min(r0 + kRowTile, S.n) - 1;
   const int j0 = warp_search(t, S.n, (double)t[r0] - R.cut_early, false);
   const int j1 = warp_search(t, S.n, (double)t[r1] + R.cut_late, true);
-  const int c0 = j0 / kColTile;
+  const int c0 = min(j0 / kColTile, S.nct - 1);  // in range even for times a caller left unsorted
   const int c1 = min((j1 + kColTile - 1) / kColTile, S.nct);
   return make_int2(c0, max(c1, c0 + 1));
 }
@@ -354,18 +385,24 @@ __device__ void finish_request(const Request &R) {
 // sums do not depend on the order in which items finish. Returns true in the one CTA that
 // completes the root: it then holds the tile's full row sums. store(slot) writes the CTA's
 // current sums to a slot, merge(slot) adds a slot's sums to them (reading through L2). Called
-// by every thread of the CTA. Two protocols, same sums:
+// by every thread of the CTA. Returns 1 in the CTA that completes the root, 0 in a CTA that
+// stopped at a node, -1 in a CTA that gave up waiting (the caller then calls mark_timeout for
+// every request whose sums it carried). Two protocols, same sums:
 //  - PUBLISH_FIRST: a CTA counts its arrival first; only the first stores (then adds a ready
 //    mark), and the second waits for the mark if it is not there yet. The climbing CTA never
 //    stores, which shortens the path of the last items (loglik + gradient: 24.6 KB slots).
 //  - otherwise every arriving CTA stores before counting, so the second never waits (faster
 //    for the 8 KB loglik slots, whose siblings tend to arrive close together).
 // The wait is for a CTA that has already arrived and has nothing left to wait for, so it ends;
-// it is still bounded (kMergeSpin polls), and a CTA that gives up writes NaN to the request's
-// results instead of hanging.
+// it is still bounded (kMergeSpin polls and kMergeWaitNs of the global timer, whichever comes
+// first), and a CTA that gives up sets kStatusMergeTimeout in the request's status word, which
+// the host turns into HAWKES_E_DEVICE, writes NaN to the request's results and returns.
+// With kFlagTestWithholdReady (tests only) the first CTA at each node of row tile 0 publishes its
+// sums without the ready mark, so that its sibling's wait runs out.
 // a node's counter: arrivals add 1 (at most 2, bits 0-1), the publisher's ready mark adds 4
 constexpr unsigned kMergeArrived = 1u, kMergeReady = 4u;
 constexpr int kMergeSpin = 1 << 22;
+constexpr unsigned long long kMergeWaitNs = 500000000ull;  // 0.5 s
 
 __device__ __forceinline__ unsigned load_acquire(const unsigned *p) {
   unsigned v;
@@ -373,8 +410,21 @@ __device__ __forceinline__ unsigned load_acquire(const unsigned *p) {
   return v;
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// A device wait of request R ran out: report it in R's status word and make its results NaN.
+// Called by every thread of the CTA.
+__device__ __forceinline__ void mark_timeout(const Request &R) {
+  if (threadIdx.x == 0 && R.status) atomicOr(R.status, kStatusMergeTimeout);
+  if (threadIdx.x < 7) R.out[threadIdx.x] = __longlong_as_double(0x7ff8000000000000ll);
+}
+
 template <bool PUBLISH_FIRST, class Store, class Merge>
-__device__ bool merge_tree(const Request &R, const PairItem &it, Store store, Merge merge) {
+__device__ int merge_tree(const Request &R, const PairItem &it, Store store, Merge merge) {
   __shared__ unsigned s_old, s_ok;
   const int K = R.slices;
   unsigned *cnt = R.rt_count + 2 * (size_t)it.rt * K;
@@ -390,7 +440,7 @@ __device__ bool merge_tree(const Request &R, const PairItem &it, Store store, Me
         __syncthreads();
         if (threadIdx.x == 0) s_old = atomicAdd(c, kMergeArrived);
         __syncthreads();
-        if (s_old == 0u) return false;
+        if (s_old == 0u) return 0;
         __threadfence();
         merge(it.base + sib * width / it.span);
         __syncthreads();
@@ -407,20 +457,26 @@ __device__ bool merge_tree(const Request &R, const PairItem &it, Store store, Me
         store(it.base + node * width / it.span);
         __threadfence();
         __syncthreads();
-        if (threadIdx.x == 0) atomicAdd(c, kMergeReady);
-        return false;
+        const bool withhold = (R.flags & kFlagTestWithholdReady) && it.rt == 0;
+        if (threadIdx.x == 0 && !withhold) atomicAdd(c, kMergeReady);
+        return 0;
       }
       if (threadIdx.x == 0) {  // second: wait for the sibling's sums if they are not out yet
-        int k = 0;
-        if (!(old & kMergeReady))
-          while (!(load_acquire(c) & kMergeReady) && ++k < kMergeSpin) __nanosleep(64);
-        s_ok = k < kMergeSpin;
+        bool ok = true;
+        if (!(old & kMergeReady)) {
+          const unsigned long long t0 = global_ns();
+          for (int k = 0; !(load_acquire(c) & kMergeReady); ++k) {
+            if (k >= kMergeSpin || global_ns() - t0 > kMergeWaitNs) {
+              ok = false;
+              break;
+            }
+            __nanosleep(64);
+          }
+        }
+        s_ok = ok;
       }
       __syncthreads();
-      if (!s_ok) {  // gave up waiting (never expected): mark the results invalid
-        if (threadIdx.x < 7) R.out[threadIdx.x] = __longlong_as_double(0x7ff8000000000000ll);
-        return false;
-      }
+      if (!s_ok) return -1;  // gave up waiting (never expected)
       __threadfence();
       merge(it.base + sib * width / it.span);
       __syncthreads();
@@ -429,7 +485,7 @@ __device__ bool merge_tree(const Request &R, const PairItem &it, Store store, Me
     node = parent;
     width <<= 1;
   }
-  return true;
+  return 1;
 }
 
 // Log-intensity and gradient moments of event i from its row sums (Section 2.1, Eq. 1):

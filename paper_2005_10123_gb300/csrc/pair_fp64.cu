@@ -164,7 +164,9 @@ __device__ void run_piece64(const Batch &B, const Request &R, const PairItem &it
 #pragma unroll
       for (int s = 0; s < NS; ++s) acc[s][k] += __ldcg(src + s * kRowTile + warp * kWarpRows64 + lane + 32 * k);
   };
-  if (!merge_tree<true>(R, it, store, merge)) return;
+  const int root = merge_tree<true>(R, it, store, merge);
+  if (root < 0) mark_timeout(R);
+  if (root <= 0) return;
   double v[GRAD ? 7 : 1] = {};
 #pragma unroll
   for (int k = 0; k < 4; ++k) {

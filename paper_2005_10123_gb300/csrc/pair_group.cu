@@ -10,7 +10,8 @@
 //   e_s = 2^(cn_k r^2 + wn_k dt),     cn = -log2(e)/(2 h^2),    wn = -omega log2(e)
 // with the same row sums as the single-request kernel (S_b, S_s, R_b, T_b, R_s, U_s), the
 // moments in raw units (r^2 in km^2, dt in days). Shared work per pair: 6 float32 operations;
-// per request and background term: 5 (exponent 2, sum, 2 moments); per trigger term: 5.
+// per request and background term: 5 (exponent 2, sum, 2 moments), 6 with the gradient, whose
+// b2 enters as a float32 head and tail; per trigger term: 5.
 //
 // Work items: one compensator item per (request, row tile), then one pair item per (group,
 // row tile, slice), the slice being an equal share of the union of the group's column
@@ -56,7 +57,7 @@ struct GAcc {
 
 template <int G>
 struct GConst {
-  float2 a2[G], b2[G], cn[G], wn[G];
+  float2 a2[G], b2[G], b2lo[G], cn[G], wn[G];
 };
 
 // One column tile against this thread's two rows for every request of the group. KIND as in
@@ -85,7 +86,11 @@ __device__ __forceinline__ void gtile_pass(const float4 *__restrict__ sxy, const
     for (int k = 0; k < G; ++k) {
       {
         if (kBg) {
-          const float2 q = __ffma2_rn(rho, K.a2[k], __fmul2_rn(u, K.b2[k]));
+          // with the gradient, b2 enters as head + tail, so that u b2 is the correctly rounded
+          // product with the float64 b2: a float32-rounded b2 would shift tau_t for every pair,
+          // and d ell / d tau_t, nearly stationary on the N = 85,000 workload, would show it
+          const float2 ub = GRAD ? __ffma2_rn(u, K.b2[k], __fmul2_rn(u, K.b2lo[k])) : __fmul2_rn(u, K.b2[k]);
+          const float2 q = __ffma2_rn(rho, K.a2[k], ub);
           float2 eb = make_float2(gex2(-q.x), gex2(-q.y));
           if (KIND == 2 && excl) {
             if (col == row_a) eb.x = 0.f;
@@ -155,9 +160,10 @@ __device__ void group_item(const Batch &B, int leader, int gsize, const PairItem
 #pragma unroll
   for (int k = 0; k < G; ++k) {
     const Request &R = B.req[leader + (k < gsize ? k : 0)];
-    const float b2 = R.beta * R.beta;
+    const float b2 = R.b2;
     K.a2[k] = make_float2(R.a2, R.a2);
     K.b2[k] = make_float2(b2, b2);
+    K.b2lo[k] = make_float2(R.b2_lo, R.b2_lo);
     K.cn[k] = make_float2(R.cn, R.cn);
     const float wn = (float)(-R.omega * log2e);
     K.wn[k] = make_float2(wn, wn);
@@ -251,7 +257,10 @@ __device__ void group_item(const Batch &B, int leader, int gsize, const PairItem
       }
     }
   };
-  if (!merge_tree<GRAD>(R0, it, store, merge)) return;
+  const int root = merge_tree<GRAD>(R0, it, store, merge);
+  if (root < 0)
+    for (int k = 0; k < gsize; ++k) mark_timeout(B.req[leader + k]);
+  if (root <= 0) return;
   for (int k = 0; k < gsize; ++k) {
     const Request &R = B.req[leader + k];
     double v[GRAD ? 7 : 1] = {};

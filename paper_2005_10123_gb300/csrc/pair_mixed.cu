@@ -8,7 +8,9 @@
 //   R_b = sum r^2 e_b,  T_b = sum dt'^2 e_b,  R_s = sum r^2 e_s,  U_s = sum dt' e_s
 // with r^2 = |x_n - x_n'|^2 and dt' = beta (t_n - t_n'), beta^2 = log2(e)/(2 tau_t^2); times
 // enter relative to the first row of the tile before scaling, so nearby time differences
-// keep full relative precision. The CTA that completes a row tile's merge tree turns its row
+// keep full relative precision, and each scaled time (and scaled coordinate) is the correctly
+// rounded product with the float64 scale (scale_split), so no float32 rounding of a bandwidth
+// biases the sums. The CTA that completes a row tile's merge tree turns its row
 // sums into lambda_n, log lambda_n and the gradient in float64 (fused epilogue).
 //
 // Arithmetic per (row, column) pair, two rows per packed f32x2 value:
@@ -253,30 +255,38 @@ __device__ __forceinline__ RawCols load_cols(const SetView &S, int ct, int tid) 
   return r;
 }
 
-__device__ __forceinline__ void store_cols(const RawCols &r, int ct, int tid, int n, float t_origin, float beta,
-                                           float sc, float4 *sxs, float4 *stx) {
+// v * (hi + lo) rounded once (to about 2^-48 of the exact product with the float64 scale).
+__device__ __forceinline__ float scale_split(float v, float hi, float lo) { return __fmaf_rn(v, hi, __fmul_rn(v, lo)); }
+
+// Scales of one request: beta for times, s for the coordinates of background-only tiles.
+struct Scales {
+  float b_hi, b_lo, s_hi, s_lo;
+};
+
+__device__ __forceinline__ void store_cols(const RawCols &r, int ct, int tid, int n, float t_origin, const Scales &k,
+                                           float4 *sxs, float4 *stx) {
 #pragma unroll
   for (int h = 0; h < kStage; ++h) {
     const int jj = tid + h * kThreads, j = ct * kColTile + jj;
-    const float sj = j < n ? (r.t[h] - t_origin) * beta : kPadScaled;
-    const float xs = __fmul_rn(r.x[h], sc), ys = __fmul_rn(r.y[h], sc);
+    const float sj = j < n ? scale_split(r.t[h] - t_origin, k.b_hi, k.b_lo) : kPadScaled;
+    const float xs = scale_split(r.x[h], k.s_hi, k.s_lo), ys = scale_split(r.y[h], k.s_hi, k.s_lo);
     sxs[jj] = make_float4(-xs, -xs, -ys, -ys);
     stx[jj] = make_float4(-sj, -sj, -r.x[h], -r.y[h]);
   }
 }
 
 // This thread's row coordinates (rows ra = wa + lane + 32 k, packed in pairs k, k + 1),
-// stored values or scaled by sc with the columns' rounding, so that dx = 0 on the diagonal.
+// stored values or scaled by s with the columns' rounding, so that dx = 0 on the diagonal.
 template <bool SCALED>
-__device__ __forceinline__ void row_coords(const SetView &S, int ra0, float sc, float2 (&X)[kPairs],
+__device__ __forceinline__ void row_coords(const SetView &S, int ra0, const Scales &k, float2 (&X)[kPairs],
                                            float2 (&Y)[kPairs]) {
 #pragma unroll
   for (int p = 0; p < kPairs; ++p) {
     const int ra = ra0 + 64 * p, rb = ra + 32;
     float xa = __ldg(S.x32 + ra), xb = __ldg(S.x32 + rb), ya = __ldg(S.y32 + ra), yb = __ldg(S.y32 + rb);
     if (SCALED) {
-      xa = __fmul_rn(xa, sc); xb = __fmul_rn(xb, sc);
-      ya = __fmul_rn(ya, sc); yb = __fmul_rn(yb, sc);
+      xa = scale_split(xa, k.s_hi, k.s_lo); xb = scale_split(xb, k.s_hi, k.s_lo);
+      ya = scale_split(ya, k.s_hi, k.s_lo); yb = scale_split(yb, k.s_hi, k.s_lo);
     }
     X[p] = make_float2(xa, xb);
     Y[p] = make_float2(ya, yb);
@@ -300,8 +310,8 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int row0 = it.rt * kRowTile;
   const float t_origin = S.t32[row0];
-  const float beta = R.beta, wn = R.wn;
-  const float sc = sqrtf(R.a2);  // spatial scale s of background-only tiles, s^2 ~ a2
+  const float wn = R.wn;
+  const Scales sk{R.beta, R.beta_lo, R.s_hi, R.s_lo};
   const int n = S.n;
   const int wa = row0 + warp * kWarpRows, wb = wa + kWarpRows - 1;
   const int lo_wa = S.lo32[wa], lo_wb = S.lo32[wb];
@@ -313,17 +323,16 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
 #pragma unroll
   for (int p = 0; p < kPairs; ++p) {
     const int ra = row_a0 + 64 * p, rb = ra + 32;
-    T[p] = make_float2(ra < n ? (S.t32[ra] - t_origin) * beta : kPadScaled,
-                       rb < n ? (S.t32[rb] - t_origin) * beta : kPadScaled);
+    T[p] = make_float2(ra < n ? scale_split(S.t32[ra] - t_origin, sk.b_hi, sk.b_lo) : kPadScaled,
+                       rb < n ? scale_split(S.t32[rb] - t_origin, sk.b_hi, sk.b_lo) : kPadScaled);
     LO[2 * p] = S.lo32[ra];
     LO[2 * p + 1] = S.lo32[rb];
   }
   // scaled row coordinates stay in registers; the stored ones are reloaded (L1) for the
   // few tiles with trigger terms
   float2 XS[kPairs], YS[kPairs];
-  row_coords<true>(S, row_a0, sc, XS, YS);
-  const float a2 = sc * sc;
-  const float2 A2 = make_float2(a2, a2), CN = make_float2(R.cn, R.cn), WN = make_float2(wn, wn);
+  row_coords<true>(S, row_a0, sk, XS, YS);
+  const float2 A2 = make_float2(R.a2, R.a2), CN = make_float2(R.cn, R.cn), WN = make_float2(wn, wn);
   const float s_first = __shfl_sync(0xffffffffu, T[0].x, 0);            // scaled time of the warp's
   const float s_last = __shfl_sync(0xffffffffu, T[kPairs - 1].y, 31);  // first and last rows
 
@@ -335,7 +344,7 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
 
   int ct = c_begin;
   if (ct < c_end) {  // an empty slice of the window writes zero partial sums
-    store_cols(load_cols(S, ct, tid), ct, tid, n, t_origin, beta, sc, sxs[0], stx[0]);
+    store_cols(load_cols(S, ct, tid), ct, tid, n, t_origin, sk, sxs[0], stx[0]);
     cta_sync();
   }
   for (int k = 0; ct < c_end; ++ct, ++k) {
@@ -365,7 +374,7 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
     if (kind == 0) {
       tile_pass<0, GRAD>(sxs[buf], stx[buf], XS, YS, T, LO, row_a0, c0, excl, A2, CN, WN, WN, acc);
     } else if (kind == 1 || kind == 3) {
-      row_coords<false>(S, row_a0, sc, X, Y);
+      row_coords<false>(S, row_a0, sk, X, Y);
       const float sref = -stx[buf][kColTile - 1].x;  // t'_ref: the tile's latest column
       const float2 SREF = make_float2(sref, sref);
       if (kind == 1) tile_pass<1, GRAD>(sxs[buf], stx[buf], X, Y, T, LO, row_a0, c0, excl, A2, CN, WN, SREF, acc);
@@ -383,7 +392,7 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
         }
       }
     } else if (kind == 2) {
-      row_coords<false>(S, row_a0, sc, X, Y);
+      row_coords<false>(S, row_a0, sk, X, Y);
       tile_pass<2, GRAD>(sxs[buf], stx[buf], X, Y, T, LO, row_a0, c0, excl, A2, CN, WN, WN, acc);
     }  // kind -1: every term of the tile is exactly zero for this warp
     // fold the tile's sums into float64; a tile without trigger (background) terms leaves
@@ -399,7 +408,7 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
         sacc[(s * kRowsPerThread + 2 * p + 1) * kThreads + tid] += (double)acc.v[s][p].y;
       }
     }
-    if (has_next) store_cols(nxt, ct + 1, tid, n, t_origin, beta, sc, sxs[buf ^ 1], stx[buf ^ 1]);
+    if (has_next) store_cols(nxt, ct + 1, tid, n, t_origin, sk, sxs[buf ^ 1], stx[buf ^ 1]);
     cta_sync();
   }
   // this thread's rows: la = warp * kWarpRows + lane + 32 k, sums at sacc[(s R + k) T + tid]
@@ -423,9 +432,10 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
       for (int s = 0; s < NS; ++s)
         sacc[(s * kRowsPerThread + k) * kThreads + tid] += __ldcg(src + s * kRowTile + warp * kWarpRows + lane + 32 * k);
   };
-  if (!merge_tree<GRAD>(R, it, store, merge)) return;
+  const int root = merge_tree<GRAD>(R, it, store, merge);
+  if (root < 0) mark_timeout(R);
+  if (root <= 0) return;
   double v[GRAD ? 7 : 1] = {};
-  const double inv_s2 = 1.0 / ((double)sc * (double)sc);
 #pragma unroll
   for (int k = 0; k < kRowsPerThread; ++k) {
     const int i = row0 + warp * kWarpRows + lane + 32 * k;
@@ -433,7 +443,7 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
       double sums[NS];
 #pragma unroll
       for (int s = 0; s < NS; ++s) sums[s] = sacc[(s * kRowsPerThread + k) * kThreads + tid];
-      if (GRAD) sums[2] = (sums[2] - sums[3]) * inv_s2;  // R_b from Q and T_b
+      if (GRAD) sums[2] = (sums[2] - sums[3]) * R.inv_a2;  // R_b from Q and T_b
       row_terms<GRAD>(R, i, sums, v);
     }
   }

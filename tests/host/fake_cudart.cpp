@@ -151,7 +151,7 @@ static void check_schedule(const Request &R, int mode) {
     if (seen[i] != 1) ok = false;
   if (S.npad != S.nrt * kRowTile || S.nct * kColTile != S.npad || S.n > S.npad || S.n < 1) ok = false;
   if (!(R.cut_early > 0.0) || !(R.cut_late > 0.0)) ok = false;
-  if (!R.partials || !R.comp || !R.rt_sum || !R.rt_count || !R.out) ok = false;
+  if (!R.partials || !R.comp || !R.rt_sum || !R.rt_count || !R.out || !R.status) ok = false;
   for (int i = 0; ok && i < request_counters(R); ++i)
     if (R.rt_count[i] != 0u) ok = false;  // merge-tree and completion counters zeroed before the launch
   if (!ok) g_schedule_errors++;
@@ -161,6 +161,11 @@ static void check_schedule(const Request &R, int mode) {
 static void fake_outputs(const Batch &b, bool grad) {
   for (int r = 0; r < b.nreq; ++r) {
     const Request &R = b.req[r];
+    if (grad && (R.flags & kFlagTestWithholdReady)) {  // the kernels' merge wait ran out
+      if (R.status) *R.status |= kStatusMergeTimeout;
+      for (int q = 0; q < 7; ++q) R.out[q] = std::nan("");
+      continue;
+    }
     R.out[0] = R.mu0 * 1000.0 + R.set.n + (b.mode ? 0.5 : 0.0);
     if (grad) {
       const double th[6] = {R.mu0, R.tau_x, R.tau_t, R.theta, R.omega, R.h};

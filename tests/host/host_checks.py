@@ -149,6 +149,20 @@ def main():
     for (w, i), (ll, gr) in out.items():
         assert ll == fake_value(ths[(w * 50 + i) % 64], 513, 1)
 
+    # a bounded device wait that ran out (the fake models it for the test flag): HAWKES_E_DEVICE on
+    # the blocking, batched and serving paths; the context stays usable
+    ctx.hawkes_set_flags(binding.HAWKES_FLAG_TEST_WITHHOLD_READY)
+    expect_status(lambda: ctx.hawkes_loglik_grad(sids[1000], TH, 1), -11)
+    expect_status(lambda: ctx.hawkes_loglik_grad(sids[1000], TH, 0), -11)
+    expect_status(lambda: ctx.hawkes_loglik_batch(sids[1000], ths[:5], 1, want_grad=True), -11)
+    assert ctx.hawkes_loglik(sids[1000], TH, 1) == fake_value(TH, 1000, 1)  # loglik never waits
+    t = ctx.hawkes_submit(sids[1000], TH, True, 1)
+    expect_status(lambda: ctx.hawkes_wait(t, 5000), -11)
+    ctx.hawkes_set_flags(0)
+    assert ctx.hawkes_loglik_grad(sids[1000], TH, 1)[0] == fake_value(TH, 1000, 1)
+    t = ctx.hawkes_submit(sids[1000], TH, True, 1)
+    assert ctx.hawkes_wait(t, 5000)[0] == fake_value(TH, 1000, 1)
+
     # timeouts: an event that stays "not ready"
     fake.fake_event_delay(10 ** 9)
     t = ctx.hawkes_submit(sids[1000], TH, False, 1)

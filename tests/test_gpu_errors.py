@@ -114,3 +114,40 @@ def test_release_while_queued_then_destroy(binding):
     for _ in range(8):
         ctx.hawkes_submit(sid2, synth.THETA0, True, 0)
     ctx.close()
+
+
+def test_device_wait_runs_out_and_is_reported(binding):
+    """The one wait on the GPU (the gradient merge tree's climbing item waits for its sibling's
+    ready mark) is bounded. With HAWKES_FLAG_TEST_WITHHOLD_READY the first item at each merge
+    node of row tile 0 publishes its sums without the mark, so the wait runs out (after at most
+    0.5 s): the blocking, batched and serving calls return HAWKES_E_DEVICE, nothing hangs, and
+    calls without the flag on the same context still give the right results."""
+    ev = synth.simulate(4000, 1500.0, seed=17)
+    with binding.Context(device=0) as ctx:
+        sid = ctx.hawkes_upload_events(ev.x, ev.y, ev.t)
+        want = {m: ctx.hawkes_loglik_grad(sid, synth.THETA0, m) for m in (0, 1)}
+        ths = synth.theta_batch(5, seed=18)
+        want_batch = ctx.hawkes_loglik_batch(sid, ths, 1, want_grad=True)
+        want_ll = ctx.hawkes_loglik(sid, synth.THETA0, 1)
+        ctx.hawkes_set_flags(binding.HAWKES_FLAG_TEST_WITHHOLD_READY)
+        for mode in (0, 1):
+            with pytest.raises(binding.HawkesError) as e:
+                ctx.hawkes_loglik_grad(sid, synth.THETA0, mode)
+            assert e.value.status == -11
+        with pytest.raises(binding.HawkesError) as e:
+            ctx.hawkes_loglik_batch(sid, ths, 1, want_grad=True)
+        assert e.value.status == -11
+        t = ctx.hawkes_submit(sid, synth.THETA0, True, 1)
+        with pytest.raises(binding.HawkesError) as e:
+            ctx.hawkes_wait(t, 20000)
+        assert e.value.status == -11
+        assert ctx.hawkes_loglik(sid, synth.THETA0, 1) == want_ll  # loglik alone never waits
+        ctx.hawkes_set_flags(0)
+        for m in (0, 1):
+            ll, g = ctx.hawkes_loglik_grad(sid, synth.THETA0, m)
+            assert ll == want[m][0] and np.array_equal(g, want[m][1])
+        ll, g = ctx.hawkes_loglik_batch(sid, ths, 1, want_grad=True)
+        assert np.array_equal(ll, want_batch[0]) and np.array_equal(g, want_batch[1])
+        t = ctx.hawkes_submit(sid, synth.THETA0, True, 1)
+        ll, g = ctx.hawkes_wait(t, 20000)
+        assert ll == want[1][0] and np.array_equal(g, want[1][1])

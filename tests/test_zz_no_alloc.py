@@ -64,3 +64,65 @@ def test_noalloc_rejects_sizes_beyond_the_maximum():
         binding.hawkes_loglik_noalloc(buf.data_ptr(), buf.data_ptr(), buf.data_ptr(), n, synth.THETA0, 0,
                                       out.data_ptr(), 0)
     assert e.value.status == -1
+
+
+def test_noalloc_flags_match_context_path():
+    """HAWKES_FLAG_EXCLUDE_SELF on a set with float32 ties (the tie indices are formed on the
+    device by the entry point itself), and HAWKES_FLAG_DENSE, against the context path with the
+    same flags."""
+    torch = pytest.importorskip("torch")
+    from paper_2005_10123_gb300 import binding
+    ev = synth.simulate(3000, 300.0, seed=64)
+    ev.t = 4000.0 + np.cumsum(np.where(np.arange(ev.n) % 3 == 0, 0.05, 3e-5))  # ties after rounding
+    ev = ev.rounded32()
+    assert len(np.unique(ev.t)) < 0.5 * ev.n
+    th = (0.05, 0.7, 5.0, 0.5, 2.0, 0.2)
+    flags_list = [binding.HAWKES_FLAG_EXCLUDE_SELF, binding.HAWKES_FLAG_DENSE,
+                  binding.HAWKES_FLAG_EXCLUDE_SELF | binding.HAWKES_FLAG_DENSE]
+    refs = []
+    with binding.Context(device=0) as ctx:
+        sid = ctx.hawkes_upload_events(ev.x, ev.y, ev.t)
+        for f in flags_list:
+            ctx.hawkes_set_flags(f)
+            refs.append(ctx.hawkes_loglik(sid, th, binding.HAWKES_MIXED))
+        ctx.hawkes_set_flags(0)
+    x, y, t = _device_events(torch, ev)
+    out = torch.full((len(flags_list),), float("nan"), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    torch.cuda.synchronize()
+    for k, f in enumerate(flags_list):
+        binding.hawkes_loglik_noalloc(x.data_ptr(), y.data_ptr(), t.data_ptr(), ev.n, th, f,
+                                      out[k:k + 1].data_ptr(), stream)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    for k in range(len(flags_list)):
+        assert rel(got[k], refs[k]) <= TOL_MIXED_LL, (flags_list[k], got[k], refs[k])
+
+
+def test_noalloc_bad_inputs_give_nan_then_recover():
+    """Inputs the context path rejects at upload (unsorted, negative or non-finite times,
+    non-finite coordinates) are checked on the device here and make the result NaN; the next
+    call with good inputs, reusing the same array, is right again."""
+    torch = pytest.importorskip("torch")
+    from paper_2005_10123_gb300 import binding
+    ev = synth.simulate(5000, 800.0, seed=65).rounded32()
+    with binding.Context(device=0) as ctx:
+        sid = ctx.hawkes_upload_events(ev.x, ev.y, ev.t)
+        ref = ctx.hawkes_loglik(sid, synth.THETA0, binding.HAWKES_MIXED)
+    bad = []
+    t1 = ev.t.copy(); t1[2500], t1[2501] = t1[2501] + 1.0, t1[2500]; bad.append((ev.x, ev.y, t1))  # unsorted
+    t2 = ev.t.copy(); t2[0] = -1.0; bad.append((ev.x, ev.y, t2))  # negative time
+    t3 = ev.t.copy(); t3[4999] = np.inf; bad.append((ev.x, ev.y, t3))  # non-finite time
+    x4 = ev.x.copy(); x4[1234] = np.nan; bad.append((x4, ev.y, ev.t))  # non-finite coordinate
+    out = torch.zeros(len(bad) + 1, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    f = lambda a: torch.tensor(np.asarray(a, dtype=np.float32), device="cuda")
+    dev = [(f(a), f(b), f(c)) for a, b, c in bad] + [_device_events(torch, ev)]
+    torch.cuda.synchronize()
+    for k, (x, y, t) in enumerate(dev):
+        binding.hawkes_loglik_noalloc(x.data_ptr(), y.data_ptr(), t.data_ptr(), ev.n, synth.THETA0, 0,
+                                      out[k:k + 1].data_ptr(), stream)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    assert np.all(np.isnan(got[:len(bad)])), got
+    assert rel(got[len(bad)], ref) <= TOL_MIXED_LL, (got[len(bad)], ref)
