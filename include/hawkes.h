@@ -77,6 +77,15 @@ extern "C" {
 /* ---- flags (hawkes_set_flags) ----------------------------------------------------- */
 #define HAWKES_FLAG_EXCLUDE_SELF 1 /* drop n' = n from the background sum of lambda_n    */
 #define HAWKES_FLAG_DENSE 2        /* visit all N^2 pairs (see below)                      */
+#define HAWKES_FLAG_NO_SYMMETRY 4  /* HAWKES_MIXED: evaluate every ordered pair on its own     */
+/* By default a mixed-precision evaluation without HAWKES_FLAG_EXCLUDE_SELF or HAWKES_FLAG_DENSE
+ * shares background terms: e_b(n, n') = e_b(n', n), so for column tiles far enough before a row
+ * tile that no trigger term can be nonzero (beyond the trigger's exact-zero reach) each pair term
+ * is formed once and added to both events' rows. The column sums are added as exact fixed-point
+ * integers (2^-F resolution, F = 62 - ceil(log2 N_padded), about 3e-14 at N = 85,000), so results
+ * stay bit-identical from run to run and alone or batched; they differ from the row-by-row
+ * evaluation (HAWKES_FLAG_NO_SYMMETRY) by float32 rounding only. The paper's evaluation visits
+ * every ordered pair (Section 2.3); this is a reorganisation of the same sum. */
 /* For testing the failure path only: in loglik + gradient evaluations the first work item to
  * reach each merge node of row tile 0 publishes its partial sums without marking them ready,
  * so the bounded device wait of its sibling runs out (after at most 0.5 s) and the call
@@ -171,15 +180,17 @@ int hawkes_loglik_batch(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_par
 
 /* Work accounting for an evaluation at Theta (host computation on the set's stored times, read
  * back from the device; no kernel launch):
- *   out[0] (row, column) pairs inside the exact-zero windows the kernels visit (see
+ *   out[0] ordered (row, column) pairs inside the exact-zero windows the kernels cover (see
  *          HAWKES_FLAG_DENSE), counted over real events;
  *   out[1] N^2, the pairs of Eq. 1's double sum;
  *   out[2] ordered pairs whose background term can be nonzero at the mode's precision
  *          (|t_n - t_n'| below the background's exact-zero reach, n' = n included);
  *   out[3] ordered pairs whose trigger term can be nonzero (0 <= t_n - t_n' below the trigger's
- *          exact-zero reach; pairs with equal times counted although their term is zero). */
+ *          exact-zero reach; pairs with equal times counted although their term is zero);
+ *   out[4] pair terms the kernels evaluate: out[0] less the far pairs whose background term
+ *          serves both events (see HAWKES_FLAG_NO_SYMMETRY), which are evaluated once. */
 int hawkes_pair_work(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *params, hawkes_mode mode,
-                     int64_t out[4]);
+                     int64_t out[5]);
 
 /* Per-event terms of Eq. 2: mu_out[n] = mu(x_n, t_n) (background rate at event n)
  * and xi_out[n] = lambda_n - mu_n (the self-excitation part), so lambda_n =
@@ -248,7 +259,8 @@ int hawkes_stats(hawkes_ctx *ctx, int64_t out[7]);
  * HAWKES_E_INVAL. The event values are never read on the host: they are checked on the
  * device, and inputs that hawkes_upload_events would reject (unsorted, negative or
  * non-finite times, non-finite coordinates), or a time span too long for the float32 path at
- * this tau_t, make device_out NaN. flags: HAWKES_FLAG_EXCLUDE_SELF and HAWKES_FLAG_DENSE.
+ * this tau_t, make device_out NaN. flags: HAWKES_FLAG_EXCLUDE_SELF, HAWKES_FLAG_DENSE and
+ * HAWKES_FLAG_NO_SYMMETRY (this entry point always evaluates every ordered pair on its own).
  * device_out: device pointer to one double that receives ell. cuda_stream: the stream to
  * enqueue on (NULL = the legacy default stream). The call is asynchronous: the caller
  * synchronises the stream before reading device_out.

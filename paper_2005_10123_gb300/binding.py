@@ -18,6 +18,7 @@ HAWKES_FP64 = 0
 HAWKES_MIXED = 1
 HAWKES_FLAG_EXCLUDE_SELF = 1
 HAWKES_FLAG_DENSE = 2
+HAWKES_FLAG_NO_SYMMETRY = 4
 HAWKES_FLAG_TEST_WITHHOLD_READY = 1 << 30  # tests of the device-wait failure path only
 
 STATUS = {
@@ -238,13 +239,14 @@ class Context:
         return pi, ll
 
     def hawkes_pair_work(self, set_id: int, theta, mode: int = HAWKES_MIXED) -> dict:
-        """Pair counts of an evaluation at theta: visited (inside the windows), all (N^2),
-        bg (background term possibly nonzero), trig (trigger term possibly nonzero)."""
-        out = (ctypes.c_int64 * 4)()
+        """Pair counts of an evaluation at theta: visited (ordered pairs inside the windows), all
+        (N^2), bg (background term possibly nonzero), trig (trigger term possibly nonzero),
+        evaluated (pair terms formed; a far pair's background term serves both events)."""
+        out = (ctypes.c_int64 * 5)()
         p = _params(theta)
         self._check(self.lib.hawkes_pair_work(self.h, int(set_id), ctypes.byref(p), int(mode), out),
                     "hawkes_pair_work")
-        return {"visited": out[0], "all": out[1], "bg": out[2], "trig": out[3]}
+        return {"visited": out[0], "all": out[1], "bg": out[2], "trig": out[3], "evaluated": out[4]}
 
     def hawkes_submit(self, set_id: int, theta, want_grad: bool = False, mode: int = HAWKES_MIXED) -> int:
         p = _params(theta)

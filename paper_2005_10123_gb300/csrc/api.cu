@@ -194,7 +194,8 @@ void launch_tiers(int nrt, int mode, bool grouped, int *wide, int *coarse) {
 // dt^2 / (2 tau_t^2) reaches 805 (float64); a trigger term once omega dt log2(e) reaches 131
 // (float32) or omega dt reaches 805 (float64). One percent of margin covers the rounding
 // of the time differences. Columns later than a row only carry background terms.
-void exact_zero_cutoffs(const hawkes_params *p, int mode, float beta32, double *early, double *late) {
+void exact_zero_cutoffs(const hawkes_params *p, int mode, float beta32, double *early, double *late,
+                        double *trig_out = nullptr) {
   double bg, trig;
   if (mode == HAWKES_MIXED) {
     bg = 1.01 * std::sqrt(130.0) / (double)beta32;
@@ -205,6 +206,16 @@ void exact_zero_cutoffs(const hawkes_params *p, int mode, float beta32, double *
   }
   *early = std::max(bg, trig);
   *late = bg;
+  if (trig_out) *trig_out = trig;
+}
+
+// Whether a request on S shares the background terms of far column tiles (see SymPlan in
+// hk_internal.h): mixed precision, a time table, and none of the flags that ask for row-by-row
+// evaluation (exclude-self makes lambda_n's background sum unbounded below, which the fixed-point
+// column sums would not resolve; dense and no-symmetry ask for every ordered pair).
+bool use_symmetry(const EventSetRec *S, int mode, int flags) {
+  return mode == HAWKES_MIXED && S->win32.nb > 0 &&
+         !(flags & (HAWKES_FLAG_EXCLUDE_SELF | HAWKES_FLAG_DENSE | HAWKES_FLAG_NO_SYMMETRY));
 }
 
 // Float64 constants of the epilogue and compensator, from Theta (Section 2.1, d = 2).
@@ -249,7 +260,14 @@ int make_request(hawkes_ctx *ctx, const EventSetRec *S, const hawkes_params *p, 
     R->t_last = S->t_last64;
     R->tscale = 1.0;
   }
-  exact_zero_cutoffs(p, mode, R->beta, &R->cut_early, &R->cut_late);
+  exact_zero_cutoffs(p, mode, R->beta, &R->cut_early, &R->cut_late, &R->trig_cut);
+  R->sym = use_symmetry(S, mode, flags) ? 1 : 0;
+  // fixed-point scale of the column sums: every event's total is at most npad (terms <= 1, and
+  // q 2^-q <= 1), so round(total 2^F) stays below 2^62
+  int bits = 0;
+  while (((int64_t)1 << bits) < S->npad) ++bits;
+  R->fix_scale = std::ldexp(1.0f, 62 - bits);
+  R->fix_inv = std::ldexp(1.0, bits - 62);
   (void)ctx;
   return HAWKES_OK;
 }
@@ -274,10 +292,16 @@ size_t request_footprint(const EventSetRec *S, int mode, int grad) {
   return b;
 }
 
-// Bytes of a request's completion counters (the merge-tree nodes of its row tiles and one
-// final counter, see Request::rt_count), kept in one zeroed region per batch.
-size_t counter_bytes(const EventSetRec *S, int mode, int grad) {
-  return align_up((2 * (size_t)S->nrt * S->slices[kind_of(mode, grad)] + 1) * sizeof(unsigned), 64);
+// Bytes of a request's counters, kept in one zeroed region per batch: the merge-tree nodes of
+// its row tiles and one final counter (Request::rt_count); with sym, the row tiles' completion
+// counters (Request::rt_done) and the fixed-point column sums (Request::colfix).
+size_t merge_counter_bytes(const EventSetRec *S, int mode, int grad) {
+  return (2 * (size_t)S->nrt * S->slices[kind_of(mode, grad)] + 1) * sizeof(unsigned);
+}
+size_t counter_bytes(const EventSetRec *S, int mode, int grad, int sym) {
+  size_t b = merge_counter_bytes(S, mode, grad);
+  if (sym) b = align_up(b + (size_t)S->nrt * sizeof(unsigned), 256) + colfix_sums(grad != 0) * S->npad * 8;
+  return align_up(b, 256);
 }
 
 // Batch workspace: a 256-byte header holding one device status word per request (see
@@ -296,9 +320,15 @@ int device_status(const void *header, int r) {
   return ((const unsigned *)header)[r] ? HAWKES_E_DEVICE : HAWKES_OK;
 }
 
-// Carve one request's workspace out of `base` (as sized by request_footprint).
+// Carve one request's workspace out of `base` (as sized by request_footprint) and its counters
+// out of `counters` (as sized by counter_bytes).
 void bind_workspace(Request *R, const EventSetRec *S, int mode, int grad, char *base, double *out,
                     unsigned *counters) {
+  if (R->sym) {
+    const size_t m = merge_counter_bytes(S, mode, grad);
+    R->rt_done = (unsigned *)((char *)counters + m);
+    R->colfix = (long long *)((char *)counters + align_up(m + (size_t)S->nrt * sizeof(unsigned), 256));
+  }
   const size_t items = set_slots(S, mode, grad);
   size_t off = 0;
   R->partials = (double *)(base + off);
@@ -453,7 +483,15 @@ int eval_locked(hawkes_ctx *ctx, EventSetRec *S, int k, const hawkes_params *par
   const size_t row_bytes = align_up((size_t)S->n * sizeof(double), 256);
   const size_t rows_bytes =
       ((mu_out || xi_out) && !direct_rows ? 2 * row_bytes : 0) + (pi_out && !pi_dev ? (size_t)k * row_bytes : 0);
-  const size_t cnt = align_up(counter_bytes(S, mode, grad) * k, 256);
+  // Two or more mixed-precision requests on this set share each pair's geometry (grouped
+  // kernel, moments in raw units). Groups are consecutive requests in order of tau_t, so a
+  // group's members have similar column windows; request r of the launch is params[order[r]]
+  // and writes its results to that parameter vector's place. The other launches share the
+  // background terms of far column tiles where use_symmetry allows it.
+  const bool grouped = k >= 2 && mode == HAWKES_MIXED && group_size(grad != 0) > 1;
+  const int sym = !grouped && use_symmetry(S, mode, ctx->flags) ? 1 : 0;
+  const size_t cnt_one = counter_bytes(S, mode, grad, sym);
+  const size_t cnt = align_up(cnt_one * k, 256);
   const size_t need = kFixedBytes + cnt + rows_bytes + per * k;
   if (int rc = ensure_sync_ws(ctx, need)) return rc;
   char *base = (char *)ctx->sync_ws.dev;
@@ -464,11 +502,6 @@ int eval_locked(hawkes_ctx *ctx, EventSetRec *S, int k, const hawkes_params *par
   char *cnt_base = base + kFixedBytes;
   char *rows_base = cnt_base + cnt;
   char *req_base = rows_base + rows_bytes;
-  // Two or more mixed-precision requests on this set share each pair's geometry (grouped
-  // kernel, moments in raw units). Groups are consecutive requests in order of tau_t, so a
-  // group's members have similar column windows; request r of the launch is params[order[r]]
-  // and writes its results to that parameter vector's place.
-  const bool grouped = k >= 2 && mode == HAWKES_MIXED && group_size(grad != 0) > 1;
   int order[kMaxBatch];
   for (int r = 0; r < k; ++r) order[r] = r;
   if (grouped)
@@ -476,9 +509,9 @@ int eval_locked(hawkes_ctx *ctx, EventSetRec *S, int k, const hawkes_params *par
   for (int r = 0; r < k; ++r) {
     const int q = order[r];
     if (int rc = make_request(ctx, S, &params[q], mode, grad, ctx->flags, &b->req[r])) return rc;
+    b->req[r].sym = sym;
     bind_workspace(&b->req[r], S, mode, grad, req_base + (size_t)r * per,
-                   device_out ? device_out + 8 * q : outs + 8 * q,
-                   (unsigned *)(cnt_base + (size_t)r * counter_bytes(S, mode, grad)));
+                   device_out ? device_out + 8 * q : outs + 8 * q, (unsigned *)(cnt_base + (size_t)r * cnt_one));
     b->req[r].status = (unsigned *)base + q;
     if (grouped) {
       b->req[r].tscale = 1.0;
@@ -601,8 +634,8 @@ bool launch_pending(hawkes_ctx *ctx, Flight &F) {
         ctx->done_cv.notify_all();
         continue;
       }
-      if (bytes + T.footprint + counter_bytes(sit->second, mode, grad) > room) {
-        const bool never_fits = kFixedBytes + 512 + T.footprint + counter_bytes(sit->second, mode, grad) + fixed_used >
+      if (bytes + T.footprint + counter_bytes(sit->second, mode, grad, use_symmetry(sit->second, mode, T.flags)) > room) {
+        const bool never_fits = kFixedBytes + 512 + T.footprint + counter_bytes(sit->second, mode, grad, use_symmetry(sit->second, mode, T.flags)) + fixed_used >
                                 ctx->budget;
         if (take.empty() && !any_flight && never_fits) {
           complete_ticket(ctx, *it, HAWKES_E_ADMISSION, nullptr);
@@ -613,8 +646,8 @@ bool launch_pending(hawkes_ctx *ctx, Flight &F) {
         }
         break;  // first-come first-served within a kind: wait for memory to free up
       }
-      bytes += T.footprint + counter_bytes(sit->second, mode, grad);
-      cnt += counter_bytes(sit->second, mode, grad);
+      bytes += T.footprint + counter_bytes(sit->second, mode, grad, use_symmetry(sit->second, mode, T.flags));
+      cnt += counter_bytes(sit->second, mode, grad, use_symmetry(sit->second, mode, T.flags));
       take.push_back(*it);
       sets.push_back(sit->second);
       it = ctx->pending.erase(it);
@@ -643,7 +676,7 @@ bool launch_pending(hawkes_ctx *ctx, Flight &F) {
       rc = make_request(ctx, sets[r], &T.p, mode, grad, T.flags, &b->req[r]);
       bind_workspace(&b->req[r], sets[r], mode, grad, cur, outs + 8 * r, (unsigned *)cnt_cur);
       b->req[r].status = (unsigned *)base + r;
-      cnt_cur += counter_bytes(sets[r], mode, grad);
+      cnt_cur += counter_bytes(sets[r], mode, grad, b->req[r].sym);
       cur += T.footprint;
     }
     if (rc == HAWKES_OK) rc = launch_batch(ctx, *b, mode, grad, F.stream);
@@ -834,7 +867,8 @@ int hawkes_destroy(hawkes_ctx *ctx) {
 }
 
 int hawkes_set_flags(hawkes_ctx *ctx, int flags) {
-  if (!ctx || (flags & ~(HAWKES_FLAG_EXCLUDE_SELF | HAWKES_FLAG_DENSE | HAWKES_FLAG_TEST_WITHHOLD_READY)))
+  if (!ctx || (flags & ~(HAWKES_FLAG_EXCLUDE_SELF | HAWKES_FLAG_DENSE | HAWKES_FLAG_NO_SYMMETRY |
+                         HAWKES_FLAG_TEST_WITHHOLD_READY)))
     return HAWKES_E_INVAL;
   std::lock_guard<std::mutex> lock(ctx->mu);
   ctx->flags = flags;
@@ -969,7 +1003,7 @@ int hawkes_set_info(hawkes_ctx *ctx, int32_t set_id, int64_t *n_out, size_t *dev
 }
 
 int hawkes_pair_work(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *params, hawkes_mode mode,
-                     int64_t out[4]) {
+                     int64_t out[5]) {
   if (!ctx || !params || !out || (mode != HAWKES_FP64 && mode != HAWKES_MIXED)) return HAWKES_E_INVAL;
   if (int rc = check_params(params)) return rc;
   std::lock_guard<std::mutex> lock(ctx->mu);
@@ -1007,6 +1041,10 @@ int hawkes_pair_work(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *param
     W.first = wh.data();
     W.last = wh.data() + W.nb;
   }
+  int64_t evaluated = 0;
+  auto cols_in = [&](int c0, int c1) {  // real columns of column tiles [c0, c1)
+    return std::max<int64_t>(0, std::min<int64_t>((int64_t)c1 * kColTile, n) - (int64_t)c0 * kColTile);
+  };
   for (int rt = 0; rt < S->nrt; ++rt) {  // the window the kernels use (table_window_rt)
     const int64_t r0 = (int64_t)rt * kRowTile, r1 = std::min<int64_t>(r0 + kRowTile, n) - 1;
     int c0 = 0, c1 = S->nct;
@@ -1020,8 +1058,14 @@ int hawkes_pair_work(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *param
       c0 = (int)(j0 / kColTile);
       c1 = std::max(std::min((int)((j1 + kColTile - 1) / kColTile), S->nct), c0 + 1);
     }
-    const int64_t cols = std::min<int64_t>((int64_t)c1 * kColTile, n) - (int64_t)c0 * kColTile;
-    visited += (r1 - r0 + 1) * cols;
+    if (R.sym) {  // far column tiles serve both events of a pair (SymPlan)
+      const SymPlan pl = sym_plan_scan(R, W, rt, make_int2(c0, c1), [&](int K) { return t[(size_t)K * kRowTile]; });
+      visited += (r1 - r0 + 1) * (cols_in(c0, pl.end) + cols_in(c0, pl.sym_end));
+      evaluated += (r1 - r0 + 1) * cols_in(c0, pl.end);
+    } else {
+      visited += (r1 - r0 + 1) * cols_in(c0, c1);
+      evaluated += (r1 - r0 + 1) * cols_in(c0, c1);
+    }
   }
   for (int64_t i = 0; i < n; ++i) {  // pairs whose term can be nonzero at the working precision
     const double ti = t[(size_t)i];
@@ -1034,6 +1078,7 @@ int hawkes_pair_work(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *param
   out[1] = n * n;
   out[2] = bg_pairs;
   out[3] = trig_pairs;
+  out[4] = evaluated;
   return HAWKES_OK;
 }
 
@@ -1180,7 +1225,7 @@ int hawkes_submit(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *params, 
     if (int rc = make_request(ctx, S, params, mode, T.grad, ctx->flags, &probe)) return rc;
     T.flags = ctx->flags;
     T.footprint = request_footprint(S, mode, T.grad);
-    if (T.footprint + 4096 > ctx->budget) return HAWKES_E_ADMISSION;
+    if (T.footprint + counter_bytes(S, mode, T.grad, probe.sym) + 4096 > ctx->budget) return HAWKES_E_ADMISSION;
     S->refs++;
   }
   std::lock_guard<std::mutex> lk(ctx->smu);

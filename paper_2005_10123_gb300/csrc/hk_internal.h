@@ -27,12 +27,16 @@ constexpr int kRowTile = kThreads * kRowsPerThread;  // 256: 64 threads x 4 rows
 constexpr int kColTile = HK_COL_TILE;
 constexpr int kWarpRows = 32 * kRowsPerThread;       // consecutive rows per warp
 constexpr int kPadTo = kRowTile > kColTile ? kRowTile : kColTile;  // event arrays padded to this
+#ifndef HK_SYM_DESC
+#define HK_SYM_DESC 1  // shared-background launches: row tiles latest first (see item_at)
+#endif
 constexpr int kEpiThreads = 256;                     // rows per CTA of the allocation-free epilogue
 constexpr int kMaxBatch = 64;                        // requests per launch
 constexpr int kSumsLoglik = 2;                       // S_b, S_s
 constexpr int kSumsGrad = 6;                         // S_b, S_s, R_b, T_b, R_s, U_s
 constexpr int kFlagExcludeSelf = 1;                  // HAWKES_FLAG_EXCLUDE_SELF
 constexpr int kFlagDense = 2;                        // HAWKES_FLAG_DENSE
+constexpr int kFlagNoSymmetry = 4;                   // HAWKES_FLAG_NO_SYMMETRY
 constexpr int kFlagTestWithholdReady = 1 << 30;      // HAWKES_FLAG_TEST_WITHHOLD_READY (tests only)
 constexpr unsigned kStatusMergeTimeout = 1u;         // Request::status: a merge-tree wait ran out
 // widest pair-kernel CTA: the grouped kernel's, two rows per thread
@@ -63,14 +67,20 @@ struct SetView {
 // Column tiles [x, y) that hold every column with time in [tau0, tau1] (a superset by at most
 // the columns of two buckets on each side; columns outside the exact range only add exact
 // zeros). One bucket of margin on each side absorbs the rounding of the bucket index.
+// The first column tile of such a window: every column tile before it holds only times below
+// tau0.
+__host__ __device__ inline int table_first(const WinTable &W, double tau0) {
+  const double u0 = (tau0 - W.t0) * W.inv;
+  if (!(u0 >= 1.0)) return 0;
+  const double b = floor(u0) - 1.0;
+  return W.first[b >= (double)(W.nb - 1) ? W.nb - 1 : (int)b];
+}
+
 __host__ __device__ inline int2 table_window(const WinTable &W, int n, int nct, double tau0, double tau1) {
   const int real = (n + kColTile - 1) / kColTile;  // column tiles holding real events
-  int c0 = 0, c1 = real;
-  const double u0 = (tau0 - W.t0) * W.inv, u1 = (tau1 - W.t0) * W.inv;
-  if (u0 >= 1.0) {
-    const double b = floor(u0) - 1.0;
-    c0 = W.first[b >= (double)(W.nb - 1) ? W.nb - 1 : (int)b];
-  }
+  int c1 = real;
+  const int c0 = table_first(W, tau0);
+  const double u1 = (tau1 - W.t0) * W.inv;
   if (u1 < (double)(W.nb - 1)) c1 = W.last[u1 < 0.0 ? 0 : (int)floor(u1) + 1];
   c1 = c1 < nct ? c1 : nct;
   return make_int2(c0, c1 > c0 + 1 ? c1 : c0 + 1);
@@ -131,6 +141,14 @@ struct Request {
                        // merge-tree nodes of every row tile (2 slices from 2 rt slices), then
                        // the finished row-tile epilogues and compensator items
   double *rt_sum;      // nrt * 8: per row tile, sum of log lambda_n and of the gradient terms
+  // symmetric background (see SymPlan): far column tiles share each background term between its
+  // row and its column; column sums go to colfix as exact fixed-point integers
+  int sym;             // 1: on (mixed, fused, set with a time table, no exclude-self/dense/no-symmetry)
+  double trig_cut;     // days: columns earlier than t_n - trig_cut give exactly zero trigger terms
+  long long *colfix;   // sym: column sums of S_b (and Q, T_b with the gradient), [k][npad], zero at launch
+  unsigned *rt_done;   // sym: per row tile, row-side root plus column contributions, zero at launch
+  float fix_scale;     // 2^F: a float32 column sum v enters colfix as round(v 2^F)
+  double fix_inv;      // 2^-F
   double *out;         // 7 doubles: ell, d ell / d Theta
   unsigned *status;    // device word, zero at launch: kStatusMergeTimeout if a device wait of
                        // this request ran out (its results are then NaN), or nullptr
@@ -179,15 +197,91 @@ __host__ __device__ inline int pair_items(const Request &R) {
 __host__ __device__ inline int request_items(const Request &R) { return comp_items(R) + pair_items(R); }
 // Merge-tree nodes (fewer than 2 per leaf) of every row tile, then the final counter.
 __host__ __device__ inline int request_counters(const Request &R) { return 2 * R.set.nrt * R.slices + 1; }
+// Column sums kept in colfix per event: S_b, and Q, T_b with the gradient.
+__host__ __device__ inline int colfix_sums(bool grad) { return grad ? 3 : 1; }
 
 // The request's p-th pair item in launch order: row tile rt, index `node` among the row tile's
 // items, leaves [node * span, min(node * span + span, slices)), and `base`, the slot of the row
 // tile's first item (the item's own slot is base + node = p). Row tiles go out from the middle
 // of the time range (m, m - 1, m + 1, m - 2, ...): the first and last row tiles, whose column
-// windows are cut off by t = 0 and t = t_N, launch last.
+// windows are cut off by t = 0 and t = t_N, launch last. With the shared background (R.sym) they
+// go out latest first: a row tile's far contributors are the later row tiles, which then launch
+// before it, and the launch ends on the earliest row tiles, whose windows t = 0 cuts short.
 struct PairItem {
   int rt, node, span, base;
 };
+// Launch position k of row tile rt (the inverse of the middle-out order of item_at) and the
+// number of its first pair item (its `base`).
+__host__ __device__ inline int first_item_of(const Request &R, int rt) {
+  const int m = R.set.nrt / 2;
+  const int k = R.sym && HK_SYM_DESC ? R.set.nrt - 1 - rt : rt == m ? 0 : rt < m ? 2 * (m - rt) - 1 : 2 * (rt - m);
+  const int K = R.slices, n4 = (K + 3) / 4, n2 = (K + 1) / 2;
+  if (k < R.wide) return k * n4;
+  if (k < R.coarse) return R.wide * n4 + (k - R.wide) * n2;
+  return R.wide * n4 + (R.coarse - R.wide) * n2 + (k - R.coarse) * K;
+}
+
+// ---- symmetric background ----------------------------------------------------------------
+// A background term e_b(n, n') = e_b(n', n) serves the rows of both events. With R.sym, a row
+// tile K evaluates the column tiles J of its window that lie beyond the trigger's exact-zero
+// reach (every trigger term of K's rows with them is zero) once, adding each term to its row
+// (float64 row sums, as for any tile) and to its column (float32 column sums per tile, added to
+// colfix as integers round(v 2^F), which commute exactly, so the totals do not depend on the
+// order in which tiles finish). Those "far" column tiles are [c0(K), 2 ib(K)):
+//   c0(K) = table_first(t_K - cut_early), ib(K) = table_first(t_K - trig_cut) / 2,
+// with t_K the time of row tile K's first event; they end on a row-tile boundary, so a far
+// block always covers whole row tiles' columns. Every other pair is evaluated row by row as
+// before: row tile I visits the column tiles [max(c0(I), 2 ib(I)), min(c1(I), 2 kmax(I) + 2)),
+// kmax(I) = the last row tile K with ib(K) <= I (the later row tiles for which I is not far).
+// A pair (n in I, n' in K > I) is so covered exactly once in each direction: by K's far block
+// when I < ib(K), else by I's late columns (K <= kmax(I)) and K's near early columns. Row tile
+// I is complete when its row-side merge-tree root and the e_col(I) far blocks holding its
+// columns have arrived at rt_done[I]: each far column tile adds 1, the root adds
+// kSymRootMark - e_col(I), and the arrival that brings the counter to kSymRootMark runs I's
+// epilogue (the root stores its row sums in the slot of I's first item before it arrives).
+constexpr unsigned kSymRootMark = 1u << 30;
+
+struct SymK {
+  int c0, ib;  // first window column tile and first non-far row tile of row tile K
+};
+__host__ __device__ inline SymK sym_k(const Request &R, const WinTable &W, double t_first) {
+  return SymK{table_first(W, t_first - R.cut_early), table_first(W, t_first - R.trig_cut) / 2};
+}
+
+// The plan of row tile I: far column tiles [c0, sym_end), near ones [sym_end, end), and e_col,
+// the far column tiles of later row tiles that hold I's columns.
+struct SymPlan {
+  int sym_end, end, e_col;
+};
+
+// One row tile K's contribution to the plan of row tile I < K: its far column tiles among I's
+// two column tiles (e_col), and whether I is near for K (then I's near columns reach into K).
+__host__ __device__ inline void sym_visit(const SymK &k, int I, int *e_col, bool *near) {
+  *e_col += (k.c0 <= 2 * I && 2 * I < 2 * k.ib) + (k.c0 <= 2 * I + 1 && 2 * I + 1 < 2 * k.ib);
+  *near = k.ib <= I;
+}
+// Later row tiles K stop mattering to I once both hold: K's window starts after I's columns and
+// I is far for K (c0 and ib are non-decreasing in K).
+__host__ __device__ inline bool sym_done(const SymK &k, int I) { return k.c0 > 2 * I + 1 && k.ib > I; }
+
+// The plan of row tile I from its window [c0, c1) (table_window_rt), by a plain scan over the
+// later row tiles; tfirst(K) is row tile K's first event time. Host code and reference for the
+// kernels' warp-parallel version.
+template <class TFirst>
+__host__ __device__ inline SymPlan sym_plan_scan(const Request &R, const WinTable &W, int I, int2 win, TFirst tfirst) {
+  const SymK own = sym_k(R, W, tfirst(I));
+  int e_col = 0, kmax = I;
+  for (int K = I + 1; K < R.set.nrt; ++K) {
+    const SymK k = sym_k(R, W, tfirst(K));
+    if (sym_done(k, I)) break;
+    bool near;
+    sym_visit(k, I, &e_col, &near);
+    if (near) kmax = K;
+  }
+  const int sym_end = win.x > 2 * own.ib ? win.x : 2 * own.ib;
+  const int end = win.y < 2 * kmax + 2 ? win.y : 2 * kmax + 2;
+  return SymPlan{sym_end, end, e_col};
+}
 __host__ __device__ inline PairItem item_at(const Request &R, int p) {
   const int K = R.slices, n4 = (K + 3) / 4, n2 = (K + 1) / 2;
   const int p2 = R.wide * n4, p1 = p2 + (R.coarse - R.wide) * n2;  // first 2-leaf and 1-leaf items
@@ -196,7 +290,7 @@ __host__ __device__ inline PairItem item_at(const Request &R, int p) {
   else if (p < p1) { k = (p - p2) / n2; node = p - p2 - k * n2; k += R.wide; span = 2; }
   else { k = (p - p1) / K; node = p - p1 - k * K; k += R.coarse; span = 1; }
   const int m = R.set.nrt / 2;
-  const int rt = k == 0 ? m : (k & 1) ? m - (k + 1) / 2 : m + k / 2;
+  const int rt = R.sym && HK_SYM_DESC ? R.set.nrt - 1 - k : k == 0 ? m : (k & 1) ? m - (k + 1) / 2 : m + k / 2;
   return PairItem{rt, node, span, p - node};
 }
 

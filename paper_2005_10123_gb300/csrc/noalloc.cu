@@ -222,7 +222,7 @@ extern "C" int hawkes_loglik_noalloc(const float *x, const float *y, const float
                                      void *cuda_stream) {
   if (!x || !y || !t || !p || !device_out) return HAWKES_E_INVAL;
   if (n < 1 || n > kNoallocMax) return HAWKES_E_INVAL;  // above HAWKES_NOALLOC_MAX_EVENTS
-  if (flags & ~(HAWKES_FLAG_EXCLUDE_SELF | HAWKES_FLAG_DENSE)) return HAWKES_E_INVAL;
+  if (flags & ~(HAWKES_FLAG_EXCLUDE_SELF | HAWKES_FLAG_DENSE | HAWKES_FLAG_NO_SYMMETRY)) return HAWKES_E_INVAL;
   const double vals[6] = {p->mu0, p->tau_x, p->tau_t, p->theta, p->omega, p->h};
   for (int k = 0; k < 6; ++k)
     if (!std::isfinite(vals[k]) || (k == 3 ? vals[k] < 0.0 : vals[k] <= 0.0)) return HAWKES_E_INVAL;

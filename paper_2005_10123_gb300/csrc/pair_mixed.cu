@@ -45,6 +45,12 @@
 #ifndef HK_COL_UNROLL_LL
 #define HK_COL_UNROLL_LL 8  // loglik only
 #endif
+#ifndef HK_SYM_UNROLL
+#define HK_SYM_UNROLL 2  // steps unrolled in the far (shared-background) tile pass
+#endif
+#ifndef HK_FAR_WEIGHT
+#define HK_FAR_WEIGHT 10  // cost of a far column tile in tenths of a near one, for the leaf split
+#endif
 #ifndef HK_PACK_ADD
 #define HK_PACK_ADD 1  // differences dx, dy, dt
 #endif
@@ -106,7 +112,7 @@ __device__ __forceinline__ float2 accfma2(float2 a, float2 e, float2 s) {
 }
 
 constexpr int kPairs = kRowsPerThread / 2;  // packed row pairs per thread
-constexpr int kColUnroll = HK_COL_UNROLL, kColUnrollLL = HK_COL_UNROLL_LL;
+constexpr int kColUnroll = HK_COL_UNROLL, kColUnrollLL = HK_COL_UNROLL_LL, kSymUnroll = HK_SYM_UNROLL;
 
 template <int NS>
 struct Acc32 {
@@ -227,6 +233,93 @@ __device__ __forceinline__ void tile_pass(const float4 *__restrict__ sxs, const 
   }
 }
 
+// A float32 column sum v >= 0 into a fixed-point accumulator: round(v 2^F) as an integer, so
+// that the totals are exact and independent of the order of the additions.
+__device__ __forceinline__ void red_fix(long long *p, float v, float scale) {
+  if (v != 0.f) atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)__float2ll_rn(v * scale));
+}
+
+// A far column tile (background terms only, see SymPlan in hk_internal.h) against this warp's
+// rows, each term serving its row and its column; columns are taken in pairs (a, b) = (2m, 2m + 1).
+// The tile is staged in pair
+// layout (store_cols_pairs): sC[m] = {-s x_a, -s x_b, -s y_a, -s y_b}, sC[64 + m] the same with a
+// and b swapped, sT[m] = {-t'_a, -t'_b, -t'_b, -t'_a}. A packed row pair (r0, r1) meets a column
+// pair in two packed evaluations, e1 = (e(r0, a), e(r1, b)) and e2 = (e(r0, b), e(r1, a)): both
+// add to the row pair's sums as they are, and column a collects e1.x + e2.y, column b
+// e1.y + e2.x. Lane L owns column pair L of a 64-column chunk and at step k takes pair
+// (L + k) mod 32, so each step covers 2 row pairs x 1 column pair = 8 unordered pairs (16 terms);
+// the step's shares of the pair's column sums (over the lane's four rows) go by shuffle to the
+// owner, which receives from lane (L - k) mod 32, and after 32 steps each owner adds its pair's
+// sums over the warp's 128 rows to colfix. Every sum is formed in a fixed order. Per step and
+// lane (with the gradient): 49 packed and 6 scalar float32 operations, 8 ex2, 3 loads, 6
+// shuffles, against 72 packed operations for the same 16 terms row by row.
+template <bool GRAD>
+__device__ __forceinline__ void tile_pass_sym_pairs(const float4 *__restrict__ sC, const float4 *__restrict__ sT,
+                                                    const float2 (&XS)[kPairs], const float2 (&YS)[kPairs],
+                                                    const float2 (&T)[kPairs],
+                                                    Acc32<GRAD ? kSumsGrad : kSumsLoglik> &acc,
+                                                    long long *__restrict__ colfix, int npad, int c0, float fix_scale) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll 1
+  for (int h = 0; h < kColTile / 64; ++h) {
+    float2 cs = make_float2(0.f, 0.f), cq = cs, cu = cs;  // the owned pair's column sums
+#pragma unroll kSymUnroll
+    for (int k = 0; k < 32; ++k) {
+      const int m = h * 32 + ((lane + k) & 31);
+      const float4 C = sC[m], W = sC[64 + m], T4 = sT[m];
+      const float2 cx[2] = {make_float2(C.x, C.y), make_float2(W.x, W.y)};
+      const float2 cy[2] = {make_float2(C.z, C.w), make_float2(W.z, W.w)};
+      const float2 ct[2] = {make_float2(T4.x, T4.y), make_float2(T4.z, T4.w)};
+      float2 ps[2], pq[2], pu[2];  // per variant, summed over the row pairs
+#pragma unroll
+      for (int p = 0; p < kPairs; ++p)
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+          const float2 dx = add2(XS[p], cx[v]), dy = add2(YS[p], cy[v]), dt = add2(T[p], ct[v]);
+          const float2 u = mul2(dt, dt);
+          const float2 q = fma2(dy, dy, fma2(dx, dx, u));
+          const float2 e = make_float2(ex2(-q.x), ex2(-q.y));
+          acc.v[0][p] = acc2(acc.v[0][p], e);
+          if (GRAD) {
+            acc.v[2][p] = accfma2(q, e, acc.v[2][p]);
+            acc.v[3][p] = accfma2(u, e, acc.v[3][p]);
+          }
+          if (p == 0) {
+            ps[v] = e;
+            if (GRAD) {
+              pq[v] = mul2(q, e);
+              pu[v] = mul2(u, e);
+            }
+          } else {
+            ps[v] = acc2(ps[v], e);
+            if (GRAD) {
+              pq[v] = fma2(q, e, pq[v]);
+              pu[v] = fma2(u, e, pu[v]);
+            }
+          }
+        }
+      const int dst = (lane - k) & 31;  // the lane whose share of this lane's own pair comes now
+      cs = add2(cs, make_float2(__shfl_sync(0xffffffffu, ps[0].x + ps[1].y, dst),
+                                __shfl_sync(0xffffffffu, ps[0].y + ps[1].x, dst)));
+      if (GRAD) {
+        cq = add2(cq, make_float2(__shfl_sync(0xffffffffu, pq[0].x + pq[1].y, dst),
+                                  __shfl_sync(0xffffffffu, pq[0].y + pq[1].x, dst)));
+        cu = add2(cu, make_float2(__shfl_sync(0xffffffffu, pu[0].x + pu[1].y, dst),
+                                  __shfl_sync(0xffffffffu, pu[0].y + pu[1].x, dst)));
+      }
+    }
+    long long *f = colfix + (size_t)c0 + 2 * (h * 32 + lane);
+    red_fix(f, cs.x, fix_scale);
+    red_fix(f + 1, cs.y, fix_scale);
+    if (GRAD) {
+      red_fix(f + npad, cq.x, fix_scale);
+      red_fix(f + npad + 1, cq.y, fix_scale);
+      red_fix(f + 2 * (size_t)npad, cu.x, fix_scale);
+      red_fix(f + 2 * (size_t)npad + 1, cu.y, fix_scale);
+    }
+  }
+}
+
 // Exact-zero gaps in scaled time dt' between a warp's earliest row and a tile's latest
 // column: past kBgZeroGap every background exponent exceeds 130 (ex2 flushes 2^-130 to
 // zero); past kTrigZeroExp / -wn every trigger row factor 2^(wn dt') is below 2^-131.
@@ -238,6 +331,7 @@ constexpr float kTrigZeroExp = 132.31f;   // 1.01 * 131
 // tile ahead, then scaled, negated and (for packed operands) duplicated into shared memory.
 constexpr int kStage = kColTile / kThreads;
 static_assert(kColTile % kThreads == 0, "column tile must be a multiple of the CTA width");
+static_assert(kColTile == 2 * kThreads, "pair staging of far tiles: one column pair per thread");
 
 struct RawCols {
   float x[kStage], y[kStage], t[kStage];
@@ -275,6 +369,32 @@ __device__ __forceinline__ void store_cols(const RawCols &r, int ct, int tid, in
   }
 }
 
+// Pair-layout staging of a far tile (tile_pass_sym_pairs): thread tid loads columns 2 tid and
+// 2 tid + 1 and writes pair tid of the tile.
+__device__ __forceinline__ RawCols load_cols_pairs(const SetView &S, int ct, int tid) {
+  RawCols r;
+  const int j = ct * kColTile + 2 * tid;
+  const float2 x = __ldg(reinterpret_cast<const float2 *>(S.x32 + j));
+  const float2 y = __ldg(reinterpret_cast<const float2 *>(S.y32 + j));
+  const float2 t = __ldg(reinterpret_cast<const float2 *>(S.t32 + j));
+  r.x[0] = x.x; r.x[1] = x.y;
+  r.y[0] = y.x; r.y[1] = y.y;
+  r.t[0] = t.x; r.t[1] = t.y;
+  return r;
+}
+
+__device__ __forceinline__ void store_cols_pairs(const RawCols &r, int ct, int tid, int n, float t_origin,
+                                                 const Scales &k, float4 *sC, float4 *sT) {
+  const int j = ct * kColTile + 2 * tid;
+  const float ta = j < n ? scale_split(r.t[0] - t_origin, k.b_hi, k.b_lo) : kPadScaled;
+  const float tb = j + 1 < n ? scale_split(r.t[1] - t_origin, k.b_hi, k.b_lo) : kPadScaled;
+  const float xa = scale_split(r.x[0], k.s_hi, k.s_lo), xb = scale_split(r.x[1], k.s_hi, k.s_lo);
+  const float ya = scale_split(r.y[0], k.s_hi, k.s_lo), yb = scale_split(r.y[1], k.s_hi, k.s_lo);
+  sC[tid] = make_float4(-xa, -xb, -ya, -yb);
+  sC[64 + tid] = make_float4(-xb, -xa, -yb, -ya);
+  sT[tid] = make_float4(-ta, -tb, -tb, -ta);
+}
+
 // This thread's row coordinates (rows ra = wa + lane + 32 k, packed in pairs k, k + 1),
 // stored values or scaled by s with the columns' rounding, so that dx = 0 on the diagonal.
 template <bool SCALED>
@@ -302,9 +422,41 @@ __device__ __forceinline__ void cta_sync() {
 // One pair item: the row sums of row tile it.rt over column tiles [c_begin, c_end), then
 // (fused) the row tile's merge tree and, in the CTA that completes it, the tile's epilogue;
 // otherwise the sums go to the item's partial-sum slot.
+// The epilogue of row tile I (Section 2.1, Eq. 1): every event's row sums, get(s, k) for sum s of
+// this thread's row k (rows warp * kWarpRows + lane + 32 k), plus with R.sym the column sums its
+// far blocks left in colfix; then log lambda_n, the moment ratios and the fixed-order reductions
+// (hk_internal.h). Called by every thread of the CTA.
+template <bool GRAD, class Get>
+__device__ void rowtile_epilogue(const Request &R, int I, Get get) {
+  constexpr int NS = GRAD ? kSumsGrad : kSumsLoglik;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int n = R.set.n;
+  const size_t np = (size_t)R.set.npad;
+  double v[GRAD ? 7 : 1] = {};
+#pragma unroll
+  for (int k = 0; k < kRowsPerThread; ++k) {
+    const int i = I * kRowTile + warp * kWarpRows + lane + 32 * k;
+    if (i < n) {
+      double sums[NS];
+#pragma unroll
+      for (int s = 0; s < NS; ++s) sums[s] = get(s, k);
+      if (R.sym) {  // S_b, Q, T_b from the far blocks holding this event's column
+        sums[0] += (double)__ldcg(R.colfix + i) * R.fix_inv;
+        if (GRAD) {
+          sums[2] += (double)__ldcg(R.colfix + np + i) * R.fix_inv;
+          sums[3] += (double)__ldcg(R.colfix + 2 * np + i) * R.fix_inv;
+        }
+      }
+      if (GRAD) sums[2] = (sums[2] - sums[3]) * R.inv_a2;  // R_b from Q and T_b
+      row_terms<GRAD>(R, i, sums, v);
+    }
+  }
+  rowtile_reduce<GRAD>(R, I, v);
+}
+
 template <bool GRAD>
 __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, int c_begin, int c_end,
-                          float4 (*sxs)[kColTile], float4 (*stx)[kColTile], double *sacc) {
+                          const SymPlan &plan, float4 (*sxs)[kColTile], float4 (*stx)[kColTile], double *sacc) {
   constexpr int NS = GRAD ? kSumsGrad : kSumsLoglik;
   const SetView &S = R.set;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -342,19 +494,25 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
 #pragma unroll
     for (int k = 0; k < kRowsPerThread; ++k) sacc[(s * kRowsPerThread + k) * kThreads + tid] = 0.0;
 
+  // far tiles are staged in pair layout (tile_pass_sym_pairs)
+  auto paired = [&](int c) { return R.sym && c < plan.sym_end; };
   int ct = c_begin;
   if (ct < c_end) {  // an empty slice of the window writes zero partial sums
-    store_cols(load_cols(S, ct, tid), ct, tid, n, t_origin, sk, sxs[0], stx[0]);
+    if (paired(ct)) store_cols_pairs(load_cols_pairs(S, ct, tid), ct, tid, n, t_origin, sk, sxs[0], stx[0]);
+    else store_cols(load_cols(S, ct, tid), ct, tid, n, t_origin, sk, sxs[0], stx[0]);
     cta_sync();
   }
   for (int k = 0; ct < c_end; ++ct, ++k) {
     const int buf = k & 1;
-    const bool has_next = ct + 1 < c_end;
+    const bool has_next = ct + 1 < c_end, next_paired = paired(ct + 1);
     RawCols nxt;
-    if (has_next) nxt = load_cols(S, ct + 1, tid);
+    if (has_next) nxt = next_paired ? load_cols_pairs(S, ct + 1, tid) : load_cols(S, ct + 1, tid);
     const int c0 = ct * kColTile, c1 = c0 + kColTile;
     int kind;
-    if (c1 <= lo_wa) {  // every pair causal: which of the two terms can be nonzero?
+    if (R.sym && ct < plan.sym_end) {  // far: background only, shared with the columns' rows
+      const float gap = s_first + stx[buf][kColTile / 2 - 1].y;  // pair layout: the latest column
+      kind = gap >= kBgZeroGap ? -1 : 4;
+    } else if (c1 <= lo_wa) {  // every pair causal: which of the two terms can be nonzero?
       const float gap = s_first + stx[buf][kColTile - 1].x;  // t'(first row) - t'(latest column)
       const bool bg_zero = gap >= kBgZeroGap, trig_zero = wn * gap <= -kTrigZeroExp;
       kind = bg_zero ? (trig_zero ? -1 : 3) : (trig_zero ? 0 : 1);
@@ -373,6 +531,8 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
     float2 X[kPairs], Y[kPairs];  // stored row coordinates, tiles with trigger terms
     if (kind == 0) {
       tile_pass<0, GRAD>(sxs[buf], stx[buf], XS, YS, T, LO, row_a0, c0, excl, A2, CN, WN, WN, acc);
+    } else if (kind == 4) {
+      tile_pass_sym_pairs<GRAD>(sxs[buf], stx[buf], XS, YS, T, acc, R.colfix, S.npad, c0, R.fix_scale);
     } else if (kind == 1 || kind == 3) {
       row_coords<false>(S, row_a0, sk, X, Y);
       const float sref = -stx[buf][kColTile - 1].x;  // t'_ref: the tile's latest column
@@ -397,7 +557,7 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
     }  // kind -1: every term of the tile is exactly zero for this warp
     // fold the tile's sums into float64; a tile without trigger (background) terms leaves
     // those sums at zero, so they are skipped
-    const bool fold_bg = kind == 0 || kind == 1 || kind == 2, fold_trig = kind >= 1;
+    const bool fold_bg = kind == 0 || kind == 1 || kind == 2 || kind == 4, fold_trig = kind >= 1 && kind <= 3;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       const bool trig_sum = s == 1 || s == 4 || s == 5;  // S_s, R_s, U_s
@@ -408,7 +568,10 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
         sacc[(s * kRowsPerThread + 2 * p + 1) * kThreads + tid] += (double)acc.v[s][p].y;
       }
     }
-    if (has_next) store_cols(nxt, ct + 1, tid, n, t_origin, sk, sxs[buf ^ 1], stx[buf ^ 1]);
+    if (has_next) {
+      if (next_paired) store_cols_pairs(nxt, ct + 1, tid, n, t_origin, sk, sxs[buf ^ 1], stx[buf ^ 1]);
+      else store_cols(nxt, ct + 1, tid, n, t_origin, sk, sxs[buf ^ 1], stx[buf ^ 1]);
+    }
     cta_sync();
   }
   // this thread's rows: la = warp * kWarpRows + lane + 32 k, sums at sacc[(s R + k) T + tid]
@@ -432,22 +595,71 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
       for (int s = 0; s < NS; ++s)
         sacc[(s * kRowsPerThread + k) * kThreads + tid] += __ldcg(src + s * kRowTile + warp * kWarpRows + lane + 32 * k);
   };
+  __shared__ unsigned s_arrive;
+  const int f_end = min(c_end, plan.sym_end);
+  if (R.sym && c_begin < f_end) {
+    // this item's far column tiles [c_begin, f_end) arrive at the row tiles holding their columns;
+    // the arrival that completes a row tile runs its epilogue from the slot of its first item
+    __threadfence();
+    cta_sync();
+    for (int I = c_begin / 2; I <= (f_end - 1) / 2; ++I) {
+      const unsigned tiles = (unsigned)(min(f_end, 2 * I + 2) - max(c_begin, 2 * I));
+      if (tid == 0) s_arrive = atomicAdd(R.rt_done + I, tiles) + tiles == kSymRootMark;
+      cta_sync();
+      if (s_arrive) {
+        __threadfence();
+        const double *slot = R.partials + (size_t)first_item_of(R, I) * NS * kRowTile;
+        rowtile_epilogue<GRAD>(R, I, [&](int s, int k) {
+          return __ldcg(slot + s * kRowTile + warp * kWarpRows + lane + 32 * k);
+        });
+      }
+      cta_sync();
+    }
+  }
   const int root = merge_tree<GRAD>(R, it, store, merge);
   if (root < 0) mark_timeout(R);
   if (root <= 0) return;
-  double v[GRAD ? 7 : 1] = {};
-#pragma unroll
-  for (int k = 0; k < kRowsPerThread; ++k) {
-    const int i = row0 + warp * kWarpRows + lane + 32 * k;
-    if (i < n) {
-      double sums[NS];
-#pragma unroll
-      for (int s = 0; s < NS; ++s) sums[s] = sacc[(s * kRowsPerThread + k) * kThreads + tid];
-      if (GRAD) sums[2] = (sums[2] - sums[3]) * R.inv_a2;  // R_b from Q and T_b
-      row_terms<GRAD>(R, i, sums, v);
-    }
+  if (R.sym) {  // the row side is complete: store it, then arrive (kSymRootMark - e_col)
+    store(it.base);
+    __threadfence();
+    cta_sync();
+    if (tid == 0)
+      s_arrive = atomicAdd(R.rt_done + it.rt, kSymRootMark - (unsigned)plan.e_col) == (unsigned)plan.e_col;
+    cta_sync();
+    if (!s_arrive) return;
+    __threadfence();
   }
-  rowtile_reduce<GRAD>(R, it.rt, v);
+  rowtile_epilogue<GRAD>(R, it.rt, [&](int s, int k) { return sacc[(s * kRowsPerThread + k) * kThreads + tid]; });
+}
+
+// sym_plan_scan (hk_internal.h) with the later row tiles taken 32 at a time, one per lane; called
+// by one full warp, every lane returns the plan of row tile I.
+__device__ SymPlan sym_plan_warp(const Request &R, int I, int2 win) {
+  const WinTable &W = R.set.win32;
+  const float *t = R.set.t32;
+  const int lane = threadIdx.x & 31;
+  const SymK own = sym_k(R, W, (double)__ldg(t + (size_t)I * kRowTile));
+  int e_col = 0, kmax = I;
+  for (int base = I + 1; base < R.set.nrt; base += 32) {
+    const int K = base + lane;
+    bool done = true;
+    if (K < R.set.nrt) {
+      const SymK k = sym_k(R, W, (double)__ldg(t + (size_t)K * kRowTile));
+      done = sym_done(k, I);
+      if (!done) {
+        bool near;
+        sym_visit(k, I, &e_col, &near);
+        if (near) kmax = K;
+      }
+    }
+    if (__any_sync(0xffffffffu, done)) break;  // every later row tile is done too
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    e_col += __shfl_xor_sync(0xffffffffu, e_col, off);
+    kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, off));
+  }
+  return SymPlan{max(win.x, 2 * own.ib), min(win.y, 2 * kmax + 2), e_col};
 }
 
 template <bool GRAD>
@@ -476,10 +688,27 @@ __global__ void __launch_bounds__(kThreads, GRAD ? HK_MIN_CTAS : HK_MIN_CTAS_LL)
     cta_sync();
     w = s_win;
   }
-  const int width = w.y - w.x;
-  const int c_begin = w.x + (int)((long long)width * l0 / ns);
-  const int c_end = w.x + (int)((long long)width * l1 / ns);
-  run_piece<GRAD>(B, R, it, c_begin, c_end, sxs, stx, sacc);
+  SymPlan plan{w.x, w.y, 0};
+  if (R.sym) {  // far and near column tiles of this row tile (the host enables sym only with a table)
+    __shared__ SymPlan s_plan;
+    if (threadIdx.x < 32) {
+      const SymPlan v = sym_plan_warp(R, rt, w);
+      if (threadIdx.x == 0) s_plan = v;
+    }
+    cta_sync();
+    plan = s_plan;
+    w.y = plan.end;
+  }
+  // leaves: equal shares of the window's cost, a far column tile weighing HK_FAR_WEIGHT / 10 near
+  // ones (without sym every tile weighs the same)
+  const long long fw = R.sym ? HK_FAR_WEIGHT : 10, nf = plan.sym_end - w.x, nn = w.y - plan.sym_end;
+  const long long total = nf * fw + nn * 10;
+  auto at = [&](int l) {  // column tile where leaf l starts
+    const long long pos = total * l / ns;
+    return pos < nf * fw ? w.x + (int)(pos / fw) : plan.sym_end + (int)((pos - nf * fw) / 10);
+  };
+  const int c_begin = at(l0), c_end = at(l1);
+  run_piece<GRAD>(B, R, it, c_begin, c_end, plan, sxs, stx, sacc);
 }
 
 }  // namespace

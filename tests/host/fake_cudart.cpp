@@ -28,6 +28,7 @@ namespace {
 std::atomic<long> g_fail_after{-1};
 std::atomic<int> g_event_delay{0};
 std::atomic<long> g_schedule_errors{0};
+std::atomic<long> g_sym_checked{0};  // launches whose shared-background plan was checked in full
 std::atomic<long> g_launches{0};
 std::atomic<long> g_live_allocs{0};
 std::mutex g_mu;
@@ -48,6 +49,7 @@ void fake_fail_alloc_after(long k) { g_fail_after = k; }
 void fake_event_delay(int k) { g_event_delay = k; }
 void fake_release_events() { g_epoch++; }
 long fake_schedule_errors() { return g_schedule_errors.load(); }
+long fake_sym_checked() { return g_sym_checked.load(); }
 long fake_launches() { return g_launches.load(); }
 long fake_live_allocs() { return g_live_allocs.load(); }
 
@@ -128,6 +130,63 @@ cudaError_t cudaEventQuery(cudaEvent_t e) {
 
 namespace hk {
 
+// With the shared background (Request::sym): the completion counters and fixed-point column sums
+// start at zero, and the far/near plan of every row tile (SymPlan, as the kernels compute it from
+// the set's time table) covers every ordered block (rows of column tile H, columns of column tile
+// J) at most once, and exactly once where a term can be nonzero (J inside the window of H's row
+// tile, and, for a later J, H inside the window of J's row tile); e_col(I) counts the far column
+// tiles of later row tiles that hold I's columns.
+static bool sym_fail(const char *what, int a, int b, int c) {
+  std::fprintf(stderr, "symmetric plan check failed: %s (%d, %d, %d)\n", what, a, b, c);
+  return false;
+}
+
+static bool check_symmetry(const Request &R) {
+  const SetView &S = R.set;
+  if (!R.rt_done || !R.colfix || S.win32.nb == 0 || !(R.fix_scale > 0.f)) return sym_fail("set-up", S.n, 0, 0);
+  for (int I = 0; I < S.nrt; ++I)
+    if (R.rt_done[I] != 0u) return sym_fail("rt_done not zero", S.n, I, 0);
+  for (size_t i = 0; i < (size_t)colfix_sums(R.grad != 0) * S.npad; ++i)
+    if (R.colfix[i] != 0) return sym_fail("colfix not zero", S.n, (int)i, 0);
+  if (S.nct > 1024) return true;  // the block table below grows as nct^2
+  g_sym_checked++;
+  auto tfirst = [&](int K) { return (double)S.t32[(size_t)K * kRowTile]; };
+  std::vector<int2> win(S.nrt);
+  std::vector<SymPlan> plan(S.nrt);
+  for (int I = 0; I < S.nrt; ++I) {
+    const int r1 = std::min((I + 1) * kRowTile, S.n) - 1;
+    win[I] = table_window(S.win32, S.n, S.nct, tfirst(I) - R.cut_early, (double)S.t32[r1] + R.cut_late);
+    plan[I] = sym_plan_scan(R, S.win32, I, win[I], tfirst);
+    const int real = (S.n + kColTile - 1) / kColTile;  // column tiles holding real events
+    if (plan[I].sym_end < win[I].x || plan[I].sym_end > 2 * I || plan[I].end < std::min(2 * I + 2, real) ||
+        plan[I].end > win[I].y)
+      return sym_fail("plan bounds", S.n, I, plan[I].sym_end * 10000 + plan[I].end);
+  }
+  const size_t nct = (size_t)S.nct;
+  std::vector<int> cov(nct * nct, 0), ecol(S.nrt, 0);
+  for (int I = 0; I < S.nrt; ++I)
+    for (int J = win[I].x; J < plan[I].end; ++J) {  // row side: every column tile of I's window
+      cov[(size_t)(2 * I) * nct + J]++;
+      cov[(size_t)(2 * I + 1) * nct + J]++;
+    }
+  for (int K = 0; K < S.nrt; ++K)
+    for (int H = win[K].x; H < plan[K].sym_end; ++H) {  // column side of K's far tiles
+      cov[(size_t)H * nct + 2 * K]++;
+      cov[(size_t)H * nct + 2 * K + 1]++;
+      ecol[H / 2]++;
+    }
+  for (int I = 0; I < S.nrt; ++I)
+    if (ecol[I] != plan[I].e_col) return sym_fail("e_col", S.n, I, ecol[I] * 10000 + plan[I].e_col);
+  for (int H = 0; H < S.nct; ++H)
+    for (int J = 0; J < S.nct; ++J) {
+      const int c = cov[(size_t)H * nct + J];
+      const int I = H / 2, IJ = J / 2;
+      const bool need = J >= win[I].x && J < win[I].y && (J <= H || (H >= win[IJ].x && H < win[IJ].y));
+      if (c > 1 || (need && c != 1)) return sym_fail("coverage", S.n, H, J * 10 + c);
+    }
+  return true;
+}
+
 // Check one request's work decomposition against its set.
 static void check_schedule(const Request &R, int mode) {
   const SetView &S = R.set;
@@ -142,6 +201,7 @@ static void check_schedule(const Request &R, int mode) {
     const PairItem it = item_at(R, p);
     if (it.rt < 0 || it.rt >= S.nrt || it.node < 0 || it.base + it.node != p || it.base < 0) { ok = false; break; }
     if (it.span != 1 && it.span != 2 && it.span != 4) { ok = false; break; }
+    if (first_item_of(R, it.rt) != it.base) { ok = false; break; }  // the inverse of the launch order
     const int l0 = it.node * it.span, l1 = std::min(l0 + it.span, R.slices);
     if (l0 >= R.slices) { ok = false; break; }
     for (int l = l0; l < l1; ++l)
@@ -154,6 +214,7 @@ static void check_schedule(const Request &R, int mode) {
   if (!R.partials || !R.comp || !R.rt_sum || !R.rt_count || !R.out || !R.status) ok = false;
   for (int i = 0; ok && i < request_counters(R); ++i)
     if (R.rt_count[i] != 0u) ok = false;  // merge-tree and completion counters zeroed before the launch
+  if (ok && R.sym) ok = check_symmetry(R);
   if (!ok) g_schedule_errors++;
 }
 

@@ -62,6 +62,25 @@ def main():
             ll, g = ctx.hawkes_loglik_grad(sid, TH, mode)
             assert ll == fake_value(TH, n, mode) and np.array_equal(g, TH)
     assert fake.fake_schedule_errors() == 0, "schedule coverage errors"
+    assert fake.fake_sym_checked() > 0, "no launch used the shared background"
+    # every ordered pair evaluated row by row when asked; shared far terms counted once otherwise
+    for n in (20000, 85000):
+        w = ctx.hawkes_pair_work(sids[n], TH, 1)
+        assert w["evaluated"] < w["visited"], (n, w)
+        ctx.hawkes_set_flags(binding.HAWKES_FLAG_NO_SYMMETRY)
+        w2 = ctx.hawkes_pair_work(sids[n], TH, 1)
+        ctx.hawkes_set_flags(0)
+        assert w2["evaluated"] == w2["visited"], (n, w2)
+        ll = ctx.hawkes_loglik_grad(sids[n], TH, 1)[0]
+        assert ll == fake_value(TH, n, 1)
+    # the plan's coverage for reaches on either side of the trigger's (checked by the fake at launch)
+    for th in [(0.02, 0.5, 5.0, 0.6, 0.02, 0.05), (0.01, 2.0, 300.0, 0.4, 0.05, 0.3), (0.05, 0.8, 2.0, 0.5, 3.0, 0.1),
+               (0.01, 1.0, 30.0, 0.5, 20.0, 0.1)]:
+        for n in (257, 4097, 20000, 85000):
+            for g in (False, True):
+                r = ctx.hawkes_loglik_grad(sids[n], th, 1) if g else (ctx.hawkes_loglik(sids[n], th, 1),)
+                assert r[0] == fake_value(th, n, 1)
+    assert fake.fake_schedule_errors() == 0, "shared-background plan errors"
     ths = synth.theta_batch(64, seed=3)
     ll, g = ctx.hawkes_loglik_batch(sids[20000], ths, 1, want_grad=True)
     for k in range(64):

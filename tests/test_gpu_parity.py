@@ -175,19 +175,53 @@ def test_pi_batch(ctx, mode):
 @pytest.mark.parametrize("mode", [0, 1], ids=["fp64", "mixed"])
 def test_exact_zero_window_matches_dense(ctx, mode):
     """Skipping the columns whose pair terms are exactly zero at the working precision changes
-    nothing but the grouping of the float64 partial sums."""
+    nothing but the grouping of the float64 partial sums (row-by-row evaluation: the mixed path
+    with HAWKES_FLAG_NO_SYMMETRY, which HAWKES_FLAG_DENSE implies)."""
     from paper_2005_10123_gb300 import binding
     ev = synth.simulate(20000, 5000.0, seed=71)  # long time span: most column tiles skipped
     sid = ctx.hawkes_upload_events(ev.x, ev.y, ev.t)
     try:
         for th in [TH0, (0.02, 0.5, 5.0, 0.6, 3.0, 0.05), (0.01, 2.0, 300.0, 0.4, 0.05, 0.3),
                    (0.02, 0.5, 5.0, 0.6, 0.02, 0.05)]:
-            ctx.hawkes_set_flags(0)
+            ctx.hawkes_set_flags(binding.HAWKES_FLAG_NO_SYMMETRY)
             a, ga = ctx.hawkes_loglik_grad(sid, th, mode)
             ctx.hawkes_set_flags(binding.HAWKES_FLAG_DENSE)
             b, gb = ctx.hawkes_loglik_grad(sid, th, mode)
             assert rel(a, b) <= 1e-14, (th, a, b)
             assert grad_err(ga, gb) <= 1e-13, (th, ga, gb)
+    finally:
+        ctx.hawkes_set_flags(0)
+        ctx.hawkes_release_events(sid)
+
+
+@pytest.mark.parametrize("n,T", [(20000, 5000.0), (20000, 300.0), (6000, 3000.0), (85000, 5000.0)],
+                         ids=["n20k-long", "n20k-dense", "n6k", "n85k"])
+def test_shared_background_matches_row_by_row(ctx, n, T):
+    """The mixed path's shared background terms (far column tiles evaluated once for both events,
+    column sums in exact fixed point) against row-by-row evaluation of every ordered pair
+    (HAWKES_FLAG_NO_SYMMETRY), for reaches on either side of the trigger's; both within the mixed
+    tolerance of each other, per-event terms included, and bitwise repeatable."""
+    from paper_2005_10123_gb300 import binding
+    ev = synth.simulate(n, T, seed=72 + n) if n != 85000 else synth.large_workload()
+    sid = ctx.hawkes_upload_events(ev.x, ev.y, ev.t)
+    try:
+        for th in [TH0, (0.02, 0.5, 5.0, 0.6, 3.0, 0.05), (0.01, 2.0, 300.0, 0.4, 0.05, 0.3),
+                   (0.012, 1.3, 20.0, 0.4, 1.5, 0.12)]:
+            ctx.hawkes_set_flags(binding.HAWKES_FLAG_NO_SYMMETRY)
+            b, gb = ctx.hawkes_loglik_grad(sid, th, 1)
+            mub, xib, lb = ctx.hawkes_event_terms(sid, th, 1)
+            ctx.hawkes_set_flags(0)
+            a, ga = ctx.hawkes_loglik_grad(sid, th, 1)
+            a2, ga2 = ctx.hawkes_loglik_grad(sid, th, 1)
+            mua, xia, la = ctx.hawkes_event_terms(sid, th, 1)
+            assert a == a2 and np.array_equal(ga, ga2)
+            assert rel(a, b) <= 2e-7, (th, a, b)
+            assert grad_err(ga, gb) <= 2e-7, (th, ga, gb)
+            assert la == ctx.hawkes_loglik(sid, th, 1)
+            np.testing.assert_allclose(mua, mub, rtol=2e-6)
+            np.testing.assert_allclose(xia, xib, rtol=2e-6, atol=2e-6 * np.max(xib))
+            w = ctx.hawkes_pair_work(sid, th, 1)
+            assert w["evaluated"] <= w["visited"]
     finally:
         ctx.hawkes_set_flags(0)
         ctx.hawkes_release_events(sid)
