@@ -314,6 +314,21 @@ def serving_runs(ctx, n_requests):
     return out
 
 
+def probe_units():
+    """Build and run paper_2005_10123_gb300/probes/units.cu: measured float32-pipe and MUFU.EX2
+    rates (lane operations per second) and the relative-error profile of ex2.approx."""
+    from paper_2005_10123_gb300 import build as lib_build
+    src = os.path.join(ROOT, "paper_2005_10123_gb300", "probes", "units.cu")
+    exe = os.path.join(lib_build.OUT_DIR, "probe_units")
+    os.makedirs(lib_build.OUT_DIR, exist_ok=True)
+    subprocess.check_call([lib_build._nvcc(), *lib_build.ARCH, "-O3", "-o", exe, src])
+    d = json.loads(subprocess.check_output([exe], text=True))
+    d["lanes_per_clk_per_sm_at_max_clock"] = {k: v / (d["sms"] * MAX_MHZ * 1e6)
+                                              for k, v in d["lane_ops_per_s"].items()}
+    print(json.dumps(d))
+    return 0
+
+
 def run_reference(args):
     rank, world, _ = _dist_env()
     if rank != 0:
@@ -579,7 +594,11 @@ def main():
                     help="run only the float64 loglik of the N=2,000 workload (the FP64 kernel's ncu case)")
     ap.add_argument("--profile", action="store_true",
                     help="run only warm-up + steps of the mixed loglik+grad call (the case profiled with ncu)")
+    ap.add_argument("--probe-units", action="store_true",
+                    help="measure the float32-pipe and ex2 rates and ex2.approx's error profile, then exit")
     args = ap.parse_args()
+    if args.probe_units:
+        return probe_units()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
