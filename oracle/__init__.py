@@ -25,6 +25,15 @@ class _Params(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in PARAM_NAMES]
 
 
+MIX_MAX = 2  # trigger components of the mixture extension (oracle_loglik_mix)
+
+
+class _MixParams(ctypes.Structure):
+    _fields_ = [("mu0", ctypes.c_double), ("tau_x", ctypes.c_double), ("tau_t", ctypes.c_double),
+                ("theta", ctypes.c_double * MIX_MAX), ("omega", ctypes.c_double * MIX_MAX),
+                ("h", ctypes.c_double * MIX_MAX)]
+
+
 _lib = None
 
 
@@ -43,7 +52,12 @@ def _load():
         lib.oracle_intensity.argtypes = [i64, d, d, d, ctypes.POINTER(_Params), ctypes.c_int,
                                          i64, d, d, d, d]
         lib.oracle_compensator.argtypes = [i64, d, ctypes.POINTER(_Params), d, d]
-        for f in (lib.oracle_loglik, lib.oracle_rows, lib.oracle_intensity, lib.oracle_compensator):
+        lib.oracle_loglik_mix.argtypes = [i64, d, d, d, ctypes.POINTER(_MixParams), ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_int, d, d]
+        lib.oracle_intensity_mix.argtypes = [i64, d, d, d, ctypes.POINTER(_MixParams), ctypes.c_int, i64,
+                                             d, d, d, d]
+        for f in (lib.oracle_loglik, lib.oracle_rows, lib.oracle_intensity, lib.oracle_compensator,
+                  lib.oracle_loglik_mix, lib.oracle_intensity_mix):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -141,3 +155,43 @@ def compensator(t, theta):
                                 g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     _check(rc, "oracle_compensator")
     return L.value, g
+
+
+def _mix_params(mix_theta):
+    """(mu0, tau_x, tau_t, theta_1, omega_1, h_1[, theta_2, omega_2, h_2]) -> (struct, M)."""
+    v = [float(a) for a in mix_theta]
+    if len(v) not in (6, 9):
+        raise ValueError("a mixture Theta has 3 + 3 M entries, M = 1 or 2")
+    M = (len(v) - 3) // 3
+    p = _MixParams()
+    p.mu0, p.tau_x, p.tau_t = v[:3]
+    for m in range(M):
+        p.theta[m], p.omega[m], p.h[m] = v[3 + 3 * m: 6 + 3 * m]
+    return p, M
+
+
+def loglik_mix(x, y, t, mix_theta, flags=0, grad=False, threads=None):
+    """ell of Eq. 1 with the mixture of triggering functions (oracle_loglik_mix); with grad=True
+    also its gradient, in the order (mu0, tau_x, tau_t, theta_1, omega_1, h_1, ...)."""
+    lib = _load()
+    (x, px), (y, py), (t, pt) = _arr(x), _arr(y), _arr(t)
+    p, M = _mix_params(mix_theta)
+    ell = ctypes.c_double()
+    g = np.zeros(3 + 3 * M)
+    rc = lib.oracle_loglik_mix(len(t), px, py, pt, ctypes.byref(p), M, flags, threads or default_threads(),
+                               ctypes.byref(ell), g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if grad else None)
+    _check(rc, "oracle_loglik_mix")
+    return (ell.value, g) if grad else ell.value
+
+
+def intensity_mix(x, y, t, mix_theta, qx, qy, qt):
+    """lambda(q) of the mixture model at query points."""
+    lib = _load()
+    (x, px), (y, py), (t, pt) = _arr(x), _arr(y), _arr(t)
+    (qx, pqx), (qy, pqy), (qt, pqt) = _arr(qx), _arr(qy), _arr(qt)
+    p, M = _mix_params(mix_theta)
+    out = np.zeros(len(qt))
+    rc = lib.oracle_intensity_mix(len(t), px, py, pt, ctypes.byref(p), M, len(qt), pqx, pqy, pqt,
+                                  out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    _check(rc, "oracle_intensity_mix")
+    return out

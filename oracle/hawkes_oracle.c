@@ -310,3 +310,177 @@ int oracle_compensator(int64_t n, const double *t, const oracle_params *p,
   if (grad_out) for (int k = 0; k < 6; ++k) grad_out[k] = nsum_get(&g[k]);
   return 0;
 }
+
+/* ==========================================================================
+ * Mixture of triggering functions (the extension the paper's Discussion
+ * proposes: several triggering functions that combine a very short time frame,
+ * multi-shot events, with a longer one, retaliation over days to months).
+ * Reading: each component is the paper's triggering function with its own
+ * (theta_m, omega_m, h_m), taken with the same prefactor reading as above,
+ *
+ *   g(dx, dt) = sum_{m=1..M} theta_m * omega_m / h_m^2 * exp(-omega_m dt) * phi2(dx / h_m),
+ *
+ * so the branching ratio is sum_m theta_m, M = 1 is the model of Section 2.1,
+ * and the compensator's trigger part is sum_m theta_m (1 - e^{-omega_m (t_N - t_n)}).
+ * The background, the self term, ties and the window are as above. Gradient
+ * order: (mu0, tau_x, tau_t, theta_1, omega_1, h_1, ..., theta_M, omega_M, h_M).
+ * ========================================================================== */
+#define ORACLE_MIX_MAX 2
+
+typedef struct {
+  double mu0, tau_x, tau_t;
+  double theta[ORACLE_MIX_MAX], omega[ORACLE_MIX_MAX], h[ORACLE_MIX_MAX];
+} oracle_mix_params;
+
+/* The background-only parameter view (theta unused) of a mixture. */
+static oracle_params mix_background(const oracle_mix_params *p) {
+  oracle_params b;
+  memset(&b, 0, sizeof b);
+  b.mu0 = p->mu0; b.tau_x = p->tau_x; b.tau_t = p->tau_t;
+  return b;
+}
+
+/* Per-row quantities of the mixture for event `row`: out[0] = mu_n, out[1] = xi_n (all
+ * components), out[2 .. 2 + 3 + 3M) = d lambda_n / d Theta in the gradient order above. */
+static void mix_row_terms(int64_t n, const double *x, const double *y, const double *t,
+                          const oracle_mix_params *p, int M, int flags, int64_t row, int want_grad,
+                          double *out) {
+  const oracle_params bp = mix_background(p);
+  const int np = 3 + 3 * M;
+  nsum mu = {0, 0}, xi = {0, 0}, g[3 + 3 * ORACLE_MIX_MAX];
+  memset(g, 0, sizeof g);
+  const double xr = x[row], yr = y[row], tr = t[row];
+  for (int64_t j = 0; j < n; ++j) {
+    const double dx = xr - x[j], dy = yr - y[j], dt = tr - t[j];
+    const double r2 = dx * dx + dy * dy;
+    if (!((flags & ORACLE_EXCLUDE_SELF) && j == row)) {
+      const double b = background_term(&bp, dx, dy, dt);
+      nsum_add(&mu, b);
+      if (want_grad) {
+        nsum_add(&g[0], b / p->mu0);
+        nsum_add(&g[1], b * (-2.0 / p->tau_x + r2 / (p->tau_x * p->tau_x * p->tau_x)));
+        nsum_add(&g[2], b * (-1.0 / p->tau_t + dt * dt / (p->tau_t * p->tau_t * p->tau_t)));
+      }
+    }
+    if (t[j] < tr) { /* strict indicator on stored times */
+      for (int m = 0; m < M; ++m) {
+        const double hm = p->h[m], om = p->omega[m];
+        const double kern = om / (hm * hm) * exp(-om * dt) * phi2(dx / hm, dy / hm); /* s_m / theta_m */
+        const double s = p->theta[m] * kern;
+        nsum_add(&xi, s);
+        if (want_grad) {
+          nsum_add(&g[3 + 3 * m], kern);
+          nsum_add(&g[4 + 3 * m], s * (1.0 / om - dt));
+          nsum_add(&g[5 + 3 * m], s * (-2.0 / hm + r2 / (hm * hm * hm)));
+        }
+      }
+    }
+  }
+  out[0] = nsum_get(&mu);
+  out[1] = nsum_get(&xi);
+  for (int k = 0; k < np; ++k) out[2 + k] = want_grad ? nsum_get(&g[k]) : 0.0;
+}
+
+/* Lambda_n of the mixture and its derivatives in the gradient order (out[0] = Lambda_n). */
+static void mix_compensator_terms(double tn, double tN, const oracle_mix_params *p, int M, double *out) {
+  const double a = (tN - tn) / p->tau_t, b = -tn / p->tau_t, D = tN - tn;
+  out[0] = p->mu0 * (Phi(a) - Phi(b));
+  out[1] = Phi(a) - Phi(b);
+  out[2] = 0.0;
+  out[3] = p->mu0 / p->tau_t * (-a * phi1(a) + b * phi1(b));
+  for (int m = 0; m < M; ++m) {
+    const double e = exp(-p->omega[m] * D);
+    out[0] += p->theta[m] * (1.0 - e);
+    out[4 + 3 * m] = 1.0 - e;
+    out[5 + 3 * m] = p->theta[m] * D * e;
+    out[6 + 3 * m] = 0.0;
+  }
+}
+
+typedef struct {
+  int64_t n;
+  const double *x, *y, *t;
+  const oracle_mix_params *p;
+  int M, flags, want_grad;
+  int64_t lo, hi;
+  nsum ell, grad[3 + 3 * ORACLE_MIX_MAX];
+} mix_job;
+
+static void *run_mix_job(void *arg) {
+  mix_job *J = (mix_job *)arg;
+  const double tN = J->t[J->n - 1];
+  const int np = 3 + 3 * J->M;
+  memset(&J->ell, 0, sizeof J->ell);
+  memset(J->grad, 0, sizeof J->grad);
+  for (int64_t row = J->lo; row < J->hi; ++row) {
+    double rt[2 + 3 + 3 * ORACLE_MIX_MAX], ct[1 + 3 + 3 * ORACLE_MIX_MAX];
+    mix_row_terms(J->n, J->x, J->y, J->t, J->p, J->M, J->flags, row, J->want_grad, rt);
+    mix_compensator_terms(J->t[row], tN, J->p, J->M, ct);
+    const double lam = rt[0] + rt[1];
+    nsum_add(&J->ell, log(lam) - ct[0]);
+    if (J->want_grad)
+      for (int k = 0; k < np; ++k) nsum_add(&J->grad[k], rt[2 + k] / lam - ct[1 + k]);
+  }
+  return NULL;
+}
+
+/*
+ * Log-likelihood (Eq. 1 with the mixture trigger) and, if grad_out is not NULL, its gradient
+ * (3 + 3M entries in the order above). 1 <= M <= ORACLE_MIX_MAX. Returns 0, -1 (bad
+ * arguments), -2 (times not sorted), -3 (no memory).
+ */
+int oracle_loglik_mix(int64_t n, const double *x, const double *y, const double *t,
+                      const oracle_mix_params *p, int M, int flags, int nthreads,
+                      double *ell_out, double *grad_out) {
+  if (M < 1 || M > ORACLE_MIX_MAX || !p || !t || n < 1) return -1;
+  for (int64_t i = 1; i < n; ++i)
+    if (!(t[i] >= t[i - 1])) return -2;
+  const int np = 3 + 3 * M;
+  if (nthreads < 1) nthreads = 1;
+  if (nthreads > n) nthreads = (int)n;
+  mix_job *jobs = (mix_job *)calloc((size_t)nthreads, sizeof(mix_job));
+  pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
+  if (!jobs || !th) { free(jobs); free(th); return -3; }
+  for (int k = 0; k < nthreads; ++k) {
+    jobs[k].n = n; jobs[k].x = x; jobs[k].y = y; jobs[k].t = t; jobs[k].p = p;
+    jobs[k].M = M; jobs[k].flags = flags; jobs[k].want_grad = grad_out != NULL;
+    jobs[k].lo = n * k / nthreads;
+    jobs[k].hi = n * (k + 1) / nthreads;
+  }
+  for (int k = 1; k < nthreads; ++k) pthread_create(&th[k], NULL, run_mix_job, &jobs[k]);
+  run_mix_job(&jobs[0]);
+  for (int k = 1; k < nthreads; ++k) pthread_join(th[k], NULL);
+  nsum ell = {0, 0}, g[3 + 3 * ORACLE_MIX_MAX];
+  memset(g, 0, sizeof g);
+  for (int k = 0; k < nthreads; ++k) {
+    nsum_add(&ell, nsum_get(&jobs[k].ell));
+    for (int q = 0; q < np; ++q) nsum_add(&g[q], nsum_get(&jobs[k].grad[q]));
+  }
+  if (ell_out) *ell_out = nsum_get(&ell);
+  if (grad_out) for (int q = 0; q < np; ++q) grad_out[q] = nsum_get(&g[q]);
+  free(jobs);
+  free(th);
+  return 0;
+}
+
+/* The mixture intensity lambda(q) at query points (background over all events, every
+ * component's trigger over events strictly earlier than qt), for the integral pins. */
+int oracle_intensity_mix(int64_t n, const double *x, const double *y, const double *t,
+                         const oracle_mix_params *p, int M, int64_t m,
+                         const double *qx, const double *qy, const double *qt, double *out) {
+  if (n < 1 || m < 0 || !p || M < 1 || M > ORACLE_MIX_MAX) return -1;
+  const oracle_params bp = mix_background(p);
+  for (int64_t q = 0; q < m; ++q) {
+    nsum s = {0, 0};
+    for (int64_t j = 0; j < n; ++j) {
+      const double dx = qx[q] - x[j], dy = qy[q] - y[j], dt = qt[q] - t[j];
+      nsum_add(&s, background_term(&bp, dx, dy, dt));
+      if (t[j] < qt[q])
+        for (int c = 0; c < M; ++c)
+          nsum_add(&s, p->theta[c] * p->omega[c] / (p->h[c] * p->h[c]) * exp(-p->omega[c] * dt) *
+                           phi2(dx / p->h[c], dy / p->h[c]));
+    }
+    out[q] = nsum_get(&s);
+  }
+  return 0;
+}

@@ -3,7 +3,9 @@ as computed by the FP64 CPU oracle (oracle/, the only code this script calls bes
 input generator):
 
   tests/golden/small_cases.json   ell and gradient for small seeded event sets;
-  tests/golden/full_85k.json      ell and gradient for the N = 85,000 workload (--full).
+  tests/golden/full_85k.json      ell and gradient for the N = 85,000 workload (--full);
+  tests/golden/mix_cases.json     the mixture of triggering functions: small sets and the
+                                  N = 85,000 workload at one mixture vector (--mix).
 
 Each small case stores its inputs (x, y, t as float64), Theta, the flags, and the oracle's
 ell and gradient both for the inputs as given ("f64") and for the same inputs rounded to
@@ -80,6 +82,44 @@ def write_small():
     print("wrote", path, len(out["cases"]), "cases")
 
 
+# Mixture of triggering functions (the Discussion's extension): a short, narrow component (hours,
+# tens of metres: multi-shot events) and a long, wide one (days to weeks: retaliation).
+MIX_CASES = [  # (name, n, T, seed, mixture Theta)
+    ("mix_n2", 2, 10.0, 201, (0.02, 0.8, 10.0, 0.3, 24.0, 0.05, 0.2, 0.1, 0.3)),
+    ("mix_n50", 50, 100.0, 202, (0.02, 0.8, 10.0, 0.3, 24.0, 0.05, 0.2, 0.1, 0.3)),
+    ("mix_n300", 300, 300.0, 203, (0.05, 1.5, 20.0, 0.25, 6.0, 0.08, 0.3, 0.3, 0.4)),
+    ("mix_n777_ragged", 777, 500.0, 204, (0.01, 1.0, 30.0, 0.3, 24.0, 0.05, 0.2, 0.1, 0.3)),
+]
+MIX_FULL = (0.01, 1.0, 30.0, 0.3, 24.0, 0.05, 0.2, 0.1, 0.3)  # the 85k workload's mixture vector
+
+
+def write_mix():
+    out = {"source": "oracle/ (FP64, mixture of triggering functions), written by tests/golden/make_golden.py --mix",
+           "param_order": ["mu0", "tau_x", "tau_t", "theta_1", "omega_1", "h_1", "theta_2", "omega_2", "h_2"],
+           "cases": []}
+    for name, n, T, seed, th in MIX_CASES:
+        ev = synth.simulate(n, T, seed=seed)
+        case = {"name": name, "n": n, "T": T, "seed": seed, "theta": list(th),
+                "x": ev.x.tolist(), "y": ev.y.tolist(), "t": ev.t.tolist()}
+        for key, e in (("f64", ev), ("f32in", ev.rounded32())):
+            ll, g = oracle.loglik_mix(e.x, e.y, e.t, th, grad=True)
+            case[key] = {"loglik": float(ll), "grad": [float(v) for v in g]}
+        out["cases"].append(case)
+    ev = synth.large_workload()
+    t0 = time.time()
+    ll, g = oracle.loglik_mix(ev.x, ev.y, ev.t, MIX_FULL, grad=True)
+    out["full_85k"] = {"workload": {"generator": "synth.large_workload", "n": int(ev.n), "seed": 20051,
+                                    "sha256_xyt_f64le": events_digest(ev)},
+                       "theta": list(MIX_FULL), "loglik": float(ll), "grad": [float(v) for v in g]}
+    print("mix 85k", ll, f"{time.time() - t0:.1f} s", flush=True)
+    path = os.path.join(HERE, "mix_cases.json")
+    with open(path, "w") as fh:
+        head = {k: v for k, v in out.items() if k != "cases"}
+        fh.write("{\n" + ",\n".join(f" {json.dumps(k)}: {json.dumps(v)}" for k, v in head.items()))
+        fh.write(',\n "cases": [\n' + ",\n".join("  " + json.dumps(c) for c in out["cases"]) + "\n ]\n}\n")
+    print("wrote", path, len(out["cases"]), "cases")
+
+
 def write_full():
     ev = synth.large_workload()
     batch = synth.theta_batch(BATCH_K, seed=BATCH_SEED)
@@ -115,6 +155,8 @@ def write_full():
 def main():
     if "--full" in sys.argv:
         write_full()
+    elif "--mix" in sys.argv:
+        write_mix()
     else:
         write_small()
 
