@@ -66,6 +66,10 @@ static const double PI = 3.14159265358979323846;
 typedef struct { double s, c; } nsum;
 static void nsum_add(nsum *a, double v) {
   double t = a->s + v;
+  if (!isfinite(t)) {  /* an infinite term (log 0 = -inf): the sum is that infinity, uncompensated */
+    a->s = t;
+    return;
+  }
   if (fabs(a->s) >= fabs(v)) a->c += (a->s - t) + v;
   else a->c += (v - t) + a->s;
   a->s = t;

@@ -208,6 +208,17 @@ def test_exclude_self_removes_exactly_the_self_term(small_set):
     np.testing.assert_array_equal(a["xi"], b["xi"])
 
 
+def test_exclude_self_zero_intensity_gives_minus_infinity():
+    """With the self term excluded, a lone event (or the earliest of events far apart in time)
+    has lambda = 0: log 0 = -inf makes ell = -inf (Eq. 1), also with the trigger mixture."""
+    th = (0.05, 0.8, 10.0, 0.4, 0.7, 0.2)
+    assert oracle.loglik([1.0], [2.0], [3.0], th, flags=oracle.EXCLUDE_SELF) == -math.inf
+    assert math.isfinite(oracle.loglik([1.0], [2.0], [3.0], th))
+    mix = th + (0.3, 0.1, 0.5)
+    assert oracle.loglik_mix([1.0], [2.0], [3.0], mix, flags=oracle.EXCLUDE_SELF) == -math.inf
+    assert oracle.loglik([0.0, 0.0], [0.0, 0.0], [1.0, 1.0e6], th, flags=oracle.EXCLUDE_SELF) == -math.inf
+
+
 def test_probabilities_eq2(small_set):
     ev = small_set
     th = (0.05, 0.8, 10.0, 0.4, 0.7, 0.2)
