@@ -159,6 +159,29 @@ int hawkes_loglik(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *params,
 int hawkes_loglik_grad(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *params,
                        hawkes_mode mode, double *loglik_out, double grad_out[6]);
 
+/* ---- mixture of triggering functions --------------------------------------------------
+ * The paper's Discussion proposes a mixture of triggering functions for gunfire, combining a
+ * very short time frame (multi-shot events) with a longer one (retaliation over days to
+ * months). Read here as M components, each the triggering function of Section 2.1 with its own
+ * (theta_m, omega_m, h_m):
+ *   g(dx, dt) = sum_m theta_m omega_m / h_m^2 exp(-omega_m dt) phi2(dx / h_m),
+ * so the compensator's trigger part is sum_m theta_m (1 - exp(-omega_m (t_N - t_n))) and M = 1
+ * is the model above. The background, the flags, the exact-zero windows (taken at the longest
+ * trigger reach) and the shared background work as for hawkes_loglik_grad. */
+#define HAWKES_MIX_MAX 2
+typedef struct {
+  double mu0, tau_x, tau_t;
+  double theta[HAWKES_MIX_MAX], omega[HAWKES_MIX_MAX], h[HAWKES_MIX_MAX];
+} hawkes_mix_params;
+
+/* ell of Eq. 1 with the first m (1 or 2) components of `params`, and with want_grad its gradient:
+ * grad_out receives 3 + 3 m entries, (mu0, tau_x, tau_t, theta_1, omega_1, h_1[, theta_2,
+ * omega_2, h_2]); it may be NULL when want_grad is 0. Domain: as hawkes_params for each
+ * component (theta_m >= 0; omega_m, h_m > 0). Blocks like hawkes_loglik_grad. Errors as
+ * hawkes_loglik_grad. */
+int hawkes_loglik_mix(hawkes_ctx *ctx, int32_t set_id, const hawkes_mix_params *params, int m,
+                      hawkes_mode mode, int want_grad, double *loglik_out, double *grad_out);
+
 /* Asynchronous form for callers that keep results on the device: enqueue the
  * evaluation on the context's stream and return at once. `device_out` is a device
  * pointer to 7 doubles (ell, then the gradient if want_grad; the gradient entries

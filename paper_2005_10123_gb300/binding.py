@@ -33,8 +33,9 @@ EXPORTS = (
     "hawkes_release_events", "hawkes_set_info", "hawkes_loglik", "hawkes_loglik_grad",
     "hawkes_loglik_async", "hawkes_loglik_batch", "hawkes_event_terms", "hawkes_submit",
     "hawkes_poll", "hawkes_wait", "hawkes_stats", "hawkes_strerror", "hawkes_last_cuda_error",
-    "hawkes_loglik_noalloc", "hawkes_pair_work", "hawkes_poll_timed", "hawkes_pi_batch",
+    "hawkes_loglik_noalloc", "hawkes_pair_work", "hawkes_poll_timed", "hawkes_pi_batch", "hawkes_loglik_mix",
 )
+HAWKES_MIX_MAX = 2
 HAWKES_NOALLOC_MAX_EVENTS = 65536
 
 
@@ -49,6 +50,24 @@ class HawkesError(RuntimeError):
 
 class hawkes_params(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in ("mu0", "tau_x", "tau_t", "theta", "omega", "h")]
+
+
+class hawkes_mix_params(ctypes.Structure):
+    _fields_ = [("mu0", ctypes.c_double), ("tau_x", ctypes.c_double), ("tau_t", ctypes.c_double),
+                ("theta", ctypes.c_double * 2), ("omega", ctypes.c_double * 2), ("h", ctypes.c_double * 2)]
+
+
+def _mix_params(mix_theta):
+    """(mu0, tau_x, tau_t, theta_1, omega_1, h_1[, theta_2, omega_2, h_2]) -> (struct, m)."""
+    v = [float(a) for a in mix_theta]
+    if len(v) not in (6, 9):
+        raise ValueError("a mixture Theta has 3 + 3 m entries, m = 1 or 2")
+    m = (len(v) - 3) // 3
+    p = hawkes_mix_params()
+    p.mu0, p.tau_x, p.tau_t = v[:3]
+    for c in range(m):
+        p.theta[c], p.omega[c], p.h[c] = v[3 + 3 * c: 6 + 3 * c]
+    return p, m
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -92,6 +111,8 @@ def load(build_if_missing: bool = False, path: str | None = None):
         "hawkes_stats": [vp, ctypes.POINTER(i64)],
         "hawkes_loglik_noalloc": [vp, vp, vp, i64, P, ctypes.c_int, vp, vp],
         "hawkes_pair_work": [vp, i32, P, ctypes.c_int, ctypes.POINTER(i64)],
+        "hawkes_loglik_mix": [vp, i32, ctypes.POINTER(hawkes_mix_params), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                              _D, _D],
         "hawkes_poll_timed": [vp, u64, ctypes.POINTER(ctypes.c_int), _D, _D, ctypes.POINTER(i64),
                               ctypes.POINTER(i64)],
     }
@@ -196,6 +217,18 @@ class Context:
                                                 ctypes.byref(out), g.ctypes.data_as(_D)),
                     "hawkes_loglik_grad")
         return out.value, g
+
+    def hawkes_loglik_mix(self, set_id: int, mix_theta, mode: int = HAWKES_MIXED, want_grad: bool = True):
+        """ell with a mixture of m = 1 or 2 triggering functions; mix_theta = (mu0, tau_x, tau_t,
+        theta_1, omega_1, h_1[, theta_2, omega_2, h_2]). Returns ell, or (ell, grad[3 + 3 m])."""
+        p, m = _mix_params(mix_theta)
+        out = ctypes.c_double()
+        g = np.zeros(3 + 3 * m)
+        self._check(self.lib.hawkes_loglik_mix(self.h, int(set_id), ctypes.byref(p), m, int(mode),
+                                               1 if want_grad else 0, ctypes.byref(out),
+                                               g.ctypes.data_as(_D) if want_grad else None),
+                    "hawkes_loglik_mix")
+        return (out.value, g) if want_grad else out.value
 
     def hawkes_loglik_async(self, set_id: int, theta, mode: int, want_grad: bool, device_out_ptr: int):
         p = _params(theta)

@@ -36,7 +36,8 @@ constexpr int kFlights = 3;  // serving launches in flight at once
 constexpr double kLog2e = 1.4426950408889634074;
 
 int kind_of(int mode, int grad) { return mode == HAWKES_MIXED ? (grad ? 1 : 0) : 2; }
-int sums_of(int grad) { return grad ? kSumsGrad : kSumsLoglik; }
+// Pair sums per event of a request with m trigger components (partial-sum slot width / kRowTile).
+int sums_of(int grad, int m = 1) { return num_sums(grad != 0, m); }
 
 struct EventSetRec {
   int32_t id = 0;
@@ -82,7 +83,7 @@ struct Flight {
   std::vector<uint64_t> ids;
   void *ws = nullptr;
   size_t ws_bytes = 0;
-  double *host_out = nullptr;  // pinned, kFixedBytes: status words, then kMaxBatch * 8 results
+  double *host_out = nullptr;  // pinned, kFixedBytes: status words, then kMaxBatch * kOut results
   std::vector<EventSetRec *> sets;
 };
 
@@ -103,7 +104,7 @@ struct hawkes_ctx {
   std::map<int32_t, EventSetRec *> sets;
   int32_t next_set = 1;
   Workspace sync_ws;
-  double *pinned_out = nullptr;  // kFixedBytes: status words, then kMaxBatch * 8 results
+  double *pinned_out = nullptr;  // kFixedBytes: status words, then kMaxBatch * kOut results
   cudaMemPool_t pool = nullptr;   // device memory of event sets and serving workspaces (stream-ordered)
   char *stage = nullptr;          // pinned host word for the upload checks (guarded by mu)
   char *bounce = nullptr;         // pinned bounce buffer for per-event rows (guarded by mu)
@@ -262,6 +263,7 @@ int make_request(hawkes_ctx *ctx, const EventSetRec *S, const hawkes_params *p, 
   }
   exact_zero_cutoffs(p, mode, R->beta, &R->cut_early, &R->cut_late, &R->trig_cut);
   R->sym = use_symmetry(S, mode, flags) ? 1 : 0;
+  R->mix = 1;
   // fixed-point scale of the column sums: every event's total is at most npad (terms <= 1, and
   // q 2^-q <= 1), so round(total 2^F) stays below 2^62
   int bits = 0;
@@ -269,6 +271,33 @@ int make_request(hawkes_ctx *ctx, const EventSetRec *S, const hawkes_params *p, 
   R->fix_scale = std::ldexp(1.0f, 62 - bits);
   R->fix_inv = std::ldexp(1.0, bits - 62);
   (void)ctx;
+  return HAWKES_OK;
+}
+
+// Component 2 of a trigger mixture (the Discussion's extension; hawkes_loglik_mix): the second
+// triggering function's constants go to the launch (Batch::mix2), and the exact-zero windows take
+// the longer of the two trigger reaches. R holds the request made from component 1.
+int set_mixture(const hawkes_mix_params *m, int mode, Request *R, MixConst *M2) {
+  const double log2e = kLog2e, th2 = m->theta[1], om2 = m->omega[1], h2 = m->h[1];
+  if (!std::isfinite(th2) || th2 < 0.0 || !finite_pos(om2) || !finite_pos(h2)) return HAWKES_E_INVAL;
+  std::memset(M2, 0, sizeof(*M2));
+  M2->theta2 = th2;
+  M2->omega2 = om2;
+  M2->h2 = h2;
+  M2->dc2 = 1.0 / (2.0 * h2 * h2);
+  M2->k_cw2 = om2 / (6.28318530717958647693 * h2 * h2);
+  M2->inv_h2 = 1.0 / h2;
+  M2->inv_om2 = 1.0 / om2;
+  M2->wn2 = (float)(-om2 * log2e / (1.0 / R->tscale));
+  M2->cn2 = (float)(-log2e / (2.0 * h2 * h2));
+  if (mode == HAWKES_FP64) M2->wn2 = 0.f;  // the float64 kernel uses omega2 and dc2
+  else if (!std::isfinite(M2->wn2) || !(M2->cn2 < 0.f) || !std::isfinite(M2->cn2)) return HAWKES_E_INVAL;
+  hawkes_params p2{R->mu0, R->tau_x, R->tau_t, th2, om2, h2};
+  double early2, late2, trig2;
+  exact_zero_cutoffs(&p2, mode, R->beta, &early2, &late2, &trig2);
+  R->trig_cut = std::max(R->trig_cut, trig2);
+  R->cut_early = std::max(R->cut_early, early2);
+  R->mix = 2;
   return HAWKES_OK;
 }
 
@@ -285,10 +314,10 @@ size_t set_slots(const EventSetRec *S, int mode, int grad) {
   return (size_t)std::max(alone, pair_items(R));
 }
 
-size_t request_footprint(const EventSetRec *S, int mode, int grad) {
+size_t request_footprint(const EventSetRec *S, int mode, int grad, int m = 1) {
   const size_t items = set_slots(S, mode, grad);
-  size_t b = align_up(items * sums_of(grad) * kRowTile * sizeof(double), 256);
-  b += 2 * align_up((size_t)S->nrt * 8 * sizeof(double), 256);
+  size_t b = align_up(items * sums_of(grad, m) * kRowTile * sizeof(double), 256);
+  b += 2 * align_up((size_t)S->nrt * kOut * sizeof(double), 256);
   return b;
 }
 
@@ -310,7 +339,7 @@ size_t counter_bytes(const EventSetRec *S, int mode, int grad, int sym) {
 // that must start at 0; one copy of the first kHdrBytes + 64 k bytes brings the status words
 // and results back.
 constexpr size_t kHdrBytes = 256;
-constexpr size_t kOutBytes = (size_t)kMaxBatch * 8 * sizeof(double);
+constexpr size_t kOutBytes = (size_t)kMaxBatch * kOut * sizeof(double);
 constexpr size_t kFixedBytes = kHdrBytes + kOutBytes;
 static_assert(kHdrBytes >= kMaxBatch * sizeof(unsigned), "one status word per request");
 
@@ -320,10 +349,10 @@ int device_status(const void *header, int r) {
   return ((const unsigned *)header)[r] ? HAWKES_E_DEVICE : HAWKES_OK;
 }
 
-// Carve one request's workspace out of `base` (as sized by request_footprint) and its counters
-// out of `counters` (as sized by counter_bytes).
+// Carve one request's workspace out of `base` (as sized by request_footprint with the same m) and
+// its counters out of `counters` (as sized by counter_bytes).
 void bind_workspace(Request *R, const EventSetRec *S, int mode, int grad, char *base, double *out,
-                    unsigned *counters) {
+                    unsigned *counters, int m = 1) {
   if (R->sym) {
     const size_t m = merge_counter_bytes(S, mode, grad);
     R->rt_done = (unsigned *)((char *)counters + m);
@@ -332,9 +361,9 @@ void bind_workspace(Request *R, const EventSetRec *S, int mode, int grad, char *
   const size_t items = set_slots(S, mode, grad);
   size_t off = 0;
   R->partials = (double *)(base + off);
-  off += align_up(items * sums_of(grad) * kRowTile * sizeof(double), 256);
+  off += align_up(items * sums_of(grad, m) * kRowTile * sizeof(double), 256);
   R->comp = (double *)(base + off);
-  off += align_up((size_t)S->nrt * 8 * sizeof(double), 256);
+  off += align_up((size_t)S->nrt * kOut * sizeof(double), 256);
   R->rt_sum = (double *)(base + off);
   R->rt_count = counters;
   R->out = out;
@@ -447,19 +476,21 @@ int rows_to_host(hawkes_ctx *ctx, double *const *dst, const char *const *src, in
 }
 
 // Synchronous evaluation of k requests on one set (k = 1 for the single calls).
-// Results (7 doubles per request) land in host_out[8 * r]; device_out, if given
+// Results (ell and the gradient per request) land in host_out[kOut * r]; device_out, if given
 // (k = 1 only), receives them on the device instead and the call does not block.
 // mu_out / xi_out (k = 1) receive the per-event mu_n and xi_n of Eq. 2, pi_out (k rows of n)
 // the per-event pi_n of every request.
 // eval_sync with ctx->mu held and the set found. pi_dev (device, rows of row_bytes for each
 // parameter vector) receives pi instead of pi_out when given; with device_out the call
 // returns once the launch is enqueued.
+// mix (k = 1 only): a two-component trigger mixture; params[0] then holds its component 1.
 int eval_locked(hawkes_ctx *ctx, EventSetRec *S, int k, const hawkes_params *params, int mode, int grad,
                 double *host_out, double *device_out, double *mu_out, double *xi_out, double *pi_out,
-                char *pi_dev);
+                char *pi_dev, const hawkes_mix_params *mix = nullptr);
 
 int eval_sync(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_params *params, int mode, int grad,
-              double *host_out, double *device_out, double *mu_out, double *xi_out, double *pi_out) {
+              double *host_out, double *device_out, double *mu_out, double *xi_out, double *pi_out,
+              const hawkes_mix_params *mix = nullptr) {
   if (mode != HAWKES_FP64 && mode != HAWKES_MIXED) return HAWKES_E_INVAL;
   if (k < 1 || k > kMaxBatch) return HAWKES_E_INVAL;
   for (int r = 0; r < k; ++r)
@@ -467,13 +498,15 @@ int eval_sync(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_params *param
   std::lock_guard<std::mutex> lock(ctx->mu);
   EventSetRec *S = find_set(ctx, set_id);
   if (!S) return HAWKES_E_NOSET;
-  return eval_locked(ctx, S, k, params, mode, grad, host_out, device_out, mu_out, xi_out, pi_out, nullptr);
+  return eval_locked(ctx, S, k, params, mode, grad, host_out, device_out, mu_out, xi_out, pi_out, nullptr, mix);
 }
 
 int eval_locked(hawkes_ctx *ctx, EventSetRec *S, int k, const hawkes_params *params, int mode, int grad,
                 double *host_out, double *device_out, double *mu_out, double *xi_out, double *pi_out,
-                char *pi_dev) {
-  const size_t per = request_footprint(S, mode, grad);
+                char *pi_dev, const hawkes_mix_params *mix) {
+  if (mix && k != 1) return HAWKES_E_INVAL;
+  const int m = mix ? 2 : 1;  // trigger components
+  const size_t per = request_footprint(S, mode, grad, m);
   // per-event rows. mu and xi (one request) are written by the kernel straight into the
   // caller's host arrays where the device writes pageable host memory (0.50 -> 0.40 ms at
   // 85k). pi rows (k requests) are staged in device memory and copied out through the bounce
@@ -510,8 +543,11 @@ int eval_locked(hawkes_ctx *ctx, EventSetRec *S, int k, const hawkes_params *par
     const int q = order[r];
     if (int rc = make_request(ctx, S, &params[q], mode, grad, ctx->flags, &b->req[r])) return rc;
     b->req[r].sym = sym;
+    if (mix)
+      if (int rc = set_mixture(mix, mode, &b->req[r], &b->mix2)) return rc;
     bind_workspace(&b->req[r], S, mode, grad, req_base + (size_t)r * per,
-                   device_out ? device_out + 8 * q : outs + 8 * q, (unsigned *)(cnt_base + (size_t)r * cnt_one));
+                   device_out ? device_out + kOut * q : outs + kOut * q, (unsigned *)(cnt_base + (size_t)r * cnt_one),
+                   m);
     b->req[r].status = (unsigned *)base + q;
     if (grouped) {
       b->req[r].tscale = 1.0;
@@ -534,7 +570,7 @@ int eval_locked(hawkes_ctx *ctx, EventSetRec *S, int k, const hawkes_params *par
   HK_CUDA(ctx, cudaMemsetAsync(base, 0, kFixedBytes + cnt, ctx->stream));
   if (int rc = launch_batch(ctx, *b, mode, grad, ctx->stream)) return rc;
   if (device_out) return HAWKES_OK;
-  HK_CUDA(ctx, cudaMemcpyAsync(ctx->pinned_out, base, kHdrBytes + (size_t)k * 8 * sizeof(double),
+  HK_CUDA(ctx, cudaMemcpyAsync(ctx->pinned_out, base, kHdrBytes + (size_t)k * kOut * sizeof(double),
                                cudaMemcpyDeviceToHost, ctx->stream));
   const size_t nb = (size_t)S->n * sizeof(double);
   std::vector<double *> dst;
@@ -551,7 +587,7 @@ int eval_locked(hawkes_ctx *ctx, EventSetRec *S, int k, const hawkes_params *par
   HK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   for (int q = 0; q < k; ++q)
     if (int rc = device_status(ctx->pinned_out, q)) return rc;
-  std::memcpy(host_out, (const char *)ctx->pinned_out + kHdrBytes, (size_t)k * 8 * sizeof(double));
+  std::memcpy(host_out, (const char *)ctx->pinned_out + kHdrBytes, (size_t)k * kOut * sizeof(double));
   return HAWKES_OK;
 }
 
@@ -591,7 +627,7 @@ void reap_flights(hawkes_ctx *ctx) {
     const double *vals = (const double *)((const char *)F.host_out + kHdrBytes);
     for (size_t r = 0; r < F.ids.size(); ++r) {
       const int st = status == HAWKES_OK ? device_status(F.host_out, (int)r) : status;
-      complete_ticket(ctx, F.ids[r], st, vals + 8 * r);
+      complete_ticket(ctx, F.ids[r], st, vals + kOut * r);
     }
     {
       std::lock_guard<std::mutex> lock(ctx->mu);
@@ -674,14 +710,14 @@ bool launch_pending(hawkes_ctx *ctx, Flight &F) {
     for (size_t r = 0; r < take.size() && rc == HAWKES_OK; ++r) {
       TicketRec &T = ctx->tickets[take[r]];
       rc = make_request(ctx, sets[r], &T.p, mode, grad, T.flags, &b->req[r]);
-      bind_workspace(&b->req[r], sets[r], mode, grad, cur, outs + 8 * r, (unsigned *)cnt_cur);
+      bind_workspace(&b->req[r], sets[r], mode, grad, cur, outs + kOut * r, (unsigned *)cnt_cur);
       b->req[r].status = (unsigned *)base + r;
       cnt_cur += counter_bytes(sets[r], mode, grad, b->req[r].sym);
       cur += T.footprint;
     }
     if (rc == HAWKES_OK) rc = launch_batch(ctx, *b, mode, grad, F.stream);
     if (rc == HAWKES_OK) {
-      e = cudaMemcpyAsync(F.host_out, base, kHdrBytes + take.size() * 8 * sizeof(double), cudaMemcpyDeviceToHost,
+      e = cudaMemcpyAsync(F.host_out, base, kHdrBytes + take.size() * kOut * sizeof(double), cudaMemcpyDeviceToHost,
                           F.stream);
       if (e != cudaSuccess) rc = cuda_fail(ctx, e);
     }
@@ -1086,7 +1122,7 @@ int hawkes_loglik(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *params, 
                   double *loglik_out) {
   if (!ctx || !params || !loglik_out) return HAWKES_E_INVAL;
   cudaSetDevice(ctx->device);
-  double out[8];
+  double out[kOut];
   int rc = eval_sync(ctx, set_id, 1, params, mode, 0, out, nullptr, nullptr, nullptr, nullptr);
   if (rc == HAWKES_OK) *loglik_out = out[0];
   return rc;
@@ -1096,13 +1132,29 @@ int hawkes_loglik_grad(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *par
                        double *loglik_out, double grad_out[6]) {
   if (!ctx || !params || !loglik_out || !grad_out) return HAWKES_E_INVAL;
   cudaSetDevice(ctx->device);
-  double out[8];
+  double out[kOut];
   int rc = eval_sync(ctx, set_id, 1, params, mode, 1, out, nullptr, nullptr, nullptr, nullptr);
   if (rc == HAWKES_OK) {
     *loglik_out = out[0];
     for (int q = 0; q < 6; ++q) grad_out[q] = out[1 + q];
   }
   return rc;
+}
+
+int hawkes_loglik_mix(hawkes_ctx *ctx, int32_t set_id, const hawkes_mix_params *params, int m, hawkes_mode mode,
+                      int want_grad, double *loglik_out, double *grad_out) {
+  if (!ctx || !params || !loglik_out || (want_grad && !grad_out) || m < 1 || m > HAWKES_MIX_MAX)
+    return HAWKES_E_INVAL;
+  cudaSetDevice(ctx->device);
+  const hawkes_params p1{params->mu0, params->tau_x, params->tau_t, params->theta[0], params->omega[0], params->h[0]};
+  double out[kOut];
+  const int rc = eval_sync(ctx, set_id, 1, &p1, mode, want_grad ? 1 : 0, out, nullptr, nullptr, nullptr, nullptr,
+                           m > 1 ? params : nullptr);
+  if (rc != HAWKES_OK) return rc;
+  *loglik_out = out[0];
+  if (want_grad)
+    for (int q = 0; q < 3 + 3 * m; ++q) grad_out[q] = out[1 + q];
+  return HAWKES_OK;
 }
 
 int hawkes_loglik_async(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *params, hawkes_mode mode,
@@ -1117,13 +1169,13 @@ int hawkes_loglik_batch(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_par
   if (!ctx || !params || !loglik_out || (want_grad && !grad_out) || k < 1 || k > kMaxBatch)
     return HAWKES_E_INVAL;
   cudaSetDevice(ctx->device);
-  std::vector<double> out((size_t)k * 8);
+  std::vector<double> out((size_t)k * kOut);
   int rc = eval_sync(ctx, set_id, k, params, mode, want_grad ? 1 : 0, out.data(), nullptr, nullptr, nullptr, nullptr);
   if (rc != HAWKES_OK) return rc;
   for (int r = 0; r < k; ++r) {
-    loglik_out[r] = out[(size_t)r * 8];
+    loglik_out[r] = out[(size_t)r * kOut];
     if (want_grad)
-      for (int q = 0; q < 6; ++q) grad_out[(size_t)r * 6 + q] = out[(size_t)r * 8 + 1 + q];
+      for (int q = 0; q < 6; ++q) grad_out[(size_t)r * 6 + q] = out[(size_t)r * kOut + 1 + q];
   }
   return HAWKES_OK;
 }
@@ -1132,7 +1184,7 @@ int hawkes_event_terms(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *par
                        double *mu_out, double *xi_out, double *loglik_out) {
   if (!ctx || !params || !mu_out || !xi_out) return HAWKES_E_INVAL;
   cudaSetDevice(ctx->device);
-  double out[8];
+  double out[kOut];
   int rc = eval_sync(ctx, set_id, 1, params, mode, 0, out, nullptr, mu_out, xi_out, nullptr);
   if (rc == HAWKES_OK && loglik_out) *loglik_out = out[0];
   return rc;
@@ -1161,8 +1213,8 @@ int hawkes_pi_batch(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_params 
     HK_CUDA(ctx, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     ctx->chunk_ev.push_back(ev);
   }
-  if (ctx->used.load() + outs_off + (size_t)k * 8 * sizeof(double) > ctx->budget) return HAWKES_E_ADMISSION;
-  const size_t dev_bytes = outs_off + (size_t)k * 8 * sizeof(double);
+  if (ctx->used.load() + outs_off + (size_t)k * kOut * sizeof(double) > ctx->budget) return HAWKES_E_ADMISSION;
+  const size_t dev_bytes = outs_off + (size_t)k * kOut * sizeof(double);
   void *dev = nullptr;
   HK_CUDA(ctx, cudaMallocFromPoolAsync(&dev, dev_bytes, ctx->pool, ctx->stream));
   ctx->used += dev_bytes;
@@ -1172,7 +1224,7 @@ int hawkes_pi_batch(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_params 
   int launched = 0;
   for (int c = 0; c < chunks && rc == HAWKES_OK; ++c, ++launched) {
     const int r0 = c * kMaxBatch, m = std::min(kMaxBatch, k - r0);
-    rc = eval_locked(ctx, S, m, params + r0, mode, 0, nullptr, outs + (size_t)8 * r0, nullptr, nullptr, nullptr,
+    rc = eval_locked(ctx, S, m, params + r0, mode, 0, nullptr, outs + (size_t)kOut * r0, nullptr, nullptr, nullptr,
                      rows + (size_t)r0 * row_bytes);
     if (rc == HAWKES_OK && cudaEventRecord(ctx->chunk_ev[c], ctx->stream) != cudaSuccess) rc = HAWKES_E_CUDA;
   }
@@ -1189,7 +1241,7 @@ int hawkes_pi_batch(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_params 
     }
     rc = rows_to_host(ctx, dst.data(), src.data(), m, (size_t)S->n * sizeof(double), ctx->copy_stream);
   }
-  std::vector<double> host((size_t)k * 8);
+  std::vector<double> host((size_t)k * kOut);
   if (rc == HAWKES_OK && cudaMemcpyAsync(host.data(), outs, host.size() * sizeof(double), cudaMemcpyDeviceToHost,
                                          ctx->stream) != cudaSuccess)
     rc = HAWKES_E_CUDA;
@@ -1200,9 +1252,9 @@ int hawkes_pi_batch(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_params 
   if (e1 != cudaSuccess) return cuda_fail(ctx, e1);
   if (e2 != cudaSuccess) return cuda_fail(ctx, e2);
   for (int r = 0; r < k; ++r)  // the status words of earlier launches are cleared by later ones:
-    if (std::isnan(host[(size_t)8 * r])) return HAWKES_E_DEVICE;  // a NaN ell is a device wait that ran out
+    if (std::isnan(host[(size_t)kOut * r])) return HAWKES_E_DEVICE;  // a NaN ell is a device wait that ran out
   if (loglik_out)
-    for (int r = 0; r < k; ++r) loglik_out[r] = host[(size_t)8 * r];
+    for (int r = 0; r < k; ++r) loglik_out[r] = host[(size_t)kOut * r];
   return HAWKES_OK;
 }
 

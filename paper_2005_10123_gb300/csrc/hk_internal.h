@@ -34,6 +34,14 @@ constexpr int kEpiThreads = 256;                     // rows per CTA of the allo
 constexpr int kMaxBatch = 64;                        // requests per launch
 constexpr int kSumsLoglik = 2;                       // S_b, S_s
 constexpr int kSumsGrad = 6;                         // S_b, S_s, R_b, T_b, R_s, U_s
+// Mixture of triggering functions (the extension of the paper's Discussion): MIX components, each
+// with its own (theta, omega, h); component 2 adds a trigger sum (and two moments) per row.
+constexpr int kMixMax = 2;
+// Row sums of a kernel: S_b, S_s1[, S_s2] (loglik); S_b, S_s1, R_b, T_b, R_s1, U_s1[, S_s2, R_s2, U_s2]
+__host__ __device__ constexpr int num_sums(bool grad, int mix) { return grad ? 3 + 3 * mix : 1 + mix; }
+// Gradient entries: (mu0, tau_x, tau_t) and (theta, omega, h) per component.
+__host__ __device__ constexpr int num_grad(int mix) { return 3 + 3 * mix; }
+constexpr int kOut = 16;  // doubles per request in out, comp and rt_sum: ell, then up to 9 gradient terms
 constexpr int kFlagExcludeSelf = 1;                  // HAWKES_FLAG_EXCLUDE_SELF
 constexpr int kFlagDense = 2;                        // HAWKES_FLAG_DENSE
 constexpr int kFlagNoSymmetry = 4;                   // HAWKES_FLAG_NO_SYMMETRY
@@ -120,6 +128,7 @@ struct Request {
   float b2, b2_lo;       // beta^2 = b2 + b2_lo                  multiplies dt^2 (grouped kernel)
   float wn;              // -omega log2(e) / beta                multiplies scaled dt
   float cn;              // -log2(e) / (2 h^2)                   multiplies r^2
+  int mix;               // trigger components: 1 (Section 2.1) or 2 (mixture; Batch::mix2)
   // float64 pair constants (fp64 mode)
   double da;   // 1 / (2 tau_x^2)
   double db;   // 1 / (2 tau_t^2)
@@ -135,12 +144,12 @@ struct Request {
   double inv_tx, inv_tt, inv_h, inv_om;
   // workspace (device)
   double *partials;    // one slot of S * kRowTile float64 row sums per pair item
-  double *comp;        // nrt * 8: per row tile, the sums of Lambda_n and d Lambda_n / d Theta
+  double *comp;        // nrt * kOut: per row tile, the sums of Lambda_n and d Lambda_n / d Theta
                        // (written by the compensator items), or nullptr (not formed)
   unsigned *rt_count;  // request_counters(R) counters, zero at launch (fused epilogue): the
                        // merge-tree nodes of every row tile (2 slices from 2 rt slices), then
                        // the finished row-tile epilogues and compensator items
-  double *rt_sum;      // nrt * 8: per row tile, sum of log lambda_n and of the gradient terms
+  double *rt_sum;      // nrt * kOut: per row tile, sum of log lambda_n and of the gradient terms
   // symmetric background (see SymPlan): far column tiles share each background term between its
   // row and its column; column sums go to colfix as exact fixed-point integers
   int sym;             // 1: on (mixed, fused, set with a time table, no exclude-self/dense/no-symmetry)
@@ -149,7 +158,7 @@ struct Request {
   unsigned *rt_done;   // sym: per row tile, row-side root plus column contributions, zero at launch
   float fix_scale;     // 2^F: a float32 column sum v enters colfix as round(v 2^F)
   double fix_inv;      // 2^-F
-  double *out;         // 7 doubles: ell, d ell / d Theta
+  double *out;         // ell, then d ell / d Theta (6 entries, 9 for a two-component mixture)
   unsigned *status;    // device word, zero at launch: kStatusMergeTimeout if a device wait of
                        // this request ran out (its results are then NaN), or nullptr
   double *mu_out;      // optional per-event mu_n (n doubles) or nullptr
@@ -157,7 +166,17 @@ struct Request {
   double *pi_out;      // optional per-event pi_n = xi_n / lambda_n (n doubles) or nullptr
 };
 
+// Component 2 of a two-component trigger mixture. A mixture launch holds one request, so its
+// second component's constants sit in the Batch (kernel parameters are limited to 32 KB).
+struct MixConst {
+  float wn2, cn2;          // as Request::wn, cn
+  double theta2, omega2, h2;
+  double dc2;              // 1 / (2 h_2^2)
+  double k_cw2, inv_h2, inv_om2;
+};
+
 struct Batch {
+  MixConst mix2;  // used when a request has mix = 2
   int nreq;
   int total_items;  // pair-kernel items (= CTAs) over all requests
   int mode;         // 0 fp64, 1 mixed (one mode per launch)
@@ -387,16 +406,33 @@ __device__ __forceinline__ double std_normal_pdf(double u) {
 
 // Compensator of Section 2.1 for the rows of row tile rt, summed in a fixed order over the
 // CTA: Lambda_n = mu0 (Phi((t_N - t_n)/tau_t) - Phi(-t_n/tau_t)) + theta (1 - e^{-omega (t_N -
-// t_n)}) and, with `grad`, its derivatives with respect to (mu0, tau_x, tau_t, theta, omega,
-// h). Thread 0 writes the 7 sums to R.comp[8 rt ...]. Called by every thread of the CTA of a
-// compensator item; these items come first in a request, so their float64 work overlaps the
+// t_n)}) (plus theta_2 (1 - e^{-omega_2 (t_N - t_n)}) for a mixture) and, with `grad`, its
+// derivatives in the gradient order (mu0, tau_x, tau_t, theta, omega, h[, theta_2, omega_2,
+// h_2]). Thread 0 writes the sums to R.comp[kOut rt ...]. Called by every thread of the CTA of
+// a compensator item; these items come first in a request, so their float64 work overlaps the
 // pair items instead of ending the launch.
-template <typename TT>
-__device__ void compensator_tile(const Request &R, const TT *t, int rt, bool grad) {
-  __shared__ double red[kMaxCtaWarps][8];
+// Scratch of the CTA-wide float64 reductions (compensator_tile, rowtile_reduce, finish_request):
+// one array per kernel, reused in turn (each use starts after a barrier and ends with one), so
+// that the three cost the pair kernels' occupancy one small array. Row w of the warps' partial
+// sums starts at w * kRedWidth; the totals follow the kMaxCtaWarps rows.
+constexpr int kRedWidth = 1 + num_grad(kMixMax);  // most values reduced at once
+__device__ __forceinline__ double *reduce_scratch() {
+  __shared__ double buf[(kMaxCtaWarps + 1) * kRedWidth];
+  return buf;
+}
+
+template <int MIX = 1, typename TT>
+__device__ void compensator_tile(const Request &R, const MixConst &M2, const TT *t, int rt, bool grad) {
+  constexpr int NC = 1 + num_grad(MIX);
+  static_assert(NC <= kRedWidth, "reduction scratch too narrow");
+  double *red = reduce_scratch();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = (blockDim.x + 31) >> 5;
   const double mu0 = R.mu0, th = R.theta, om = R.omega, tN = R.t_last, inv_tt = R.inv_tt;
-  double v[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  const double th2 = M2.theta2, om2 = M2.omega2;
+  const int nv = grad ? NC : 1;
+  double v[NC];
+#pragma unroll
+  for (int q = 0; q < NC; ++q) v[q] = 0.0;
   const int end = min((rt + 1) * kRowTile, R.set.n);
   for (int i = rt * kRowTile + tid; i < end; i += blockDim.x) {
     const double tn = (double)t[i];
@@ -415,19 +451,27 @@ __device__ void compensator_tile(const Request &R, const TT *t, int rt, bool gra
       v[4] += 1.0 - e;
       v[5] += th * D * e;
     }
+    if constexpr (MIX > 1) {  // component 2 of a mixture
+      const double e2 = om2 * D > 746.0 ? 0.0 : exp(-om2 * D);
+      v[0] += th2 * (1.0 - e2);
+      if (grad) {
+        v[7] += 1.0 - e2;
+        v[8] += th2 * D * e2;
+      }
+    }
   }
 #pragma unroll
-  for (int q = 0; q < 7; ++q) {
+  for (int q = 0; q < NC; ++q) {
     double x = v[q];
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
-    if (lane == 0) red[warp][q] = x;
+    if (lane == 0) red[warp * kRedWidth + q] = x;
   }
   __syncthreads();
-  if (tid < 7) {
+  if (tid < nv) {
     double x = 0.0;
-    for (int w = 0; w < nw; ++w) x += red[w][tid];
-    R.comp[(size_t)rt * 8 + tid] = x;
+    for (int w = 0; w < nw; ++w) x += red[w * kRedWidth + tid];
+    R.comp[(size_t)rt * kOut + tid] = x;
   }
   __syncthreads();
 }
@@ -436,10 +480,11 @@ __device__ void compensator_tile(const Request &R, const TT *t, int rt, bool gra
 // finishes the last of them writes ell = sum over row tiles of (rt_sum - comp) and the
 // gradient, in a fixed order, to R.out. Called by every thread of the CTA after its results
 // are written.
-template <bool GRAD>
+template <bool GRAD, int MIX = 1>
 __device__ void finish_request(const Request &R) {
-  constexpr int NV = GRAD ? 7 : 1;
-  __shared__ double red3[kMaxCtaWarps][8];
+  constexpr int NV = GRAD ? 1 + num_grad(MIX) : 1;
+  static_assert(NV <= kRedWidth, "reduction scratch too narrow");
+  double *red3 = reduce_scratch();
   __shared__ int s_final;
   const SetView &S = R.set;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = (blockDim.x + 31) >> 5;
@@ -454,17 +499,17 @@ __device__ void finish_request(const Request &R) {
     for (int q = 0; q < NV; ++q) {
       double x = 0.0;
       for (int r = tid; r < S.nrt; r += blockDim.x) {
-        x += __ldcg(R.rt_sum + (size_t)r * 8 + q);
-        if (R.comp) x -= __ldcg(R.comp + (size_t)r * 8 + q);
+        x += __ldcg(R.rt_sum + (size_t)r * kOut + q);
+        if (R.comp) x -= __ldcg(R.comp + (size_t)r * kOut + q);
       }
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
-      if (lane == 0) red3[warp][q] = x;
+      if (lane == 0) red3[warp * kRedWidth + q] = x;
     }
     __syncthreads();
     if (tid < NV) {
       double x = 0.0;
-      for (int w = 0; w < nw; ++w) x += red3[w][tid];
+      for (int w = 0; w < nw; ++w) x += red3[w * kRedWidth + tid];
       R.out[tid] = x;
     }
   }
@@ -588,10 +633,15 @@ __device__ int merge_tree(const Request &R, const PairItem &it, Store store, Mer
 // Eq. 2 when the request asks for them. Every gradient term (d lambda_i / d Theta) / lambda_i
 // is a fixed linear combination of these six ratios, so rowtile_reduce applies the Theta
 // factors once per row tile (grad_from_moments).
-template <bool GRAD>
-__device__ __forceinline__ void row_terms(const Request &R, int i, const double *sums, double *v) {
+// With a two-component mixture (MIX = 2) the row sums carry S_s2 (and R_s2, U_s2) after the
+// single-kernel ones, lambda_i = A S_b + C S_s1 + C_2 S_s2, and v[1 ..] takes all nine ratios.
+template <bool GRAD, int MIX = 1>
+__device__ __forceinline__ void row_terms(const Request &R, const MixConst &M2, int i, const double *sums, double *v) {
+  constexpr int NS = num_sums(GRAD, MIX);
   const double A = R.mu0 * R.k_ab, C = R.theta * R.k_cw;
-  const double mu = A * sums[0], xi = C * sums[1], lam = mu + xi;
+  double xi = C * sums[1];
+  if (MIX > 1) xi = fma(M2.theta2 * M2.k_cw2, sums[GRAD ? 6 : 2], xi);
+  const double mu = A * sums[0], lam = mu + xi;
   if (R.mu_out) R.mu_out[i] = mu;
   if (R.xi_out) R.xi_out[i] = xi;
   if (R.pi_out) R.pi_out[i] = xi / lam;
@@ -599,7 +649,7 @@ __device__ __forceinline__ void row_terms(const Request &R, int i, const double 
   if (GRAD) {
     const double inv = 1.0 / lam;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) v[1 + k] = fma(sums[k], inv, v[1 + k]);
+    for (int k = 0; k < NS; ++k) v[1 + k] = fma(sums[k], inv, v[1 + k]);
   }
 }
 
@@ -611,7 +661,10 @@ __device__ __forceinline__ void row_terms(const Request &R, int i, const double 
 //   d/d theta  = k_cw m_Ss
 //   d/d omega  = C (m_Ss / omega - m_Us)
 //   d/d h      = C/h (-2 m_Ss + m_Rs / h^2)
-__device__ __forceinline__ void grad_from_moments(const Request &R, const double *m, double *g) {
+// (component 2 of a mixture, from m[6..8] = S_s2, R_s2, U_s2 ratios: the same three formulas with
+// theta_2, omega_2, h_2 into g[6..8]).
+template <int MIX = 1>
+__device__ __forceinline__ void grad_from_moments(const Request &R, const MixConst &M2, const double *m, double *g) {
   const double A = R.mu0 * R.k_ab, C = R.theta * R.k_cw;
   const double itx = R.inv_tx, itt = R.inv_tt, ih = R.inv_h, iom = R.inv_om;
   const double Sb = m[0], Ss = m[1], Rb = m[2], Tb = m[3] * R.tscale * R.tscale, Rs = m[4], Us = m[5] * R.tscale;
@@ -621,41 +674,49 @@ __device__ __forceinline__ void grad_from_moments(const Request &R, const double
   g[3] = R.k_cw * Ss;
   g[4] = C * (Ss * iom - Us);
   g[5] = C * ih * (-2.0 * Ss + Rs * ih * ih);
+  if (MIX > 1) {
+    const double C2 = M2.theta2 * M2.k_cw2, ih2 = M2.inv_h2;
+    const double Ss2 = m[6], Rs2 = m[7], Us2 = m[8] * R.tscale;
+    g[6] = M2.k_cw2 * Ss2;
+    g[7] = C2 * (Ss2 * M2.inv_om2 - Us2);
+    g[8] = C2 * ih2 * (-2.0 * Ss2 + Rs2 * ih2 * ih2);
+  }
 }
 
 // End of row tile rt's epilogue: sum every thread's row terms v in a fixed order (warp tree,
 // warps in order), turn the moment ratios into gradient terms (grad_from_moments), store
 // them in R.rt_sum, then finish_request. Called by every thread of the CTA.
-template <bool GRAD>
-__device__ void rowtile_reduce(const Request &R, int rt, const double *v) {
-  constexpr int NV = GRAD ? 7 : 1;
-  __shared__ double red2[kMaxCtaWarps][8];
-  __shared__ double tot[8];
+template <bool GRAD, int MIX = 1>
+__device__ void rowtile_reduce(const Request &R, const MixConst &M2, int rt, const double *v) {
+  constexpr int NV = GRAD ? 1 + num_sums(true, MIX) : 1;  // log lambda and the moment ratios
+  static_assert(NV <= kRedWidth, "reduction scratch too narrow");
+  double *red2 = reduce_scratch(), *tot = red2 + kMaxCtaWarps * kRedWidth;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();  // the scratch's previous use is over
 #pragma unroll
   for (int q = 0; q < NV; ++q) {
     double x = v[q];
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
-    if (lane == 0) red2[warp][q] = x;
+    if (lane == 0) red2[warp * kRedWidth + q] = x;
   }
   __syncthreads();
   if (tid < NV) {
     double x = 0.0;
-    for (int w = 0; w < nw; ++w) x += red2[w][tid];
+    for (int w = 0; w < nw; ++w) x += red2[w * kRedWidth + tid];
     tot[tid] = x;
   }
   __syncthreads();
   if (tid == 0) {
-    R.rt_sum[(size_t)rt * 8] = tot[0];
+    R.rt_sum[(size_t)rt * kOut] = tot[0];
     if (GRAD) {
-      double g[6];
-      grad_from_moments(R, tot + 1, g);
+      double g[num_grad(MIX)];
+      grad_from_moments<MIX>(R, M2, tot + 1, g);
 #pragma unroll
-      for (int k = 0; k < 6; ++k) R.rt_sum[(size_t)rt * 8 + 1 + k] = g[k];
+      for (int k = 0; k < num_grad(MIX); ++k) R.rt_sum[(size_t)rt * kOut + 1 + k] = g[k];
     }
   }
-  finish_request<GRAD>(R);
+  finish_request<GRAD, MIX>(R);
 }
 #endif
 

@@ -29,13 +29,16 @@ constexpr int kChunk64 = HK_CHUNK64;
 constexpr int kChunksPerTile64 = kColTile / kChunk64;
 static_assert(kColTile % kChunk64 == 0, "column chunks must tile a column tile");
 
-template <int KIND, bool GRAD>
+// With a two-component trigger mixture (MIX = 2) component 2 (omega2, dc2) goes to the sums after
+// the single-kernel ones.
+template <int KIND, bool GRAD, int MIX>
 __device__ __forceinline__ void tile_pass64(const double *__restrict__ sx, const double *__restrict__ sy,
                                             const double *__restrict__ st, const double (&X)[4],
                                             const double (&Y)[4], const double (&T)[4], const int (&LO)[4],
                                             int row_a0, int c0, int j0, int j1, bool excl, double da, double db,
-                                            double dc, double omega,
-                                            double (&acc)[GRAD ? kSumsGrad : kSumsLoglik][4]) {
+                                            double dc, double omega, double dc2, double omega2,
+                                            double (&acc)[num_sums(GRAD, MIX)][4]) {
+  constexpr int S2 = GRAD ? 6 : 2;
 #pragma unroll 2
   for (int j = j0; j < j1; ++j) {
     const double cx = sx[j], cy = sy[j], ctj = st[j];
@@ -62,15 +65,24 @@ __device__ __forceinline__ void tile_pass64(const double *__restrict__ sx, const
           acc[4][k] = __fma_rn(r2, es, acc[4][k]);
           acc[5][k] = __fma_rn(dt, es, acc[5][k]);
         }
+        if (MIX > 1) {
+          double es2 = exp(-__fma_rn(omega2, dt, __dmul_rn(r2, dc2)));
+          if (KIND == 2) es2 = (col < LO[k]) ? es2 : 0.0;
+          acc[S2][k] += es2;
+          if (GRAD) {
+            acc[S2 + 1][k] = __fma_rn(r2, es2, acc[S2 + 1][k]);
+            acc[S2 + 2][k] = __fma_rn(dt, es2, acc[S2 + 2][k]);
+          }
+        }
       }
     }
   }
 }
 
-template <bool GRAD>
+template <bool GRAD, int MIX>
 __device__ void run_piece64(const Batch &B, const Request &R, const PairItem &it, int4 piece, double (*sx)[kColTile],
                             double (*sy)[kColTile], double (*st)[kColTile]) {
-  constexpr int NS = GRAD ? kSumsGrad : kSumsLoglik;
+  constexpr int NS = num_sums(GRAD, MIX);
   const SetView &S = R.set;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int row0 = piece.x * kRowTile;
@@ -79,10 +91,11 @@ __device__ void run_piece64(const Batch &B, const Request &R, const PairItem &it
   const int lo_wa = S.lo64[wa], lo_wb = S.lo64[wb];
   const bool excl = (R.flags & 1) != 0;
   const double da = R.da, db = R.db, dc = R.dc, omega = R.omega;
+  const double dc2 = B.mix2.dc2, omega2 = B.mix2.omega2;
   // exact-zero gaps (days) between the warp's earliest row and a tile's latest column: the
   // background exponent exceeds 805 past bg_gap, the trigger exponent past trig_gap (exp
   // returns +0 far below -745); one percent of margin
-  const double bg_gap = 1.01 * sqrt(805.0 / db), trig_gap = 1.01 * 805.0 / omega;
+  const double bg_gap = 1.01 * sqrt(805.0 / db), trig_gap = 1.01 * 805.0 / (MIX > 1 ? fmin(omega, omega2) : omega);
 
   double X[4], Y[4], T[4];
   int LO[4];
@@ -135,13 +148,17 @@ __device__ void run_piece64(const Batch &B, const Request &R, const PairItem &it
     if (excl && c0 <= wb && c1 > wa) kind = 2;
     const int row_a0 = wa + lane;
     if (kind == 0)
-      tile_pass64<0, GRAD>(sx[buf], sy[buf], st[buf], X, Y, T, LO, row_a0, c0, j0, j1, excl, da, db, dc, omega, acc);
+      tile_pass64<0, GRAD, MIX>(sx[buf], sy[buf], st[buf], X, Y, T, LO, row_a0, c0, j0, j1, excl, da, db, dc, omega,
+                                dc2, omega2, acc);
     else if (kind == 1)
-      tile_pass64<1, GRAD>(sx[buf], sy[buf], st[buf], X, Y, T, LO, row_a0, c0, j0, j1, excl, da, db, dc, omega, acc);
+      tile_pass64<1, GRAD, MIX>(sx[buf], sy[buf], st[buf], X, Y, T, LO, row_a0, c0, j0, j1, excl, da, db, dc, omega,
+                                dc2, omega2, acc);
     else if (kind == 2)
-      tile_pass64<2, GRAD>(sx[buf], sy[buf], st[buf], X, Y, T, LO, row_a0, c0, j0, j1, excl, da, db, dc, omega, acc);
+      tile_pass64<2, GRAD, MIX>(sx[buf], sy[buf], st[buf], X, Y, T, LO, row_a0, c0, j0, j1, excl, da, db, dc, omega,
+                                dc2, omega2, acc);
     else if (kind == 3)
-      tile_pass64<3, GRAD>(sx[buf], sy[buf], st[buf], X, Y, T, LO, row_a0, c0, j0, j1, excl, da, db, dc, omega, acc);
+      tile_pass64<3, GRAD, MIX>(sx[buf], sy[buf], st[buf], X, Y, T, LO, row_a0, c0, j0, j1, excl, da, db, dc, omega,
+                                dc2, omega2, acc);
     if (ct + 1 < ct_end) stage(ct + 1, buf ^ 1);
     __syncthreads();
   }
@@ -167,7 +184,7 @@ __device__ void run_piece64(const Batch &B, const Request &R, const PairItem &it
   const int root = merge_tree<true>(R, it, store, merge);
   if (root < 0) mark_timeout(R);
   if (root <= 0) return;
-  double v[GRAD ? 7 : 1] = {};
+  double v[GRAD ? 1 + NS : 1] = {};
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const int i = row0 + warp * kWarpRows64 + lane + 32 * k;
@@ -175,13 +192,13 @@ __device__ void run_piece64(const Batch &B, const Request &R, const PairItem &it
       double sums[NS];
 #pragma unroll
       for (int s = 0; s < NS; ++s) sums[s] = acc[s][k];
-      row_terms<GRAD>(R, i, sums, v);
+      row_terms<GRAD, MIX>(R, B.mix2, i, sums, v);
     }
   }
-  rowtile_reduce<GRAD>(R, piece.x, v);
+  rowtile_reduce<GRAD, MIX>(R, B.mix2, piece.x, v);
 }
 
-template <bool GRAD>
+template <bool GRAD, int MIX>
 __global__ void __launch_bounds__(kThreads64, HK_FP64_MIN_CTAS) pair_fp64_kernel(const __grid_constant__ Batch B) {
   __shared__ double sx[2][kColTile], sy[2][kColTile], st[2][kColTile];
   __shared__ int2 s_win;
@@ -189,8 +206,8 @@ __global__ void __launch_bounds__(kThreads64, HK_FP64_MIN_CTAS) pair_fp64_kernel
   const Request &R = B.req[find_request(B, item)];
   const int local = item - R.item_begin, nc = comp_items(R);
   if (local < nc) {  // compensator item of row tile `local`
-    compensator_tile(R, R.set.t64, local, GRAD);
-    if (B.fused) finish_request<GRAD>(R);
+    compensator_tile<MIX>(R, B.mix2, R.set.t64, local, GRAD);
+    if (B.fused) finish_request<GRAD, MIX>(R);
     return;
   }
   const PairItem it = item_at(R, local - nc);
@@ -208,15 +225,21 @@ __global__ void __launch_bounds__(kThreads64, HK_FP64_MIN_CTAS) pair_fp64_kernel
   const int cw0 = w.x * kChunksPerTile64, width = (w.y - w.x) * kChunksPerTile64;
   const int c_begin = cw0 + (int)((long long)width * l0 / ns);
   const int c_end = cw0 + (int)((long long)width * l1 / ns);
-  run_piece64<GRAD>(B, R, it, make_int4(rt, c_begin, c_end, 0), sx, sy, st);
+  run_piece64<GRAD, MIX>(B, R, it, make_int4(rt, c_begin, c_end, 0), sx, sy, st);
 }
 
 }  // namespace
 
 cudaError_t launch_pair_fp64(const Batch &b, bool grad, cudaStream_t s) {
   if (b.total_items < 1) return cudaErrorInvalidValue;
-  if (grad) pair_fp64_kernel<true><<<b.total_items, kThreads64, 0, s>>>(b);
-  else pair_fp64_kernel<false><<<b.total_items, kThreads64, 0, s>>>(b);
+  if (b.req[0].mix > 1) {  // a trigger mixture (one request per launch)
+    if (grad) pair_fp64_kernel<true, 2><<<b.total_items, kThreads64, 0, s>>>(b);
+    else pair_fp64_kernel<false, 2><<<b.total_items, kThreads64, 0, s>>>(b);
+  } else if (grad) {
+    pair_fp64_kernel<true, 1><<<b.total_items, kThreads64, 0, s>>>(b);
+  } else {
+    pair_fp64_kernel<false, 1><<<b.total_items, kThreads64, 0, s>>>(b);
+  }
   return cudaGetLastError();
 }
 
@@ -224,8 +247,8 @@ int fp64_chunks_per_tile() { return kChunksPerTile64; }
 
 int occupancy_pair_fp64(bool grad) {
   int n = 0;
-  if (grad) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_fp64_kernel<true>, kThreads64, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_fp64_kernel<false>, kThreads64, 0);
+  if (grad) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_fp64_kernel<true, 1>, kThreads64, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_fp64_kernel<false, 1>, kThreads64, 0);
   return n;
 }
 

@@ -3,8 +3,8 @@
 //
 // A batch of K parameter vectors on one set (Section 2.2: many MH chains, or one chain's
 // proposals) shares every pair's geometry. For each (row n, column n') the CTA forms once
-//   dx, dy, r^2 = dx^2 + dy^2, dt = t_n - t_n' (days, relative to the row tile's first event),
-//   dt^2
+//   dx, dy, r^2 = dx^2 + dy^2, dt = t_n - t_n' (days, the difference of the stored float32
+//   times, rounded once: exact where t_n' >= t_n / 2), dt^2
 // and then, for each request k of its group, the terms of Section 2.1, Eq. 1 from those:
 //   e_b = 2^-(a2_k r^2 + b2_k dt^2),  a2 = log2(e)/(2 tau_x^2), b2 = log2(e)/(2 tau_t^2)
 //   e_s = 2^(cn_k r^2 + wn_k dt),     cn = -log2(e)/(2 h^2),    wn = -omega log2(e)
@@ -38,7 +38,7 @@ namespace {
 
 constexpr int kGThreads = kRowTile / 2;  // two rows (one packed pair) per thread
 constexpr int kGWarpRows = 64;           // consecutive rows per warp
-constexpr float kPadRaw = 1.0e18f;       // relative time of a padded event: dt^2 stays finite
+constexpr float kPadRaw = 1.0e18f;       // time of a padded event: dt^2 stays finite
 static_assert(kGThreads <= 32 * kMaxCtaWarps, "CTA too wide");
 // exact-zero gaps (scaled units, as in the single-request kernel)
 constexpr float kGBgZero = 11.5157f;    // 1.01 * sqrt(130)
@@ -74,7 +74,7 @@ __device__ __forceinline__ void gtile_pass(const float4 *__restrict__ sxy, const
 #pragma unroll 2
   for (int j = 0; j < kColTile; ++j) {
     const float4 c = sxy[j];  // {-x, -x, -y, -y}
-    const float2 ct = st[j];  // {-t, -t} relative to the row tile's first event
+    const float2 ct = st[j];  // {-t, -t}, the stored times
     const float2 dx = __fadd2_rn(X, make_float2(c.x, c.y));
     const float2 dy = __fadd2_rn(Y, make_float2(c.z, c.w));
     const float2 rho = __ffma2_rn(dy, dy, __fmul2_rn(dx, dx));
@@ -125,11 +125,11 @@ struct GStage {
   float2 st[2][kColTile];
 };
 
-__device__ __forceinline__ void gstage(const SetView &S, int ct, float t0, float4 *sxy, float2 *st) {
+__device__ __forceinline__ void gstage(const SetView &S, int ct, float4 *sxy, float2 *st) {
   for (int jj = threadIdx.x; jj < kColTile; jj += kGThreads) {
     const int j = ct * kColTile + jj;
     const float x = __ldg(S.x32 + j), y = __ldg(S.y32 + j);
-    const float t = j < S.n ? __ldg(S.t32 + j) - t0 : kPadRaw;
+    const float t = j < S.n ? __ldg(S.t32 + j) : kPadRaw;
     sxy[jj] = make_float4(-x, -x, -y, -y);
     st[jj] = make_float2(-t, -t);
   }
@@ -142,14 +142,13 @@ __device__ void group_item(const Batch &B, int leader, int gsize, const PairItem
   const SetView &S = R0.set;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int rt = it.rt, row0 = rt * kRowTile, n = S.n;
-  const float t0 = S.t32[row0];
   const int wa = row0 + warp * kGWarpRows, wb = wa + kGWarpRows - 1;
   const int lo_wa = S.lo32[wa], lo_wb = S.lo32[wb];
   const bool excl = (R0.flags & kFlagExcludeSelf) != 0;
   const int ra = wa + lane, rb = ra + 32;
   const float2 X = make_float2(S.x32[ra], S.x32[rb]);
   const float2 Y = make_float2(S.y32[ra], S.y32[rb]);
-  const float2 T = make_float2(ra < n ? S.t32[ra] - t0 : kPadRaw, rb < n ? S.t32[rb] - t0 : kPadRaw);
+  const float2 T = make_float2(ra < n ? S.t32[ra] : kPadRaw, rb < n ? S.t32[rb] : kPadRaw);
   const int lo_a = S.lo32[ra], lo_b = S.lo32[rb];
 
   // per-request constants, the group's column window (union) and its exact-zero gaps (days)
@@ -193,7 +192,7 @@ __device__ void group_item(const Batch &B, int leader, int gsize, const PairItem
   const float t_first = __shfl_sync(0xffffffffu, T.x, 0);  // the warp's first and last rows
   const float t_last = __shfl_sync(0xffffffffu, T.y, 31);
   if (c_begin < c_end) {
-    gstage(S, c_begin, t0, sg.sxy[0], sg.st[0]);
+    gstage(S, c_begin, sg.sxy[0], sg.st[0]);
     __syncthreads();
   }
   for (int ct = c_begin, k = 0; ct < c_end; ++ct, ++k) {
@@ -219,7 +218,7 @@ __device__ void group_item(const Batch &B, int leader, int gsize, const PairItem
       gtile_pass<2, G, GRAD>(sg.sxy[buf], sg.st[buf], X, Y, T, lo_a, lo_b, ra, c0, excl, K, acc);
     else if (kind == 3)
       gtile_pass<3, G, GRAD>(sg.sxy[buf], sg.st[buf], X, Y, T, lo_a, lo_b, ra, c0, excl, K, acc);
-    if (ct + 1 < c_end) gstage(S, ct + 1, t0, sg.sxy[buf ^ 1], sg.st[buf ^ 1]);
+    if (ct + 1 < c_end) gstage(S, ct + 1, sg.sxy[buf ^ 1], sg.st[buf ^ 1]);
     __syncthreads();
   }
 
@@ -272,10 +271,10 @@ __device__ void group_item(const Batch &B, int leader, int gsize, const PairItem
         double sums[NS];
 #pragma unroll
         for (int s = 0; s < NS; ++s) sums[s] = gsum[(k * NS + s) * kRowTile + rows[h]];
-        row_terms<GRAD>(R, i, sums, v);
+        row_terms<GRAD>(R, B.mix2, i, sums, v);
       }
     }
-    rowtile_reduce<GRAD>(R, rt, v);
+    rowtile_reduce<GRAD>(R, B.mix2, rt, v);
   }
 }
 
@@ -286,7 +285,7 @@ __global__ void __launch_bounds__(kGThreads, HK_GROUP_MIN_CTAS) pair_group_kerne
   const int nrt = B.req[0].set.nrt;
   if (item < B.comp_total) {  // compensator item of (request item / nrt, row tile item % nrt)
     const Request &R = B.req[item / nrt];
-    compensator_tile(R, R.set.t32, item % nrt, GRAD);
+    compensator_tile(R, B.mix2, R.set.t32, item % nrt, GRAD);
     if (B.fused) finish_request<GRAD>(R);
     return;
   }

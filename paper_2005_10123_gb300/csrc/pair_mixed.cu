@@ -39,8 +39,17 @@
 #ifndef HK_MIN_CTAS_LL
 #define HK_MIN_CTAS_LL 12  // resident CTAs per SM, loglik only (80 registers, no spills)
 #endif
+#ifndef HK_MIN_CTAS_MIX
+#define HK_MIN_CTAS_MIX 7  // resident CTAs per SM, two-component trigger mixture, loglik + gradient (shared memory allows 7)
+#endif
+#ifndef HK_MIN_CTAS_MIX_LL
+#define HK_MIN_CTAS_MIX_LL 8  // two-component trigger mixture, loglik only
+#endif
 #ifndef HK_COL_UNROLL
 #define HK_COL_UNROLL 8  // columns unrolled per step of the tile loop, loglik + gradient
+#endif
+#ifndef HK_COL_UNROLL_SEP
+#define HK_COL_UNROLL_SEP 4  // separable trigger tiles, loglik + gradient (8 spills registers)
 #endif
 #ifndef HK_COL_UNROLL_LL
 #define HK_COL_UNROLL_LL 8  // loglik only
@@ -67,6 +76,7 @@
 namespace hk {
 namespace {
 
+constexpr double kLog2eD = 1.4426950408889634074;  // log2(e)
 constexpr float kPadScaled = 1.0e18f;  // scaled time of a padded event: dt'^2 = 1e36 stays finite
 
 __device__ __forceinline__ float ex2(float x) {
@@ -113,6 +123,7 @@ __device__ __forceinline__ float2 accfma2(float2 a, float2 e, float2 s) {
 
 constexpr int kPairs = kRowsPerThread / 2;  // packed row pairs per thread
 constexpr int kColUnroll = HK_COL_UNROLL, kColUnrollLL = HK_COL_UNROLL_LL, kSymUnroll = HK_SYM_UNROLL;
+constexpr int kColUnrollSep = HK_COL_UNROLL_SEP;
 
 template <int NS>
 struct Acc32 {
@@ -128,18 +139,30 @@ struct Acc32 {
 // coordinates, because the trigger term's Gaussian is narrow (h) and needs r^2 from exact
 // differences: there q = a2 r^2 + dt'^2 with a2 = s*s rounded. Every kind accumulates the
 // background moment Q = sum q e_b in sum 2; the epilogue recovers R_b = (Q - T_b) / s^2.
-// The separable column factor b = wn (t'_ref - t') is formed per column from the staged
-// time: one rounded difference, then one rounded product.
-template <int KIND, bool GRAD>
+// The trigger terms take their time differences from the stored (unscaled, unshifted) float32
+// times, dt = t_n - t_n' rounded once (exact where t_n' >= t_n / 2), with the slope WN = -omega
+// log2(e) per unit of time: the background's scaled times t' = beta (t - t_origin) carry an
+// absolute rounding error of about 2^-24 |t'|, which a trigger decaying within a small part of
+// the row tile's time span (omega times the span large) would feel as a relative error of
+// omega 2^-24 |t - t_origin| in each term. The moment U_s = sum dt e_s is therefore in units of
+// time (rowtile_epilogue converts it). The separable column factor b = WN (t_ref - t') is formed
+// per column from the staged stored time: one rounded difference, then one rounded product.
+// With a two-component trigger mixture (MIX = 2) each trigger term is formed for both components
+// (CN2, WN2), component 2 into the sums after the single-kernel ones.
+template <int KIND, bool GRAD, int MIX>
 __device__ __forceinline__ void tile_pass(const float4 *__restrict__ sxs, const float4 *__restrict__ stx,
-                                          const float2 (&X)[kPairs], const float2 (&Y)[kPairs],
-                                          const float2 (&T)[kPairs], const int (&LO)[kRowsPerThread],
+                                          const float *__restrict__ srt, const float2 (&X)[kPairs],
+                                          const float2 (&Y)[kPairs], const float2 (&T)[kPairs],
+                                          const float2 (&TR)[kPairs], const int (&LO)[kRowsPerThread],
                                           int row_a0, int c0, bool excl, float2 A2, float2 CN, float2 WN,
-                                          float2 SREF, Acc32<GRAD ? kSumsGrad : kSumsLoglik> &acc) {
+                                          float2 CN2, float2 WN2, float2 SREF,
+                                          Acc32<num_sums(GRAD, MIX)> &acc) {
+  constexpr int S2 = GRAD ? 6 : 2;  // component 2's trigger sum (then R_s2, U_s2 with the gradient)
   constexpr bool kBg = KIND != 3;
   constexpr bool kTrig = KIND != 0;
-  constexpr bool kNeedDt = kBg || KIND == 2 || GRAD;
-  constexpr int kUnroll = GRAD ? kColUnroll : kColUnrollLL;
+  constexpr bool kNeedDt = kBg;                               // scaled dt' (background)
+  constexpr bool kNeedDtr = KIND == 2;                        // stored-time dt (trigger, per pair)
+  constexpr int kUnroll = GRAD ? ((KIND == 1 || KIND == 3) ? kColUnrollSep : kColUnroll) : kColUnrollLL;
   if constexpr (KIND == 0 && !GRAD) {
     // background only, loglik: the unused trigger sum holds the odd columns' background sum,
     // halving the dependent chain of the accumulation (1.4% faster loglik; no gain with the
@@ -170,7 +193,8 @@ __device__ __forceinline__ void tile_pass(const float4 *__restrict__ sxs, const 
       const float4 d = stx[j];  // {-t', -t', -x, -y}
       const float2 ct = make_float2(d.x, d.y);
       const int col = c0 + j;
-      float2 cx, cy, bj;
+      float2 cx, cy, bj, bj2, cr, dref;
+      if (kTrig) cr = make_float2(srt[j], srt[j]);  // -t (stored)
       if (KIND == 0) {
         const float4 c = sxs[j];  // {-s x, -s x, -s y, -s y}
         cx = make_float2(c.x, c.y);
@@ -179,13 +203,18 @@ __device__ __forceinline__ void tile_pass(const float4 *__restrict__ sxs, const 
         cx = make_float2(d.z, d.z);
         cy = make_float2(d.w, d.w);
       }
-      if (KIND == 1 || KIND == 3) bj = mul2(add2(SREF, ct), WN);
+      if (KIND == 1 || KIND == 3) {
+        dref = add2(SREF, cr);  // t_ref - t_n' >= 0
+        bj = mul2(dref, WN);
+        if (MIX > 1) bj2 = mul2(dref, WN2);
+      }
 #pragma unroll
       for (int p = 0; p < kPairs; ++p) {
         const float2 dx = add2(X[p], cx);
         const float2 dy = add2(Y[p], cy);
-        float2 dt = make_float2(0.f, 0.f);
+        float2 dt = make_float2(0.f, 0.f), dtr = dt;
         if (kNeedDt) dt = add2(T[p], ct);
+        if (kNeedDtr) dtr = add2(TR[p], cr);
         if (KIND == 0) {
           const float2 u = mul2(dt, dt);
           const float2 q = fma2(dy, dy, fma2(dx, dx, u));
@@ -215,7 +244,7 @@ __device__ __forceinline__ void tile_pass(const float4 *__restrict__ sxs, const 
         }
         if (kTrig) {
           float2 arg;
-          if (KIND == 2) arg = fma2(rho, CN, mul2(dt, WN));
+          if (KIND == 2) arg = fma2(rho, CN, mul2(dtr, WN));
           else arg = fma2(rho, CN, bj);
           float2 es = make_float2(ex2(arg.x), ex2(arg.y));
           if (KIND == 2) {
@@ -225,7 +254,23 @@ __device__ __forceinline__ void tile_pass(const float4 *__restrict__ sxs, const 
           acc.v[1][p] = acc2(acc.v[1][p], es);
           if (GRAD) {
             acc.v[4][p] = accfma2(rho, es, acc.v[4][p]);
-            acc.v[5][p] = accfma2(dt, es, acc.v[5][p]);
+            // separable kinds: the column part t_ref - t_n' of dt (the caller adds t_n - t_ref)
+            acc.v[5][p] = accfma2(KIND == 2 ? dtr : dref, es, acc.v[5][p]);
+          }
+          if (MIX > 1) {
+            float2 arg2;
+            if (KIND == 2) arg2 = fma2(rho, CN2, mul2(dtr, WN2));
+            else arg2 = fma2(rho, CN2, bj2);
+            float2 es2 = make_float2(ex2(arg2.x), ex2(arg2.y));
+            if (KIND == 2) {
+              es2.x = (col < LO[2 * p]) ? es2.x : 0.f;
+              es2.y = (col < LO[2 * p + 1]) ? es2.y : 0.f;
+            }
+            acc.v[S2][p] = acc2(acc.v[S2][p], es2);
+            if (GRAD) {
+              acc.v[S2 + 1][p] = accfma2(rho, es2, acc.v[S2 + 1][p]);
+              acc.v[S2 + 2][p] = accfma2(KIND == 2 ? dtr : dref, es2, acc.v[S2 + 2][p]);
+            }
           }
         }
       }
@@ -253,11 +298,10 @@ __device__ __forceinline__ void red_fix(long long *p, float v, float scale) {
 // sums over the warp's 128 rows to colfix. Every sum is formed in a fixed order. Per step and
 // lane (with the gradient): 49 packed and 6 scalar float32 operations, 8 ex2, 3 loads, 6
 // shuffles, against 72 packed operations for the same 16 terms row by row.
-template <bool GRAD>
+template <bool GRAD, int NS>
 __device__ __forceinline__ void tile_pass_sym_pairs(const float4 *__restrict__ sC, const float4 *__restrict__ sT,
                                                     const float2 (&XS)[kPairs], const float2 (&YS)[kPairs],
-                                                    const float2 (&T)[kPairs],
-                                                    Acc32<GRAD ? kSumsGrad : kSumsLoglik> &acc,
+                                                    const float2 (&T)[kPairs], Acc32<NS> &acc,
                                                     long long *__restrict__ colfix, int npad, int c0, float fix_scale) {
   const int lane = threadIdx.x & 31;
 #pragma unroll 1
@@ -357,8 +401,9 @@ struct Scales {
   float b_hi, b_lo, s_hi, s_lo;
 };
 
+// srt[j] = -t_j, the stored time (padded events hold t_N, so differences stay finite).
 __device__ __forceinline__ void store_cols(const RawCols &r, int ct, int tid, int n, float t_origin, const Scales &k,
-                                           float4 *sxs, float4 *stx) {
+                                           float4 *sxs, float4 *stx, float *srt) {
 #pragma unroll
   for (int h = 0; h < kStage; ++h) {
     const int jj = tid + h * kThreads, j = ct * kColTile + jj;
@@ -366,6 +411,7 @@ __device__ __forceinline__ void store_cols(const RawCols &r, int ct, int tid, in
     const float xs = scale_split(r.x[h], k.s_hi, k.s_lo), ys = scale_split(r.y[h], k.s_hi, k.s_lo);
     sxs[jj] = make_float4(-xs, -xs, -ys, -ys);
     stx[jj] = make_float4(-sj, -sj, -r.x[h], -r.y[h]);
+    srt[jj] = -r.t[h];
   }
 }
 
@@ -413,6 +459,12 @@ __device__ __forceinline__ void row_coords(const SetView &S, int ra0, const Scal
   }
 }
 
+// This thread's stored row times (tiles with trigger terms; padded rows hold t_N).
+__device__ __forceinline__ void row_times(const SetView &S, int ra0, float2 (&TR)[kPairs]) {
+#pragma unroll
+  for (int p = 0; p < kPairs; ++p) TR[p] = make_float2(__ldg(S.t32 + ra0 + 64 * p), __ldg(S.t32 + ra0 + 64 * p + 32));
+}
+
 // CTA-wide barrier; a single-warp CTA only needs the warp to converge.
 __device__ __forceinline__ void cta_sync() {
   if (kThreads == 32) __syncwarp();
@@ -426,13 +478,14 @@ __device__ __forceinline__ void cta_sync() {
 // this thread's row k (rows warp * kWarpRows + lane + 32 k), plus with R.sym the column sums its
 // far blocks left in colfix; then log lambda_n, the moment ratios and the fixed-order reductions
 // (hk_internal.h). Called by every thread of the CTA.
-template <bool GRAD, class Get>
-__device__ void rowtile_epilogue(const Request &R, int I, Get get) {
-  constexpr int NS = GRAD ? kSumsGrad : kSumsLoglik;
+template <bool GRAD, int MIX, class Get>
+__device__ void rowtile_epilogue(const Request &R, const MixConst &M2, int I, Get get) {
+  constexpr int NS = num_sums(GRAD, MIX);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int n = R.set.n;
   const size_t np = (size_t)R.set.npad;
-  double v[GRAD ? 7 : 1] = {};
+  const double to_scaled = 1.0 / R.tscale;  // beta
+  double v[GRAD ? 1 + NS : 1] = {};
 #pragma unroll
   for (int k = 0; k < kRowsPerThread; ++k) {
     const int i = I * kRowTile + warp * kWarpRows + lane + 32 * k;
@@ -447,22 +500,29 @@ __device__ void rowtile_epilogue(const Request &R, int I, Get get) {
           sums[3] += (double)__ldcg(R.colfix + 2 * np + i) * R.fix_inv;
         }
       }
-      if (GRAD) sums[2] = (sums[2] - sums[3]) * R.inv_a2;  // R_b from Q and T_b
-      row_terms<GRAD>(R, i, sums, v);
+      if (GRAD) {
+        sums[2] = (sums[2] - sums[3]) * R.inv_a2;  // R_b from Q and T_b
+        sums[5] *= to_scaled;                      // U_s: from units of time to scaled time
+        if (MIX > 1) sums[8] *= to_scaled;
+      }
+      row_terms<GRAD, MIX>(R, M2, i, sums, v);
     }
   }
-  rowtile_reduce<GRAD>(R, I, v);
+  rowtile_reduce<GRAD, MIX>(R, M2, I, v);
 }
 
-template <bool GRAD>
+template <bool GRAD, int MIX>
 __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, int c_begin, int c_end,
-                          const SymPlan &plan, float4 (*sxs)[kColTile], float4 (*stx)[kColTile], double *sacc) {
-  constexpr int NS = GRAD ? kSumsGrad : kSumsLoglik;
+                          const SymPlan &plan, float4 (*sxs)[kColTile], float4 (*stx)[kColTile],
+                          float (*srt)[kColTile], double *sacc) {
+  constexpr int NS = num_sums(GRAD, MIX);
+  constexpr int S2 = GRAD ? 6 : 2;  // component 2's trigger sums (mixture)
   const SetView &S = R.set;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int row0 = it.rt * kRowTile;
   const float t_origin = S.t32[row0];
-  const float wn = R.wn;
+  // tile classes: the trigger component reaching furthest (the larger wn, both are negative)
+  const float wn = MIX > 1 ? fmaxf(R.wn, B.mix2.wn2) : R.wn;
   const Scales sk{R.beta, R.beta_lo, R.s_hi, R.s_lo};
   const int n = S.n;
   const int wa = row0 + warp * kWarpRows, wb = wa + kWarpRows - 1;
@@ -484,7 +544,14 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
   // few tiles with trigger terms
   float2 XS[kPairs], YS[kPairs];
   row_coords<true>(S, row_a0, sk, XS, YS);
-  const float2 A2 = make_float2(R.a2, R.a2), CN = make_float2(R.cn, R.cn), WN = make_float2(wn, wn);
+  const float2 A2 = make_float2(R.a2, R.a2), CN = make_float2(R.cn, R.cn);
+  const float2 CN2 = make_float2(B.mix2.cn2, B.mix2.cn2);
+  // trigger slopes per unit of stored time, -omega log2(e) rounded once (formed in the tiles with
+  // trigger terms, from the launch parameters, so that they hold no register elsewhere)
+  auto slope = [&](double omega) {
+    const float w = (float)(-omega * kLog2eD);
+    return make_float2(w, w);
+  };
   const float s_first = __shfl_sync(0xffffffffu, T[0].x, 0);            // scaled time of the warp's
   const float s_last = __shfl_sync(0xffffffffu, T[kPairs - 1].y, 31);  // first and last rows
 
@@ -499,7 +566,7 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
   int ct = c_begin;
   if (ct < c_end) {  // an empty slice of the window writes zero partial sums
     if (paired(ct)) store_cols_pairs(load_cols_pairs(S, ct, tid), ct, tid, n, t_origin, sk, sxs[0], stx[0]);
-    else store_cols(load_cols(S, ct, tid), ct, tid, n, t_origin, sk, sxs[0], stx[0]);
+    else store_cols(load_cols(S, ct, tid), ct, tid, n, t_origin, sk, sxs[0], stx[0], srt[0]);
     cta_sync();
   }
   for (int k = 0; ct < c_end; ++ct, ++k) {
@@ -528,39 +595,60 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
     for (int s = 0; s < NS; ++s)
 #pragma unroll
       for (int p = 0; p < kPairs; ++p) acc.v[s][p] = make_float2(0.f, 0.f);
-    float2 X[kPairs], Y[kPairs];  // stored row coordinates, tiles with trigger terms
+    float2 X[kPairs], Y[kPairs], TR[kPairs];  // stored row coordinates and times, tiles with trigger terms
     if (kind == 0) {
-      tile_pass<0, GRAD>(sxs[buf], stx[buf], XS, YS, T, LO, row_a0, c0, excl, A2, CN, WN, WN, acc);
+      tile_pass<0, GRAD, MIX>(sxs[buf], stx[buf], srt[buf], XS, YS, T, T, LO, row_a0, c0, excl, A2, CN, CN, CN2, CN2,
+                              CN, acc);
     } else if (kind == 4) {
       tile_pass_sym_pairs<GRAD>(sxs[buf], stx[buf], XS, YS, T, acc, R.colfix, S.npad, c0, R.fix_scale);
     } else if (kind == 1 || kind == 3) {
       row_coords<false>(S, row_a0, sk, X, Y);
-      const float sref = -stx[buf][kColTile - 1].x;  // t'_ref: the tile's latest column
+      row_times(S, row_a0, TR);
+      const float sref = -srt[buf][kColTile - 1];  // t_ref: the tile's latest column (stored time)
       const float2 SREF = make_float2(sref, sref);
-      if (kind == 1) tile_pass<1, GRAD>(sxs[buf], stx[buf], X, Y, T, LO, row_a0, c0, excl, A2, CN, WN, SREF, acc);
-      else tile_pass<3, GRAD>(sxs[buf], stx[buf], X, Y, T, LO, row_a0, c0, excl, A2, CN, WN, SREF, acc);
-      // row factor 2^(wn (t'_n - t'_ref)) of the separable trigger term
+      const float2 WN = slope(R.omega), WN2 = MIX > 1 ? slope(B.mix2.omega2) : WN;
+      if (kind == 1)
+        tile_pass<1, GRAD, MIX>(sxs[buf], stx[buf], srt[buf], X, Y, T, TR, LO, row_a0, c0, excl, A2, CN, WN, CN2, WN2,
+                                SREF, acc);
+      else
+        tile_pass<3, GRAD, MIX>(sxs[buf], stx[buf], srt[buf], X, Y, T, TR, LO, row_a0, c0, excl, A2, CN, WN, CN2, WN2,
+                                SREF, acc);
+      // row factor 2^(WN (t_n - t_ref)) of the separable trigger term (each component's own);
+      // U_s gets the row part of dt = (t_n - t_ref) + (t_ref - t_n'), both parts >= 0
       const float2 sr = make_float2(-sref, -sref);
 #pragma unroll
       for (int p = 0; p < kPairs; ++p) {
-        const float2 w = __fmul2_rn(__fadd2_rn(T[p], sr), WN);
+        const float2 d = __fadd2_rn(TR[p], sr);
+        const float2 w = __fmul2_rn(d, WN);
         const float2 a = make_float2(ex2(w.x), ex2(w.y));
-        acc.v[1][p] = __fmul2_rn(acc.v[1][p], a);
         if (GRAD) {
+          acc.v[5][p] = __fmul2_rn(__ffma2_rn(d, acc.v[1][p], acc.v[5][p]), a);
           acc.v[4][p] = __fmul2_rn(acc.v[4][p], a);
-          acc.v[5][p] = __fmul2_rn(acc.v[5][p], a);
+        }
+        acc.v[1][p] = __fmul2_rn(acc.v[1][p], a);
+        if (MIX > 1) {
+          const float2 w2 = __fmul2_rn(d, WN2);
+          const float2 a2 = make_float2(ex2(w2.x), ex2(w2.y));
+          if (GRAD) {
+            acc.v[S2 + 2][p] = __fmul2_rn(__ffma2_rn(d, acc.v[S2][p], acc.v[S2 + 2][p]), a2);
+            acc.v[S2 + 1][p] = __fmul2_rn(acc.v[S2 + 1][p], a2);
+          }
+          acc.v[S2][p] = __fmul2_rn(acc.v[S2][p], a2);
         }
       }
     } else if (kind == 2) {
       row_coords<false>(S, row_a0, sk, X, Y);
-      tile_pass<2, GRAD>(sxs[buf], stx[buf], X, Y, T, LO, row_a0, c0, excl, A2, CN, WN, WN, acc);
+      row_times(S, row_a0, TR);
+      const float2 WN = slope(R.omega), WN2 = MIX > 1 ? slope(B.mix2.omega2) : WN;
+      tile_pass<2, GRAD, MIX>(sxs[buf], stx[buf], srt[buf], X, Y, T, TR, LO, row_a0, c0, excl, A2, CN, WN, CN2, WN2,
+                              WN, acc);
     }  // kind -1: every term of the tile is exactly zero for this warp
     // fold the tile's sums into float64; a tile without trigger (background) terms leaves
     // those sums at zero, so they are skipped
     const bool fold_bg = kind == 0 || kind == 1 || kind == 2 || kind == 4, fold_trig = kind >= 1 && kind <= 3;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-      const bool trig_sum = s == 1 || s == 4 || s == 5;  // S_s, R_s, U_s
+      const bool trig_sum = GRAD ? (s == 1 || s >= 4) : s >= 1;  // S_s, R_s, U_s (each component)
       if (trig_sum ? !fold_trig : !fold_bg) continue;
 #pragma unroll
       for (int p = 0; p < kPairs; ++p) {
@@ -570,7 +658,7 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
     }
     if (has_next) {
       if (next_paired) store_cols_pairs(nxt, ct + 1, tid, n, t_origin, sk, sxs[buf ^ 1], stx[buf ^ 1]);
-      else store_cols(nxt, ct + 1, tid, n, t_origin, sk, sxs[buf ^ 1], stx[buf ^ 1]);
+      else store_cols(nxt, ct + 1, tid, n, t_origin, sk, sxs[buf ^ 1], stx[buf ^ 1], srt[buf ^ 1]);
     }
     cta_sync();
   }
@@ -609,7 +697,7 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
       if (s_arrive) {
         __threadfence();
         const double *slot = R.partials + (size_t)first_item_of(R, I) * NS * kRowTile;
-        rowtile_epilogue<GRAD>(R, I, [&](int s, int k) {
+        rowtile_epilogue<GRAD, MIX>(R, B.mix2, I, [&](int s, int k) {
           return __ldcg(slot + s * kRowTile + warp * kWarpRows + lane + 32 * k);
         });
       }
@@ -629,7 +717,8 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
     if (!s_arrive) return;
     __threadfence();
   }
-  rowtile_epilogue<GRAD>(R, it.rt, [&](int s, int k) { return sacc[(s * kRowsPerThread + k) * kThreads + tid]; });
+  rowtile_epilogue<GRAD, MIX>(R, B.mix2, it.rt,
+                              [&](int s, int k) { return sacc[(s * kRowsPerThread + k) * kThreads + tid]; });
 }
 
 // sym_plan_scan (hk_internal.h) with the later row tiles taken 32 at a time, one per lane; called
@@ -662,19 +751,24 @@ __device__ SymPlan sym_plan_warp(const Request &R, int I, int2 win) {
   return SymPlan{max(win.x, 2 * own.ib), min(win.y, 2 * kmax + 2), e_col};
 }
 
-template <bool GRAD>
-__global__ void __launch_bounds__(kThreads, GRAD ? HK_MIN_CTAS : HK_MIN_CTAS_LL) pair_mixed_kernel(const __grid_constant__ Batch B) {
-  constexpr int NS = GRAD ? kSumsGrad : kSumsLoglik;
+template <bool GRAD, int MIX>
+__global__ void __launch_bounds__(kThreads, MIX > 1 ? (GRAD ? HK_MIN_CTAS_MIX : HK_MIN_CTAS_MIX_LL)
+                                                      : GRAD ? HK_MIN_CTAS : HK_MIN_CTAS_LL)
+    pair_mixed_kernel(const __grid_constant__ Batch B) {
+  constexpr int NS = num_sums(GRAD, MIX);
+  // static shared memory, loglik + gradient: 21,944 bytes with the reductions' scratch; ten
+  // resident CTAs need at most 22,272 (10 x (22,272 + 1,024 reserved) <= 228 KB in 128-byte units)
   __shared__ __align__(16) float4 sxs[2][kColTile];
   __shared__ __align__(16) float4 stx[2][kColTile];
+  __shared__ float srt[2][kColTile];
   __shared__ double sacc[NS * kRowsPerThread * kThreads];
   __shared__ int2 s_win;
   const int item = blockIdx.x;
   const Request &R = B.req[find_request(B, item)];
   const int local = item - R.item_begin, nc = comp_items(R);
   if (local < nc) {  // compensator item of row tile `local`
-    compensator_tile(R, R.set.t32, local, GRAD);
-    if (B.fused) finish_request<GRAD>(R);
+    compensator_tile<MIX>(R, B.mix2, R.set.t32, local, GRAD);
+    if (B.fused) finish_request<GRAD, MIX>(R);
     return;
   }
   const PairItem it = item_at(R, local - nc);
@@ -708,22 +802,28 @@ __global__ void __launch_bounds__(kThreads, GRAD ? HK_MIN_CTAS : HK_MIN_CTAS_LL)
     return pos < nf * fw ? w.x + (int)(pos / fw) : plan.sym_end + (int)((pos - nf * fw) / 10);
   };
   const int c_begin = at(l0), c_end = at(l1);
-  run_piece<GRAD>(B, R, it, c_begin, c_end, plan, sxs, stx, sacc);
+  run_piece<GRAD, MIX>(B, R, it, c_begin, c_end, plan, sxs, stx, srt, sacc);
 }
 
 }  // namespace
 
 cudaError_t launch_pair_mixed(const Batch &b, bool grad, cudaStream_t s) {
   if (b.total_items < 1) return cudaErrorInvalidValue;
-  if (grad) pair_mixed_kernel<true><<<b.total_items, kThreads, 0, s>>>(b);
-  else pair_mixed_kernel<false><<<b.total_items, kThreads, 0, s>>>(b);
+  if (b.req[0].mix > 1) {  // a trigger mixture (one request per launch)
+    if (grad) pair_mixed_kernel<true, 2><<<b.total_items, kThreads, 0, s>>>(b);
+    else pair_mixed_kernel<false, 2><<<b.total_items, kThreads, 0, s>>>(b);
+  } else if (grad) {
+    pair_mixed_kernel<true, 1><<<b.total_items, kThreads, 0, s>>>(b);
+  } else {
+    pair_mixed_kernel<false, 1><<<b.total_items, kThreads, 0, s>>>(b);
+  }
   return cudaGetLastError();
 }
 
 int occupancy_pair_mixed(bool grad) {
   int n = 0;
-  if (grad) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_mixed_kernel<true>, kThreads, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_mixed_kernel<false>, kThreads, 0);
+  if (grad) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_mixed_kernel<true, 1>, kThreads, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_mixed_kernel<false, 1>, kThreads, 0);
   return n;
 }
 

@@ -227,10 +227,11 @@ static void fake_outputs(const Batch &b, bool grad) {
       for (int q = 0; q < 7; ++q) R.out[q] = std::nan("");
       continue;
     }
-    R.out[0] = R.mu0 * 1000.0 + R.set.n + (b.mode ? 0.5 : 0.0);
+    R.out[0] = R.mu0 * 1000.0 + R.set.n + (b.mode ? 0.5 : 0.0) + (R.mix > 1 ? 0.25 : 0.0);
     if (grad) {
-      const double th[6] = {R.mu0, R.tau_x, R.tau_t, R.theta, R.omega, R.h};
-      for (int q = 0; q < 6; ++q) R.out[1 + q] = th[q];
+      const double th[9] = {R.mu0, R.tau_x, R.tau_t, R.theta, R.omega, R.h,
+                            b.mix2.theta2, b.mix2.omega2, b.mix2.h2};
+      for (int q = 0; q < (R.mix > 1 ? 9 : 6); ++q) R.out[1 + q] = th[q];
     }
     if (R.mu_out)
       for (int i = 0; i < R.set.n; ++i) { R.mu_out[i] = i; R.xi_out[i] = -i; }
@@ -257,6 +258,11 @@ static cudaError_t fake_pair(const Batch &b, bool grad) {
       if (b.req[r].item_begin != items) g_schedule_errors++;
       items += request_items(b.req[r]);
       check_schedule(b.req[r], b.mode);
+      // every pair item's partial-sum slot (num_sums doubles per row of the tile) lies before the
+      // compensator sums, which the workspace places right after the slots
+      const Request &R = b.req[r];
+      const size_t slots = (size_t)pair_items(R) * num_sums(R.grad != 0, R.mix) * kRowTile;
+      if (R.partials + slots > R.comp) g_schedule_errors++;
     }
   }
   if (items != b.total_items || !b.fused) g_schedule_errors++;

@@ -168,6 +168,18 @@ def main():
     for (w, i), (ll, gr) in out.items():
         assert ll == fake_value(ths[(w * 50 + i) % 64], 513, 1)
 
+    # the trigger mixture: component 2 reaches the launch, the gradient has 3 + 3 m entries
+    mix = TH[:3] + (0.3, 24.0, 0.05, 0.2, 0.1, 0.3)
+    for mode in (0, 1):
+        ll, g = ctx.hawkes_loglik_mix(sids[4097], mix, mode)
+        assert ll == fake_value(TH, 4097, mode) + 0.25 - (TH[0] - mix[0]) * 1000.0, (ll, mode)
+        assert np.array_equal(g, [mix[0], mix[1], mix[2], mix[3], mix[4], mix[5], mix[6], mix[7], mix[8]]), g
+        ll1, g1 = ctx.hawkes_loglik_mix(sids[4097], mix[:6], mode)
+        assert ll1 == fake_value(mix[:6], 4097, mode) and np.array_equal(g1, mix[:6])
+    expect_status(lambda: ctx.hawkes_loglik_mix(sids[4097], mix[:6] + (0.1, -1.0, 0.2)), -1)
+    expect_status(lambda: ctx.hawkes_loglik_mix(sids[4097], mix[:6] + (-0.1, 1.0, 0.2)), -1)
+    assert fake.fake_schedule_errors() == 0
+
     # a bounded device wait that ran out (the fake models it for the test flag): HAWKES_E_DEVICE on
     # the blocking, batched and serving paths; the context stays usable
     ctx.hawkes_set_flags(binding.HAWKES_FLAG_TEST_WITHHOLD_READY)
