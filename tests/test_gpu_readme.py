@@ -18,3 +18,4 @@ def test_readme_example_runs():
     assert scope["ll"] < 0 and len(scope["grad"]) == 6 and scope["pi"].shape[0] == 8
     assert abs(scope["ll"] - scope["ll64"]) <= 1e-6 * abs(scope["ll64"])
     assert abs(scope["ll_t"] - scope["ll"]) <= 1e-9 * abs(scope["ll"])
+    assert len(scope["g2"]) == 9 and scope["ll2"] < 0
