@@ -31,6 +31,8 @@
 //
 // The HK_PACK_* switches choose, per operation kind, packed f32x2 instructions or two
 // scalar ones (same rounding either way: each is one IEEE round-to-nearest operation).
+#include <type_traits>
+
 #include "hk_internal.h"
 
 #ifndef HK_MIN_CTAS
@@ -147,9 +149,10 @@ struct Acc32 {
 // omega 2^-24 |t - t_origin| in each term. The moment U_s = sum dt e_s is therefore in units of
 // time (rowtile_epilogue converts it). The separable column factor b = WN (t_ref - t') is formed
 // per column from the staged stored time: one rounded difference, then one rounded product.
-// With a two-component trigger mixture (MIX = 2) each trigger term is formed for both components
-// (CN2, WN2), component 2 into the sums after the single-kernel ones.
-template <int KIND, bool GRAD, int MIX>
+// With a two-component trigger mixture (MIX = 2) the trigger terms are formed for the components
+// in COMP (bit 0: component 1, bit 1: component 2 with CN2, WN2, into the sums after the
+// single-kernel ones); the caller leaves out a component whose terms are all exactly zero.
+template <int KIND, bool GRAD, int MIX, int COMP = 1>
 __device__ __forceinline__ void tile_pass(const float4 *__restrict__ sxs, const float4 *__restrict__ stx,
                                           const float *__restrict__ srt, const float2 (&X)[kPairs],
                                           const float2 (&Y)[kPairs], const float2 (&T)[kPairs],
@@ -158,6 +161,7 @@ __device__ __forceinline__ void tile_pass(const float4 *__restrict__ sxs, const 
                                           float2 CN2, float2 WN2, float2 SREF,
                                           Acc32<num_sums(GRAD, MIX)> &acc) {
   constexpr int S2 = GRAD ? 6 : 2;  // component 2's trigger sum (then R_s2, U_s2 with the gradient)
+  constexpr bool kC1 = (COMP & 1) != 0, kC2 = MIX > 1 && (COMP & 2) != 0;
   constexpr bool kBg = KIND != 3;
   constexpr bool kTrig = KIND != 0;
   constexpr bool kNeedDt = kBg;                               // scaled dt' (background)
@@ -205,8 +209,8 @@ __device__ __forceinline__ void tile_pass(const float4 *__restrict__ sxs, const 
       }
       if (KIND == 1 || KIND == 3) {
         dref = add2(SREF, cr);  // t_ref - t_n' >= 0
-        bj = mul2(dref, WN);
-        if (MIX > 1) bj2 = mul2(dref, WN2);
+        if (kC1) bj = mul2(dref, WN);
+        if (kC2) bj2 = mul2(dref, WN2);
       }
 #pragma unroll
       for (int p = 0; p < kPairs; ++p) {
@@ -242,7 +246,7 @@ __device__ __forceinline__ void tile_pass(const float4 *__restrict__ sxs, const 
             acc.v[3][p] = accfma2(u, eb, acc.v[3][p]);
           }
         }
-        if (kTrig) {
+        if (kTrig && kC1) {
           float2 arg;
           if (KIND == 2) arg = fma2(rho, CN, mul2(dtr, WN));
           else arg = fma2(rho, CN, bj);
@@ -257,20 +261,20 @@ __device__ __forceinline__ void tile_pass(const float4 *__restrict__ sxs, const 
             // separable kinds: the column part t_ref - t_n' of dt (the caller adds t_n - t_ref)
             acc.v[5][p] = accfma2(KIND == 2 ? dtr : dref, es, acc.v[5][p]);
           }
-          if (MIX > 1) {
-            float2 arg2;
-            if (KIND == 2) arg2 = fma2(rho, CN2, mul2(dtr, WN2));
-            else arg2 = fma2(rho, CN2, bj2);
-            float2 es2 = make_float2(ex2(arg2.x), ex2(arg2.y));
-            if (KIND == 2) {
-              es2.x = (col < LO[2 * p]) ? es2.x : 0.f;
-              es2.y = (col < LO[2 * p + 1]) ? es2.y : 0.f;
-            }
-            acc.v[S2][p] = acc2(acc.v[S2][p], es2);
-            if (GRAD) {
-              acc.v[S2 + 1][p] = accfma2(rho, es2, acc.v[S2 + 1][p]);
-              acc.v[S2 + 2][p] = accfma2(KIND == 2 ? dtr : dref, es2, acc.v[S2 + 2][p]);
-            }
+        }
+        if (kTrig && kC2) {
+          float2 arg2;
+          if (KIND == 2) arg2 = fma2(rho, CN2, mul2(dtr, WN2));
+          else arg2 = fma2(rho, CN2, bj2);
+          float2 es2 = make_float2(ex2(arg2.x), ex2(arg2.y));
+          if (KIND == 2) {
+            es2.x = (col < LO[2 * p]) ? es2.x : 0.f;
+            es2.y = (col < LO[2 * p + 1]) ? es2.y : 0.f;
+          }
+          acc.v[S2][p] = acc2(acc.v[S2][p], es2);
+          if (GRAD) {
+            acc.v[S2 + 1][p] = accfma2(rho, es2, acc.v[S2 + 1][p]);
+            acc.v[S2 + 2][p] = accfma2(KIND == 2 ? dtr : dref, es2, acc.v[S2 + 2][p]);
           }
         }
       }
@@ -575,7 +579,7 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
     RawCols nxt;
     if (has_next) nxt = next_paired ? load_cols_pairs(S, ct + 1, tid) : load_cols(S, ct + 1, tid);
     const int c0 = ct * kColTile, c1 = c0 + kColTile;
-    int kind;
+    int kind, comps = 1;  // comps: the mixture components with nonzero trigger terms (bit mask)
     if (R.sym && ct < plan.sym_end) {  // far: background only, shared with the columns' rows
       const float gap = s_first + stx[buf][kColTile / 2 - 1].y;  // pair layout: the latest column
       kind = gap >= kBgZeroGap ? -1 : 4;
@@ -583,6 +587,8 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
       const float gap = s_first + stx[buf][kColTile - 1].x;  // t'(first row) - t'(latest column)
       const bool bg_zero = gap >= kBgZeroGap, trig_zero = wn * gap <= -kTrigZeroExp;
       kind = bg_zero ? (trig_zero ? -1 : 3) : (trig_zero ? 0 : 1);
+      if (MIX > 1)
+        comps = (R.wn * gap <= -kTrigZeroExp ? 0 : 1) | (B.mix2.wn2 * gap <= -kTrigZeroExp ? 0 : 2);
     } else if (c0 >= lo_wb) {  // no causal pair: background only, zero past its reach
       const float gap = -stx[buf][0].x - s_last;  // t'(earliest column) - t'(last row)
       kind = gap >= kBgZeroGap ? -1 : 0;
@@ -607,26 +613,44 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
       const float sref = -srt[buf][kColTile - 1];  // t_ref: the tile's latest column (stored time)
       const float2 SREF = make_float2(sref, sref);
       const float2 WN = slope(R.omega), WN2 = MIX > 1 ? slope(B.mix2.omega2) : WN;
-      if (kind == 1)
-        tile_pass<1, GRAD, MIX>(sxs[buf], stx[buf], srt[buf], X, Y, T, TR, LO, row_a0, c0, excl, A2, CN, WN, CN2, WN2,
-                                SREF, acc);
-      else
-        tile_pass<3, GRAD, MIX>(sxs[buf], stx[buf], srt[buf], X, Y, T, TR, LO, row_a0, c0, excl, A2, CN, WN, CN2, WN2,
-                                SREF, acc);
+      auto pass = [&](auto kind_c, auto comp_c) {
+        tile_pass<decltype(kind_c)::value, GRAD, MIX, decltype(comp_c)::value>(
+            sxs[buf], stx[buf], srt[buf], X, Y, T, TR, LO, row_a0, c0, excl, A2, CN, WN, CN2, WN2, SREF, acc);
+      };
+      using K1 = std::integral_constant<int, 1>;
+      using K3 = std::integral_constant<int, 3>;
+      using C1 = std::integral_constant<int, 1>;
+      using C2 = std::integral_constant<int, 2>;
+      using C3 = std::integral_constant<int, 3>;
+      if constexpr (MIX == 1) {
+        if (kind == 1) pass(K1{}, C1{});
+        else pass(K3{}, C1{});
+      } else if (comps == 3) {
+        if (kind == 1) pass(K1{}, C3{});
+        else pass(K3{}, C3{});
+      } else if (comps == 1) {
+        if (kind == 1) pass(K1{}, C1{});
+        else pass(K3{}, C1{});
+      } else {
+        if (kind == 1) pass(K1{}, C2{});
+        else pass(K3{}, C2{});
+      }
       // row factor 2^(WN (t_n - t_ref)) of the separable trigger term (each component's own);
       // U_s gets the row part of dt = (t_n - t_ref) + (t_ref - t_n'), both parts >= 0
       const float2 sr = make_float2(-sref, -sref);
 #pragma unroll
       for (int p = 0; p < kPairs; ++p) {
         const float2 d = __fadd2_rn(TR[p], sr);
-        const float2 w = __fmul2_rn(d, WN);
-        const float2 a = make_float2(ex2(w.x), ex2(w.y));
-        if (GRAD) {
-          acc.v[5][p] = __fmul2_rn(__ffma2_rn(d, acc.v[1][p], acc.v[5][p]), a);
-          acc.v[4][p] = __fmul2_rn(acc.v[4][p], a);
+        if (MIX == 1 || (comps & 1)) {
+          const float2 w = __fmul2_rn(d, WN);
+          const float2 a = make_float2(ex2(w.x), ex2(w.y));
+          if (GRAD) {
+            acc.v[5][p] = __fmul2_rn(__ffma2_rn(d, acc.v[1][p], acc.v[5][p]), a);
+            acc.v[4][p] = __fmul2_rn(acc.v[4][p], a);
+          }
+          acc.v[1][p] = __fmul2_rn(acc.v[1][p], a);
         }
-        acc.v[1][p] = __fmul2_rn(acc.v[1][p], a);
-        if (MIX > 1) {
+        if (MIX > 1 && (comps & 2)) {
           const float2 w2 = __fmul2_rn(d, WN2);
           const float2 a2 = make_float2(ex2(w2.x), ex2(w2.y));
           if (GRAD) {
@@ -640,16 +664,18 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
       row_coords<false>(S, row_a0, sk, X, Y);
       row_times(S, row_a0, TR);
       const float2 WN = slope(R.omega), WN2 = MIX > 1 ? slope(B.mix2.omega2) : WN;
-      tile_pass<2, GRAD, MIX>(sxs[buf], stx[buf], srt[buf], X, Y, T, TR, LO, row_a0, c0, excl, A2, CN, WN, CN2, WN2,
-                              WN, acc);
+      tile_pass<2, GRAD, MIX, 3>(sxs[buf], stx[buf], srt[buf], X, Y, T, TR, LO, row_a0, c0, excl, A2, CN, WN, CN2,
+                                 WN2, WN, acc);
     }  // kind -1: every term of the tile is exactly zero for this warp
     // fold the tile's sums into float64; a tile without trigger (background) terms leaves
     // those sums at zero, so they are skipped
     const bool fold_bg = kind == 0 || kind == 1 || kind == 2 || kind == 4, fold_trig = kind >= 1 && kind <= 3;
+    if (kind == 2) comps = 3;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       const bool trig_sum = GRAD ? (s == 1 || s >= 4) : s >= 1;  // S_s, R_s, U_s (each component)
-      if (trig_sum ? !fold_trig : !fold_bg) continue;
+      const int comp = s >= (GRAD ? 6 : 2) ? 2 : 1;               // the component of a trigger sum
+      if (trig_sum ? !(fold_trig && (MIX == 1 || (comps & comp))) : !fold_bg) continue;
 #pragma unroll
       for (int p = 0; p < kPairs; ++p) {
         sacc[(s * kRowsPerThread + 2 * p) * kThreads + tid] += (double)acc.v[s][p].x;

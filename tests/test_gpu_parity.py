@@ -394,3 +394,30 @@ def test_largest_serving_size_sampled_rows(ctx):
     np.testing.assert_allclose(mu[idx], r["mu"], rtol=1e-5)
     np.testing.assert_allclose(xi[idx], r["xi"], rtol=1e-5, atol=1e-5 * np.max(r["xi"]))
     assert rel(llm, ll64) <= TOL_MIXED_LL and grad_err(gm, g64) <= TOL_MIXED_G
+
+
+def test_four_million_events_sampled_rows(ctx):
+    """N = 4,194,301 over 500,000 days (16,384 row tiles, float32 times with 9% ties from the
+    rounding): per-event terms at sampled rows against the oracle in both precisions, ell as the
+    sum of log lambda_n - Lambda_n over every event, and the mixed ell and gradient against
+    the FP64 path."""
+    from paper_2005_10123_gb300 import binding
+    ev = synth.simulate(4194301, 500000.0, seed=40000).rounded32()
+    assert np.sum(np.diff(ev.t) == 0) > 0.05 * ev.n
+    sid = ctx.hawkes_upload_events(ev.x, ev.y, ev.t)
+    try:
+        terms = {m: ctx.hawkes_event_terms(sid, TH0, m) for m in (binding.HAWKES_MIXED, binding.HAWKES_FP64)}
+        llm, gm = ctx.hawkes_loglik_grad(sid, TH0, binding.HAWKES_MIXED)
+        ll64, g64 = ctx.hawkes_loglik_grad(sid, TH0, binding.HAWKES_FP64)
+    finally:
+        ctx.hawkes_release_events(sid)
+    idx = _sample_rows(ev)
+    r = oracle.rows(ev.x, ev.y, ev.t, TH0, idx)
+    Lam, _ = oracle.compensator(ev.t, TH0)
+    for mode, tol in ((binding.HAWKES_MIXED, 1e-5), (binding.HAWKES_FP64, 1e-11)):
+        mu, xi, ll = terms[mode]
+        np.testing.assert_allclose(mu[idx], r["mu"], rtol=tol)
+        np.testing.assert_allclose(xi[idx], r["xi"], rtol=tol, atol=tol * np.max(r["xi"]))
+        assert rel(float(np.sum(np.log(mu + xi))) - Lam, ll) <= (1e-9 if mode == binding.HAWKES_MIXED else 1e-12)
+    assert rel(ll64, terms[binding.HAWKES_FP64][2]) <= 1e-12
+    assert rel(llm, ll64) <= TOL_MIXED_LL and grad_err(gm, g64) <= TOL_MIXED_G
