@@ -126,7 +126,8 @@ struct Request {
   float s_hi, s_lo;      // s = sqrt(a2)                         scales x, y (background-only tiles)
   float beta, beta_lo;   // beta = sqrt(log2(e) / (2 tau_t^2))   scales (t - t0)
   float b2, b2_lo;       // beta^2 = b2 + b2_lo                  multiplies dt^2 (grouped kernel)
-  float wn;              // -omega log2(e) / beta                multiplies scaled dt
+  float wn;              // -omega log2(e) / beta                scaled dt: tile classes (the mixed
+                         //                                      kernel's terms use -omega log2(e))
   float cn;              // -log2(e) / (2 h^2)                   multiplies r^2
   int mix;               // trigger components: 1 (Section 2.1) or 2 (mixture; Batch::mix2)
   // float64 pair constants (fp64 mode)

@@ -5,25 +5,27 @@
 // work range (Section 2.1, Eq. 1 inner sum; the gradient moments are added here):
 //   S_b = sum_n'           e_b,   e_b = exp(-r^2/(2 tau_x^2) - dt^2/(2 tau_t^2))
 //   S_s = sum_{t_n' < t_n} e_s,   e_s = exp(-omega dt - r^2/(2 h^2))
-//   R_b = sum r^2 e_b,  T_b = sum dt'^2 e_b,  R_s = sum r^2 e_s,  U_s = sum dt' e_s
-// with r^2 = |x_n - x_n'|^2 and dt' = beta (t_n - t_n'), beta^2 = log2(e)/(2 tau_t^2); times
-// enter relative to the first row of the tile before scaling, so nearby time differences
-// keep full relative precision, and each scaled time (and scaled coordinate) is the correctly
-// rounded product with the float64 scale (scale_split), so no float32 rounding of a bandwidth
-// biases the sums. The CTA that completes a row tile's merge tree turns its row
-// sums into lambda_n, log lambda_n and the gradient in float64 (fused epilogue).
+//   R_b = sum r^2 e_b,  T_b = sum dt'^2 e_b,  R_s = sum r^2 e_s,  U_s = sum dt e_s
+// with r^2 = |x_n - x_n'|^2 and, for the background, dt' = beta (t_n - t_n'), beta^2 =
+// log2(e)/(2 tau_t^2): times enter relative to the first row of the tile before scaling, and
+// each scaled time (and scaled coordinate) is the correctly rounded product with the float64
+// scale (scale_split), so no float32 rounding of a bandwidth biases the sums. The trigger
+// terms take dt = t_n - t_n' from the stored float32 times (one rounding), so a trigger that
+// decays within a small part of the tile's time span keeps full relative precision. The CTA
+// that completes a row tile's merge tree turns its row sums into lambda_n, log lambda_n and
+// the gradient in float64 (fused epilogue).
 //
 // Arithmetic per (row, column) pair, two rows per packed f32x2 value:
 //   e_b = 2^-q with q = a2 r^2 + dt'^2, a2 = s^2 = log2(e)/(2 tau_x^2);
-//   e_s = 2^(cn r^2 + wn dt'), cn = -log2(e)/(2 h^2), wn = -omega log2(e)/beta.
+//   e_s = 2^(cn r^2 + w dt), cn = -log2(e)/(2 h^2), w = -omega log2(e).
 // Tiles with background terms only (most of the window) take the differences of coordinates
 // pre-scaled by s, q = (s dx)^2 + (s dy)^2 + dt'^2; tiles with trigger terms take r^2 from
 // exact float32 differences of the stored coordinates. Sum 2 accumulates Q = sum q e_b, and
 // the epilogue forms R_b = (Q - T_b) / s^2 in float64.
-// In tiles where every pair is causal the trigger factor 2^(wn dt') splits into a column
-// factor 2^(wn (t'_ref - t'_n')) folded into the exponent and a row factor
-// 2^(wn (t'_n - t'_ref)) applied to the tile's trigger sums, with t'_ref the tile's latest
-// column time (both factors <= 1).
+// In tiles where every pair is causal the trigger factor 2^(w dt) splits into a column
+// factor 2^(w (t_ref - t_n')) folded into the exponent and a row factor 2^(w (t_n - t_ref))
+// applied to the tile's trigger sums, with t_ref the tile's latest column time (both factors
+// <= 1).
 // The causal indicator t_n' < t_n is tested on stored times through lo[n] (the first
 // index whose stored time equals t_n): for sorted times, t_n' < t_n  <=>  n' < lo[n].
 // Column tiles entirely before a warp's rows skip the test, tiles entirely after skip the

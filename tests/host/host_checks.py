@@ -178,6 +178,20 @@ def main():
         assert ll1 == fake_value(mix[:6], 4097, mode) and np.array_equal(g1, mix[:6])
     expect_status(lambda: ctx.hawkes_loglik_mix(sids[4097], mix[:6] + (0.1, -1.0, 0.2)), -1)
     expect_status(lambda: ctx.hawkes_loglik_mix(sids[4097], mix[:6] + (-0.1, 1.0, 0.2)), -1)
+    expect_status(lambda: ctx.hawkes_loglik_mix(sids[4097], mix[:6] + (0.1, 1.0, 0.0)), -1)
+    expect_status(lambda: ctx.hawkes_loglik_mix(sids[4097], mix[:6] + (0.1, float("nan"), 0.2)), -1)
+    expect_status(lambda: ctx.hawkes_loglik_mix(sids[4097], mix[:3] + (0.1, 1.0, -0.2)), -1)
+    expect_status(lambda: ctx.hawkes_loglik_mix(123456, mix), -3)
+    # the component count is checked by the library (the binding only forms m = 1 or 2)
+    p, _ = binding._mix_params(mix)
+    o = ctypes.c_double()
+    g9 = np.zeros(9)
+    for m_bad in (0, 3, -1):
+        rc = ctx.lib.hawkes_loglik_mix(ctx.h, sids[4097], ctypes.byref(p), m_bad, 1, 1, ctypes.byref(o),
+                                       g9.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        assert rc == -1, (m_bad, rc)
+    assert ctx.lib.hawkes_loglik_mix(ctx.h, sids[4097], None, 2, 1, 0, ctypes.byref(o), None) == -1
+    assert ctx.lib.hawkes_loglik_mix(ctx.h, sids[4097], ctypes.byref(p), 2, 1, 1, ctypes.byref(o), None) == -1
     assert fake.fake_schedule_errors() == 0
 
     # a bounded device wait that ran out (the fake models it for the test flag): HAWKES_E_DEVICE on
