@@ -194,10 +194,12 @@ int hawkes_loglik_async(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *pa
 /* K parameter vectors on one resident set in one launch (K <= 64): the batched
  * evaluation of many MCMC chains that share a data set. loglik_out has K entries;
  * grad_out (K x 6, row-major) may be NULL when want_grad is 0. Results are deterministic
- * for a given batch. In HAWKES_FP64 each is bit-identical to the same request evaluated
- * alone. In HAWKES_MIXED with K >= 2 groups of requests share each pair's geometry (time
- * differences in days, float32 sums over a work item rather than a tile), so the results
- * agree with single calls within the mixed-precision accuracy stated above, not bitwise. */
+ * for a given batch. In HAWKES_FP64, and in HAWKES_MIXED with K below 12 (want_grad) or
+ * 16 (loglik only), each is bit-identical to the same request evaluated alone. Larger
+ * HAWKES_MIXED batches run in groups of 4 or 8 requests that share each pair's geometry
+ * (time differences in days, float32 sums over a work item rather than a tile), so the
+ * results agree with single calls within the mixed-precision accuracy stated above, not
+ * bitwise. */
 int hawkes_loglik_batch(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_params *params,
                         hawkes_mode mode, int want_grad, double *loglik_out, double *grad_out);
 

@@ -161,6 +161,17 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 #ifndef HK_ITEMS_PER_SLOT
 #define HK_ITEMS_PER_SLOT 4
 #endif
+// Smallest mixed-precision batch run by the grouped kernel; smaller batches run as independent
+// requests in one launch, each with the shared background, which was faster below these sizes
+// (N = 85,000: 2 requests 0.89 against 1.00 ms, 8 requests 3.19 against 3.35 ms, 16 requests
+// 6.55 against 6.41 ms with the gradient; sets of 8,000 and 20,000 events cross over between 8
+// and 16).
+#ifndef HK_GROUP_MIN_K
+#define HK_GROUP_MIN_K 12  // loglik + gradient
+#endif
+#ifndef HK_GROUP_MIN_K_LL
+#define HK_GROUP_MIN_K_LL 16  // loglik only
+#endif
 constexpr int kItemsPerSlot = HK_ITEMS_PER_SLOT;
 #ifndef HK_TIER_WIDE_PCT
 #define HK_TIER_WIDE_PCT 50  // percent of the row tiles (launched first) with 4-leaf items
@@ -516,12 +527,13 @@ int eval_locked(hawkes_ctx *ctx, EventSetRec *S, int k, const hawkes_params *par
   const size_t row_bytes = align_up((size_t)S->n * sizeof(double), 256);
   const size_t rows_bytes =
       ((mu_out || xi_out) && !direct_rows ? 2 * row_bytes : 0) + (pi_out && !pi_dev ? (size_t)k * row_bytes : 0);
-  // Two or more mixed-precision requests on this set share each pair's geometry (grouped
-  // kernel, moments in raw units). Groups are consecutive requests in order of tau_t, so a
-  // group's members have similar column windows; request r of the launch is params[order[r]]
-  // and writes its results to that parameter vector's place. The other launches share the
-  // background terms of far column tiles where use_symmetry allows it.
-  const bool grouped = k >= 2 && mode == HAWKES_MIXED && group_size(grad != 0) > 1;
+  // From HK_GROUP_MIN_K (gradient) or HK_GROUP_MIN_K_LL mixed-precision requests on this set,
+  // groups of group_size(grad, k) share each pair's geometry (grouped kernel, moments in raw
+  // units). Groups are consecutive requests in order of tau_t, so a group's members have
+  // similar column windows; request r of the launch is params[order[r]] and writes its
+  // results to that parameter vector's place. The other launches run each request as it runs
+  // alone, sharing the background terms of far column tiles where use_symmetry allows it.
+  const bool grouped = k >= (grad ? HK_GROUP_MIN_K : HK_GROUP_MIN_K_LL) && mode == HAWKES_MIXED;
   const int sym = !grouped && use_symmetry(S, mode, ctx->flags) ? 1 : 0;
   const size_t cnt_one = counter_bytes(S, mode, grad, sym);
   const size_t cnt = align_up(cnt_one * k, 256);
@@ -554,7 +566,7 @@ int eval_locked(hawkes_ctx *ctx, EventSetRec *S, int k, const hawkes_params *par
       launch_tiers(S->nrt, mode, true, &b->req[r].wide, &b->req[r].coarse);
     }
   }
-  if (grouped) b->group = group_size(grad != 0);
+  if (grouped) b->group = group_size(grad != 0, k);
   char *rows_cur = rows_base;
   if (direct_rows) {
     b->req[0].mu_out = mu_out;

@@ -318,11 +318,35 @@ __host__ __device__ inline PairItem item_at(const Request &R, int p) {
 // b.total_items.
 cudaError_t launch_pair_mixed(const Batch &b, bool grad, cudaStream_t s);
 cudaError_t launch_pair_fp64(const Batch &b, bool grad, cudaStream_t s);
-// Grouped mixed kernel (pair_group.cu): requests on one set in groups of group_size(grad), each
+// Grouped mixed kernel (pair_group.cu): requests on one set in groups of G = b.group, each
 // pair's geometry shared by the group. Items: nreq * nrt compensator items, then
-// ceil(nreq / group_size(grad)) * nrt * slices pair items. b.group must equal group_size(grad).
+// ceil(nreq / G) * nrt * slices pair items. G must be one of kGroupSizes(grad).
 cudaError_t launch_pair_group(const Batch &b, bool grad, cudaStream_t s);
-int group_size(bool grad);
+// The group sizes the grouped kernel is built for; the largest of each was tuned on 64 requests
+// at N = 85,000 (4 with the gradient at 4 resident CTAs per SM, 8 for the log-likelihood).
+constexpr int kGroupSizesGrad[] = {4};
+constexpr int kGroupSizesLoglik[] = {4, 8};
+// Group size for a batch of k requests: a group forms each pair's geometry once (about 6 float32
+// operations) and then about 6 (gradient) or 5 (log-likelihood) per request and term, and a
+// partial last group evaluates its missing members as copies of its first. The size minimises
+// ceil(k / G) (6 + c G) over the built sizes, larger G on ties (64 requests: 4 and 8; 17
+// log-likelihood requests: 4, where groups of 8 would evaluate 7 copies).
+inline int group_size(bool grad, int k) {
+  const int c = grad ? 6 : 5;
+  const int *sizes = grad ? kGroupSizesGrad : kGroupSizesLoglik;
+  const int count = grad ? (int)(sizeof(kGroupSizesGrad) / sizeof(int)) : (int)(sizeof(kGroupSizesLoglik) / sizeof(int));
+  int best = sizes[0];
+  long long best_cost = -1;
+  for (int i = 0; i < count; ++i) {
+    const int G = sizes[i];
+    const long long cost = (long long)((k + G - 1) / G) * (6 + c * G);
+    if (best_cost < 0 || cost <= best_cost) {
+      best = G;
+      best_cost = cost;
+    }
+  }
+  return best;
+}
 // Resident CTAs per SM of each pair kernel (sets the number of slices).
 int occupancy_pair_mixed(bool grad);
 int occupancy_pair_fp64(bool grad);

@@ -23,14 +23,8 @@
 // sums over an item rather than a tile).
 #include "hk_internal.h"
 
-#ifndef HK_GROUP
-#define HK_GROUP 4  // requests per CTA, loglik + gradient
-#endif
 #ifndef HK_GROUP_MIN_CTAS
 #define HK_GROUP_MIN_CTAS 4  // resident CTAs per SM: 128 registers (7% faster than 3 CTAs at 164)
-#endif
-#ifndef HK_GROUP_LL
-#define HK_GROUP_LL 8  // loglik only
 #endif
 
 namespace hk {
@@ -308,11 +302,17 @@ cudaError_t launch_group(const Batch &b, cudaStream_t s) {
 
 }  // namespace
 
-int group_size(bool grad) { return grad ? HK_GROUP : HK_GROUP_LL; }
+static_assert(sizeof(kGroupSizesGrad) == sizeof(int) && kGroupSizesGrad[0] == 4,
+              "the launcher below instantiates these group sizes");
+static_assert(sizeof(kGroupSizesLoglik) == 2 * sizeof(int) && kGroupSizesLoglik[0] == 4 && kGroupSizesLoglik[1] == 8,
+              "the launcher below instantiates these group sizes");
 
 cudaError_t launch_pair_group(const Batch &b, bool grad, cudaStream_t s) {
-  if (b.total_items < 1 || b.group != group_size(grad)) return cudaErrorInvalidValue;
-  return grad ? launch_group<HK_GROUP, true>(b, s) : launch_group<HK_GROUP_LL, false>(b, s);
+  if (b.total_items < 1) return cudaErrorInvalidValue;
+  if (grad && b.group == 4) return launch_group<4, true>(b, s);
+  if (!grad && b.group == 4) return launch_group<4, false>(b, s);
+  if (!grad && b.group == 8) return launch_group<8, false>(b, s);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace hk

@@ -28,6 +28,8 @@ namespace {
 std::atomic<long> g_fail_after{-1};
 std::atomic<int> g_event_delay{0};
 std::atomic<long> g_schedule_errors{0};
+std::atomic<int> g_last_group{0};
+std::atomic<long> g_group_launches{0};
 std::atomic<long> g_sym_checked{0};  // launches whose shared-background plan was checked in full
 std::atomic<long> g_launches{0};
 std::atomic<long> g_live_allocs{0};
@@ -49,6 +51,8 @@ void fake_fail_alloc_after(long k) { g_fail_after = k; }
 void fake_event_delay(int k) { g_event_delay = k; }
 void fake_release_events() { g_epoch++; }
 long fake_schedule_errors() { return g_schedule_errors.load(); }
+int fake_last_group() { return g_last_group.load(); }
+long fake_group_launches() { return g_group_launches.load(); }
 long fake_sym_checked() { return g_sym_checked.load(); }
 long fake_launches() { return g_launches.load(); }
 long fake_live_allocs() { return g_live_allocs.load(); }
@@ -319,10 +323,19 @@ cudaError_t launch_upload_prep(const UploadPrep &u, cudaStream_t) {
 cudaError_t launch_pair_mixed(const Batch &b, bool grad, cudaStream_t) { return fake_pair(b, grad); }
 cudaError_t launch_pair_fp64(const Batch &b, bool grad, cudaStream_t) { return fake_pair(b, grad); }
 cudaError_t launch_pair_group(const Batch &b, bool grad, cudaStream_t) {
-  if (!b.group) g_schedule_errors++;
+  // the group size the host picked for this batch, and one the kernel is built for
+  bool built = false;
+  if (grad) {
+    for (int G : kGroupSizesGrad) built |= b.group == G;
+  } else {
+    for (int G : kGroupSizesLoglik) built |= b.group == G;
+  }
+  if (!built || b.group != group_size(grad, b.nreq)) g_schedule_errors++;
+  g_last_group = b.group;
+  g_group_launches++;
   return fake_pair(b, grad);
 }
-int group_size(bool grad) { return grad ? 4 : 8; }
+
 int fp64_chunks_per_tile() { return 8; }
 
 int occupancy_pair_mixed(bool) { return 4; }

@@ -86,6 +86,21 @@ def main():
     for k in range(64):
         assert ll[k] == fake_value(ths[k], 20000, 1) and np.array_equal(g[k], ths[k])
     expect_status(lambda: ctx.hawkes_loglik_batch(sids[20000], np.tile(ths, (2, 1)), 1), -1)  # K > 64
+    # batches of 12 (gradient) or 16 (loglik) requests and more run the grouped kernel, smaller ones
+    # as independent requests in one launch; group size by batch size: ceil(k / G) (6 + c G)
+    # smallest over the built sizes (c = 6 with the gradient, 5 without; larger G on ties)
+    for k, grad, want in [(64, True, 4), (64, False, 8), (12, True, 4), (11, True, 0), (2, True, 0),
+                          (16, False, 8), (15, False, 0), (17, False, 4), (24, False, 8), (25, False, 4),
+                          (13, True, 4), (2, False, 0)]:
+        before = fake.fake_group_launches()
+        r = ctx.hawkes_loglik_batch(sids[20000], ths[:k], 1, want_grad=grad)
+        llk = r[0] if grad else r
+        grouped = fake.fake_group_launches() - before
+        assert grouped == (1 if want else 0), (k, grad, grouped)
+        if want:
+            assert fake.fake_last_group() == want, (k, grad, fake.fake_last_group(), want)
+        for q in range(k):
+            assert llk[q] == fake_value(ths[q], 20000, 1)
     # work accounting: the exact-zero window visits a subset of the N^2 pairs; dense visits all
     for n in (1, 513, 20000, 85000):
         for mode in (0, 1):

@@ -240,9 +240,10 @@ def test_repeatable_bitwise(ctx):
 
 
 def test_batch_matches_single(ctx):
-    """FP64 batches run the single-request kernel: bitwise equal. Mixed batches run the grouped
-    kernel (shared pair geometry, raw time differences): equal within the mixed tolerance, and
-    bitwise repeatable."""
+    """FP64 batches, and mixed batches below the grouping sizes (12 with the gradient, 16 for the
+    log-likelihood), run every request as it runs alone: bitwise equal to single calls. Larger
+    mixed batches run the grouped kernel (shared pair geometry, raw time differences): equal
+    within the mixed tolerance, and bitwise repeatable."""
     ev = synth.simulate(6000, 2000.0, seed=4)
     sid = ctx.hawkes_upload_events(ev.x, ev.y, ev.t)
     try:
@@ -255,21 +256,31 @@ def test_batch_matches_single(ctx):
         for k in range(len(ths)):
             assert ll0[k] == ctx.hawkes_loglik(sid, ths[k], 0)
         ll, g = ctx.hawkes_loglik_batch(sid, ths, 1, want_grad=True)
-        ll2, g2 = ctx.hawkes_loglik_batch(sid, ths, 1, want_grad=True)
-        assert np.array_equal(ll, ll2) and np.array_equal(g, g2)
+        llm = ctx.hawkes_loglik_batch(sid, ths, 1, want_grad=False)
         for k in range(len(ths)):
             a, ga = ctx.hawkes_loglik_grad(sid, ths[k], 1)
+            assert ll[k] == a and np.array_equal(g[k], ga), (k, ll[k], a)
+            assert llm[k] == ctx.hawkes_loglik(sid, ths[k], 1)
+        big = synth.theta_batch(20, seed=13)
+        ll, g = ctx.hawkes_loglik_batch(sid, big, 1, want_grad=True)
+        ll2, g2 = ctx.hawkes_loglik_batch(sid, big, 1, want_grad=True)
+        assert np.array_equal(ll, ll2) and np.array_equal(g, g2)
+        for k in range(len(big)):
+            a, ga = ctx.hawkes_loglik_grad(sid, big[k], 1)
             assert rel(ll[k], a) <= TOL_MIXED_LL and grad_err(g[k], ga) <= TOL_MIXED_G, (k, ll[k], a)
     finally:
         ctx.hawkes_release_events(sid)
 
 
-@pytest.mark.parametrize("n,k,flags,grad", [(4099, 7, 0, True), (4099, 7, 0, False), (1007, 5, 1, True),
-                                            (513, 2, 0, True), (33, 9, 0, True)],
-                         ids=["n4099-k7-grad", "n4099-k7-ll", "n1007-k5-exclself", "n513-k2", "n33-k9"])
+@pytest.mark.parametrize("n,k,flags,grad", [(4099, 13, 0, True), (4099, 17, 0, False), (1007, 12, 1, True),
+                                            (33, 16, 0, False), (2049, 24, 0, True), (513, 2, 0, True),
+                                            (777, 3, 0, False)],
+                         ids=["n4099-k13-grad", "n4099-k17-ll", "n1007-k12-exclself", "n33-k16-ll",
+                              "n2049-k24-grad", "n513-k2-single-path", "n777-k3-ll-single-path"])
 def test_grouped_batch_vs_oracle(ctx, n, k, flags, grad):
-    """The grouped mixed kernel (up to 4 requests share each pair's geometry; partial last
-    group) against the oracle on the float32-rounded inputs, request by request."""
+    """Mixed batches against the oracle on the float32-rounded inputs, request by request: the
+    grouped kernel from 12 (gradient) or 16 (log-likelihood) requests on (groups of 4 or 8 share
+    each pair's geometry; partial last groups), independent requests in one launch below."""
     ev = synth.simulate(n, 1500.0, seed=90 + n)
     ths = synth.theta_batch(k, seed=91 + k)
     ctx.hawkes_set_flags(flags)
