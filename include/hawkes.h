@@ -28,10 +28,10 @@
  * all reductions are float64. All reductions run in a fixed order: the same call on
  * the same inputs returns bit-identical results. A request served through
  * hawkes_submit returns the same bits whatever it is batched with. hawkes_loglik_batch
- * returns bit-identical results to single calls in HAWKES_FP64; in HAWKES_MIXED with
- * two or more parameter vectors it runs a kernel that shares each pair's geometry
- * across requests, and its results agree with single calls within the mixed-precision
- * accuracy below, not bitwise.
+ * returns bit-identical results to single calls in HAWKES_FP64, and in HAWKES_MIXED below
+ * 12 (with the gradient) or 16 parameter vectors; larger mixed batches run a kernel that
+ * shares each pair's geometry across requests, and their results agree with single calls
+ * within the mixed-precision accuracy below, not bitwise.
  *
  * Mixed-precision accuracy (against float64 on the same float32-rounded inputs, measured
  * on the N = 85,000 workload): ell to about 1e-7 relative and the gradient to about 1e-7
@@ -92,11 +92,17 @@ extern "C" {
  * returns HAWKES_E_DEVICE. Nothing faults or hangs; later calls without the flag are
  * unaffected. */
 #define HAWKES_FLAG_TEST_WITHHOLD_READY (1 << 30)
-/* By default each row only visits the columns whose pair terms can be nonzero at the working
- * precision: a pair term whose exponent is so negative that float32 ex2 (flushing subnormals
- * to zero) or float64 exp returns exactly +0 cannot change a sum. Every term computed is the
- * same as when all N^2 pairs are visited; only the grouping of the float64 partial sums
- * differs (results agree to about 1e-16 relative). HAWKES_FLAG_DENSE visits all pairs. */
+/* By default each row only visits the columns whose pair terms can change its sums at the
+ * working precision. HAWKES_MIXED: a pair term whose exponent is so negative that float32 ex2
+ * (flushing subnormals to zero) returns exactly +0; every term computed is the same as when all
+ * N^2 pairs are visited, and only the grouping of the float64 partial sums differs (results
+ * agree to about 1e-16 relative). HAWKES_FP64 with the self term: the background sum holds the
+ * term n' = n = 1, so lambda_n >= A = mu0 / ((2 pi)^(3/2) tau_x^2 tau_t); columns whose terms
+ * are each below 2^-70 A / N (background exponent beyond ln N + 70 ln 2, trigger exponent
+ * beyond that plus ln(C / A), C = theta omega / (2 pi h^2)) are skipped, so the skipped part of
+ * a row stays below 2^-70 of lambda_n, 1/128 of float64's rounding unit. HAWKES_FP64 with
+ * HAWKES_FLAG_EXCLUDE_SELF (no such floor): float64 exp's exact zeros, as in mixed precision.
+ * HAWKES_FLAG_DENSE visits all pairs (in HAWKES_FP64 up to float64 exp's exact zeros). */
 
 typedef struct hawkes_ctx hawkes_ctx;
 
@@ -205,13 +211,13 @@ int hawkes_loglik_batch(hawkes_ctx *ctx, int32_t set_id, int k, const hawkes_par
 
 /* Work accounting for an evaluation at Theta (host computation on the set's stored times, read
  * back from the device; no kernel launch):
- *   out[0] ordered (row, column) pairs inside the exact-zero windows the kernels cover (see
- *          HAWKES_FLAG_DENSE), counted over real events;
+ *   out[0] ordered (row, column) pairs inside the column windows the kernels cover (see
+ *          HAWKES_FLAG_DENSE and the note above it), counted over real events;
  *   out[1] N^2, the pairs of Eq. 1's double sum;
- *   out[2] ordered pairs whose background term can be nonzero at the mode's precision
- *          (|t_n - t_n'| below the background's exact-zero reach, n' = n included);
- *   out[3] ordered pairs whose trigger term can be nonzero (0 <= t_n - t_n' below the trigger's
- *          exact-zero reach; pairs with equal times counted although their term is zero);
+ *   out[2] ordered pairs whose background term can change the sums at the mode's precision
+ *          (|t_n - t_n'| below the background's reach, n' = n included);
+ *   out[3] ordered pairs whose trigger term can change the sums (0 <= t_n - t_n' below the
+ *          trigger's reach; pairs with equal times counted although their term is zero);
  *   out[4] pair terms the kernels evaluate: out[0] less the far pairs whose background term
  *          serves both events (see HAWKES_FLAG_NO_SYMMETRY), which are evaluated once. */
 int hawkes_pair_work(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *params, hawkes_mode mode,

@@ -200,22 +200,45 @@ void launch_tiers(int nrt, int mode, bool grouped, int *wide, int *coarse) {
   }
 }
 
-// Exact-zero cut-offs (days) of Section 2.1's pair terms at the working precision:
-// float32 ex2.approx.ftz returns +0 for every exponent <= -126, float64 exp returns +0 far
-// below -745. A background term is zero once dt' = beta dt reaches sqrt(130) (float32) or
-// dt^2 / (2 tau_t^2) reaches 805 (float64); a trigger term once omega dt log2(e) reaches 131
-// (float32) or omega dt reaches 805 (float64). One percent of margin covers the rounding
-// of the time differences. Columns later than a row only carry background terms.
-void exact_zero_cutoffs(const hawkes_params *p, int mode, float beta32, double *early, double *late,
-                        double *trig_out = nullptr) {
-  double bg, trig;
+// Reaches (days) of Section 2.1's pair terms: past bg of |t_n - t_n'| a background term, past
+// trig of t_n - t_n' a trigger term contributes nothing at the working precision.
+// - float32 (mixed): ex2.approx.ftz returns +0 for every exponent <= -126, so a background
+//   term is exactly zero once dt' = beta dt reaches sqrt(130), a trigger term once
+//   omega dt log2(e) reaches 131.
+// - float64 with the self term in the background sum (the default): S_b >= 1, so lambda_n >= A
+//   = mu0 / ((2 pi)^(3/2) tau_x^2 tau_t). A background term beyond dt^2 / (2 tau_t^2) = E,
+//   E = ln N + 70 ln 2, is below e^-E, and all N of a row together stay below 2^-70 of
+//   lambda_n (1/128 of float64's rounding unit); a trigger term of weight C = theta omega /
+//   (2 pi h^2) beyond omega dt = E + ln(C / A) (when C > A) likewise. The sums are those of
+//   every pair up to float64 rounding, and the window is a third to a quarter as long.
+// - float64 without that floor (HAWKES_FLAG_EXCLUDE_SELF, where S_b can be as small as one
+//   term), or with HAWKES_FLAG_DENSE (every pair): exp returns +0 far below -745, so both
+//   exponents go to 805.
+void term_reaches(const hawkes_params *p, int mode, float beta32, int flags, int64_t n, double *bg, double *trig) {
   if (mode == HAWKES_MIXED) {
-    bg = 1.01 * std::sqrt(130.0) / (double)beta32;
-    trig = 1.01 * 131.0 / (p->omega * kLog2e);
+    *bg = std::sqrt(130.0) / (double)beta32;
+    *trig = 131.0 / (p->omega * kLog2e);
+  } else if (!(flags & (HAWKES_FLAG_EXCLUDE_SELF | HAWKES_FLAG_DENSE))) {
+    const double two_pi = 6.28318530717958647693;
+    const double A = p->mu0 / (two_pi * std::sqrt(two_pi) * p->tau_x * p->tau_x * p->tau_t);
+    const double C = p->theta * p->omega / (two_pi * p->h * p->h);
+    const double E = std::log((double)std::max<int64_t>(n, 1)) + 70.0 * std::log(2.0);
+    *bg = std::sqrt(E * 2.0) * p->tau_t;
+    *trig = (E + (C > A ? std::log(C / A) : 0.0)) / p->omega;
   } else {
-    bg = 1.01 * std::sqrt(805.0 * 2.0) * p->tau_t;
-    trig = 1.01 * 805.0 / p->omega;
+    *bg = std::sqrt(805.0 * 2.0) * p->tau_t;
+    *trig = 805.0 / p->omega;
   }
+}
+
+// The column windows' cut-offs: the reaches with one percent of margin for the rounding of the
+// time differences. Columns earlier than a row carry both terms, later ones the background only.
+void exact_zero_cutoffs(const hawkes_params *p, int mode, float beta32, int flags, int64_t n, double *early,
+                        double *late, double *trig_out = nullptr) {
+  double bg, trig;
+  term_reaches(p, mode, beta32, flags, n, &bg, &trig);
+  bg *= 1.01;
+  trig *= 1.01;
   *early = std::max(bg, trig);
   *late = bg;
   if (trig_out) *trig_out = trig;
@@ -272,7 +295,7 @@ int make_request(hawkes_ctx *ctx, const EventSetRec *S, const hawkes_params *p, 
     R->t_last = S->t_last64;
     R->tscale = 1.0;
   }
-  exact_zero_cutoffs(p, mode, R->beta, &R->cut_early, &R->cut_late, &R->trig_cut);
+  exact_zero_cutoffs(p, mode, R->beta, flags, S->n, &R->cut_early, &R->cut_late, &R->trig_cut);
   R->sym = use_symmetry(S, mode, flags) ? 1 : 0;
   R->mix = 1;
   // fixed-point scale of the column sums: every event's total is at most npad (terms <= 1, and
@@ -305,7 +328,7 @@ int set_mixture(const hawkes_mix_params *m, int mode, Request *R, MixConst *M2) 
   else if (!std::isfinite(M2->wn2) || !(M2->cn2 < 0.f) || !std::isfinite(M2->cn2)) return HAWKES_E_INVAL;
   hawkes_params p2{R->mu0, R->tau_x, R->tau_t, th2, om2, h2};
   double early2, late2, trig2;
-  exact_zero_cutoffs(&p2, mode, R->beta, &early2, &late2, &trig2);
+  exact_zero_cutoffs(&p2, mode, R->beta, R->flags, R->set.n, &early2, &late2, &trig2);
   R->trig_cut = std::max(R->trig_cut, trig2);
   R->cut_early = std::max(R->cut_early, early2);
   R->mix = 2;
@@ -1071,15 +1094,9 @@ int hawkes_pair_work(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *param
     HK_CUDA(ctx, cudaMemcpyAsync(t.data(), S->t64, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     HK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   }
-  // exact-zero reach (days) of each term on its own (the window uses the larger on the early side)
+  // reach (days) of each term on its own (the window uses the larger on the early side)
   double bg_reach, trig_reach;
-  if (mode == HAWKES_MIXED) {
-    bg_reach = std::sqrt(130.0) / (double)R.beta;
-    trig_reach = 131.0 / (params->omega * kLog2e);
-  } else {
-    bg_reach = std::sqrt(805.0 * 2.0) * params->tau_t;
-    trig_reach = 805.0 / params->omega;
-  }
+  term_reaches(params, mode, R.beta, ctx->flags, n, &bg_reach, &trig_reach);
   int64_t visited = 0, bg_pairs = 0, trig_pairs = 0;
   WinTable W = mode == HAWKES_MIXED ? S->win32 : S->win64;  // the kernels' table, read back
   std::vector<int> wh((size_t)2 * W.nb);

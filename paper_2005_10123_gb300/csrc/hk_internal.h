@@ -97,8 +97,9 @@ __host__ __device__ inline int2 table_window(const WinTable &W, int n, int nct, 
 // Work decomposition: the pair kernels run one CTA per item. A request's items are first
 // one compensator item per row tile (when comp is set), then the pair items. For a pair item
 // the kernel finds the window of column tiles of its row tile rt that can hold a nonzero pair
-// term (every other pair term is exactly zero at the working precision, see cut_early and
-// cut_late) and cuts it into `slices` near-equal leaves. Row tiles are launched from the
+// term (every other pair term is exactly zero in mixed precision, or below 2^-70 of lambda_n
+// in float64 with the self term, see cut_early and cut_late) and cuts it into `slices`
+// near-equal leaves. Row tiles are launched from the
 // middle of the time range outwards; one item covers `span` consecutive leaves of its row
 // tile, with span 4 for the first `wide` row tiles launched, 2 up to `coarse` and 1 for the
 // rest, so that the launch starts on long items and ends on short ones. Items are numbered in
@@ -154,7 +155,8 @@ struct Request {
   // symmetric background (see SymPlan): far column tiles share each background term between its
   // row and its column; column sums go to colfix as exact fixed-point integers
   int sym;             // 1: on (mixed, fused, set with a time table, no exclude-self/dense/no-symmetry)
-  double trig_cut;     // days: columns earlier than t_n - trig_cut give exactly zero trigger terms
+  double trig_cut;     // days: columns earlier than t_n - trig_cut give trigger terms that contribute
+                       // nothing (exact zeros in mixed precision; below 2^-70 of lambda_n in float64)
   long long *colfix;   // sym: column sums of S_b (and Q, T_b with the gradient), [k][npad], zero at launch
   unsigned *rt_done;   // sym: per row tile, row-side root plus column contributions, zero at launch
   float fix_scale;     // 2^F: a float32 column sum v enters colfix as round(v 2^F)

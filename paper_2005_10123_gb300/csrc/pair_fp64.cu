@@ -92,10 +92,10 @@ __device__ void run_piece64(const Batch &B, const Request &R, const PairItem &it
   const bool excl = (R.flags & 1) != 0;
   const double da = R.da, db = R.db, dc = R.dc, omega = R.omega;
   const double dc2 = B.mix2.dc2, omega2 = B.mix2.omega2;
-  // exact-zero gaps (days) between the warp's earliest row and a tile's latest column: the
-  // background exponent exceeds 805 past bg_gap, the trigger exponent past trig_gap (exp
-  // returns +0 far below -745); one percent of margin
-  const double bg_gap = 1.01 * sqrt(805.0 / db), trig_gap = 1.01 * 805.0 / (MIX > 1 ? fmin(omega, omega2) : omega);
+  // gaps (days) between the warp's earliest row and a tile's latest column past which every
+  // background (bg_gap) or trigger (trig_gap) term of the tile contributes nothing at float64
+  // precision: the host's reaches with their one percent of margin (term_reaches in api.cu)
+  const double bg_gap = R.cut_late, trig_gap = R.trig_cut;
 
   double X[4], Y[4], T[4];
   int LO[4];

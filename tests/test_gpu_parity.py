@@ -174,9 +174,10 @@ def test_pi_batch(ctx, mode):
 
 @pytest.mark.parametrize("mode", [0, 1], ids=["fp64", "mixed"])
 def test_exact_zero_window_matches_dense(ctx, mode):
-    """Skipping the columns whose pair terms are exactly zero at the working precision changes
-    nothing but the grouping of the float64 partial sums (row-by-row evaluation: the mixed path
-    with HAWKES_FLAG_NO_SYMMETRY, which HAWKES_FLAG_DENSE implies)."""
+    """Skipping the columns whose pair terms are exactly zero (mixed precision), or in float64
+    below 2^-70 of lambda_n in all (the self term's floor), changes nothing but the grouping of
+    the float64 partial sums (row-by-row evaluation: the mixed path with
+    HAWKES_FLAG_NO_SYMMETRY, which HAWKES_FLAG_DENSE implies)."""
     from paper_2005_10123_gb300 import binding
     ev = synth.simulate(20000, 5000.0, seed=71)  # long time span: most column tiles skipped
     sid = ctx.hawkes_upload_events(ev.x, ev.y, ev.t)
