@@ -372,6 +372,8 @@ def probe_units():
     d = json.loads(subprocess.check_output([exe], text=True))
     d["lanes_per_clk_per_sm_at_max_clock"] = {k: v / (d["sms"] * MAX_MHZ * 1e6)
                                               for k, v in d["lane_ops_per_s"].items()}
+    d["sequences_per_clk_per_sm_at_max_clock"] = {k: v / (d["sms"] * MAX_MHZ * 1e6)
+                                                  for k, v in d["sequences_per_s"].items()}
     print(json.dumps(d))
     return 0
 

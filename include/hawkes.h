@@ -81,16 +81,23 @@ extern "C" {
 /* By default a mixed-precision evaluation without HAWKES_FLAG_EXCLUDE_SELF or HAWKES_FLAG_DENSE
  * shares background terms: e_b(n, n') = e_b(n', n), so for column tiles far enough before a row
  * tile that no trigger term can be nonzero (beyond the trigger's exact-zero reach) each pair term
- * is formed once and added to both events' rows. The column sums are added as exact fixed-point
- * integers (2^-F resolution, F = 62 - ceil(log2 N_padded), about 3e-14 at N = 85,000), so results
- * stay bit-identical from run to run and alone or batched; they differ from the row-by-row
- * evaluation (HAWKES_FLAG_NO_SYMMETRY) by float32 rounding only. The paper's evaluation visits
- * every ordered pair (Section 2.3); this is a reorganisation of the same sum. */
-/* For testing the failure path only: in loglik + gradient evaluations the first work item to
- * reach each merge node of row tile 0 publishes its partial sums without marking them ready,
- * so the bounded device wait of its sibling runs out (after at most 0.5 s) and the call
- * returns HAWKES_E_DEVICE. Nothing faults or hangs; later calls without the flag are
- * unaffected. */
+ * is formed once and added to both events' rows. Every event's sums (its row's, and the shares of
+ * the far tiles holding it) are then added as exact fixed-point integers: 2^-F resolution with
+ * F = 62 - ceil(log2 N_padded) for the background sums (about 3e-14 at N = 85,000, against a
+ * background sum of at least 1, the self term) and a per-sum F from Theta for the trigger
+ * moments. Integer addition commutes, so results stay bit-identical from run to run and alone or
+ * batched; they differ from the row-by-row evaluation (HAWKES_FLAG_NO_SYMMETRY) by float32
+ * rounding only, and the evaluation needs no partial-sum workspace (num_sums x N_padded
+ * integers instead: 4.1 MB for loglik + gradient at N = 85,000). A sum that is not finite or
+ * leaves the fixed-point range (possible only for inputs whose float32 pair terms overflow)
+ * makes ell and the gradient NaN, with status OK. The paper's evaluation visits every ordered
+ * pair (Section 2.3); this is a reorganisation of the same sum. */
+/* For testing the failure path only: in loglik + gradient evaluations that merge partial sums in
+ * a tree (HAWKES_FP64, the row-by-row HAWKES_MIXED evaluation, which this flag selects, and
+ * grouped batches) the first work item to reach each merge node of row tile 0 publishes its
+ * partial sums without marking them ready, so the bounded device wait of its sibling runs out
+ * (after at most 0.5 s) and the call returns HAWKES_E_DEVICE. Nothing faults or hangs; later
+ * calls without the flag are unaffected. */
 #define HAWKES_FLAG_TEST_WITHHOLD_READY (1 << 30)
 /* By default each row only visits the columns whose pair terms can change its sums at the
  * working precision. HAWKES_MIXED: a pair term whose exponent is so negative that float32 ex2

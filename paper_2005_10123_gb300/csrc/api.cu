@@ -248,9 +248,11 @@ void exact_zero_cutoffs(const hawkes_params *p, int mode, float beta32, int flag
 // hk_internal.h): mixed precision, a time table, and none of the flags that ask for row-by-row
 // evaluation (exclude-self makes lambda_n's background sum unbounded below, which the fixed-point
 // column sums would not resolve; dense and no-symmetry ask for every ordered pair).
+// The test flag that withholds a merge-tree ready mark asks for the merge tree, which the shared
+// background does not use.
 bool use_symmetry(const EventSetRec *S, int mode, int flags) {
   return mode == HAWKES_MIXED && S->win32.nb > 0 &&
-         !(flags & (HAWKES_FLAG_EXCLUDE_SELF | HAWKES_FLAG_DENSE | HAWKES_FLAG_NO_SYMMETRY));
+         !(flags & (HAWKES_FLAG_EXCLUDE_SELF | HAWKES_FLAG_DENSE | HAWKES_FLAG_NO_SYMMETRY | kFlagTestWithholdReady));
 }
 
 // Float64 constants of the epilogue and compensator, from Theta (Section 2.1, d = 2).
@@ -298,12 +300,7 @@ int make_request(hawkes_ctx *ctx, const EventSetRec *S, const hawkes_params *p, 
   exact_zero_cutoffs(p, mode, R->beta, flags, S->n, &R->cut_early, &R->cut_late, &R->trig_cut);
   R->sym = use_symmetry(S, mode, flags) ? 1 : 0;
   R->mix = 1;
-  // fixed-point scale of the column sums: every event's total is at most npad (terms <= 1, and
-  // q 2^-q <= 1), so round(total 2^F) stays below 2^62
-  int bits = 0;
-  while (((int64_t)1 << bits) < S->npad) ++bits;
-  R->fix_scale = std::ldexp(1.0f, 62 - bits);
-  R->fix_inv = std::ldexp(1.0, bits - 62);
+  set_fix_bits(R, grad, 1, p->h, p->omega, 0.0, 0.0, S->t_last32 - S->t_first32);
   (void)ctx;
   return HAWKES_OK;
 }
@@ -311,7 +308,7 @@ int make_request(hawkes_ctx *ctx, const EventSetRec *S, const hawkes_params *p, 
 // Component 2 of a trigger mixture (the Discussion's extension; hawkes_loglik_mix): the second
 // triggering function's constants go to the launch (Batch::mix2), and the exact-zero windows take
 // the longer of the two trigger reaches. R holds the request made from component 1.
-int set_mixture(const hawkes_mix_params *m, int mode, Request *R, MixConst *M2) {
+int set_mixture(const hawkes_mix_params *m, int mode, double span, Request *R, MixConst *M2) {
   const double log2e = kLog2e, th2 = m->theta[1], om2 = m->omega[1], h2 = m->h[1];
   if (!std::isfinite(th2) || th2 < 0.0 || !finite_pos(om2) || !finite_pos(h2)) return HAWKES_E_INVAL;
   std::memset(M2, 0, sizeof(*M2));
@@ -332,6 +329,7 @@ int set_mixture(const hawkes_mix_params *m, int mode, Request *R, MixConst *M2) 
   R->trig_cut = std::max(R->trig_cut, trig2);
   R->cut_early = std::max(R->cut_early, early2);
   R->mix = 2;
+  set_fix_bits(R, R->grad, 2, R->h, R->omega, h2, om2, span);
   return HAWKES_OK;
 }
 
@@ -348,8 +346,10 @@ size_t set_slots(const EventSetRec *S, int mode, int grad) {
   return (size_t)std::max(alone, pair_items(R));
 }
 
-size_t request_footprint(const EventSetRec *S, int mode, int grad, int m = 1) {
-  const size_t items = set_slots(S, mode, grad);
+// With the shared background (sym) a request keeps no partial-sum slots: its per-event sums sit
+// in fixed point among its counters (counter_bytes).
+size_t request_footprint(const EventSetRec *S, int mode, int grad, int m = 1, int sym = 0) {
+  const size_t items = sym ? 0 : set_slots(S, mode, grad);
   size_t b = align_up(items * sums_of(grad, m) * kRowTile * sizeof(double), 256);
   b += 2 * align_up((size_t)S->nrt * kOut * sizeof(double), 256);
   return b;
@@ -357,13 +357,14 @@ size_t request_footprint(const EventSetRec *S, int mode, int grad, int m = 1) {
 
 // Bytes of a request's counters, kept in one zeroed region per batch: the merge-tree nodes of
 // its row tiles and one final counter (Request::rt_count); with sym, the row tiles' completion
-// counters (Request::rt_done) and the fixed-point column sums (Request::colfix).
+// counters (Request::rt_done) and the per-event fixed-point sums (Request::fixsum, num_sums x
+// npad integers: 4.1 MB for loglik + gradient at N = 85,000).
 size_t merge_counter_bytes(const EventSetRec *S, int mode, int grad) {
   return (2 * (size_t)S->nrt * S->slices[kind_of(mode, grad)] + 1) * sizeof(unsigned);
 }
-size_t counter_bytes(const EventSetRec *S, int mode, int grad, int sym) {
+size_t counter_bytes(const EventSetRec *S, int mode, int grad, int sym, int m = 1) {
   size_t b = merge_counter_bytes(S, mode, grad);
-  if (sym) b = align_up(b + (size_t)S->nrt * sizeof(unsigned), 256) + colfix_sums(grad != 0) * S->npad * 8;
+  if (sym) b = align_up(b + (size_t)S->nrt * sizeof(unsigned), 256) + (size_t)num_sums(grad != 0, m) * S->npad * 8;
   return align_up(b, 256);
 }
 
@@ -378,21 +379,22 @@ constexpr size_t kFixedBytes = kHdrBytes + kOutBytes;
 static_assert(kHdrBytes >= kMaxBatch * sizeof(unsigned), "one status word per request");
 
 // The status of request r from the copied-back header: HAWKES_E_DEVICE if one of its device
-// waits ran out (its results are NaN), else HAWKES_OK.
+// waits ran out (its results are NaN), else HAWKES_OK (a sum outside the fixed-point range,
+// kStatusFixRange, leaves NaN results with HAWKES_OK, as any non-finite evaluation does).
 int device_status(const void *header, int r) {
-  return ((const unsigned *)header)[r] ? HAWKES_E_DEVICE : HAWKES_OK;
+  return (((const unsigned *)header)[r] & kStatusMergeTimeout) ? HAWKES_E_DEVICE : HAWKES_OK;
 }
 
-// Carve one request's workspace out of `base` (as sized by request_footprint with the same m) and
-// its counters out of `counters` (as sized by counter_bytes).
+// Carve one request's workspace out of `base` (as sized by request_footprint with the same m and
+// R->sym) and its counters out of `counters` (as sized by counter_bytes).
 void bind_workspace(Request *R, const EventSetRec *S, int mode, int grad, char *base, double *out,
                     unsigned *counters, int m = 1) {
   if (R->sym) {
     const size_t m = merge_counter_bytes(S, mode, grad);
     R->rt_done = (unsigned *)((char *)counters + m);
-    R->colfix = (long long *)((char *)counters + align_up(m + (size_t)S->nrt * sizeof(unsigned), 256));
+    R->fixsum = (long long *)((char *)counters + align_up(m + (size_t)S->nrt * sizeof(unsigned), 256));
   }
-  const size_t items = set_slots(S, mode, grad);
+  const size_t items = R->sym ? 0 : set_slots(S, mode, grad);
   size_t off = 0;
   R->partials = (double *)(base + off);
   off += align_up(items * sums_of(grad, m) * kRowTile * sizeof(double), 256);
@@ -540,7 +542,6 @@ int eval_locked(hawkes_ctx *ctx, EventSetRec *S, int k, const hawkes_params *par
                 char *pi_dev, const hawkes_mix_params *mix) {
   if (mix && k != 1) return HAWKES_E_INVAL;
   const int m = mix ? 2 : 1;  // trigger components
-  const size_t per = request_footprint(S, mode, grad, m);
   // per-event rows. mu and xi (one request) are written by the kernel straight into the
   // caller's host arrays where the device writes pageable host memory (0.50 -> 0.40 ms at
   // 85k). pi rows (k requests) are staged in device memory and copied out through the bounce
@@ -558,7 +559,8 @@ int eval_locked(hawkes_ctx *ctx, EventSetRec *S, int k, const hawkes_params *par
   // alone, sharing the background terms of far column tiles where use_symmetry allows it.
   const bool grouped = k >= (grad ? HK_GROUP_MIN_K : HK_GROUP_MIN_K_LL) && mode == HAWKES_MIXED;
   const int sym = !grouped && use_symmetry(S, mode, ctx->flags) ? 1 : 0;
-  const size_t cnt_one = counter_bytes(S, mode, grad, sym);
+  const size_t per = request_footprint(S, mode, grad, m, sym);
+  const size_t cnt_one = counter_bytes(S, mode, grad, sym, m);
   const size_t cnt = align_up(cnt_one * k, 256);
   const size_t need = kFixedBytes + cnt + rows_bytes + per * k;
   if (int rc = ensure_sync_ws(ctx, need)) return rc;
@@ -579,7 +581,7 @@ int eval_locked(hawkes_ctx *ctx, EventSetRec *S, int k, const hawkes_params *par
     if (int rc = make_request(ctx, S, &params[q], mode, grad, ctx->flags, &b->req[r])) return rc;
     b->req[r].sym = sym;
     if (mix)
-      if (int rc = set_mixture(mix, mode, &b->req[r], &b->mix2)) return rc;
+      if (int rc = set_mixture(mix, mode, S->t_last32 - S->t_first32, &b->req[r], &b->mix2)) return rc;
     bind_workspace(&b->req[r], S, mode, grad, req_base + (size_t)r * per,
                    device_out ? device_out + kOut * q : outs + kOut * q, (unsigned *)(cnt_base + (size_t)r * cnt_one),
                    m);
@@ -1305,7 +1307,7 @@ int hawkes_submit(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *params, 
     Request probe;
     if (int rc = make_request(ctx, S, params, mode, T.grad, ctx->flags, &probe)) return rc;
     T.flags = ctx->flags;
-    T.footprint = request_footprint(S, mode, T.grad);
+    T.footprint = request_footprint(S, mode, T.grad, 1, probe.sym);
     if (T.footprint + counter_bytes(S, mode, T.grad, probe.sym) + 4096 > ctx->budget) return HAWKES_E_ADMISSION;
     S->refs++;
   }

@@ -39,6 +39,7 @@ constexpr int kSumsGrad = 6;                         // S_b, S_s, R_b, T_b, R_s,
 constexpr int kMixMax = 2;
 // Row sums of a kernel: S_b, S_s1[, S_s2] (loglik); S_b, S_s1, R_b, T_b, R_s1, U_s1[, S_s2, R_s2, U_s2]
 __host__ __device__ constexpr int num_sums(bool grad, int mix) { return grad ? 3 + 3 * mix : 1 + mix; }
+constexpr int kMaxSums = num_sums(true, kMixMax);
 // Gradient entries: (mu0, tau_x, tau_t) and (theta, omega, h) per component.
 __host__ __device__ constexpr int num_grad(int mix) { return 3 + 3 * mix; }
 constexpr int kOut = 16;  // doubles per request in out, comp and rt_sum: ell, then up to 9 gradient terms
@@ -47,6 +48,8 @@ constexpr int kFlagDense = 2;                        // HAWKES_FLAG_DENSE
 constexpr int kFlagNoSymmetry = 4;                   // HAWKES_FLAG_NO_SYMMETRY
 constexpr int kFlagTestWithholdReady = 1 << 30;      // HAWKES_FLAG_TEST_WITHHOLD_READY (tests only)
 constexpr unsigned kStatusMergeTimeout = 1u;         // Request::status: a merge-tree wait ran out
+constexpr unsigned kStatusFixRange = 2u;             // Request::status: a sum left the fixed-point range
+                                                     // (not finite, or |v 2^F| >= 2^62): results NaN
 // widest pair-kernel CTA: the grouped kernel's, two rows per thread
 constexpr int kMaxCtaWarps = (kRowTile / 2 > kThreads ? kRowTile / 2 : kThreads) / 32;
 static_assert(kThreads <= 32 * kMaxCtaWarps && kRowTile / 4 <= 32 * kMaxCtaWarps, "CTA too wide");
@@ -153,14 +156,14 @@ struct Request {
                        // the finished row-tile epilogues and compensator items
   double *rt_sum;      // nrt * kOut: per row tile, sum of log lambda_n and of the gradient terms
   // symmetric background (see SymPlan): far column tiles share each background term between its
-  // row and its column; column sums go to colfix as exact fixed-point integers
+  // row and its column. Every event's sums, from its row's items and from the far column tiles
+  // holding it, go to fixsum as exact fixed-point integers (no partial-sum slots, no merge tree).
   int sym;             // 1: on (mixed, fused, set with a time table, no exclude-self/dense/no-symmetry)
+  signed char fix_bits[kMaxSums];  // sym: sum s enters fixsum as round(v 2^fix_bits[s]) (fix_bits_for)
   double trig_cut;     // days: columns earlier than t_n - trig_cut give trigger terms that contribute
                        // nothing (exact zeros in mixed precision; below 2^-70 of lambda_n in float64)
-  long long *colfix;   // sym: column sums of S_b (and Q, T_b with the gradient), [k][npad], zero at launch
-  unsigned *rt_done;   // sym: per row tile, row-side root plus column contributions, zero at launch
-  float fix_scale;     // 2^F: a float32 column sum v enters colfix as round(v 2^F)
-  double fix_inv;      // 2^-F
+  long long *fixsum;   // sym: [num_sums][npad] per-event sums in fixed point, zero at launch
+  unsigned *rt_done;   // sym: per row tile, its items' and the far column tiles' arrivals, zero at launch
   double *out;         // ell, then d ell / d Theta (6 entries, 9 for a two-component mixture)
   unsigned *status;    // device word, zero at launch: kStatusMergeTimeout if a device wait of
                        // this request ran out (its results are then NaN), or nullptr
@@ -219,8 +222,42 @@ __host__ __device__ inline int pair_items(const Request &R) {
 __host__ __device__ inline int request_items(const Request &R) { return comp_items(R) + pair_items(R); }
 // Merge-tree nodes (fewer than 2 per leaf) of every row tile, then the final counter.
 __host__ __device__ inline int request_counters(const Request &R) { return 2 * R.set.nrt * R.slices + 1; }
-// Column sums kept in colfix per event: S_b, and Q, T_b with the gradient.
-__host__ __device__ inline int colfix_sums(bool grad) { return grad ? 3 : 1; }
+// Pair items of a row tile whose items span `span` leaves each.
+__host__ __device__ inline int rowtile_items(const Request &R, int span) { return (R.slices + span - 1) / span; }
+
+// Fixed-point scales of the per-event sums (Request::fixsum). A sum over at most npad terms, each
+// at most B, stays below 2^62 as round(v 2^F) when 2^F <= 2^62 / (npad B); F = 62 - ceil(log2
+// npad) - ceil(log2 B). The per-term bounds B, in the units the kernels accumulate:
+//   S_b, S_s: 1 (terms 2^-q, q >= 0);  Q = sum q 2^-q and T_b = sum u 2^-q with 0 <= u <= q:
+//   q 2^-q <= 1 / (e ln 2) < 1;  R_s = sum r^2 e_s: r^2 2^(cn r^2) <= 2 h^2 / e;
+//   U_s = sum dt e_s (units of time): dt e^(-omega dt) <= min(1 / (e omega), span of the times).
+// The absolute resolution 2^-F is about npad B 2^-62 (2.8e-14 for S_b at N = 85,000, against a
+// floor of 1 for the self term, so S_b keeps 14 digits; every other sum enters lambda_n and the
+// gradient through ratios to lambda_n, so its absolute resolution is what matters).
+inline int fix_bits_for(int64_t npad, double bound) {
+  int bits = 0;
+  while (((int64_t)1 << bits) < npad) ++bits;
+  int b = 0;
+  if (bound > 1.0) b = (int)std::ceil(std::log2(bound));
+  else if (bound > 0.0) b = -(int)std::floor(-std::log2(bound));  // ceil(log2 bound) <= 0
+  const int F = 62 - bits - b;
+  return F < -100 ? -100 : F > 120 ? 120 : F;
+}
+// The fixed-point scales of one request: component c's trigger sums with its own h and omega.
+inline void set_fix_bits(Request *R, int grad, int mix, double h1, double om1, double h2, double om2, double span) {
+  const double e = 2.71828182845904523536;
+  const int64_t np = R->set.npad;
+  for (int s = 0; s < kMaxSums; ++s) R->fix_bits[s] = (signed char)fix_bits_for(np, 1.0);
+  if (!grad) return;
+  auto rs = [&](double h) { return 2.0 * h * h / e; };
+  auto us = [&](double om) { return std::fmin(1.0 / (e * om), span > 0.0 ? span : 1.0); };
+  R->fix_bits[4] = (signed char)fix_bits_for(np, rs(h1));
+  R->fix_bits[5] = (signed char)fix_bits_for(np, us(om1));
+  if (mix > 1) {
+    R->fix_bits[7] = (signed char)fix_bits_for(np, rs(h2));
+    R->fix_bits[8] = (signed char)fix_bits_for(np, us(om2));
+  }
+}
 
 // The request's p-th pair item in launch order: row tile rt, index `node` among the row tile's
 // items, leaves [node * span, min(node * span + span, slices)), and `base`, the slot of the row
@@ -247,20 +284,22 @@ __host__ __device__ inline int first_item_of(const Request &R, int rt) {
 // A background term e_b(n, n') = e_b(n', n) serves the rows of both events. With R.sym, a row
 // tile K evaluates the column tiles J of its window that lie beyond the trigger's exact-zero
 // reach (every trigger term of K's rows with them is zero) once, adding each term to its row
-// (float64 row sums, as for any tile) and to its column (float32 column sums per tile, added to
-// colfix as integers round(v 2^F), which commute exactly, so the totals do not depend on the
-// order in which tiles finish). Those "far" column tiles are [c0(K), 2 ib(K)):
+// and to its column. Those "far" column tiles are [c0(K), 2 ib(K)):
 //   c0(K) = table_first(t_K - cut_early), ib(K) = table_first(t_K - trig_cut) / 2,
 // with t_K the time of row tile K's first event; they end on a row-tile boundary, so a far
 // block always covers whole row tiles' columns. Every other pair is evaluated row by row as
 // before: row tile I visits the column tiles [max(c0(I), 2 ib(I)), min(c1(I), 2 kmax(I) + 2)),
 // kmax(I) = the last row tile K with ib(K) <= I (the later row tiles for which I is not far).
 // A pair (n in I, n' in K > I) is so covered exactly once in each direction: by K's far block
-// when I < ib(K), else by I's late columns (K <= kmax(I)) and K's near early columns. Row tile
-// I is complete when its row-side merge-tree root and the e_col(I) far blocks holding its
-// columns have arrived at rt_done[I]: each far column tile adds 1, the root adds
-// kSymRootMark - e_col(I), and the arrival that brings the counter to kSymRootMark runs I's
-// epilogue (the root stores its row sums in the slot of I's first item before it arrives).
+// when I < ib(K), else by I's late columns (K <= kmax(I)) and K's near early columns.
+// Every event's sums reach R.fixsum as integers round(v 2^F) (fix_bits_for): each item adds its
+// rows' float64 sums, each far block its columns' float32 sums. Integer additions commute
+// exactly, so the totals do not depend on the order in which items finish. Row tile I is
+// complete when its items and the e_col(I) far blocks holding its columns have arrived at
+// rt_done[I]: each far column tile adds 1, each item of I adds 1 except I's first item (node 0),
+// which adds kSymRootMark - e_col(I) - (items(I) - 1); the arrival that brings the counter to
+// kSymRootMark runs I's epilogue from fixsum. Every arrival comes after its additions and a
+// fence, so nothing waits for anything.
 constexpr unsigned kSymRootMark = 1u << 30;
 
 struct SymK {
@@ -505,8 +544,8 @@ __device__ void compensator_tile(const Request &R, const MixConst &M2, const TT 
 
 // Count one finished row-tile epilogue or compensator item of request R; the CTA that
 // finishes the last of them writes ell = sum over row tiles of (rt_sum - comp) and the
-// gradient, in a fixed order, to R.out. Called by every thread of the CTA after its results
-// are written.
+// gradient, in a fixed order, to R.out (NaN if a sum of the request left the fixed-point range,
+// kStatusFixRange). Called by every thread of the CTA after its results are written.
 template <bool GRAD, int MIX = 1>
 __device__ void finish_request(const Request &R) {
   constexpr int NV = GRAD ? 1 + num_grad(MIX) : 1;
@@ -537,6 +576,8 @@ __device__ void finish_request(const Request &R) {
     if (tid < NV) {
       double x = 0.0;
       for (int w = 0; w < nw; ++w) x += red3[w * kRedWidth + tid];
+      // a sum that left the fixed-point range (red_fix) was not added: the results are NaN
+      if (R.status && (__ldcg(R.status) & kStatusFixRange)) x = __longlong_as_double(0x7ff8000000000000ll);
       R.out[tid] = x;
     }
   }

@@ -284,11 +284,42 @@ __device__ __forceinline__ void tile_pass(const float4 *__restrict__ sxs, const 
   }
 }
 
-// A float32 column sum v >= 0 into a fixed-point accumulator: round(v 2^F) as an integer, so
-// that the totals are exact and independent of the order of the additions.
-__device__ __forceinline__ void red_fix(long long *p, float v, float scale) {
-  if (v != 0.f) atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)__float2ll_rn(v * scale));
+// A sum v >= 0 into a fixed-point accumulator: round(v 2^F) as an integer (scale = 2^F), so that
+// the totals are exact and independent of the order of the additions. A value outside the range
+// (not finite, or |v 2^F| >= 2^62) is not added and sets the CTA's flag *bad (shared memory; the
+// request's results then become NaN).
+__device__ __forceinline__ void red_fix(long long *p, float v, float scale, int *bad) {
+  const float x = v * scale;
+  if (x == 0.f) return;
+  if (!(fabsf(x) < 0x1p62f)) { *bad = 1; return; }
+  atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)__float2ll_rn(x));
 }
+#ifndef HK_FIX_INT_CONVERT
+#define HK_FIX_INT_CONVERT 0
+#endif
+__device__ __forceinline__ void red_fix(long long *p, double v, double scale, int *bad) {
+#if HK_FIX_INT_CONVERT
+  // v 2^F truncated toward zero from the bits of v (integer pipe; scale = 2^F exactly)
+  const int F = (int)((__double_as_longlong(scale) >> 52) & 0x7ff) - 1023;
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int e = (int)(b >> 52) & 0x7ff;
+  if (e == 0) return;  // zero, or below 2^-1022
+  const int sh = e - 1075 + F;
+  if (e == 0x7ff || sh >= 9) { *bad = 1; return; }  // not finite, or |v 2^F| >= 2^62
+  if (sh <= -53) return;
+  const unsigned long long m = (b & 0xfffffffffffffull) | 0x10000000000000ull;
+  const unsigned long long r = sh >= 0 ? m << sh : m >> -sh;
+  atomicAdd(reinterpret_cast<unsigned long long *>(p), (b >> 63) ? 0ull - r : r);
+#else
+  const double x = v * scale;
+  if (x == 0.0) return;
+  if (!(fabs(x) < 0x1p62)) { *bad = 1; return; }
+  atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)__double2ll_rn(x));
+#endif
+}
+// 2^e as a double (|e| <= 1000) and as a float (|e| <= 126), from the exponent bits.
+__device__ __forceinline__ double pow2d(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
 
 // A far column tile (background terms only, see SymPlan in hk_internal.h) against this warp's
 // rows, each term serving its row and its column; columns are taken in pairs (a, b) = (2m, 2m + 1).
@@ -301,14 +332,16 @@ __device__ __forceinline__ void red_fix(long long *p, float v, float scale) {
 // (L + k) mod 32, so each step covers 2 row pairs x 1 column pair = 8 unordered pairs (16 terms);
 // the step's shares of the pair's column sums (over the lane's four rows) go by shuffle to the
 // owner, which receives from lane (L - k) mod 32, and after 32 steps each owner adds its pair's
-// sums over the warp's 128 rows to colfix. Every sum is formed in a fixed order. Per step and
+// sums over the warp's 128 rows to fixsum (S_b, Q and T_b: rows 0, 2 and 3). Every sum is formed
+// in a fixed order. Per step and
 // lane (with the gradient): 49 packed and 6 scalar float32 operations, 8 ex2, 3 loads, 6
 // shuffles, against 72 packed operations for the same 16 terms row by row.
 template <bool GRAD, int NS>
 __device__ __forceinline__ void tile_pass_sym_pairs(const float4 *__restrict__ sC, const float4 *__restrict__ sT,
                                                     const float2 (&XS)[kPairs], const float2 (&YS)[kPairs],
                                                     const float2 (&T)[kPairs], Acc32<NS> &acc,
-                                                    long long *__restrict__ colfix, int npad, int c0, float fix_scale) {
+                                                    long long *__restrict__ fixsum, int npad, int c0, float fix_scale,
+                                                    int *bad) {
   const int lane = threadIdx.x & 31;
 #pragma unroll 1
   for (int h = 0; h < kColTile / 64; ++h) {
@@ -358,14 +391,14 @@ __device__ __forceinline__ void tile_pass_sym_pairs(const float4 *__restrict__ s
                                   __shfl_sync(0xffffffffu, pu[0].y + pu[1].x, dst)));
       }
     }
-    long long *f = colfix + (size_t)c0 + 2 * (h * 32 + lane);
-    red_fix(f, cs.x, fix_scale);
-    red_fix(f + 1, cs.y, fix_scale);
+    long long *f = fixsum + (size_t)c0 + 2 * (h * 32 + lane);
+    red_fix(f, cs.x, fix_scale, bad);
+    red_fix(f + 1, cs.y, fix_scale, bad);
     if (GRAD) {
-      red_fix(f + npad, cq.x, fix_scale);
-      red_fix(f + npad + 1, cq.y, fix_scale);
-      red_fix(f + 2 * (size_t)npad, cu.x, fix_scale);
-      red_fix(f + 2 * (size_t)npad + 1, cu.y, fix_scale);
+      red_fix(f + 2 * (size_t)npad, cq.x, fix_scale, bad);
+      red_fix(f + 2 * (size_t)npad + 1, cq.y, fix_scale, bad);
+      red_fix(f + 3 * (size_t)npad, cu.x, fix_scale, bad);
+      red_fix(f + 3 * (size_t)npad + 1, cu.y, fix_scale, bad);
     }
   }
 }
@@ -481,15 +514,13 @@ __device__ __forceinline__ void cta_sync() {
 // (fused) the row tile's merge tree and, in the CTA that completes it, the tile's epilogue;
 // otherwise the sums go to the item's partial-sum slot.
 // The epilogue of row tile I (Section 2.1, Eq. 1): every event's row sums, get(s, k) for sum s of
-// this thread's row k (rows warp * kWarpRows + lane + 32 k), plus with R.sym the column sums its
-// far blocks left in colfix; then log lambda_n, the moment ratios and the fixed-order reductions
-// (hk_internal.h). Called by every thread of the CTA.
+// this thread's row k (rows warp * kWarpRows + lane + 32 k); then log lambda_n, the moment ratios
+// and the fixed-order reductions (hk_internal.h). Called by every thread of the CTA.
 template <bool GRAD, int MIX, class Get>
 __device__ void rowtile_epilogue(const Request &R, const MixConst &M2, int I, Get get) {
   constexpr int NS = num_sums(GRAD, MIX);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int n = R.set.n;
-  const size_t np = (size_t)R.set.npad;
   const double to_scaled = 1.0 / R.tscale;  // beta
   double v[GRAD ? 1 + NS : 1] = {};
 #pragma unroll
@@ -499,13 +530,6 @@ __device__ void rowtile_epilogue(const Request &R, const MixConst &M2, int I, Ge
       double sums[NS];
 #pragma unroll
       for (int s = 0; s < NS; ++s) sums[s] = get(s, k);
-      if (R.sym) {  // S_b, Q, T_b from the far blocks holding this event's column
-        sums[0] += (double)__ldcg(R.colfix + i) * R.fix_inv;
-        if (GRAD) {
-          sums[2] += (double)__ldcg(R.colfix + np + i) * R.fix_inv;
-          sums[3] += (double)__ldcg(R.colfix + 2 * np + i) * R.fix_inv;
-        }
-      }
       if (GRAD) {
         sums[2] = (sums[2] - sums[3]) * R.inv_a2;  // R_b from Q and T_b
         sums[5] *= to_scaled;                      // U_s: from units of time to scaled time
@@ -561,6 +585,10 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
   const float s_first = __shfl_sync(0xffffffffu, T[0].x, 0);            // scaled time of the warp's
   const float s_last = __shfl_sync(0xffffffffu, T[kPairs - 1].y, 31);  // first and last rows
 
+  __shared__ int s_bad;  // with R.sym: a sum of this item left the fixed-point range (red_fix)
+  if (tid == 0) s_bad = 0;
+  if (R.sym) cta_sync();
+
   // float64 row accumulators live in shared memory, one slot per (sum, row, thread)
 #pragma unroll
   for (int s = 0; s < NS; ++s)
@@ -608,7 +636,8 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
       tile_pass<0, GRAD, MIX>(sxs[buf], stx[buf], srt[buf], XS, YS, T, T, LO, row_a0, c0, excl, A2, CN, CN, CN2, CN2,
                               CN, acc);
     } else if (kind == 4) {
-      tile_pass_sym_pairs<GRAD>(sxs[buf], stx[buf], XS, YS, T, acc, R.colfix, S.npad, c0, R.fix_scale);
+      tile_pass_sym_pairs<GRAD>(sxs[buf], stx[buf], XS, YS, T, acc, R.fixsum, S.npad, c0, pow2f(R.fix_bits[0]),
+                                &s_bad);
     } else if (kind == 1 || kind == 3) {
       row_coords<false>(S, row_a0, sk, X, Y);
       row_times(S, row_a0, TR);
@@ -703,6 +732,54 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
     store(it.rt * R.slices + it.node * it.span);
     return;
   }
+  if (R.sym) {
+    // Every event's sums go to fixsum: this item's far column tiles [c_begin, f_end) have added
+    // their columns' shares there; now its rows' float64 sums. Then it arrives at the row tiles
+    // holding its far columns and at its own (SymPlan); the arrival that completes a row tile
+    // runs that tile's epilogue from fixsum.
+    const size_t np = (size_t)S.npad;
+    long long *fx = R.fixsum + row0 + warp * kWarpRows + lane;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const double scale = pow2d(R.fix_bits[s]);
+#pragma unroll
+      for (int k = 0; k < kRowsPerThread; ++k)
+        red_fix(fx + s * np + 32 * k, sacc[(s * kRowsPerThread + k) * kThreads + tid], scale, &s_bad);
+    }
+    cta_sync();
+    if (tid == 0 && s_bad && R.status) atomicOr(R.status, kStatusFixRange);
+#ifndef HK_ARRIVE_FENCE_ONE
+#define HK_ARRIVE_FENCE_ONE 0
+#endif
+#if HK_ARRIVE_FENCE_ONE
+    if (tid == 0) __threadfence();  // after the barrier: orders every thread's additions
+#else
+    __threadfence();
+    cta_sync();
+#endif
+    auto from_fix = [&](int I) {
+      __threadfence();
+      const long long *src = R.fixsum + (size_t)I * kRowTile + warp * kWarpRows + lane;
+      rowtile_epilogue<GRAD, MIX>(R, B.mix2, I, [&](int s, int k) {
+        return (double)__ldcg(src + s * np + 32 * k) * pow2d(-R.fix_bits[s]);
+      });
+    };
+    __shared__ unsigned s_arrive;
+    const int f_end = min(c_end, plan.sym_end);
+    for (int I = c_begin / 2; c_begin < f_end && I <= (f_end - 1) / 2; ++I) {
+      const unsigned tiles = (unsigned)(min(f_end, 2 * I + 2) - max(c_begin, 2 * I));
+      if (tid == 0) s_arrive = atomicAdd(R.rt_done + I, tiles) + tiles == kSymRootMark;
+      cta_sync();
+      if (s_arrive) from_fix(I);
+      cta_sync();
+    }
+    const unsigned items = (unsigned)rowtile_items(R, it.span);
+    const unsigned add = it.node == 0 ? kSymRootMark - (unsigned)plan.e_col - (items - 1u) : 1u;
+    if (tid == 0) s_arrive = atomicAdd(R.rt_done + it.rt, add) + add == kSymRootMark;
+    cta_sync();
+    if (s_arrive) from_fix(it.rt);
+    return;
+  }
   auto merge = [&](int from) {
     const double *src = R.partials + (size_t)from * NS * kRowTile;
 #pragma unroll
@@ -711,40 +788,9 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
       for (int s = 0; s < NS; ++s)
         sacc[(s * kRowsPerThread + k) * kThreads + tid] += __ldcg(src + s * kRowTile + warp * kWarpRows + lane + 32 * k);
   };
-  __shared__ unsigned s_arrive;
-  const int f_end = min(c_end, plan.sym_end);
-  if (R.sym && c_begin < f_end) {
-    // this item's far column tiles [c_begin, f_end) arrive at the row tiles holding their columns;
-    // the arrival that completes a row tile runs its epilogue from the slot of its first item
-    __threadfence();
-    cta_sync();
-    for (int I = c_begin / 2; I <= (f_end - 1) / 2; ++I) {
-      const unsigned tiles = (unsigned)(min(f_end, 2 * I + 2) - max(c_begin, 2 * I));
-      if (tid == 0) s_arrive = atomicAdd(R.rt_done + I, tiles) + tiles == kSymRootMark;
-      cta_sync();
-      if (s_arrive) {
-        __threadfence();
-        const double *slot = R.partials + (size_t)first_item_of(R, I) * NS * kRowTile;
-        rowtile_epilogue<GRAD, MIX>(R, B.mix2, I, [&](int s, int k) {
-          return __ldcg(slot + s * kRowTile + warp * kWarpRows + lane + 32 * k);
-        });
-      }
-      cta_sync();
-    }
-  }
   const int root = merge_tree<GRAD>(R, it, store, merge);
   if (root < 0) mark_timeout(R);
   if (root <= 0) return;
-  if (R.sym) {  // the row side is complete: store it, then arrive (kSymRootMark - e_col)
-    store(it.base);
-    __threadfence();
-    cta_sync();
-    if (tid == 0)
-      s_arrive = atomicAdd(R.rt_done + it.rt, kSymRootMark - (unsigned)plan.e_col) == (unsigned)plan.e_col;
-    cta_sync();
-    if (!s_arrive) return;
-    __threadfence();
-  }
   rowtile_epilogue<GRAD, MIX>(R, B.mix2, it.rt,
                               [&](int s, int k) { return sacc[(s * kRowsPerThread + k) * kThreads + tid]; });
 }

@@ -6,6 +6,8 @@
 // 2. Mean and RMS relative error of ex2.approx.ftz.f32 against exp2 in double, for arguments
 //    -q with q drawn uniformly from each quarter-unit bin of [0, 16): the argument-dependent
 //    bias of the float32 exponential that the pair kernels use.
+// 3. Rates of the float64 and conversion sequences that accumulate the row sums (see
+//    rate64_kernel), in sequences per second.
 // Prints one JSON object. Built and run by bench.py --probe-units.
 #include <cmath>
 #include <cstdio>
@@ -68,6 +70,61 @@ double lane_ops_per_s(int sms, double lanes_per_iter_and_chain) {
   return (double)blocks * threads * kIters * kChains * lanes_per_iter_and_chain / (best * 1e-3);
 }
 
+// Float64 and conversion rates, one dependent chain per (thread, chain), the same launch shape:
+// 7 DADD; 8 a float32 value folded into a float64 sum (FMUL, F2F.F64.F32, DADD); 9 a float32
+// value into an int64 sum (FMUL, F2I.S64.F32, 64-bit add); 10 a double into an int64 sum (DMUL,
+// F2I.S64.F64, 64-bit add); 11 a 64-bit integer add.
+template <int OP>
+__global__ void rate64_kernel(float *out, float s) {
+  double d[kChains];
+  float f[kChains];
+  long long l[kChains];
+  const double c = 1.0000001 + (double)s * 1e-9;
+  for (int i = 0; i < kChains; ++i) {
+    d[i] = threadIdx.x * 1e-9 + i;
+    f[i] = 1.0f + i * 0.25f;
+    l[i] = threadIdx.x + i;
+  }
+  for (int it = 0; it < kIters; ++it) {
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) {
+      if (OP == 7) d[i] = __dadd_rn(d[i], c);
+      if (OP == 8) { f[i] = __fmul_rn(f[i], s); d[i] = __dadd_rn(d[i], (double)f[i]); }
+      if (OP == 9) { f[i] = __fmul_rn(f[i], s); l[i] += __float2ll_rn(f[i]); }
+      if (OP == 10) { d[i] = __dmul_rn(d[i], c); l[i] += __double2ll_rn(d[i]); }
+      if (OP == 11) l[i] += (long long)s + it;
+    }
+  }
+  double acc = 0.0;
+  for (int i = 0; i < kChains; ++i) acc += d[i] + f[i] + (double)l[i];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = (float)acc;
+}
+
+template <int OP>
+double ops64_per_s(int sms) {
+  const int threads = 256, blocks = sms * 4;
+  float *out = nullptr;
+  if (cudaMalloc(&out, (size_t)blocks * threads * sizeof(float)) != cudaSuccess) return -1.0;
+  rate64_kernel<OP><<<blocks, threads>>>(out, 1.0001f);  // warm-up
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  for (int rep = 0; rep < 3; ++rep) {
+    cudaEventRecord(e0);
+    rate64_kernel<OP><<<blocks, threads>>>(out, 1.0001f);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) best = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  return (double)blocks * threads * kIters * kChains / (best * 1e-3);
+}
+
 constexpr int kBins = 64;  // q in [0, 16), bins of 0.25
 
 __global__ void ex2_error_kernel(unsigned long long seed, double *sum, double *sum2, unsigned long long *cnt) {
@@ -101,6 +158,12 @@ int main() {
   std::printf("\"fadd\": %.6e, ", lane_ops_per_s<4>(sms, 2.0));
   std::printf("\"fadd2_ffma2\": %.6e, ", lane_ops_per_s<5>(sms, 4.0));
   std::printf("\"mufu_ex2\": %.6e}, ", lane_ops_per_s<6>(sms, 1.0));
+  std::printf("\"sequences_per_s\": {");
+  std::printf("\"dadd\": %.6e, ", ops64_per_s<7>(sms));
+  std::printf("\"fold_f32_into_f64\": %.6e, ", ops64_per_s<8>(sms));
+  std::printf("\"f32_into_int64\": %.6e, ", ops64_per_s<9>(sms));
+  std::printf("\"f64_into_int64\": %.6e, ", ops64_per_s<10>(sms));
+  std::printf("\"iadd64\": %.6e}, ", ops64_per_s<11>(sms));
   double *s1 = nullptr, *s2 = nullptr;
   unsigned long long *c = nullptr;
   if (cudaMalloc(&s1, kBins * 8) != cudaSuccess || cudaMalloc(&s2, kBins * 8) != cudaSuccess ||

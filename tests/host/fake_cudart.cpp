@@ -134,8 +134,8 @@ cudaError_t cudaEventQuery(cudaEvent_t e) {
 
 namespace hk {
 
-// With the shared background (Request::sym): the completion counters and fixed-point column sums
-// start at zero, and the far/near plan of every row tile (SymPlan, as the kernels compute it from
+// With the shared background (Request::sym): the completion counters and fixed-point sums start
+// at zero, and the far/near plan of every row tile (SymPlan, as the kernels compute it from
 // the set's time table) covers every ordered block (rows of column tile H, columns of column tile
 // J) at most once, and exactly once where a term can be nonzero (J inside the window of H's row
 // tile, and, for a later J, H inside the window of J's row tile); e_col(I) counts the far column
@@ -147,11 +147,13 @@ static bool sym_fail(const char *what, int a, int b, int c) {
 
 static bool check_symmetry(const Request &R) {
   const SetView &S = R.set;
-  if (!R.rt_done || !R.colfix || S.win32.nb == 0 || !(R.fix_scale > 0.f)) return sym_fail("set-up", S.n, 0, 0);
+  if (!R.rt_done || !R.fixsum || S.win32.nb == 0) return sym_fail("set-up", S.n, 0, 0);
+  for (int s = 0; s < num_sums(R.grad != 0, R.mix); ++s)  // the far pass scales by a float 2^F
+    if (R.fix_bits[s] < -100 || R.fix_bits[s] > 120 || (s == 0 && R.fix_bits[0] > 126)) return sym_fail("fix_bits", S.n, s, R.fix_bits[s]);
   for (int I = 0; I < S.nrt; ++I)
     if (R.rt_done[I] != 0u) return sym_fail("rt_done not zero", S.n, I, 0);
-  for (size_t i = 0; i < (size_t)colfix_sums(R.grad != 0) * S.npad; ++i)
-    if (R.colfix[i] != 0) return sym_fail("colfix not zero", S.n, (int)i, 0);
+  for (size_t i = 0; i < (size_t)num_sums(R.grad != 0, R.mix) * S.npad; ++i)
+    if (R.fixsum[i] != 0) return sym_fail("fixsum not zero", S.n, (int)i, 0);
   if (S.nct > 1024) return true;  // the block table below grows as nct^2
   g_sym_checked++;
   auto tfirst = [&](int K) { return (double)S.t32[(size_t)K * kRowTile]; };
@@ -265,7 +267,8 @@ static cudaError_t fake_pair(const Batch &b, bool grad) {
       // every pair item's partial-sum slot (num_sums doubles per row of the tile) lies before the
       // compensator sums, which the workspace places right after the slots
       const Request &R = b.req[r];
-      const size_t slots = (size_t)pair_items(R) * num_sums(R.grad != 0, R.mix) * kRowTile;
+      // (none with the shared background, whose sums go to fixsum)
+      const size_t slots = R.sym ? 0 : (size_t)pair_items(R) * num_sums(R.grad != 0, R.mix) * kRowTile;
       if (R.partials + slots > R.comp) g_schedule_errors++;
     }
   }

@@ -238,7 +238,7 @@ def main():
     small = binding.Context(hbm_budget_bytes=1 << 18, lib=lib)
     expect_status(lambda: small.hawkes_upload_events(ev.x, ev.y, ev.t), -4)
     small.close()
-    tight = binding.Context(hbm_budget_bytes=2_300_000, lib=lib)
+    tight = binding.Context(hbm_budget_bytes=1_000_000, lib=lib)  # the set (about 0.95 MB) fits
     sid = tight.hawkes_upload_events(ev.x, ev.y, ev.t)
     expect_status(lambda: tight.hawkes_loglik_grad(sid, TH, 1), -4)
     expect_status(lambda: tight.hawkes_submit(sid, TH, True, 1), -4)

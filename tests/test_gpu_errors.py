@@ -74,7 +74,7 @@ def test_admission_budget(binding):
             ctx.hawkes_upload_events(ev.x, ev.y, ev.t)
         assert e.value.status == -4
     # a set fits but its evaluation workspace does not
-    with binding.Context(device=0, hbm_budget_bytes=2_300_000) as ctx:
+    with binding.Context(device=0, hbm_budget_bytes=1_000_000) as ctx:  # the set takes about 0.95 MB
         sid = ctx.hawkes_upload_events(ev.x, ev.y, ev.t)
         with pytest.raises(binding.HawkesError) as e:
             ctx.hawkes_loglik_grad(sid, synth.THETA0, 1)
@@ -118,16 +118,19 @@ def test_release_while_queued_then_destroy(binding):
 
 def test_device_wait_runs_out_and_is_reported(binding):
     """The one wait on the GPU (the gradient merge tree's climbing item waits for its sibling's
-    ready mark) is bounded. With HAWKES_FLAG_TEST_WITHHOLD_READY the first item at each merge
-    node of row tile 0 publishes its sums without the mark, so the wait runs out (after at most
-    0.5 s): the blocking, batched and serving calls return HAWKES_E_DEVICE, nothing hangs, and
-    calls without the flag on the same context still give the right results."""
+    ready mark; the merge tree serves float64, row-by-row mixed and grouped evaluations, and the
+    test flag selects the row-by-row one) is bounded. With HAWKES_FLAG_TEST_WITHHOLD_READY the
+    first item at each merge node of row tile 0 publishes its sums without the mark, so the wait
+    runs out (after at most 0.5 s): the blocking, batched and serving calls return
+    HAWKES_E_DEVICE, nothing hangs, and calls without the flag on the same context still give
+    the right results."""
     ev = synth.simulate(4000, 1500.0, seed=17)
     with binding.Context(device=0) as ctx:
         sid = ctx.hawkes_upload_events(ev.x, ev.y, ev.t)
         want = {m: ctx.hawkes_loglik_grad(sid, synth.THETA0, m) for m in (0, 1)}
         ths = synth.theta_batch(5, seed=18)
         want_batch = ctx.hawkes_loglik_batch(sid, ths, 1, want_grad=True)
+        ctx.hawkes_set_flags(binding.HAWKES_FLAG_NO_SYMMETRY)  # the test flag evaluates row by row
         want_ll = ctx.hawkes_loglik(sid, synth.THETA0, 1)
         ctx.hawkes_set_flags(binding.HAWKES_FLAG_TEST_WITHHOLD_READY)
         for mode in (0, 1):
@@ -151,3 +154,25 @@ def test_device_wait_runs_out_and_is_reported(binding):
         t = ctx.hawkes_submit(sid, synth.THETA0, True, 1)
         ll, g = ctx.hawkes_wait(t, 20000)
         assert ll == want[1][0] and np.array_equal(g, want[1][1])
+
+
+def test_out_of_range_sums_give_nan(binding):
+    """Events so far apart in space that the float32 quadratic form overflows give inf * 0 in the
+    background moment Q. The per-event fixed-point sums of the shared background refuse such a
+    value (it has no integer), and ell and the gradient come back NaN with HAWKES_OK; the float64
+    sums of the row-by-row path carry the NaN into the gradient terms of Q. The log-likelihood
+    alone has no moment and stays finite."""
+    n = 3000
+    rng = np.random.default_rng(5)
+    x = np.arange(n, dtype=np.float64) * 1e25
+    y = np.zeros(n)
+    t = np.sort(rng.uniform(0.0, 2000.0, n))
+    with binding.Context(device=0) as ctx:
+        sid = ctx.hawkes_upload_events(x, y, t)
+        for flags in (0, binding.HAWKES_FLAG_NO_SYMMETRY):
+            ctx.hawkes_set_flags(flags)
+            ll, g = ctx.hawkes_loglik_grad(sid, synth.THETA0, 1)
+            assert np.isnan(g).any()
+            if flags == 0:
+                assert np.isnan(ll) and np.all(np.isnan(g))
+            assert np.isfinite(ctx.hawkes_loglik(sid, synth.THETA0, 1))
