@@ -386,15 +386,16 @@ int device_status(const void *header, int r) {
 }
 
 // Carve one request's workspace out of `base` (as sized by request_footprint with the same m and
-// R->sym) and its counters out of `counters` (as sized by counter_bytes).
+// fix) and its counters out of `counters` (as sized by counter_bytes). fix: the request adds its
+// sums in fixed point (Request::fixsum), with the shared background or in a grouped batch.
 void bind_workspace(Request *R, const EventSetRec *S, int mode, int grad, char *base, double *out,
-                    unsigned *counters, int m = 1) {
-  if (R->sym) {
+                    unsigned *counters, int m, int fix) {
+  if (fix) {
     const size_t m = merge_counter_bytes(S, mode, grad);
     R->rt_done = (unsigned *)((char *)counters + m);
     R->fixsum = (long long *)((char *)counters + align_up(m + (size_t)S->nrt * sizeof(unsigned), 256));
   }
-  const size_t items = R->sym ? 0 : set_slots(S, mode, grad);
+  const size_t items = fix ? 0 : set_slots(S, mode, grad);
   size_t off = 0;
   R->partials = (double *)(base + off);
   off += align_up(items * sums_of(grad, m) * kRowTile * sizeof(double), 256);
@@ -559,8 +560,12 @@ int eval_locked(hawkes_ctx *ctx, EventSetRec *S, int k, const hawkes_params *par
   // alone, sharing the background terms of far column tiles where use_symmetry allows it.
   const bool grouped = k >= (grad ? HK_GROUP_MIN_K : HK_GROUP_MIN_K_LL) && mode == HAWKES_MIXED;
   const int sym = !grouped && use_symmetry(S, mode, ctx->flags) ? 1 : 0;
-  const size_t per = request_footprint(S, mode, grad, m, sym);
-  const size_t cnt_one = counter_bytes(S, mode, grad, sym, m);
+  // grouped batches add their sums in fixed point too, unless exclude-self takes away the
+  // background sum's floor of 1 or the test flag asks for the merge tree
+  const int gfix = grouped && !(ctx->flags & (HAWKES_FLAG_EXCLUDE_SELF | kFlagTestWithholdReady)) ? 1 : 0;
+  const int fix = sym || gfix;
+  const size_t per = request_footprint(S, mode, grad, m, fix);
+  const size_t cnt_one = counter_bytes(S, mode, grad, fix, m);
   const size_t cnt = align_up(cnt_one * k, 256);
   const size_t need = kFixedBytes + cnt + rows_bytes + per * k;
   if (int rc = ensure_sync_ws(ctx, need)) return rc;
@@ -584,10 +589,11 @@ int eval_locked(hawkes_ctx *ctx, EventSetRec *S, int k, const hawkes_params *par
       if (int rc = set_mixture(mix, mode, S->t_last32 - S->t_first32, &b->req[r], &b->mix2)) return rc;
     bind_workspace(&b->req[r], S, mode, grad, req_base + (size_t)r * per,
                    device_out ? device_out + kOut * q : outs + kOut * q, (unsigned *)(cnt_base + (size_t)r * cnt_one),
-                   m);
+                   m, fix);
     b->req[r].status = (unsigned *)base + q;
     if (grouped) {
       b->req[r].tscale = 1.0;
+      if (gfix) set_fix_bits_raw(&b->req[r], grad, S->t_last32 - S->t_first32);
       launch_tiers(S->nrt, mode, true, &b->req[r].wide, &b->req[r].coarse);
     }
   }
@@ -747,7 +753,7 @@ bool launch_pending(hawkes_ctx *ctx, Flight &F) {
     for (size_t r = 0; r < take.size() && rc == HAWKES_OK; ++r) {
       TicketRec &T = ctx->tickets[take[r]];
       rc = make_request(ctx, sets[r], &T.p, mode, grad, T.flags, &b->req[r]);
-      bind_workspace(&b->req[r], sets[r], mode, grad, cur, outs + kOut * r, (unsigned *)cnt_cur);
+      bind_workspace(&b->req[r], sets[r], mode, grad, cur, outs + kOut * r, (unsigned *)cnt_cur, 1, b->req[r].sym);
       b->req[r].status = (unsigned *)base + r;
       cnt_cur += counter_bytes(sets[r], mode, grad, b->req[r].sym);
       cur += T.footprint;

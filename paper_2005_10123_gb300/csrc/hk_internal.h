@@ -162,8 +162,10 @@ struct Request {
   signed char fix_bits[kMaxSums];  // sym: sum s enters fixsum as round(v 2^fix_bits[s]) (fix_bits_for)
   double trig_cut;     // days: columns earlier than t_n - trig_cut give trigger terms that contribute
                        // nothing (exact zeros in mixed precision; below 2^-70 of lambda_n in float64)
-  long long *fixsum;   // sym: [num_sums][npad] per-event sums in fixed point, zero at launch
-  unsigned *rt_done;   // sym: per row tile, its items' and the far column tiles' arrivals, zero at launch
+  long long *fixsum;   // sym, or a grouped batch without exclude-self: [num_sums][npad] per-event sums
+                       // in fixed point, zero at launch (nullptr: partial-sum slots and merge trees)
+  unsigned *rt_done;   // with fixsum: per row tile, the arrivals of its items (and, with sym, of the
+                       // far column tiles holding its columns), zero at launch
   double *out;         // ell, then d ell / d Theta (6 entries, 9 for a two-component mixture)
   unsigned *status;    // device word, zero at launch: kStatusMergeTimeout if a device wait of
                        // this request ran out (its results are then NaN), or nullptr
@@ -222,6 +224,10 @@ __host__ __device__ inline int pair_items(const Request &R) {
 __host__ __device__ inline int request_items(const Request &R) { return comp_items(R) + pair_items(R); }
 // Merge-tree nodes (fewer than 2 per leaf) of every row tile, then the final counter.
 __host__ __device__ inline int request_counters(const Request &R) { return 2 * R.set.nrt * R.slices + 1; }
+// The scales of a grouped-kernel request (pair_group.cu), whose moments are in raw units:
+// R_b = sum r^2 e_b with r^2 e^(-r^2 / (2 tau_x^2)) <= 2 tau_x^2 / e, and T_b = sum dt^2 e_b with
+// dt^2 e^(-dt^2 / (2 tau_t^2)) <= 2 tau_t^2 / e.
+inline void set_fix_bits_raw(Request *R, int grad, double span);
 // Pair items of a row tile whose items span `span` leaves each.
 __host__ __device__ inline int rowtile_items(const Request &R, int span) { return (R.slices + span - 1) / span; }
 
@@ -257,6 +263,13 @@ inline void set_fix_bits(Request *R, int grad, int mix, double h1, double om1, d
     R->fix_bits[7] = (signed char)fix_bits_for(np, rs(h2));
     R->fix_bits[8] = (signed char)fix_bits_for(np, us(om2));
   }
+}
+inline void set_fix_bits_raw(Request *R, int grad, double span) {
+  set_fix_bits(R, grad, 1, R->h, R->omega, 0.0, 0.0, span);
+  if (!grad) return;
+  const double e = 2.71828182845904523536;
+  R->fix_bits[2] = (signed char)fix_bits_for(R->set.npad, 2.0 * R->tau_x * R->tau_x / e);
+  R->fix_bits[3] = (signed char)fix_bits_for(R->set.npad, 2.0 * R->tau_t * R->tau_t / e);
 }
 
 // The request's p-th pair item in launch order: row tile rt, index `node` among the row tile's

@@ -114,6 +114,15 @@ __device__ __forceinline__ void gtile_pass(const float4 *__restrict__ sxy, const
   }
 }
 
+// A float32 row sum v >= 0 into a fixed-point accumulator as round(v 2^F) (scale = 2^F); a value
+// that is not finite or reaches 2^62 is not added and sets the CTA's flag *bad.
+__device__ __forceinline__ void gred_fix(long long *p, float v, float scale, int *bad) {
+  const float x = v * scale;
+  if (x == 0.f) return;
+  if (!(fabsf(x) < 0x1p62f)) { *bad = 1; return; }
+  atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)__float2ll_rn(x));
+}
+
 struct GStage {
   float4 sxy[2][kColTile];
   float2 st[2][kColTile];
@@ -216,9 +225,61 @@ __device__ void group_item(const Batch &B, int leader, int gsize, const PairItem
     __syncthreads();
   }
 
+  const int la = warp * kGWarpRows + lane, lb = la + 32;
+  if (R0.fixsum) {
+    // Fixed-point sums (every request of the batch has them, see Request::fixsum): each
+    // request's row sums go to its own per-event integers, round(v 2^F) with the request's
+    // scales, then the item arrives at its row tile's counter (the leader's rt_done); the item
+    // that completes the row tile runs the epilogue of every request of the group.
+    __shared__ int s_bad;
+    __shared__ unsigned s_last;
+    if (tid == 0) s_bad = 0;
+    __syncthreads();
+    const size_t np = (size_t)S.npad;
+#pragma unroll
+    for (int k = 0; k < G; ++k) {
+      if (k >= gsize) break;
+      const Request &R = B.req[leader + k];
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        const float scale = __int_as_float((127 + R.fix_bits[s]) << 23);
+        gred_fix(R.fixsum + s * np + row0 + la, acc.v[k][s].x, scale, &s_bad);
+        gred_fix(R.fixsum + s * np + row0 + lb, acc.v[k][s].y, scale, &s_bad);
+      }
+    }
+    __syncthreads();
+    if (tid == 0 && s_bad)
+      for (int k = 0; k < gsize; ++k)
+        if (B.req[leader + k].status) atomicOr(B.req[leader + k].status, kStatusFixRange);
+    __threadfence();
+    __syncthreads();
+    const unsigned items = (unsigned)rowtile_items(R0, it.span);
+    const unsigned add = it.node == 0 ? kSymRootMark - (items - 1u) : 1u;
+    if (tid == 0) s_last = atomicAdd(R0.rt_done + rt, add) + add == kSymRootMark;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (int k = 0; k < gsize; ++k) {
+      const Request &R = B.req[leader + k];
+      double v[GRAD ? 7 : 1] = {};
+      const int rows[2] = {la, lb};
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int i = row0 + rows[h];
+        if (i < n) {
+          double sums[NS];
+#pragma unroll
+          for (int s = 0; s < NS; ++s)
+            sums[s] = (double)__ldcg(R.fixsum + s * np + i) * __longlong_as_double((long long)(1023 - R.fix_bits[s]) << 52);
+          row_terms<GRAD>(R, B.mix2, i, sums, v);
+        }
+      }
+      rowtile_reduce<GRAD>(R, B.mix2, rt, v);
+    }
+    return;
+  }
   // float64 sums of the group's requests for this thread's rows; they reuse the staging space
   double *gsum = reinterpret_cast<double *>(smem);  // [G][NS][kRowTile]
-  const int la = warp * kGWarpRows + lane, lb = la + 32;
 #pragma unroll
   for (int k = 0; k < G; ++k)
 #pragma unroll

@@ -294,28 +294,11 @@ __device__ __forceinline__ void red_fix(long long *p, float v, float scale, int 
   if (!(fabsf(x) < 0x1p62f)) { *bad = 1; return; }
   atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)__float2ll_rn(x));
 }
-#ifndef HK_FIX_INT_CONVERT
-#define HK_FIX_INT_CONVERT 0
-#endif
 __device__ __forceinline__ void red_fix(long long *p, double v, double scale, int *bad) {
-#if HK_FIX_INT_CONVERT
-  // v 2^F truncated toward zero from the bits of v (integer pipe; scale = 2^F exactly)
-  const int F = (int)((__double_as_longlong(scale) >> 52) & 0x7ff) - 1023;
-  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-  const int e = (int)(b >> 52) & 0x7ff;
-  if (e == 0) return;  // zero, or below 2^-1022
-  const int sh = e - 1075 + F;
-  if (e == 0x7ff || sh >= 9) { *bad = 1; return; }  // not finite, or |v 2^F| >= 2^62
-  if (sh <= -53) return;
-  const unsigned long long m = (b & 0xfffffffffffffull) | 0x10000000000000ull;
-  const unsigned long long r = sh >= 0 ? m << sh : m >> -sh;
-  atomicAdd(reinterpret_cast<unsigned long long *>(p), (b >> 63) ? 0ull - r : r);
-#else
   const double x = v * scale;
   if (x == 0.0) return;
   if (!(fabs(x) < 0x1p62)) { *bad = 1; return; }
   atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)__double2ll_rn(x));
-#endif
 }
 // 2^e as a double (|e| <= 1000) and as a float (|e| <= 126), from the exponent bits.
 __device__ __forceinline__ double pow2d(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
@@ -748,15 +731,8 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
     }
     cta_sync();
     if (tid == 0 && s_bad && R.status) atomicOr(R.status, kStatusFixRange);
-#ifndef HK_ARRIVE_FENCE_ONE
-#define HK_ARRIVE_FENCE_ONE 0
-#endif
-#if HK_ARRIVE_FENCE_ONE
-    if (tid == 0) __threadfence();  // after the barrier: orders every thread's additions
-#else
     __threadfence();
     cta_sync();
-#endif
     auto from_fix = [&](int I) {
       __threadfence();
       const long long *src = R.fixsum + (size_t)I * kRowTile + warp * kWarpRows + lane;

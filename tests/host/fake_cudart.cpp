@@ -221,6 +221,11 @@ static void check_schedule(const Request &R, int mode) {
   for (int i = 0; ok && i < request_counters(R); ++i)
     if (R.rt_count[i] != 0u) ok = false;  // merge-tree and completion counters zeroed before the launch
   if (ok && R.sym) ok = check_symmetry(R);
+  if (ok && R.fixsum && !R.sym) {  // a grouped batch's fixed-point sums: zeroed, scales in range
+    for (int s = 0; ok && s < num_sums(R.grad != 0, R.mix); ++s) ok = R.fix_bits[s] >= -100 && R.fix_bits[s] <= 120;
+    for (int I = 0; ok && I < S.nrt; ++I) ok = R.rt_done[I] == 0u;
+    for (size_t i = 0; ok && i < (size_t)num_sums(R.grad != 0, R.mix) * S.npad; ++i) ok = R.fixsum[i] == 0;
+  }
   if (!ok) g_schedule_errors++;
 }
 
@@ -258,6 +263,8 @@ static cudaError_t fake_pair(const Batch &b, bool grad) {
         g_schedule_errors++;  // one set, one decomposition, raw-unit moments
     }
     if (items != b.comp_total || b.mode != 1) g_schedule_errors++;
+    for (int r = 0; r < b.nreq; ++r)  // every request of a grouped batch in fixed point, or none
+      if ((b.req[r].fixsum != nullptr) != (b.req[0].fixsum != nullptr) || b.req[r].sym) g_schedule_errors++;
     items += (b.nreq + b.group - 1) / b.group * pair_items(b.req[0]);
   } else {
     for (int r = 0; r < b.nreq; ++r) {
