@@ -59,7 +59,10 @@
 #define HK_COL_UNROLL_LL 8  // loglik only
 #endif
 #ifndef HK_SYM_UNROLL
-#define HK_SYM_UNROLL 2  // steps unrolled in the far (shared-background) tile pass
+#define HK_SYM_UNROLL 4  // steps unrolled in the far (shared-background) tile pass, loglik + gradient
+#endif
+#ifndef HK_SYM_UNROLL_LL
+#define HK_SYM_UNROLL_LL HK_SYM_UNROLL  // the same, loglik only
 #endif
 #ifndef HK_FAR_WEIGHT
 #define HK_FAR_WEIGHT 10  // cost of a far column tile in tenths of a near one, for the leaf split
@@ -126,7 +129,7 @@ __device__ __forceinline__ float2 accfma2(float2 a, float2 e, float2 s) {
 }
 
 constexpr int kPairs = kRowsPerThread / 2;  // packed row pairs per thread
-constexpr int kColUnroll = HK_COL_UNROLL, kColUnrollLL = HK_COL_UNROLL_LL, kSymUnroll = HK_SYM_UNROLL;
+constexpr int kColUnroll = HK_COL_UNROLL, kColUnrollLL = HK_COL_UNROLL_LL;
 constexpr int kColUnrollSep = HK_COL_UNROLL_SEP;
 
 template <int NS>
@@ -307,8 +310,10 @@ __device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) 
 // A far column tile (background terms only, see SymPlan in hk_internal.h) against this warp's
 // rows, each term serving its row and its column; columns are taken in pairs (a, b) = (2m, 2m + 1).
 // The tile is staged in pair
-// layout (store_cols_pairs): sC[m] = {-s x_a, -s x_b, -s y_a, -s y_b}, sC[64 + m] the same with a
-// and b swapped, sT[m] = {-t'_a, -t'_b, -t'_b, -t'_a}. A packed row pair (r0, r1) meets a column
+// layout (store_cols_pairs): sC[m] = {-s x_a, -s x_b, -s y_a, -s y_b} and, in the time array read
+// as float2, {-t'_a, -t'_b}; the swapped pair (b, a) is formed in registers from the same loads
+// (a second staged copy cost a third shared load per step, and loglik 3.5% of its time). A
+// packed row pair (r0, r1) meets a column
 // pair in two packed evaluations, e1 = (e(r0, a), e(r1, b)) and e2 = (e(r0, b), e(r1, a)): both
 // add to the row pair's sums as they are, and column a collects e1.x + e2.y, column b
 // e1.y + e2.x. Lane L owns column pair L of a 64-column chunk and at step k takes pair
@@ -317,7 +322,7 @@ __device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) 
 // owner, which receives from lane (L - k) mod 32, and after 32 steps each owner adds its pair's
 // sums over the warp's 128 rows to fixsum (S_b, Q and T_b: rows 0, 2 and 3). Every sum is formed
 // in a fixed order. Per step and
-// lane (with the gradient): 49 packed and 6 scalar float32 operations, 8 ex2, 3 loads, 6
+// lane (with the gradient): 49 packed and 6 scalar float32 operations, 8 ex2, 2 shared loads, 6
 // shuffles, against 72 packed operations for the same 16 terms row by row.
 template <bool GRAD, int NS>
 __device__ __forceinline__ void tile_pass_sym_pairs(const float4 *__restrict__ sC, const float4 *__restrict__ sT,
@@ -325,6 +330,7 @@ __device__ __forceinline__ void tile_pass_sym_pairs(const float4 *__restrict__ s
                                                     const float2 (&T)[kPairs], Acc32<NS> &acc,
                                                     long long *__restrict__ fixsum, int npad, int c0, float fix_scale,
                                                     int *bad) {
+  constexpr int kSymUnroll = GRAD ? HK_SYM_UNROLL : HK_SYM_UNROLL_LL;
   const int lane = threadIdx.x & 31;
 #pragma unroll 1
   for (int h = 0; h < kColTile / 64; ++h) {
@@ -332,10 +338,11 @@ __device__ __forceinline__ void tile_pass_sym_pairs(const float4 *__restrict__ s
 #pragma unroll kSymUnroll
     for (int k = 0; k < 32; ++k) {
       const int m = h * 32 + ((lane + k) & 31);
-      const float4 C = sC[m], W = sC[64 + m], T4 = sT[m];
-      const float2 cx[2] = {make_float2(C.x, C.y), make_float2(W.x, W.y)};
-      const float2 cy[2] = {make_float2(C.z, C.w), make_float2(W.z, W.w)};
-      const float2 ct[2] = {make_float2(T4.x, T4.y), make_float2(T4.z, T4.w)};
+      const float4 C = sC[m];
+      const float2 T2 = reinterpret_cast<const float2 *>(sT)[m];
+      const float2 cx[2] = {make_float2(C.x, C.y), make_float2(C.y, C.x)};
+      const float2 cy[2] = {make_float2(C.z, C.w), make_float2(C.w, C.z)};
+      const float2 ct[2] = {make_float2(T2.x, T2.y), make_float2(T2.y, T2.x)};
       float2 ps[2], pq[2], pu[2];  // per variant, summed over the row pairs
 #pragma unroll
       for (int p = 0; p < kPairs; ++p)
@@ -459,8 +466,7 @@ __device__ __forceinline__ void store_cols_pairs(const RawCols &r, int ct, int t
   const float xa = scale_split(r.x[0], k.s_hi, k.s_lo), xb = scale_split(r.x[1], k.s_hi, k.s_lo);
   const float ya = scale_split(r.y[0], k.s_hi, k.s_lo), yb = scale_split(r.y[1], k.s_hi, k.s_lo);
   sC[tid] = make_float4(-xa, -xb, -ya, -yb);
-  sC[64 + tid] = make_float4(-xb, -xa, -yb, -ya);
-  sT[tid] = make_float4(-ta, -tb, -tb, -ta);
+  reinterpret_cast<float2 *>(sT)[tid] = make_float2(-ta, -tb);
 }
 
 // This thread's row coordinates (rows ra = wa + lane + 32 k, packed in pairs k, k + 1),
@@ -594,7 +600,7 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
     const int c0 = ct * kColTile, c1 = c0 + kColTile;
     int kind, comps = 1;  // comps: the mixture components with nonzero trigger terms (bit mask)
     if (R.sym && ct < plan.sym_end) {  // far: background only, shared with the columns' rows
-      const float gap = s_first + stx[buf][kColTile / 2 - 1].y;  // pair layout: the latest column
+      const float gap = s_first + reinterpret_cast<const float2 *>(stx[buf])[kColTile / 2 - 1].y;  // the latest column
       kind = gap >= kBgZeroGap ? -1 : 4;
     } else if (c1 <= lo_wa) {  // every pair causal: which of the two terms can be nonzero?
       const float gap = s_first + stx[buf][kColTile - 1].x;  // t'(first row) - t'(latest column)
