@@ -80,7 +80,7 @@ extern "C" {
 #define HAWKES_FLAG_NO_SYMMETRY 4  /* HAWKES_MIXED: evaluate every ordered pair on its own     */
 /* By default a mixed-precision evaluation without HAWKES_FLAG_EXCLUDE_SELF or HAWKES_FLAG_DENSE
  * shares background terms: e_b(n, n') = e_b(n', n), so for column tiles far enough before a row
- * tile that no trigger term can be nonzero (beyond the trigger's exact-zero reach) each pair term
+ * tile that no trigger term can change the sums (beyond the trigger's reach, see below) each pair term
  * is formed once and added to both events' rows. Every event's sums (its row's, and the shares of
  * the far tiles holding it) are then added as exact fixed-point integers: 2^-F resolution with
  * F = 62 - ceil(log2 N_padded) for the background sums (about 3e-14 at N = 85,000, against a
@@ -100,15 +100,15 @@ extern "C" {
  * calls without the flag are unaffected. */
 #define HAWKES_FLAG_TEST_WITHHOLD_READY (1 << 30)
 /* By default each row only visits the columns whose pair terms can change its sums at the
- * working precision. HAWKES_MIXED: a pair term whose exponent is so negative that float32 ex2
- * (flushing subnormals to zero) returns exactly +0; every term computed is the same as when all
- * N^2 pairs are visited, and only the grouping of the float64 partial sums differs (results
- * agree to about 1e-16 relative). HAWKES_FP64 with the self term: the background sum holds the
- * term n' = n = 1, so lambda_n >= A = mu0 / ((2 pi)^(3/2) tau_x^2 tau_t); columns whose terms
- * are each below 2^-70 A / N (background exponent beyond ln N + 70 ln 2, trigger exponent
- * beyond that plus ln(C / A), C = theta omega / (2 pi h^2)) are skipped, so the skipped part of
- * a row stays below 2^-70 of lambda_n, 1/128 of float64's rounding unit. HAWKES_FP64 with
- * HAWKES_FLAG_EXCLUDE_SELF (no such floor): float64 exp's exact zeros, as in mixed precision.
+ * working precision. With the self term, the background sum holds the term n' = n = 1, so
+ * lambda_n >= A = mu0 / ((2 pi)^(3/2) tau_x^2 tau_t), and columns whose terms are each below
+ * 2^-P A / N are skipped (background exponent beyond (P + log2 N) ln 2 in time alone, trigger
+ * exponent beyond that plus ln(C / A), C = theta omega / (2 pi h^2)): the skipped part of a row
+ * stays below 2^-P of lambda_n for each kind of term. HAWKES_FP64: P = 70, 1/128 of float64's
+ * rounding unit. HAWKES_MIXED: P = 40, 2^-16 of float32's rounding unit (the results move by
+ * less than 1e-12 relative against visiting every pair), and never past the exponents at which
+ * float32 ex2 (flushing subnormals to zero) returns exactly +0. With HAWKES_FLAG_EXCLUDE_SELF
+ * (no such floor) each mode keeps every term that is not exactly zero in its precision.
  * HAWKES_FLAG_DENSE visits all pairs (in HAWKES_FP64 up to float64 exp's exact zeros). */
 
 typedef struct hawkes_ctx hawkes_ctx;

@@ -159,7 +159,7 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 // one column tile per leaf. The mixed kernels cut twice as fine: their items span 4, 2 or 1
 // leaves along the launch order (launch_tiers).
 #ifndef HK_ITEMS_PER_SLOT
-#define HK_ITEMS_PER_SLOT 4
+#define HK_ITEMS_PER_SLOT 3  // 85k loglik+grad: 3 0.363 ms, 4 0.371 ms, 2 0.366 ms (same box)
 #endif
 // Smallest mixed-precision batch run by the grouped kernel; smaller batches run as independent
 // requests in one launch, each with the shared background, which was faster below these sizes
@@ -202,9 +202,14 @@ void launch_tiers(int nrt, int mode, bool grouped, int *wide, int *coarse) {
 
 // Reaches (days) of Section 2.1's pair terms: past bg of |t_n - t_n'| a background term, past
 // trig of t_n - t_n' a trigger term contributes nothing at the working precision.
-// - float32 (mixed): ex2.approx.ftz returns +0 for every exponent <= -126, so a background
-//   term is exactly zero once dt' = beta dt reaches sqrt(130), a trigger term once
-//   omega dt log2(e) reaches 131.
+// - float32 (mixed) with the self term in the background sum (the default): lambda_n >= A (see
+//   below). A background term is e_b = 2^-q with q >= dt'^2, dt' = beta dt; past q = Q,
+//   Q = log2 N + 40, it is below 2^-40 / N, and all N of a row together stay below 2^-40 of
+//   lambda_n (2^-16 of float32's rounding unit). A trigger term of weight C (below) past
+//   omega dt log2(e) = Q + log2(C / A) (when C > A) likewise. Both exponents stop at the point
+//   where ex2.approx.ftz returns +0 (q = 130 and 131), which is where the reaches stand without
+//   the floor: with HAWKES_FLAG_EXCLUDE_SELF or HAWKES_FLAG_DENSE every term that is not exactly
+//   zero in float32 is kept.
 // - float64 with the self term in the background sum (the default): S_b >= 1, so lambda_n >= A
 //   = mu0 / ((2 pi)^(3/2) tau_x^2 tau_t). A background term beyond dt^2 / (2 tau_t^2) = E,
 //   E = ln N + 70 ln 2, is below e^-E, and all N of a row together stay below 2^-70 of
@@ -216,8 +221,17 @@ void launch_tiers(int nrt, int mode, bool grouped, int *wide, int *coarse) {
 //   exponents go to 805.
 void term_reaches(const hawkes_params *p, int mode, float beta32, int flags, int64_t n, double *bg, double *trig) {
   if (mode == HAWKES_MIXED) {
-    *bg = std::sqrt(130.0) / (double)beta32;
-    *trig = 131.0 / (p->omega * kLog2e);
+    double qb = 130.0, qt = 131.0;
+    if (!(flags & (HAWKES_FLAG_EXCLUDE_SELF | HAWKES_FLAG_DENSE))) {
+      const double two_pi = 6.28318530717958647693;
+      const double A = p->mu0 / (two_pi * std::sqrt(two_pi) * p->tau_x * p->tau_x * p->tau_t);
+      const double C = p->theta * p->omega / (two_pi * p->h * p->h);
+      const double Q = std::log2((double)std::max<int64_t>(n, 1)) + 40.0;
+      qb = std::min(qb, Q);
+      qt = std::min(qt, Q + (C > A ? std::log2(C / A) : 0.0));
+    }
+    *bg = std::sqrt(qb) / (double)beta32;
+    *trig = qt / (p->omega * kLog2e);
   } else if (!(flags & (HAWKES_FLAG_EXCLUDE_SELF | HAWKES_FLAG_DENSE))) {
     const double two_pi = 6.28318530717958647693;
     const double A = p->mu0 / (two_pi * std::sqrt(two_pi) * p->tau_x * p->tau_x * p->tau_t);

@@ -100,8 +100,8 @@ __host__ __device__ inline int2 table_window(const WinTable &W, int n, int nct, 
 // Work decomposition: the pair kernels run one CTA per item. A request's items are first
 // one compensator item per row tile (when comp is set), then the pair items. For a pair item
 // the kernel finds the window of column tiles of its row tile rt that can hold a nonzero pair
-// term (every other pair term is exactly zero in mixed precision, or below 2^-70 of lambda_n
-// in float64 with the self term, see cut_early and cut_late) and cuts it into `slices`
+// term that matters (with the self term, every other pair term is below 2^-40 (mixed) or 2^-70
+// (float64) of lambda_n / N; without it, exactly zero; see cut_early and cut_late) and cuts it into `slices`
 // near-equal leaves. Row tiles are launched from the
 // middle of the time range outwards; one item covers `span` consecutive leaves of its row
 // tile, with span 4 for the first `wide` row tiles launched, 2 up to `coarse` and 1 for the
@@ -161,7 +161,8 @@ struct Request {
   int sym;             // 1: on (mixed, fused, set with a time table, no exclude-self/dense/no-symmetry)
   signed char fix_bits[kMaxSums];  // sym: sum s enters fixsum as round(v 2^fix_bits[s]) (fix_bits_for)
   double trig_cut;     // days: columns earlier than t_n - trig_cut give trigger terms that contribute
-                       // nothing (exact zeros in mixed precision; below 2^-70 of lambda_n in float64)
+                       // nothing (with the self term below 2^-40 (mixed) or 2^-70 (float64) of
+                       // lambda_n in all; without it exact zeros)
   long long *fixsum;   // sym, or a grouped batch without exclude-self: [num_sums][npad] per-event sums
                        // in fixed point, zero at launch (nullptr: partial-sum slots and merge trees)
   unsigned *rt_done;   // with fixsum: per row tile, the arrivals of its items (and, with sym, of the
@@ -295,8 +296,9 @@ __host__ __device__ inline int first_item_of(const Request &R, int rt) {
 
 // ---- symmetric background ----------------------------------------------------------------
 // A background term e_b(n, n') = e_b(n', n) serves the rows of both events. With R.sym, a row
-// tile K evaluates the column tiles J of its window that lie beyond the trigger's exact-zero
-// reach (every trigger term of K's rows with them is zero) once, adding each term to its row
+// tile K evaluates the column tiles J of its window that lie beyond the trigger's reach (no
+// trigger term of K's rows with them can change the sums, see trig_cut) once, adding each term
+// to its row
 // and to its column. Those "far" column tiles are [c0(K), 2 ib(K)):
 //   c0(K) = table_first(t_K - cut_early), ib(K) = table_first(t_K - trig_cut) / 2,
 // with t_K the time of row tile K's first event; they end on a row-tile boundary, so a far

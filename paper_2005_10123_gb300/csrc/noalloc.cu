@@ -263,7 +263,9 @@ extern "C" int hawkes_loglik_noalloc(const float *x, const float *y, const float
     R.k_cw = p->omega / (two_pi * p->h * p->h);
     R.inv_tx = 1.0 / p->tau_x; R.inv_tt = 1.0 / p->tau_t; R.inv_h = 1.0 / p->h; R.inv_om = 1.0 / p->omega;
   }
-  // the same exact-zero column window as the context path (see exact_zero_cutoffs there)
+  // the exact-zero column window: every term that is not exactly zero in float32 (the context
+  // path, with the self term, stops where all skipped terms of a row stay below 2^-40 of
+  // lambda_n, see term_reaches there; the two agree to that bound)
   const double bg = 1.01 * std::sqrt(130.0) / (double)R.beta, trig = 1.01 * 131.0 / (p->omega * log2e);
   R.cut_early = std::max(bg, trig);
   R.cut_late = bg;

@@ -174,10 +174,12 @@ def test_pi_batch(ctx, mode):
 
 @pytest.mark.parametrize("mode", [0, 1], ids=["fp64", "mixed"])
 def test_exact_zero_window_matches_dense(ctx, mode):
-    """Skipping the columns whose pair terms are exactly zero (mixed precision), or in float64
-    below 2^-70 of lambda_n in all (the self term's floor), changes nothing but the grouping of
-    the float64 partial sums (row-by-row evaluation: the mixed path with
-    HAWKES_FLAG_NO_SYMMETRY, which HAWKES_FLAG_DENSE implies)."""
+    """Skipping the columns whose pair terms are below 2^-P of lambda_n in all (the self term's
+    floor; P = 70 in float64, 40 in mixed precision) moves each log lambda_n by less than 2^-P
+    per kind of term (background, trigger), so ell by less than 2 N 2^-P, beyond the grouping of
+    the float64 partial sums (row-by-row evaluation: the mixed path with HAWKES_FLAG_NO_SYMMETRY,
+    which HAWKES_FLAG_DENSE implies). The gradient terms of the skipped pairs carry their
+    moments' factors (q, dt, r^2 over a bandwidth), at most a few dozen times 2^-P each."""
     from paper_2005_10123_gb300 import binding
     ev = synth.simulate(20000, 5000.0, seed=71)  # long time span: most column tiles skipped
     sid = ctx.hawkes_upload_events(ev.x, ev.y, ev.t)
@@ -188,8 +190,9 @@ def test_exact_zero_window_matches_dense(ctx, mode):
             a, ga = ctx.hawkes_loglik_grad(sid, th, mode)
             ctx.hawkes_set_flags(binding.HAWKES_FLAG_DENSE)
             b, gb = ctx.hawkes_loglik_grad(sid, th, mode)
-            assert rel(a, b) <= 1e-14, (th, a, b)
-            assert grad_err(ga, gb) <= 1e-13, (th, ga, gb)
+            P = 70 if mode == 0 else 40
+            assert abs(a - b) <= 2 * ev.n * 2.0 ** -P + 1e-14 * abs(b), (th, a, b)
+            assert grad_err(ga, gb) <= (1e-13 if mode == 0 else 1e-10), (th, ga, gb)
     finally:
         ctx.hawkes_set_flags(0)
         ctx.hawkes_release_events(sid)
