@@ -73,7 +73,8 @@ double lane_ops_per_s(int sms, double lanes_per_iter_and_chain) {
 // Float64 and conversion rates, one dependent chain per (thread, chain), the same launch shape:
 // 7 DADD; 8 a float32 value folded into a float64 sum (FMUL, F2F.F64.F32, DADD); 9 a float32
 // value into an int64 sum (FMUL, F2I.S64.F32, 64-bit add); 10 a double into an int64 sum (DMUL,
-// F2I.S64.F64, 64-bit add); 11 a 64-bit integer add.
+// F2I.S64.F64, 64-bit add); 12 log of a double (CUDA's log) and an add; 13 the correctly
+// rounded float64 reciprocal and an add; 14 a float64 division and an add.
 template <int OP>
 __global__ void rate64_kernel(float *out, float s) {
   double d[kChains];
@@ -92,7 +93,9 @@ __global__ void rate64_kernel(float *out, float s) {
       if (OP == 8) { f[i] = __fmul_rn(f[i], s); d[i] = __dadd_rn(d[i], (double)f[i]); }
       if (OP == 9) { f[i] = __fmul_rn(f[i], s); l[i] += __float2ll_rn(f[i]); }
       if (OP == 10) { d[i] = __dmul_rn(d[i], c); l[i] += __double2ll_rn(d[i]); }
-      if (OP == 11) l[i] += (long long)s + it;
+      if (OP == 12) d[i] = log(d[i]) + 3.0;
+      if (OP == 13) d[i] = __drcp_rn(d[i]) + 3.0;
+      if (OP == 14) d[i] = 1.0 / d[i] + 3.0;
     }
   }
   double acc = 0.0;
@@ -163,7 +166,9 @@ int main() {
   std::printf("\"fold_f32_into_f64\": %.6e, ", ops64_per_s<8>(sms));
   std::printf("\"f32_into_int64\": %.6e, ", ops64_per_s<9>(sms));
   std::printf("\"f64_into_int64\": %.6e, ", ops64_per_s<10>(sms));
-  std::printf("\"iadd64\": %.6e}, ", ops64_per_s<11>(sms));
+  std::printf("\"log_f64\": %.6e, ", ops64_per_s<12>(sms));
+  std::printf("\"rcp_rn_f64\": %.6e, ", ops64_per_s<13>(sms));
+  std::printf("\"div_f64\": %.6e}, ", ops64_per_s<14>(sms));
   double *s1 = nullptr, *s2 = nullptr;
   unsigned long long *c = nullptr;
   if (cudaMalloc(&s1, kBins * 8) != cudaSuccess || cudaMalloc(&s2, kBins * 8) != cudaSuccess ||
