@@ -365,7 +365,7 @@ size_t set_slots(const EventSetRec *S, int mode, int grad) {
 size_t request_footprint(const EventSetRec *S, int mode, int grad, int m = 1, int sym = 0) {
   const size_t items = sym ? 0 : set_slots(S, mode, grad);
   size_t b = align_up(items * sums_of(grad, m) * kRowTile * sizeof(double), 256);
-  b += 2 * align_up((size_t)S->nrt * kOut * sizeof(double), 256);
+  b += 3 * align_up((size_t)S->nrt * kOut * sizeof(double), 256);  // comp, rt_sum (2 nrt slots)
   return b;
 }
 
@@ -421,11 +421,14 @@ void bind_workspace(Request *R, const EventSetRec *S, int mode, int grad, char *
 }
 
 // Enqueue the pair kernel (one CTA per item) for a prepared batch on `s`; it finishes every
-// row tile and every request itself (fused epilogue). Every request's completion counters
-// must already be zero (the caller clears them with one memset).
+// row tile and every request itself (fused epilogue), except, in mixed precision, the requests
+// with the shared background, whose epilogues run in a second launch on the same stream
+// (launch_epilogue_fix). Every request's completion counters must already be zero (the caller
+// clears them with one memset).
 int launch_batch(hawkes_ctx *ctx, Batch &b, int mode, int grad, cudaStream_t s) {
   b.mode = mode == HAWKES_MIXED ? 1 : 0;
   b.fused = 1;
+  b.split = mode == HAWKES_MIXED && !b.group ? 1 : 0;
   long long items = 0;
   if (b.group) {  // grouped kernel: every request's compensator items, then the groups' pair items
     const int G = b.group;
@@ -439,9 +442,14 @@ int launch_batch(hawkes_ctx *ctx, Batch &b, int mode, int grad, cudaStream_t s) 
     }
   }
   if (items > 0x7fffffffLL) return HAWKES_E_INVAL;
+  for (int r = 0; r < b.nreq; ++r)  // a sym request's row sums are finished by the split epilogue
+    if (b.req[r].sym && !b.split) return HAWKES_E_INVAL;
   b.total_items = (int)items;
   if (b.group) HK_CUDA(ctx, launch_pair_group(b, grad != 0, s));
-  else if (mode == HAWKES_MIXED) HK_CUDA(ctx, launch_pair_mixed(b, grad != 0, s));
+  else if (mode == HAWKES_MIXED) {
+    HK_CUDA(ctx, launch_pair_mixed(b, grad != 0, s));
+    HK_CUDA(ctx, launch_epilogue_fix(b, grad != 0, s));
+  }
   else HK_CUDA(ctx, launch_pair_fp64(b, grad != 0, s));
   return HAWKES_OK;
 }

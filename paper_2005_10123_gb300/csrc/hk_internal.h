@@ -192,8 +192,16 @@ struct Batch {
   int fused;        // 1: the pair kernel finishes each row tile and each request itself
   int group;        // 0, or the grouped kernel's group size (every request on one set)
   int comp_total;   // grouped kernel: compensator items, first in the launch
+  int split;        // 1: requests with the shared background (sym) leave their epilogues to
+                    // epilogue_fix_kernel, launched after the pair kernel (see launch_epilogue_fix)
   Request req[kMaxBatch];
 };
+
+// The split epilogue (Batch::split): one CTA of kEpiRows threads per kEpiRows consecutive events
+// of each request with the shared background, one event per thread; its partial sums go to
+// rt_sum[block] (a request's rt_sum holds 2 nrt slots, at least its epi_blocks).
+constexpr int kEpiRows = 128;
+__host__ __device__ inline int epi_blocks(const Request &R) { return (R.set.n + kEpiRows - 1) / kEpiRows; }
 
 // The mixed-precision constants of a request from Theta (Section 2.1, d = 2; base-2 exponents):
 // e_b = 2^-(a2 r^2 + beta^2 dt^2), e_s = 2^(cn r^2 + wn beta dt). Host code.
@@ -309,12 +317,12 @@ __host__ __device__ inline int first_item_of(const Request &R, int rt) {
 // when I < ib(K), else by I's late columns (K <= kmax(I)) and K's near early columns.
 // Every event's sums reach R.fixsum as integers round(v 2^F) (fix_bits_for): each item adds its
 // rows' float64 sums, each far block its columns' float32 sums. Integer additions commute
-// exactly, so the totals do not depend on the order in which items finish. Row tile I is
-// complete when its items and the e_col(I) far blocks holding its columns have arrived at
-// rt_done[I]: each far column tile adds 1, each item of I adds 1 except I's first item (node 0),
-// which adds kSymRootMark - e_col(I) - (items(I) - 1); the arrival that brings the counter to
-// kSymRootMark runs I's epilogue from fixsum. Every arrival comes after its additions and a
-// fence, so nothing waits for anything.
+// exactly, so the totals do not depend on the order in which items finish. The pair kernel's
+// items only add; the batch's split epilogue (epilogue_fix_kernel, Batch::split), launched after
+// it on the same stream, turns the totals into every event's terms, so no item waits for or
+// counts another. e_col(I), the far column tiles of later row tiles that hold I's columns, is
+// part of the plan the host tests check block by block.
+// kSymRootMark: the grouped kernel's row-tile counters (pair_group.cu) count to it.
 constexpr unsigned kSymRootMark = 1u << 30;
 
 struct SymK {
@@ -373,6 +381,9 @@ __host__ __device__ inline PairItem item_at(const Request &R, int p) {
 // Launchers (defined in the kernel translation units): one CTA per item, grid =
 // b.total_items.
 cudaError_t launch_pair_mixed(const Batch &b, bool grad, cudaStream_t s);
+// With b.split: the epilogues of the batch's sym requests (epilogue_fix_kernel), after the pair
+// kernel on the same stream; nothing to launch when no request has sym.
+cudaError_t launch_epilogue_fix(const Batch &b, bool grad, cudaStream_t s);
 cudaError_t launch_pair_fp64(const Batch &b, bool grad, cudaStream_t s);
 // Grouped mixed kernel (pair_group.cu): requests on one set in groups of G = b.group, each
 // pair's geometry shared by the group. Items: nreq * nrt compensator items, then
@@ -561,15 +572,18 @@ __device__ void compensator_tile(const Request &R, const MixConst &M2, const TT 
 // finishes the last of them writes ell = sum over row tiles of (rt_sum - comp) and the
 // gradient, in a fixed order, to R.out (NaN if a sum of the request left the fixed-point range,
 // kStatusFixRange). Called by every thread of the CTA after its results are written.
+// With nsum >= 0 (the split epilogue) the parts are the request's nsum epilogue blocks, whose
+// sums sit in rt_sum[0, nsum), and the compensator sums of its nrt row tiles are subtracted.
 template <bool GRAD, int MIX = 1>
-__device__ void finish_request(const Request &R) {
+__device__ void finish_request(const Request &R, int nsum = -1) {
   constexpr int NV = GRAD ? 1 + num_grad(MIX) : 1;
   static_assert(NV <= kRedWidth, "reduction scratch too narrow");
   double *red3 = reduce_scratch();
   __shared__ int s_final;
   const SetView &S = R.set;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = (blockDim.x + 31) >> 5;
-  const unsigned parts = (unsigned)(S.nrt + comp_items(R));
+  const unsigned parts = nsum >= 0 ? (unsigned)nsum : (unsigned)(S.nrt + comp_items(R));
+  const int nrs = nsum >= 0 ? nsum : S.nrt;  // rt_sum slots
   __threadfence();
   __syncthreads();
   if (tid == 0) s_final = atomicAdd(R.rt_count + request_counters(R) - 1, 1u) == parts - 1u;
@@ -579,9 +593,9 @@ __device__ void finish_request(const Request &R) {
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
       double x = 0.0;
-      for (int r = tid; r < S.nrt; r += blockDim.x) {
-        x += __ldcg(R.rt_sum + (size_t)r * kOut + q);
-        if (R.comp) x -= __ldcg(R.comp + (size_t)r * kOut + q);
+      for (int r = tid; r < (nrs > S.nrt ? nrs : S.nrt); r += blockDim.x) {
+        if (r < nrs) x += __ldcg(R.rt_sum + (size_t)r * kOut + q);
+        if (R.comp && r < S.nrt) x -= __ldcg(R.comp + (size_t)r * kOut + q);
       }
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
@@ -769,7 +783,7 @@ __device__ __forceinline__ void grad_from_moments(const Request &R, const MixCon
 // End of row tile rt's epilogue: sum every thread's row terms v in a fixed order (warp tree,
 // warps in order), turn the moment ratios into gradient terms (grad_from_moments), store
 // them in R.rt_sum, then finish_request. Called by every thread of the CTA.
-template <bool GRAD, int MIX = 1>
+template <bool GRAD, int MIX = 1, bool FINISH = true>
 __device__ void rowtile_reduce(const Request &R, const MixConst &M2, int rt, const double *v) {
   constexpr int NV = GRAD ? 1 + num_sums(true, MIX) : 1;  // log lambda and the moment ratios
   static_assert(NV <= kRedWidth, "reduction scratch too narrow");
@@ -799,7 +813,7 @@ __device__ void rowtile_reduce(const Request &R, const MixConst &M2, int rt, con
       for (int k = 0; k < num_grad(MIX); ++k) R.rt_sum[(size_t)rt * kOut + 1 + k] = g[k];
     }
   }
-  finish_request<GRAD, MIX>(R);
+  if (FINISH) finish_request<GRAD, MIX>(R);
 }
 #endif
 

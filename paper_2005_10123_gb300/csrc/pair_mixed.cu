@@ -505,12 +505,24 @@ __device__ __forceinline__ void cta_sync() {
 // The epilogue of row tile I (Section 2.1, Eq. 1): every event's row sums, get(s, k) for sum s of
 // this thread's row k (rows warp * kWarpRows + lane + 32 k); then log lambda_n, the moment ratios
 // and the fixed-order reductions (hk_internal.h). Called by every thread of the CTA.
+// Event i's terms from its row sums as the pair kernel accumulates them: R_b from Q and T_b, U_s
+// from units of time to scaled time, then row_terms.
+template <bool GRAD, int MIX>
+__device__ __forceinline__ void row_from_sums(const Request &R, const MixConst &M2, int i, double *sums, double *v) {
+  if (GRAD) {
+    const double to_scaled = 1.0 / R.tscale;   // beta
+    sums[2] = (sums[2] - sums[3]) * R.inv_a2;  // R_b from Q and T_b
+    sums[5] *= to_scaled;                      // U_s: from units of time to scaled time
+    if (MIX > 1) sums[8] *= to_scaled;
+  }
+  row_terms<GRAD, MIX>(R, M2, i, sums, v);
+}
+
 template <bool GRAD, int MIX, class Get>
 __device__ void rowtile_epilogue(const Request &R, const MixConst &M2, int I, Get get) {
   constexpr int NS = num_sums(GRAD, MIX);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int n = R.set.n;
-  const double to_scaled = 1.0 / R.tscale;  // beta
   double v[GRAD ? 1 + NS : 1] = {};
 #pragma unroll
   for (int k = 0; k < kRowsPerThread; ++k) {
@@ -519,12 +531,7 @@ __device__ void rowtile_epilogue(const Request &R, const MixConst &M2, int I, Ge
       double sums[NS];
 #pragma unroll
       for (int s = 0; s < NS; ++s) sums[s] = get(s, k);
-      if (GRAD) {
-        sums[2] = (sums[2] - sums[3]) * R.inv_a2;  // R_b from Q and T_b
-        sums[5] *= to_scaled;                      // U_s: from units of time to scaled time
-        if (MIX > 1) sums[8] *= to_scaled;
-      }
-      row_terms<GRAD, MIX>(R, M2, i, sums, v);
+      row_from_sums<GRAD, MIX>(R, M2, i, sums, v);
     }
   }
   rowtile_reduce<GRAD, MIX>(R, M2, I, v);
@@ -722,10 +729,9 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
     return;
   }
   if (R.sym) {
-    // Every event's sums go to fixsum: this item's far column tiles [c_begin, f_end) have added
-    // their columns' shares there; now its rows' float64 sums. Then it arrives at the row tiles
-    // holding its far columns and at its own (SymPlan); the arrival that completes a row tile
-    // runs that tile's epilogue from fixsum.
+    // Every event's sums go to fixsum: this item's far column tiles have added their columns'
+    // shares there; now its rows' float64 sums. Sym requests always run in split batches
+    // (launch_batch), so the item ends here.
     const size_t np = (size_t)S.npad;
     long long *fx = R.fixsum + row0 + warp * kWarpRows + lane;
 #pragma unroll
@@ -737,30 +743,7 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
     }
     cta_sync();
     if (tid == 0 && s_bad && R.status) atomicOr(R.status, kStatusFixRange);
-    __threadfence();
-    cta_sync();
-    auto from_fix = [&](int I) {
-      __threadfence();
-      const long long *src = R.fixsum + (size_t)I * kRowTile + warp * kWarpRows + lane;
-      rowtile_epilogue<GRAD, MIX>(R, B.mix2, I, [&](int s, int k) {
-        return (double)__ldcg(src + s * np + 32 * k) * pow2d(-R.fix_bits[s]);
-      });
-    };
-    __shared__ unsigned s_arrive;
-    const int f_end = min(c_end, plan.sym_end);
-    for (int I = c_begin / 2; c_begin < f_end && I <= (f_end - 1) / 2; ++I) {
-      const unsigned tiles = (unsigned)(min(f_end, 2 * I + 2) - max(c_begin, 2 * I));
-      if (tid == 0) s_arrive = atomicAdd(R.rt_done + I, tiles) + tiles == kSymRootMark;
-      cta_sync();
-      if (s_arrive) from_fix(I);
-      cta_sync();
-    }
-    const unsigned items = (unsigned)rowtile_items(R, it.span);
-    const unsigned add = it.node == 0 ? kSymRootMark - (unsigned)plan.e_col - (items - 1u) : 1u;
-    if (tid == 0) s_arrive = atomicAdd(R.rt_done + it.rt, add) + add == kSymRootMark;
-    cta_sync();
-    if (s_arrive) from_fix(it.rt);
-    return;
+    return;  // epilogue_fix_kernel, launched after this kernel (Batch::split), finishes every row
   }
   auto merge = [&](int from) {
     const double *src = R.partials + (size_t)from * NS * kRowTile;
@@ -824,7 +807,7 @@ __global__ void __launch_bounds__(kThreads, MIX > 1 ? (GRAD ? HK_MIN_CTAS_MIX : 
   const int local = item - R.item_begin, nc = comp_items(R);
   if (local < nc) {  // compensator item of row tile `local`
     compensator_tile<MIX>(R, B.mix2, R.set.t32, local, GRAD);
-    if (B.fused) finish_request<GRAD, MIX>(R);
+    if (B.fused && !(B.split && R.sym)) finish_request<GRAD, MIX>(R);
     return;
   }
   const PairItem it = item_at(R, local - nc);
@@ -861,7 +844,54 @@ __global__ void __launch_bounds__(kThreads, MIX > 1 ? (GRAD ? HK_MIN_CTAS_MIX : 
   run_piece<GRAD, MIX>(B, R, it, c_begin, c_end, plan, sxs, stx, srt, sacc);
 }
 
+// The split epilogue (Batch::split): block b of the batch's sym requests, in request order,
+// takes events [b kEpiRows, (b + 1) kEpiRows) of its request, one per thread: the event's sums
+// from fixsum, its terms (row_from_sums), a fixed-order reduction of the block into rt_sum[b]
+// (rowtile_reduce without its finish), then the request's count of finished blocks, whose last
+// block writes ell and the gradient (finish_request over the blocks and the compensator sums).
+// The pair kernel's additions to fixsum are complete when this kernel starts (same stream).
+static_assert(kEpiRows <= 32 * kMaxCtaWarps, "reduction scratch too narrow for the split epilogue");
+template <bool GRAD, int MIX>
+__global__ void __launch_bounds__(kEpiRows) epilogue_fix_kernel(const __grid_constant__ Batch B) {
+  constexpr int NS = num_sums(GRAD, MIX);
+  int b = blockIdx.x, r = 0;
+  for (; r < B.nreq; ++r) {
+    if (!B.req[r].sym) continue;
+    const int nb = epi_blocks(B.req[r]);
+    if (b < nb) break;
+    b -= nb;
+  }
+  const Request &R = B.req[r];
+  const int i = b * kEpiRows + threadIdx.x;
+  double v[GRAD ? 1 + NS : 1] = {};
+  if (i < R.set.n) {
+    const size_t np = (size_t)R.set.npad;
+    double sums[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) sums[s] = (double)__ldcg(R.fixsum + s * np + i) * pow2d(-R.fix_bits[s]);
+    row_from_sums<GRAD, MIX>(R, B.mix2, i, sums, v);
+  }
+  rowtile_reduce<GRAD, MIX, false>(R, B.mix2, b, v);
+  finish_request<GRAD, MIX>(R, epi_blocks(R));
+}
+
 }  // namespace
+
+cudaError_t launch_epilogue_fix(const Batch &b, bool grad, cudaStream_t s) {
+  int blocks = 0;
+  for (int r = 0; r < b.nreq; ++r)
+    if (b.req[r].sym) blocks += epi_blocks(b.req[r]);
+  if (!b.split || blocks == 0) return cudaSuccess;
+  if (b.req[0].mix > 1) {
+    if (grad) epilogue_fix_kernel<true, 2><<<blocks, kEpiRows, 0, s>>>(b);
+    else epilogue_fix_kernel<false, 2><<<blocks, kEpiRows, 0, s>>>(b);
+  } else if (grad) {
+    epilogue_fix_kernel<true, 1><<<blocks, kEpiRows, 0, s>>>(b);
+  } else {
+    epilogue_fix_kernel<false, 1><<<blocks, kEpiRows, 0, s>>>(b);
+  }
+  return cudaGetLastError();
+}
 
 cudaError_t launch_pair_mixed(const Batch &b, bool grad, cudaStream_t s) {
   if (b.total_items < 1) return cudaErrorInvalidValue;

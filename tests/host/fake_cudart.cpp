@@ -269,6 +269,7 @@ static cudaError_t fake_pair(const Batch &b, bool grad) {
   } else {
     for (int r = 0; r < b.nreq; ++r) {
       if (b.req[r].item_begin != items) g_schedule_errors++;
+      if (b.req[r].sym && !b.split) g_schedule_errors++;  // sym rows are finished by the split epilogue
       items += request_items(b.req[r]);
       check_schedule(b.req[r], b.mode);
       // every pair item's partial-sum slot (num_sums doubles per row of the tile) lies before the
@@ -331,6 +332,12 @@ cudaError_t launch_upload_prep(const UploadPrep &u, cudaStream_t) {
 }
 
 cudaError_t launch_pair_mixed(const Batch &b, bool grad, cudaStream_t) { return fake_pair(b, grad); }
+// The split epilogue: fake_pair already wrote every output; count the launch and check that it
+// follows a split mixed-precision batch.
+cudaError_t launch_epilogue_fix(const Batch &b, bool, cudaStream_t) {
+  if (!b.split || b.mode != 1 || b.group) g_schedule_errors++;
+  return cudaSuccess;
+}
 cudaError_t launch_pair_fp64(const Batch &b, bool grad, cudaStream_t) { return fake_pair(b, grad); }
 cudaError_t launch_pair_group(const Batch &b, bool grad, cudaStream_t) {
   // the group size the host picked for this batch, and one the kernel is built for
