@@ -590,16 +590,29 @@ __device__ void finish_request(const Request &R, int nsum = -1) {
   __syncthreads();
   if (s_final) {
     __threadfence();
+    // per thread, slots r = tid, tid + blockDim.x, ... in that order for every value q at once
+    // (the loads of one slot issue together), then the warp tree and the warps in order
+    double x[NV];
 #pragma unroll
-    for (int q = 0; q < NV; ++q) {
-      double x = 0.0;
-      for (int r = tid; r < (nrs > S.nrt ? nrs : S.nrt); r += blockDim.x) {
-        if (r < nrs) x += __ldcg(R.rt_sum + (size_t)r * kOut + q);
-        if (R.comp && r < S.nrt) x -= __ldcg(R.comp + (size_t)r * kOut + q);
+    for (int q = 0; q < NV; ++q) x[q] = 0.0;
+    for (int r = tid; r < (nrs > S.nrt ? nrs : S.nrt); r += blockDim.x) {
+      double a[NV], c[NV];
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        a[q] = r < nrs ? __ldcg(R.rt_sum + (size_t)r * kOut + q) : 0.0;
+        c[q] = R.comp && r < S.nrt ? __ldcg(R.comp + (size_t)r * kOut + q) : 0.0;
       }
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
-      if (lane == 0) red3[warp * kRedWidth + q] = x;
+      for (int q = 0; q < NV; ++q) {
+        if (r < nrs) x[q] += a[q];
+        if (R.comp && r < S.nrt) x[q] -= c[q];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) x[q] += __shfl_down_sync(0xffffffffu, x[q], off);
+      if (lane == 0) red3[warp * kRedWidth + q] = x[q];
     }
     __syncthreads();
     if (tid < NV) {
