@@ -365,7 +365,7 @@ size_t set_slots(const EventSetRec *S, int mode, int grad) {
 size_t request_footprint(const EventSetRec *S, int mode, int grad, int m = 1, int sym = 0) {
   const size_t items = sym ? 0 : set_slots(S, mode, grad);
   size_t b = align_up(items * sums_of(grad, m) * kRowTile * sizeof(double), 256);
-  b += 3 * align_up((size_t)S->nrt * kOut * sizeof(double), 256);  // comp, rt_sum (2 nrt slots)
+  b += 4 * align_up((size_t)S->nrt * kOut * sizeof(double), 256);  // comp, rt_sum (3 nrt slots)
   return b;
 }
 
@@ -880,6 +880,8 @@ int hawkes_create(hawkes_ctx **out, int device, size_t hbm_budget_bytes, void *c
   std::unique_ptr<hawkes_ctx> ctx(new (std::nothrow) hawkes_ctx());
   if (!ctx) return HAWKES_E_NOMEM;
   ctx->device = device;
+  e = init_log_table();
+  if (e != cudaSuccess) return cuda_fail(nullptr, e);
   cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device);
   if (cudaDeviceGetAttribute(&ctx->host_direct, cudaDevAttrPageableMemoryAccess, device) != cudaSuccess)
     ctx->host_direct = 0;

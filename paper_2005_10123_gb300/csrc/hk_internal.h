@@ -199,7 +199,9 @@ struct Batch {
 
 // The split epilogue (Batch::split): one CTA of kEpiRows threads per kEpiRows consecutive events
 // of each request with the shared background, one event per thread; its partial sums go to
-// rt_sum[block] (a request's rt_sum holds 2 nrt slots, at least its epi_blocks).
+// rt_sum[block] (a request's rt_sum holds 3 nrt slots: its epi_blocks, at most 2 nrt, then the
+// sums of groups of 32 blocks from slot 2 nrt on), and the groups' counters are the first of
+// the request's merge-tree counters, which the shared background does not use.
 constexpr int kEpiRows = 128;
 __host__ __device__ inline int epi_blocks(const Request &R) { return (R.set.n + kEpiRows - 1) / kEpiRows; }
 
@@ -384,6 +386,8 @@ cudaError_t launch_pair_mixed(const Batch &b, bool grad, cudaStream_t s);
 // With b.split: the epilogues of the batch's sym requests (epilogue_fix_kernel), after the pair
 // kernel on the same stream; nothing to launch when no request has sym.
 cudaError_t launch_epilogue_fix(const Batch &b, bool grad, cudaStream_t s);
+// The split epilogue's log table on the current device (once per context, before any launch).
+cudaError_t init_log_table();
 cudaError_t launch_pair_fp64(const Batch &b, bool grad, cudaStream_t s);
 // Grouped mixed kernel (pair_group.cu): requests on one set in groups of G = b.group, each
 // pair's geometry shared by the group. Items: nreq * nrt compensator items, then
@@ -745,8 +749,16 @@ __device__ int merge_tree(const Request &R, const PairItem &it, Store store, Mer
 // factors once per row tile (grad_from_moments).
 // With a two-component mixture (MIX = 2) the row sums carry S_s2 (and R_s2, U_s2) after the
 // single-kernel ones, lambda_i = A S_b + C S_s1 + C_2 S_s2, and v[1 ..] takes all nine ratios.
-template <bool GRAD, int MIX = 1>
-__device__ __forceinline__ void row_terms(const Request &R, const MixConst &M2, int i, const double *sums, double *v) {
+// The natural log row_terms applies by default.
+struct StdLog {
+  __device__ __forceinline__ double operator()(double x) const { return log(x); }
+};
+// LogF: the log of lambda_i (StdLog, or the split epilogue's table log); FAST_RCP: 1 / lambda_i
+// from the float32 reciprocal and one Newton step in float64 (relative error about 1e-14),
+// 4 operations of the narrow float64 pipe instead of a division's 8 to 10.
+template <bool GRAD, int MIX = 1, class LogF = StdLog, bool FAST_RCP = false>
+__device__ __forceinline__ void row_terms(const Request &R, const MixConst &M2, int i, const double *sums, double *v,
+                                          LogF logf = LogF()) {
   constexpr int NS = num_sums(GRAD, MIX);
   const double A = R.mu0 * R.k_ab, C = R.theta * R.k_cw;
   double xi = C * sums[1];
@@ -755,9 +767,15 @@ __device__ __forceinline__ void row_terms(const Request &R, const MixConst &M2, 
   if (R.mu_out) R.mu_out[i] = mu;
   if (R.xi_out) R.xi_out[i] = xi;
   if (R.pi_out) R.pi_out[i] = xi / lam;
-  v[0] += log(lam);
+  v[0] += logf(lam);
   if (GRAD) {
-    const double inv = 1.0 / lam;
+    double inv;
+    if (FAST_RCP && lam > 1e-30 && lam < 1e30) {
+      const double r0 = (double)__frcp_rn(__double2float_rn(lam));
+      inv = fma(r0, fma(-lam, r0, 1.0), r0);
+    } else {
+      inv = 1.0 / lam;
+    }
 #pragma unroll
     for (int k = 0; k < NS; ++k) v[1 + k] = fma(sums[k], inv, v[1 + k]);
   }

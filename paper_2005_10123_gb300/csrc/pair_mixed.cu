@@ -507,7 +507,7 @@ __device__ __forceinline__ void cta_sync() {
 // and the fixed-order reductions (hk_internal.h). Called by every thread of the CTA.
 // Event i's terms from its row sums as the pair kernel accumulates them: R_b from Q and T_b, U_s
 // from units of time to scaled time, then row_terms.
-template <bool GRAD, int MIX>
+template <bool GRAD, int MIX, class LogF = StdLog, bool FAST_RCP = false>
 __device__ __forceinline__ void row_from_sums(const Request &R, const MixConst &M2, int i, double *sums, double *v) {
   if (GRAD) {
     const double to_scaled = 1.0 / R.tscale;   // beta
@@ -515,7 +515,7 @@ __device__ __forceinline__ void row_from_sums(const Request &R, const MixConst &
     sums[5] *= to_scaled;                      // U_s: from units of time to scaled time
     if (MIX > 1) sums[8] *= to_scaled;
   }
-  row_terms<GRAD, MIX>(R, M2, i, sums, v);
+  row_terms<GRAD, MIX, LogF, FAST_RCP>(R, M2, i, sums, v);
 }
 
 template <bool GRAD, int MIX, class Get>
@@ -846,11 +846,83 @@ __global__ void __launch_bounds__(kThreads, MIX > 1 ? (GRAD ? HK_MIN_CTAS_MIX : 
 
 // The split epilogue (Batch::split): block b of the batch's sym requests, in request order,
 // takes events [b kEpiRows, (b + 1) kEpiRows) of its request, one per thread: the event's sums
-// from fixsum, its terms (row_from_sums), a fixed-order reduction of the block into rt_sum[b]
-// (rowtile_reduce without its finish), then the request's count of finished blocks, whose last
-// block writes ell and the gradient (finish_request over the blocks and the compensator sums).
-// The pair kernel's additions to fixsum are complete when this kernel starts (same stream).
+// from fixsum, its terms (row_from_sums), a fixed-order reduction of the block, the gradient's
+// Theta factors and, in the even block of each row tile, the tile's compensator sums subtracted,
+// into rt_sum[b]. The last block of each group of kEpiGroup blocks (a counter per group) sums
+// the group in order into a group slot, and the last group of the request (the request's final
+// counter) sums the groups in order into ell and the gradient: every sum has a fixed order, and
+// the final one reads ceil(blocks / 32) slots instead of every block's. The pair kernel's
+// additions to fixsum and its compensator sums are complete when this kernel starts (same
+// stream).
+// ---- the split epilogue's float64 arithmetic ------------------------------------------------
+// GB300's float64 pipe runs about 1.6 operations per clock and SM, and the split epilogue is bound
+// by it (a 256-row block of events spends ~57 DADD-equivalents per event, 45% of them CUDA's
+// log). Three changes take it to ~25:
+// - the fixed-point sums are turned into doubles on the integer pipe (fix_to_double);
+// - 1 / lambda from the float32 reciprocal and one Newton step (row_terms' FAST_RCP);
+// - the log of lambda by a table-driven method (Tang, "Table-driven implementation of the
+//   logarithm function in IEEE floating-point arithmetic", ACM TOMS 16(4), 1990): with
+//   x = 2^e m, m in [1, 2), and j the top 7 bits of m's fraction, c_j = 1 / (1 + (j + 1/2) / 128)
+//   rounded to float32 and r = m c_j - 1 in one rounding (|r| < 2^-7.9),
+//     ln x = e ln 2 + (-ln c_j) + ln(1 + r),  ln(1 + r) = r - r^2/2 + ... + r^7/7
+//   (the first dropped term is below 2^-64); -ln c_j comes from a table computed on the host in
+//   extended precision (init_log_table), ln 2 in a 40-bit head (e ln2_hi exact) and a tail.
+//   About 12 float64 operations against ~27 for CUDA's log, and within a few units in the last
+//   place of it (the ell of hawkes_event_terms is checked against the log of its own lambda_i).
+__device__ double g_logtab[2 * 128];  // c_j, then -ln c_j
+constexpr double kLn2Hi = 0x1.62e42fefa4000p-1, kLn2Lo = -0x1.8432a1b0e2634p-43;
+
+struct TabLog {
+  __device__ __forceinline__ double operator()(double x) const {
+    const long long b = __double_as_longlong(x);
+    const int eb = (int)(b >> 52);
+    if (eb <= 0 || eb >= 0x7ff) return log(x);  // zero, negative, subnormal, inf or NaN
+    const int j = (int)((b >> 45) & 127);
+    const double m = __longlong_as_double((b & 0xfffffffffffffll) | 0x3ff0000000000000ll);
+    const double c = __ldg(g_logtab + j), t = __ldg(g_logtab + 128 + j);
+    const double r = fma(m, c, -1.0);
+    double q = fma(r, 1.0 / 7.0, -1.0 / 6.0);
+    q = fma(r, q, 0.2);
+    q = fma(r, q, -0.25);
+    q = fma(r, q, 1.0 / 3.0);
+    q = fma(r, q, -0.5);
+    const double p = fma(r * r, q, r);
+    const double e = (double)(eb - 1023);
+    return fma(e, kLn2Hi, t) + fma(e, kLn2Lo, p);
+  }
+};
+
+// The double nearest below v 2^-F for a fixed-point sum v (Request::fixsum), from the bits of v
+// on the integer pipe: the leading one of |v| sets the exponent, the next 52 bits the mantissa
+// (the rest is cut, 2^-53 relative at most), and F only moves the exponent.
+__device__ __forceinline__ double fix_to_double(long long v, int F) {
+  if (v == 0) return 0.0;
+  const unsigned long long sign = v < 0 ? 0x8000000000000000ull : 0ull;
+  const unsigned long long u = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+  const int lz = __clzll((long long)u);
+  const unsigned long long m = u << lz;  // leading one at bit 63
+  const unsigned long long e = (unsigned long long)(1023 + 63 - lz - F);
+  return __longlong_as_double((long long)(sign | (e << 52) | ((m >> 11) & 0xfffffffffffffull)));
+}
+
 static_assert(kEpiRows <= 32 * kMaxCtaWarps, "reduction scratch too narrow for the split epilogue");
+constexpr int kEpiGroup = 32;  // epilogue blocks per first-level group of the final sum
+
+// Sum of `count` slots of NV values (kOut apart) by one full warp, in a fixed order: lane l takes
+// slots l, l + 32, ... in turn, then a fixed shuffle tree; lane 0 holds the totals in x.
+template <int NV>
+__device__ __forceinline__ void warp_sum_slots(const double *slots, int count, double (&x)[NV]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) x[q] = 0.0;
+  for (int c = lane; c < count; c += 32)
+#pragma unroll
+    for (int q = 0; q < NV; ++q) x[q] += __ldcg(slots + (size_t)c * kOut + q);
+#pragma unroll
+  for (int q = 0; q < NV; ++q)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) x[q] += __shfl_down_sync(0xffffffffu, x[q], off);
+}
 template <bool GRAD, int MIX>
 __global__ void __launch_bounds__(kEpiRows) epilogue_fix_kernel(const __grid_constant__ Batch B) {
   constexpr int NS = num_sums(GRAD, MIX);
@@ -868,14 +940,84 @@ __global__ void __launch_bounds__(kEpiRows) epilogue_fix_kernel(const __grid_con
     const size_t np = (size_t)R.set.npad;
     double sums[NS];
 #pragma unroll
-    for (int s = 0; s < NS; ++s) sums[s] = (double)__ldcg(R.fixsum + s * np + i) * pow2d(-R.fix_bits[s]);
-    row_from_sums<GRAD, MIX>(R, B.mix2, i, sums, v);
+    for (int s = 0; s < NS; ++s) sums[s] = fix_to_double(__ldcg(R.fixsum + s * np + i), R.fix_bits[s]);
+    row_from_sums<GRAD, MIX, TabLog, true>(R, B.mix2, i, sums, v);
   }
-  rowtile_reduce<GRAD, MIX, false>(R, B.mix2, b, v);
-  finish_request<GRAD, MIX>(R, epi_blocks(R));
+  // block partial: log lambda and the gradient terms (grad_from_moments), less the compensator
+  // sums of row tile b / 2 in the even block of the tile, into rt_sum[b]
+  constexpr int NV = GRAD ? 1 + num_grad(MIX) : 1;
+  constexpr int NR = GRAD ? 1 + NS : 1;
+  double *red = reduce_scratch(), *tot = red + kMaxCtaWarps * kRedWidth;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int q = 0; q < NR; ++q) {
+    double x = v[q];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+    if (lane == 0) red[warp * kRedWidth + q] = x;
+  }
+  __syncthreads();
+  if (tid < NR) {
+    double x = 0.0;
+    for (int w = 0; w < kEpiRows / 32; ++w) x += red[w * kRedWidth + tid];
+    tot[tid] = x;
+  }
+  __syncthreads();
+  const int nblk = epi_blocks(R), ngrp = (nblk + kEpiGroup - 1) / kEpiGroup, g = b / kEpiGroup;
+  __shared__ unsigned s_last;
+  if (tid == 0) {
+    double val[NV];
+    val[0] = tot[0];
+    if (GRAD) grad_from_moments<MIX>(R, B.mix2, tot + 1, val + 1);
+    const bool sub = R.comp && (b & 1) == 0;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) R.rt_sum[(size_t)b * kOut + q] = sub ? val[q] - R.comp[(size_t)(b / 2) * kOut + q] : val[q];
+    __threadfence();
+    const unsigned members = (unsigned)min(kEpiGroup, nblk - g * kEpiGroup);
+    s_last = atomicAdd(R.rt_count + g, 1u) == members - 1u;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  // the last block of group g sums the group's partials in order into slot 2 nrt + g; the last
+  // group to finish sums the groups' in order into ell and the gradient
+  double *gsum = R.rt_sum + (size_t)2 * R.set.nrt * kOut;
+  if (warp == 0) {
+    __threadfence();
+    double x[NV];
+    warp_sum_slots<NV>(R.rt_sum + (size_t)g * kEpiGroup * kOut, min(kEpiGroup, nblk - g * kEpiGroup), x);
+    if (lane == 0) {
+#pragma unroll
+      for (int q = 0; q < NV; ++q) gsum[(size_t)g * kOut + q] = x[q];
+      __threadfence();
+      s_last = atomicAdd(R.rt_count + request_counters(R) - 1, 1u) == (unsigned)ngrp - 1u;
+    }
+    __syncwarp();
+    if (__shfl_sync(0xffffffffu, s_last, 0)) {
+      __threadfence();
+      warp_sum_slots<NV>(gsum, ngrp, x);
+      if (lane == 0) {
+        // a sum that left the fixed-point range (red_fix) was not added: the results are NaN
+        const bool nan = R.status && (__ldcg(R.status) & kStatusFixRange);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) R.out[q] = nan ? __longlong_as_double(0x7ff8000000000000ll) : x[q];
+      }
+    }
+  }
 }
 
 }  // namespace
+
+// The table of TabLog on the current device: c_j = 1 / (1 + (j + 1/2) / 128) rounded to float32,
+// and -ln c_j from the host's extended-precision log, rounded once to double.
+cudaError_t init_log_table() {
+  double tab[2 * 128];
+  for (int j = 0; j < 128; ++j) {
+    const float c = (float)(1.0 / (1.0 + (j + 0.5) / 128.0));
+    tab[j] = (double)c;
+    tab[128 + j] = (double)(-logl((long double)c));
+  }
+  return cudaMemcpyToSymbol(g_logtab, tab, sizeof(tab));
+}
 
 cudaError_t launch_epilogue_fix(const Batch &b, bool grad, cudaStream_t s) {
   int blocks = 0;

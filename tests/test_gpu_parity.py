@@ -349,7 +349,7 @@ def test_full_size_sampled_rows(ctx, big, mode):
     np.testing.assert_allclose(xi[idx], r["xi"], rtol=tol, atol=tol * np.max(r["xi"]))
     # the sum over every row of log lambda_n - Lambda_n is the reported ell
     Lam, _ = oracle.compensator(ev.t, TH0)
-    assert rel(float(np.sum(np.log(mu + xi))) - Lam, ll) <= (1e-9 if mode == 1 else 1e-12)
+    assert rel(float(np.sum(np.log(mu + xi))) - Lam, ll) <= 1e-12
 
 
 def test_full_size_mixed_vs_fp64(ctx, big):
@@ -433,6 +433,25 @@ def test_four_million_events_sampled_rows(ctx):
         mu, xi, ll = terms[mode]
         np.testing.assert_allclose(mu[idx], r["mu"], rtol=tol)
         np.testing.assert_allclose(xi[idx], r["xi"], rtol=tol, atol=tol * np.max(r["xi"]))
-        assert rel(float(np.sum(np.log(mu + xi))) - Lam, ll) <= (1e-9 if mode == binding.HAWKES_MIXED else 1e-12)
+        assert rel(float(np.sum(np.log(mu + xi))) - Lam, ll) <= 1e-12
     assert rel(ll64, terms[binding.HAWKES_FP64][2]) <= 1e-12
     assert rel(llm, ll64) <= TOL_MIXED_LL and grad_err(gm, g64) <= TOL_MIXED_G
+
+
+@pytest.mark.parametrize("mu0", [1e-7, 1e-2, 1e4], ids=["mu1e-7", "mu1e-2", "mu1e4"])
+def test_split_epilogue_log(ctx, mu0):
+    """The mixed path's split epilogue takes log lambda_n by its own table-driven method (and
+    1 / lambda_n from a float32 reciprocal refined once): ell must equal the sum of numpy's log of
+    the returned mu_n + xi_n, less the compensator, to float64 rounding, with lambda_n spread over
+    many binades (mu0 from 1e-7 to 1e4 moves the background's share of every lambda_n)."""
+    ev = synth.simulate(20000, 2000.0, seed=83).rounded32()
+    th = (mu0,) + tuple(TH0[1:])
+    sid = ctx.hawkes_upload_events(ev.x, ev.y, ev.t)
+    try:
+        mu, xi, ll = ctx.hawkes_event_terms(sid, th, 1)
+    finally:
+        ctx.hawkes_release_events(sid)
+    lam = mu + xi
+    assert np.ptp(np.log2(lam)) > 2.0  # several binades (and, over the cases, many exponents)
+    Lam, _ = oracle.compensator(ev.t, th)
+    assert rel(float(np.sum(np.log(lam))) - Lam, ll) <= 1e-12
