@@ -283,6 +283,18 @@ int hawkes_wait(hawkes_ctx *ctx, uint64_t ticket, int timeout_ms, double *loglik
  * and the device bytes currently held for requests. `out` has 7 entries. */
 int hawkes_stats(hawkes_ctx *ctx, int64_t out[7]);
 
+/* Kernel timing, for profiling (the paper has no counterpart; it measures whole evaluations,
+ * Section 3.1). With on != 0, every evaluation enqueued on the context's own stream (blocking,
+ * batch and asynchronous calls; not the serving path) records CUDA events before its pair
+ * kernel, between it and the split epilogue of the mixed path, and after that; on = 0 stops.
+ * The events add two or three records to each evaluation's stream work.
+ * hawkes_kernel_ms waits for the most recent timed evaluation and writes, in ms, the duration
+ * of its pair kernel (ms_out[0]) and of what followed it up to the end of the evaluation's
+ * launches (ms_out[1]: the split epilogue in HAWKES_MIXED, about 0 otherwise). Errors:
+ * E_INVAL; E_PENDING if no evaluation was timed since timing was switched on; E_CUDA. */
+int hawkes_set_kernel_timing(hawkes_ctx *ctx, int on);
+int hawkes_kernel_ms(hawkes_ctx *ctx, double ms_out[2]);
+
 /* ---- evaluation without allocation -----------------------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that must not allocate
  * device memory when they evaluate, for example a program whose device memory is reserved in

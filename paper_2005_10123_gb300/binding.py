@@ -34,6 +34,7 @@ EXPORTS = (
     "hawkes_loglik_async", "hawkes_loglik_batch", "hawkes_event_terms", "hawkes_submit",
     "hawkes_poll", "hawkes_wait", "hawkes_stats", "hawkes_strerror", "hawkes_last_cuda_error",
     "hawkes_loglik_noalloc", "hawkes_pair_work", "hawkes_poll_timed", "hawkes_pi_batch", "hawkes_loglik_mix",
+    "hawkes_set_kernel_timing", "hawkes_kernel_ms",
 )
 HAWKES_MIX_MAX = 2
 HAWKES_NOALLOC_MAX_EVENTS = 65536
@@ -109,6 +110,8 @@ def load(build_if_missing: bool = False, path: str | None = None):
         "hawkes_poll": [vp, u64, ctypes.POINTER(ctypes.c_int), _D, _D],
         "hawkes_wait": [vp, u64, ctypes.c_int, _D, _D],
         "hawkes_stats": [vp, ctypes.POINTER(i64)],
+        "hawkes_set_kernel_timing": [vp, ctypes.c_int],
+        "hawkes_kernel_ms": [vp, _D],
         "hawkes_loglik_noalloc": [vp, vp, vp, i64, P, ctypes.c_int, vp, vp],
         "hawkes_pair_work": [vp, i32, P, ctypes.c_int, ctypes.POINTER(i64)],
         "hawkes_loglik_mix": [vp, i32, ctypes.POINTER(hawkes_mix_params), ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -322,6 +325,14 @@ class Context:
         self._check(self.lib.hawkes_wait(self.h, ctypes.c_uint64(ticket), int(timeout_ms), ctypes.byref(ll),
                                          g.ctypes.data_as(_D)), "hawkes_wait")
         return ll.value, g
+
+    def hawkes_set_kernel_timing(self, on: bool) -> None:
+        self._check(self.lib.hawkes_set_kernel_timing(self.h, 1 if on else 0), "hawkes_set_kernel_timing")
+
+    def hawkes_kernel_ms(self):
+        out = np.zeros(2, dtype=np.float64)
+        self._check(self.lib.hawkes_kernel_ms(self.h, out.ctypes.data_as(_D)), "hawkes_kernel_ms")
+        return float(out[0]), float(out[1])
 
     def hawkes_stats(self) -> dict:
         out = (ctypes.c_int64 * 7)()

@@ -109,6 +109,11 @@ struct hawkes_ctx {
   char *stage = nullptr;          // pinned host word for the upload checks (guarded by mu)
   char *bounce = nullptr;         // pinned bounce buffer for per-event rows (guarded by mu)
   cudaEvent_t bounce_ev[2] = {nullptr, nullptr};
+  // hawkes_set_kernel_timing: events around the pair kernel and the split epilogue of every
+  // evaluation on the context's own stream (kev[0] before, kev[1] between, kev[2] after)
+  int ktime = 0;
+  cudaEvent_t kev[3] = {nullptr, nullptr, nullptr};
+  int kev_recorded = 0;
   cudaStream_t copy_stream = nullptr;  // copies out of pi batches, beside the launches
   std::vector<cudaEvent_t> chunk_ev;   // one per launch of a pi batch
   std::string last_cuda;
@@ -445,12 +450,17 @@ int launch_batch(hawkes_ctx *ctx, Batch &b, int mode, int grad, cudaStream_t s) 
   for (int r = 0; r < b.nreq; ++r)  // a sym request's row sums are finished by the split epilogue
     if (b.req[r].sym && !b.split) return HAWKES_E_INVAL;
   b.total_items = (int)items;
+  const bool timed = ctx->ktime && s == ctx->stream;
+  if (timed) HK_CUDA(ctx, cudaEventRecord(ctx->kev[0], s));
   if (b.group) HK_CUDA(ctx, launch_pair_group(b, grad != 0, s));
-  else if (mode == HAWKES_MIXED) {
-    HK_CUDA(ctx, launch_pair_mixed(b, grad != 0, s));
-    HK_CUDA(ctx, launch_epilogue_fix(b, grad != 0, s));
-  }
+  else if (mode == HAWKES_MIXED) HK_CUDA(ctx, launch_pair_mixed(b, grad != 0, s));
   else HK_CUDA(ctx, launch_pair_fp64(b, grad != 0, s));
+  if (timed) HK_CUDA(ctx, cudaEventRecord(ctx->kev[1], s));
+  if (!b.group && mode == HAWKES_MIXED) HK_CUDA(ctx, launch_epilogue_fix(b, grad != 0, s));
+  if (timed) {
+    HK_CUDA(ctx, cudaEventRecord(ctx->kev[2], s));
+    ctx->kev_recorded = 1;
+  }
   return HAWKES_OK;
 }
 
@@ -949,6 +959,8 @@ int hawkes_destroy(hawkes_ctx *ctx) {
     if (F.done) cudaEventDestroy(F.done);
     if (F.host_out) cudaFreeHost(F.host_out);
   }
+  for (cudaEvent_t ev : ctx->kev)
+    if (ev) cudaEventDestroy(ev);
   for (auto &kv : ctx->sets) {
     if (kv.second->dev) cudaFreeAsync(kv.second->dev, ctx->stream);
     delete kv.second;
@@ -1426,6 +1438,31 @@ int hawkes_wait(hawkes_ctx *ctx, uint64_t ticket, int timeout_ms, double *loglik
   if (loglik_out) *loglik_out = T.ll;
   if (grad_out)
     for (int q = 0; q < 6; ++q) grad_out[q] = T.grad ? T.g[q] : 0.0;
+  return HAWKES_OK;
+}
+
+int hawkes_set_kernel_timing(hawkes_ctx *ctx, int on) {
+  if (!ctx) return HAWKES_E_INVAL;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  cudaSetDevice(ctx->device);
+  if (on && !ctx->kev[0])
+    for (cudaEvent_t &ev : ctx->kev) HK_CUDA(ctx, cudaEventCreate(&ev));
+  ctx->ktime = on ? 1 : 0;
+  ctx->kev_recorded = 0;
+  return HAWKES_OK;
+}
+
+int hawkes_kernel_ms(hawkes_ctx *ctx, double ms_out[2]) {
+  if (!ctx || !ms_out) return HAWKES_E_INVAL;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  if (!ctx->kev_recorded) return HAWKES_E_PENDING;
+  cudaSetDevice(ctx->device);
+  HK_CUDA(ctx, cudaEventSynchronize(ctx->kev[2]));
+  float a = 0.f, b = 0.f;
+  HK_CUDA(ctx, cudaEventElapsedTime(&a, ctx->kev[0], ctx->kev[1]));
+  HK_CUDA(ctx, cudaEventElapsedTime(&b, ctx->kev[1], ctx->kev[2]));
+  ms_out[0] = a;
+  ms_out[1] = b;
   return HAWKES_OK;
 }
 

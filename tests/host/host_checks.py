@@ -233,6 +233,17 @@ def main():
     assert ctx.hawkes_wait(t, 5000)[0] == fake_value(TH, 1000, 1)
     ctx.close()
 
+    # ---- kernel timing: nothing timed yet, then the fake's event durations
+    c_t = binding.Context(lib=lib)
+    ev_t = synth.simulate(3000, 500.0, seed=3)
+    sid_t = c_t.hawkes_upload_events(ev_t.x, ev_t.y, ev_t.t)
+    expect_status(lambda: c_t.hawkes_kernel_ms(), -7)
+    c_t.hawkes_set_kernel_timing(True)
+    c_t.hawkes_loglik_grad(sid_t, TH, 1)
+    assert c_t.hawkes_kernel_ms() == (0.25, 0.25)
+    c_t.hawkes_set_kernel_timing(False)
+    c_t.close()
+
     # ---- admission and allocation faults ---------------------------------------------------------
     ev = synth.simulate(20000, 2000.0, seed=2)
     small = binding.Context(hbm_budget_bytes=1 << 18, lib=lib)

@@ -176,3 +176,24 @@ def test_out_of_range_sums_give_nan(binding):
             if flags == 0:
                 assert np.isnan(ll) and np.all(np.isnan(g))
             assert np.isfinite(ctx.hawkes_loglik(sid, synth.THETA0, 1))
+
+
+def test_kernel_timing(binding):
+    """hawkes_kernel_ms: E_PENDING until an evaluation is timed, then the pair kernel's and the
+    split epilogue's durations of the latest one (both positive in mixed precision, the second
+    about 0 in float64, where the pair kernel finishes its own rows)."""
+    ev = synth.simulate(20000, 2000.0, seed=9)
+    with binding.Context(device=0) as ctx:
+        sid = ctx.hawkes_upload_events(ev.x, ev.y, ev.t)
+        with pytest.raises(binding.HawkesError) as e:
+            ctx.hawkes_kernel_ms()
+        assert e.value.status == -7
+        ctx.hawkes_set_kernel_timing(True)
+        want = ctx.hawkes_loglik_grad(sid, synth.THETA0, 1)
+        pair, epi = ctx.hawkes_kernel_ms()
+        assert pair > 0.0 and epi > 0.0 and epi < pair
+        ctx.hawkes_loglik_grad(sid, synth.THETA0, 0)
+        pair64, epi64 = ctx.hawkes_kernel_ms()
+        assert pair64 > pair and epi64 < 0.05
+        ctx.hawkes_set_kernel_timing(False)
+        assert ctx.hawkes_loglik_grad(sid, synth.THETA0, 1)[0] == want[0]  # timing changes nothing
