@@ -1,5 +1,5 @@
-// Upload preparation: the interface between the host runtime (api.cu) and its one device
-// launch (upload.cu). Kept apart from the pair kernels' shared header.
+// Upload preparation: the interface between the host runtime (api.cu) and its device
+// launches (upload.cu). Kept apart from the pair kernels' shared header.
 #ifndef HK_UPLOAD_H
 #define HK_UPLOAD_H
 
@@ -7,7 +7,7 @@
 
 namespace hk {
 
-// One launch forms, from the float64 coordinates of n events (read from sx, sy, st; written to
+// Two launches form, from the float64 coordinates of n events (read from sx, sy, st; written to
 // the set's x64, y64, t64 and padded there to npad): the float32 copies, the tie indices
 // lo32/lo64, the window tables (first[nb] then last[nb], nullptr for none, buckets of `width`
 // from t0 over the float32 or float64 times) and the input checks (flags |= 1: a value out of
