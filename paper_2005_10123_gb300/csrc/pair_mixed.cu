@@ -905,6 +905,31 @@ __device__ __forceinline__ double fix_to_double(long long v, int F) {
   return __longlong_as_double((long long)(sign | (e << 52) | ((m >> 11) & 0xfffffffffffffull)));
 }
 
+// Warp totals of P values per lane (P a power of two, at most 32) by a transposing butterfly, in a
+// fixed order: at the offsets 16, 8, ... each lane keeps half of its values (the lower half where
+// its bit of the offset is 0) and adds its partner's matching half, so the P totals need
+// P - 1 + 5 - log2 P additions per lane instead of 5 P for P separate trees (the float64 pipe is
+// what bounds the split epilogue). On return lane l holds the total of value l >> (5 - log2 P)
+// in x[0] (every lane of a group holds the same bits: the last levels add a + b and b + a).
+template <int P>
+__device__ __forceinline__ void warp_transpose_sum(double (&x)[P]) {
+  static_assert(P >= 1 && P <= 32 && (P & (P - 1)) == 0, "P: a power of two up to 32");
+  const int lane = threadIdx.x & 31;
+  int o = 16;
+#pragma unroll
+  for (int m = P; m > 1; m >>= 1, o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < m / 2; ++i) {
+      const double send = up ? x[i] : x[m / 2 + i];
+      const double keep = up ? x[m / 2 + i] : x[i];
+      x[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+#pragma unroll
+  for (; o > 0; o >>= 1) x[0] += __shfl_xor_sync(0xffffffffu, x[0], o);
+}
+
 static_assert(kEpiRows <= 32 * kMaxCtaWarps, "reduction scratch too narrow for the split epilogue");
 constexpr int kEpiGroup = 32;  // epilogue blocks per first-level group of the final sum
 
@@ -949,12 +974,15 @@ __global__ void __launch_bounds__(kEpiRows) epilogue_fix_kernel(const __grid_con
   constexpr int NR = GRAD ? 1 + NS : 1;
   double *red = reduce_scratch(), *tot = red + kMaxCtaWarps * kRedWidth;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  {
+    constexpr int P = NR == 1 ? 1 : NR <= 2 ? 2 : NR <= 4 ? 4 : NR <= 8 ? 8 : 16;
+    constexpr int SH = P == 1 ? 5 : P == 2 ? 4 : P == 4 ? 3 : P == 8 ? 2 : 1;  // 5 - log2 P
+    double x[P];
 #pragma unroll
-  for (int q = 0; q < NR; ++q) {
-    double x = v[q];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
-    if (lane == 0) red[warp * kRedWidth + q] = x;
+    for (int q = 0; q < P; ++q) x[q] = q < NR ? v[q] : 0.0;
+    warp_transpose_sum<P>(x);
+    const int q = lane >> SH;
+    if ((lane & ((1 << SH) - 1)) == 0 && q < NR) red[warp * kRedWidth + q] = x[0];
   }
   __syncthreads();
   if (tid < NR) {
