@@ -1,7 +1,8 @@
 // Unit probes for the roofline and the accuracy analysis of the mixed-precision path.
 //
 // 1. Issue rate of the float32 pipe: packed FFMA2, FADD2 and FMUL2, unpacked FFMA and FADD, a
-//    packed FADD2 + FFMA2 mix, and MUFU.EX2 (ex2.approx.ftz.f32), each over 8 independent chains
+//    packed FADD2 + FFMA2 mix, MUFU.EX2 (ex2.approx.ftz.f32), and half the chains packed FFMA2
+//    with the other half scalar FFMA (whether the two share one pipe), each over 8 independent chains
 //    per thread, 4 CTAs of 256 threads per SM; lane operations per second from CUDA events.
 // 2. Mean and RMS relative error of ex2.approx.ftz.f32 against exp2 in double, for arguments
 //    -q with q drawn uniformly from each quarter-unit bin of [0, 16): the argument-dependent
@@ -38,6 +39,10 @@ __global__ void rate_kernel(float *out, float s) {
       if (OP == 4) { a[i].x = __fadd_rn(a[i].x, b.x); a[i].y = __fadd_rn(a[i].y, b.x); }
       if (OP == 5) { a[i] = __fadd2_rn(a[i], b); a[i] = __ffma2_rn(a[i], b, one); }
       if (OP == 6) a[i].x = ex2a(a[i].x);
+      if (OP == 7) {  // half the chains packed FFMA2, half two scalar FFMA
+        if (i < kChains / 2) a[i] = __ffma2_rn(a[i], b, b);
+        else { a[i].x = __fmaf_rn(a[i].x, b.x, b.y); a[i].y = __fmaf_rn(a[i].y, b.x, b.y); }
+      }
     }
   }
   float acc = 0.f;
@@ -160,7 +165,8 @@ int main() {
   std::printf("\"ffma\": %.6e, ", lane_ops_per_s<3>(sms, 2.0));
   std::printf("\"fadd\": %.6e, ", lane_ops_per_s<4>(sms, 2.0));
   std::printf("\"fadd2_ffma2\": %.6e, ", lane_ops_per_s<5>(sms, 4.0));
-  std::printf("\"mufu_ex2\": %.6e}, ", lane_ops_per_s<6>(sms, 1.0));
+  std::printf("\"mufu_ex2\": %.6e, ", lane_ops_per_s<6>(sms, 1.0));
+  std::printf("\"ffma2_ffma_mix\": %.6e}, ", lane_ops_per_s<7>(sms, 2.0));
   std::printf("\"sequences_per_s\": {");
   std::printf("\"dadd\": %.6e, ", ops64_per_s<7>(sms));
   std::printf("\"fold_f32_into_f64\": %.6e, ", ops64_per_s<8>(sms));
