@@ -143,7 +143,7 @@ int hawkes_set_flags(hawkes_ctx *ctx, int flags);
  * x, y (km) and t (days) are host arrays of n doubles; the caller keeps ownership
  * and may free them when the call returns. t must be non-decreasing and >= 0
  * (the compensator integrates from 0 to t_N, the last event). The library copies
- * the float64 arrays to the device and forms there, in one launch, the float32
+ * the float64 arrays to the device and forms there, in two launches, the float32
  * copies, the tie indices and the time tables, and checks the inputs; all in
  * structure-of-arrays layout, padded to a multiple of 256 with sentinel events that
  * contribute exactly zero. The call returns when the set is ready (or rejected). The
