@@ -79,10 +79,12 @@ extern "C" {
 #define HAWKES_FLAG_DENSE 2        /* visit all N^2 pairs (see below)                      */
 #define HAWKES_FLAG_NO_SYMMETRY 4  /* HAWKES_MIXED: evaluate every ordered pair on its own     */
 /* By default a mixed-precision evaluation without HAWKES_FLAG_EXCLUDE_SELF or HAWKES_FLAG_DENSE
- * shares background terms: e_b(n, n') = e_b(n', n), so for column tiles far enough before a row
- * tile that no trigger term can change the sums (beyond the trigger's reach, see below) each pair term
- * is formed once and added to both events' rows. Every event's sums (its row's, and the shares of
- * the far tiles holding it) are then added as exact fixed-point integers: 2^-F resolution with
+ * shares background terms: e_b(n, n') = e_b(n', n), so for the column tiles before a row tile's
+ * own each background term is formed once and added to both events' rows; the trigger terms of
+ * those tiles (nonzero only within the trigger's reach, see below) go to the later event's row
+ * alone. With a two-component mixture only the tiles beyond the trigger's reach are shared.
+ * Every event's sums (its row's, and the shares of the tiles holding it) are then added as exact
+ * fixed-point integers: 2^-F resolution with
  * F = 62 - ceil(log2 N_padded) for the background sums (about 3e-14 at N = 85,000, against a
  * background sum of at least 1, the self term) and a per-sum F from Theta for the trigger
  * moments. Integer addition commutes, so results stay bit-identical from run to run and alone or

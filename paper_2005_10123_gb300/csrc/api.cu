@@ -317,7 +317,7 @@ int make_request(hawkes_ctx *ctx, const EventSetRec *S, const hawkes_params *p, 
     R->tscale = 1.0;
   }
   exact_zero_cutoffs(p, mode, R->beta, flags, S->n, &R->cut_early, &R->cut_late, &R->trig_cut);
-  R->sym = use_symmetry(S, mode, flags) ? 1 : 0;
+  R->sym = use_symmetry(S, mode, flags) ? (HK_SYM_NEAR ? 2 : 1) : 0;
   R->mix = 1;
   set_fix_bits(R, grad, 1, p->h, p->omega, 0.0, 0.0, S->t_last32 - S->t_first32);
   (void)ctx;
@@ -348,6 +348,7 @@ int set_mixture(const hawkes_mix_params *m, int mode, double span, Request *R, M
   R->trig_cut = std::max(R->trig_cut, trig2);
   R->cut_early = std::max(R->cut_early, early2);
   R->mix = 2;
+  if (R->sym) R->sym = 1;  // the shared near tiles take one trigger component
   set_fix_bits(R, R->grad, 2, R->h, R->omega, h2, om2, span);
   return HAWKES_OK;
 }
@@ -616,7 +617,7 @@ int eval_locked(hawkes_ctx *ctx, EventSetRec *S, int k, const hawkes_params *par
   for (int r = 0; r < k; ++r) {
     const int q = order[r];
     if (int rc = make_request(ctx, S, &params[q], mode, grad, ctx->flags, &b->req[r])) return rc;
-    b->req[r].sym = sym;
+    if (!sym) b->req[r].sym = 0;  // grouped (make_request chose the level otherwise)
     if (mix)
       if (int rc = set_mixture(mix, mode, S->t_last32 - S->t_first32, &b->req[r], &b->mix2)) return rc;
     bind_workspace(&b->req[r], S, mode, grad, req_base + (size_t)r * per,
@@ -1167,9 +1168,9 @@ int hawkes_pair_work(hawkes_ctx *ctx, int32_t set_id, const hawkes_params *param
       c0 = (int)(j0 / kColTile);
       c1 = std::max(std::min((int)((j1 + kColTile - 1) / kColTile), S->nct), c0 + 1);
     }
-    if (R.sym) {  // far column tiles serve both events of a pair (SymPlan)
+    if (R.sym) {  // far (and shared near) column tiles serve both events of a pair (SymPlan)
       const SymPlan pl = sym_plan_scan(R, W, rt, make_int2(c0, c1), [&](int K) { return t[(size_t)K * kRowTile]; });
-      visited += (r1 - r0 + 1) * (cols_in(c0, pl.end) + cols_in(c0, pl.sym_end));
+      visited += (r1 - r0 + 1) * (cols_in(c0, pl.end) + cols_in(c0, pl.near_end));
       evaluated += (r1 - r0 + 1) * cols_in(c0, pl.end);
     } else {
       visited += (r1 - r0 + 1) * cols_in(c0, c1);

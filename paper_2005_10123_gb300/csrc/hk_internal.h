@@ -27,6 +27,9 @@ constexpr int kRowTile = kThreads * kRowsPerThread;  // 256: 64 threads x 4 rows
 constexpr int kColTile = HK_COL_TILE;
 constexpr int kWarpRows = 32 * kRowsPerThread;       // consecutive rows per warp
 constexpr int kPadTo = kRowTile > kColTile ? kRowTile : kColTile;  // event arrays padded to this
+#ifndef HK_SYM_NEAR
+#define HK_SYM_NEAR 1  // shared background: share the near column tiles before a row tile too
+#endif
 #ifndef HK_SYM_DESC
 #define HK_SYM_DESC 1  // shared-background launches: row tiles latest first (see item_at)
 #endif
@@ -158,7 +161,8 @@ struct Request {
   // symmetric background (see SymPlan): far column tiles share each background term between its
   // row and its column. Every event's sums, from its row's items and from the far column tiles
   // holding it, go to fixsum as exact fixed-point integers (no partial-sum slots, no merge tree).
-  int sym;             // 1: on (mixed, fused, set with a time table, no exclude-self/dense/no-symmetry)
+  int sym;             // 1: on (mixed, fused, set with a time table, no exclude-self/dense/no-symmetry);
+                       // 2: the near column tiles before the row tile shared too (one trigger)
   signed char fix_bits[kMaxSums];  // sym: sum s enters fixsum as round(v 2^fix_bits[s]) (fix_bits_for)
   double trig_cut;     // days: columns earlier than t_n - trig_cut give trigger terms that contribute
                        // nothing (with the self term below 2^-40 (mixed) or 2^-70 (float64) of
@@ -316,7 +320,9 @@ __host__ __device__ inline int first_item_of(const Request &R, int rt) {
 // before: row tile I visits the column tiles [max(c0(I), 2 ib(I)), min(c1(I), 2 kmax(I) + 2)),
 // kmax(I) = the last row tile K with ib(K) <= I (the later row tiles for which I is not far).
 // A pair (n in I, n' in K > I) is so covered exactly once in each direction: by K's far block
-// when I < ib(K), else by I's late columns (K <= kmax(I)) and K's near early columns.
+// when I < ib(K), else by I's late columns (K <= kmax(I)) and K's near early columns. With
+// R.sym == 2 (sym_plan_near) K's near early columns [sym_end(K), 2 K) serve both directions too,
+// and I's late columns are not visited.
 // Every event's sums reach R.fixsum as integers round(v 2^F) (fix_bits_for): each item adds its
 // rows' float64 sums, each far block its columns' float32 sums. Integer additions commute
 // exactly, so the totals do not depend on the order in which items finish. The pair kernel's
@@ -334,10 +340,11 @@ __host__ __device__ inline SymK sym_k(const Request &R, const WinTable &W, doubl
   return SymK{table_first(W, t_first - R.cut_early), table_first(W, t_first - R.trig_cut) / 2};
 }
 
-// The plan of row tile I: far column tiles [c0, sym_end), near ones [sym_end, end), and e_col,
-// the far column tiles of later row tiles that hold I's columns.
+// The plan of row tile I: far column tiles [c0, sym_end), shared near ones [sym_end, near_end)
+// (R.sym == 2; empty otherwise), near ones evaluated row by row [near_end, end), and e_col, the
+// far column tiles of later row tiles that hold I's columns.
 struct SymPlan {
-  int sym_end, end, e_col;
+  int sym_end, near_end, end, e_col;
 };
 
 // One row tile K's contribution to the plan of row tile I < K: its far column tiles among I's
@@ -349,6 +356,17 @@ __host__ __device__ inline void sym_visit(const SymK &k, int I, int *e_col, bool
 // Later row tiles K stop mattering to I once both hold: K's window starts after I's columns and
 // I is far for K (c0 and ib are non-decreasing in K).
 __host__ __device__ inline bool sym_done(const SymK &k, int I) { return k.c0 > 2 * I + 1 && k.ib > I; }
+
+// With R.sym == 2 the near column tiles before row tile I's own, [sym_end, 2 I), are shared as
+// well: their background terms serve both events, their trigger terms the rows. Row tile I then
+// visits its own two column tiles and no later ones row by row, because every later row tile K
+// for which I is near (ib(K) <= I) holds I's columns among its shared near tiles.
+__host__ __device__ inline SymPlan sym_plan_near(int2 win, int sym_end, int I, int e_col) {
+  const int own = 2 * I < win.y ? 2 * I : win.y;
+  const int near_end = own > sym_end ? own : sym_end;
+  const int end = win.y < 2 * I + 2 ? win.y : 2 * I + 2;
+  return SymPlan{sym_end, near_end, end, e_col};
+}
 
 // The plan of row tile I from its window [c0, c1) (table_window_rt), by a plain scan over the
 // later row tiles; tfirst(K) is row tile K's first event time. Host code and reference for the
@@ -365,8 +383,9 @@ __host__ __device__ inline SymPlan sym_plan_scan(const Request &R, const WinTabl
     if (near) kmax = K;
   }
   const int sym_end = win.x > 2 * own.ib ? win.x : 2 * own.ib;
+  if (R.sym == 2) return sym_plan_near(win, sym_end, I, e_col);
   const int end = win.y < 2 * kmax + 2 ? win.y : 2 * kmax + 2;
-  return SymPlan{sym_end, end, e_col};
+  return SymPlan{sym_end, sym_end, end, e_col};
 }
 __host__ __device__ inline PairItem item_at(const Request &R, int p) {
   const int K = R.slices, n4 = (K + 3) / 4, n2 = (K + 1) / 2;

@@ -64,6 +64,15 @@
 #ifndef HK_SYM_UNROLL_LL
 #define HK_SYM_UNROLL_LL HK_SYM_UNROLL  // the same, loglik only
 #endif
+#ifndef HK_NEAR_UNROLL
+#define HK_NEAR_UNROLL 2  // steps unrolled in the shared near tile pass, loglik + gradient
+#endif
+#ifndef HK_NEAR_UNROLL_LL
+#define HK_NEAR_UNROLL_LL HK_NEAR_UNROLL  // the same, loglik only
+#endif
+#ifndef HK_SNEAR_WEIGHT
+#define HK_SNEAR_WEIGHT 19  // cost of a shared near column tile in tenths of a row-by-row one
+#endif
 #ifndef HK_FAR_WEIGHT
 #define HK_FAR_WEIGHT 10  // cost of a far column tile in tenths of a near one, for the leaf split
 #endif
@@ -393,6 +402,121 @@ __device__ __forceinline__ void tile_pass_sym_pairs(const float4 *__restrict__ s
   }
 }
 
+// A shared near column tile (SymPlan, R.sym == 2; one trigger component): the column tile lies
+// before this row tile, within the trigger's reach, and each background term serves its row and
+// its column as in the far pass, while the trigger terms serve the rows only (the columns are the
+// earlier events). Pair layout (store_cols_near): sN[m] = {-x_a, -x_b, -y_a, -y_b} (stored
+// coordinates) and sN[kThreads + m] = {-t'_a, -t'_b, -t_a, -t_b} (scaled and stored times). The
+// terms take the row-by-row kinds' forms, q = a2 r^2 + dt'^2 and the trigger's r^2 from the
+// stored coordinates. BG: background terms, shared (their column shares reach fixsum rows 0, 2
+// and 3 as in tile_pass_sym_pairs). TRIG: trigger terms; separable (the column factor
+// WN (t_ref - t_n') with t_ref = SREF, the caller applies the row factor) unless MASK, which
+// forms WN (t_n - t_n') per pair and keeps the terms with n' < lo(n) (ties with a row).
+template <bool GRAD, bool BG, bool TRIG, bool MASK>
+__device__ __forceinline__ void tile_pass_sym_near(const float4 *__restrict__ sN, const float2 (&X)[kPairs],
+                                                   const float2 (&Y)[kPairs], const float2 (&T)[kPairs],
+                                                   const float2 (&TR)[kPairs], const int (&LO)[kRowsPerThread],
+                                                   int c0, float2 A2, float2 CN, float2 WN, float2 SREF,
+                                                   Acc32<num_sums(GRAD, 1)> &acc, long long *__restrict__ fixsum,
+                                                   int npad, float fix_scale, int *bad) {
+  constexpr int kNearUnroll = GRAD ? HK_NEAR_UNROLL : HK_NEAR_UNROLL_LL;
+  const int lane = threadIdx.x & 31;
+#pragma unroll 1
+  for (int h = 0; h < kColTile / 64; ++h) {
+    float2 cs = make_float2(0.f, 0.f), cq = cs, cu = cs;  // the owned pair's column sums (BG)
+#pragma unroll kNearUnroll
+    for (int k = 0; k < 32; ++k) {
+      const int m = h * 32 + ((lane + k) & 31);
+      const float4 C = sN[m], D = sN[kThreads + m];
+      const float2 cx[2] = {make_float2(C.x, C.y), make_float2(C.y, C.x)};
+      const float2 cy[2] = {make_float2(C.z, C.w), make_float2(C.w, C.z)};
+      const float2 ct[2] = {make_float2(D.x, D.y), make_float2(D.y, D.x)};
+      const float2 cr[2] = {make_float2(D.z, D.w), make_float2(D.w, D.z)};  // -t (stored)
+      float2 dref[2], bj[2];
+      if (TRIG && !MASK) {
+        dref[0] = add2(SREF, cr[0]);  // t_ref - t_n' >= 0
+        bj[0] = mul2(dref[0], WN);
+        dref[1] = make_float2(dref[0].y, dref[0].x);
+        bj[1] = make_float2(bj[0].y, bj[0].x);
+      }
+      float2 ps[2], pq[2], pu[2];  // per variant, summed over the row pairs (BG)
+#pragma unroll
+      for (int p = 0; p < kPairs; ++p)
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+          const float2 dx = add2(X[p], cx[v]), dy = add2(Y[p], cy[v]);
+          const float2 rho = fma2(dy, dy, mul2(dx, dx));
+          if (BG) {
+            const float2 dt = add2(T[p], ct[v]);
+            const float2 u = mul2(dt, dt);
+            const float2 q = fma2(rho, A2, u);
+            const float2 e = make_float2(ex2(-q.x), ex2(-q.y));
+            acc.v[0][p] = acc2(acc.v[0][p], e);
+            if (GRAD) {
+              acc.v[2][p] = accfma2(q, e, acc.v[2][p]);
+              acc.v[3][p] = accfma2(u, e, acc.v[3][p]);
+            }
+            if (p == 0) {
+              ps[v] = e;
+              if (GRAD) {
+                pq[v] = mul2(q, e);
+                pu[v] = mul2(u, e);
+              }
+            } else {
+              ps[v] = acc2(ps[v], e);
+              if (GRAD) {
+                pq[v] = fma2(q, e, pq[v]);
+                pu[v] = fma2(u, e, pu[v]);
+              }
+            }
+          }
+          if (TRIG) {
+            float2 arg, dtr;
+            if (MASK) {
+              dtr = add2(TR[p], cr[v]);
+              arg = fma2(rho, CN, mul2(dtr, WN));
+            } else {
+              arg = fma2(rho, CN, bj[v]);
+            }
+            float2 es = make_float2(ex2(arg.x), ex2(arg.y));
+            if (MASK) {  // variant 0 pairs the rows with (a, b), variant 1 with (b, a)
+              const int ca = c0 + 2 * m;
+              es.x = (ca + v < LO[2 * p]) ? es.x : 0.f;
+              es.y = (ca + 1 - v < LO[2 * p + 1]) ? es.y : 0.f;
+            }
+            acc.v[1][p] = acc2(acc.v[1][p], es);
+            if (GRAD) {
+              acc.v[4][p] = accfma2(rho, es, acc.v[4][p]);
+              acc.v[5][p] = accfma2(MASK ? dtr : dref[v], es, acc.v[5][p]);
+            }
+          }
+        }
+      if (BG) {
+        const int dst = (lane - k) & 31;
+        cs = add2(cs, make_float2(__shfl_sync(0xffffffffu, ps[0].x + ps[1].y, dst),
+                                  __shfl_sync(0xffffffffu, ps[0].y + ps[1].x, dst)));
+        if (GRAD) {
+          cq = add2(cq, make_float2(__shfl_sync(0xffffffffu, pq[0].x + pq[1].y, dst),
+                                    __shfl_sync(0xffffffffu, pq[0].y + pq[1].x, dst)));
+          cu = add2(cu, make_float2(__shfl_sync(0xffffffffu, pu[0].x + pu[1].y, dst),
+                                    __shfl_sync(0xffffffffu, pu[0].y + pu[1].x, dst)));
+        }
+      }
+    }
+    if (BG) {
+      long long *f = fixsum + (size_t)c0 + 2 * (h * 32 + lane);
+      red_fix(f, cs.x, fix_scale, bad);
+      red_fix(f + 1, cs.y, fix_scale, bad);
+      if (GRAD) {
+        red_fix(f + 2 * (size_t)npad, cq.x, fix_scale, bad);
+        red_fix(f + 2 * (size_t)npad + 1, cq.y, fix_scale, bad);
+        red_fix(f + 3 * (size_t)npad, cu.x, fix_scale, bad);
+        red_fix(f + 3 * (size_t)npad + 1, cu.y, fix_scale, bad);
+      }
+    }
+  }
+}
+
 // Exact-zero gaps in scaled time dt' between a warp's earliest row and a tile's latest
 // column: past kBgZeroGap every background exponent exceeds 130 (ex2 flushes 2^-130 to
 // zero); past kTrigZeroExp / -wn every trigger row factor 2^(wn dt') is below 2^-131.
@@ -467,6 +591,17 @@ __device__ __forceinline__ void store_cols_pairs(const RawCols &r, int ct, int t
   const float ya = scale_split(r.y[0], k.s_hi, k.s_lo), yb = scale_split(r.y[1], k.s_hi, k.s_lo);
   sC[tid] = make_float4(-xa, -xb, -ya, -yb);
   reinterpret_cast<float2 *>(sT)[tid] = make_float2(-ta, -tb);
+}
+
+// Pair-layout staging of a shared near tile (tile_pass_sym_near), from load_cols_pairs: the stored
+// coordinates of pair tid, then its scaled and stored times.
+__device__ __forceinline__ void store_cols_near(const RawCols &r, int ct, int tid, int n, float t_origin,
+                                                const Scales &k, float4 *sN) {
+  const int j = ct * kColTile + 2 * tid;
+  const float ta = j < n ? scale_split(r.t[0] - t_origin, k.b_hi, k.b_lo) : kPadScaled;
+  const float tb = j + 1 < n ? scale_split(r.t[1] - t_origin, k.b_hi, k.b_lo) : kPadScaled;
+  sN[tid] = make_float4(-r.x[0], -r.x[1], -r.y[0], -r.y[1]);
+  sN[kThreads + tid] = make_float4(-ta, -tb, -r.t[0], -r.t[1]);
 }
 
 // This thread's row coordinates (rows ra = wa + lane + 32 k, packed in pairs k, k + 1),
@@ -566,10 +701,9 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
     LO[2 * p] = S.lo32[ra];
     LO[2 * p + 1] = S.lo32[rb];
   }
-  // scaled row coordinates stay in registers; the stored ones are reloaded (L1) for the
-  // few tiles with trigger terms
+  // row coordinates are reloaded (L1) per tile, scaled for the background-only kinds and stored
+  // for the others, so that no kind holds the other's registers
   float2 XS[kPairs], YS[kPairs];
-  row_coords<true>(S, row_a0, sk, XS, YS);
   const float2 A2 = make_float2(R.a2, R.a2), CN = make_float2(R.cn, R.cn);
   const float2 CN2 = make_float2(B.mix2.cn2, B.mix2.cn2);
   // trigger slopes per unit of stored time, -omega log2(e) rounded once (formed in the tiles with
@@ -591,24 +725,42 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
 #pragma unroll
     for (int k = 0; k < kRowsPerThread; ++k) sacc[(s * kRowsPerThread + k) * kThreads + tid] = 0.0;
 
-  // far tiles are staged in pair layout (tile_pass_sym_pairs)
-  auto paired = [&](int c) { return R.sym && c < plan.sym_end; };
+  // far tiles are staged in pair layout (tile_pass_sym_pairs), shared near ones in their own pair
+  // layout (tile_pass_sym_near), the rest one column at a time (tile_pass)
+  auto layout = [&](int c) {
+    return R.sym && c < plan.sym_end ? 1 : MIX == 1 && c >= plan.sym_end && c < plan.near_end ? 2 : 0;
+  };
+  auto load = [&](int c, int lay) { return lay ? load_cols_pairs(S, c, tid) : load_cols(S, c, tid); };
+  auto stage = [&](const RawCols &r, int c, int lay, int b) {
+    if (lay == 1) store_cols_pairs(r, c, tid, n, t_origin, sk, sxs[b], stx[b]);
+    else if (lay == 2) store_cols_near(r, c, tid, n, t_origin, sk, sxs[b]);
+    else store_cols(r, c, tid, n, t_origin, sk, sxs[b], stx[b], srt[b]);
+  };
   int ct = c_begin;
   if (ct < c_end) {  // an empty slice of the window writes zero partial sums
-    if (paired(ct)) store_cols_pairs(load_cols_pairs(S, ct, tid), ct, tid, n, t_origin, sk, sxs[0], stx[0]);
-    else store_cols(load_cols(S, ct, tid), ct, tid, n, t_origin, sk, sxs[0], stx[0], srt[0]);
+    const int lay = layout(ct);
+    stage(load(ct, lay), ct, lay, 0);
     cta_sync();
   }
   for (int k = 0; ct < c_end; ++ct, ++k) {
     const int buf = k & 1;
-    const bool has_next = ct + 1 < c_end, next_paired = paired(ct + 1);
+    const bool has_next = ct + 1 < c_end;
+    const int next_lay = layout(ct + 1);
     RawCols nxt;
-    if (has_next) nxt = next_paired ? load_cols_pairs(S, ct + 1, tid) : load_cols(S, ct + 1, tid);
+    if (has_next) nxt = load(ct + 1, next_lay);
     const int c0 = ct * kColTile, c1 = c0 + kColTile;
     int kind, comps = 1;  // comps: the mixture components with nonzero trigger terms (bit mask)
     if (R.sym && ct < plan.sym_end) {  // far: background only, shared with the columns' rows
       const float gap = s_first + reinterpret_cast<const float2 *>(stx[buf])[kColTile / 2 - 1].y;  // the latest column
       kind = gap >= kBgZeroGap ? -1 : 4;
+    } else if (MIX == 1 && ct < plan.near_end) {  // shared near tile: the same classes as below
+      if (c1 <= lo_wa) {
+        const float gap = s_first + sxs[buf][kColTile - 1].y;  // t'(first row) - t'(latest column)
+        const bool bg_zero = gap >= kBgZeroGap, trig_zero = wn * gap <= -kTrigZeroExp;
+        kind = bg_zero ? (trig_zero ? -1 : 7) : (trig_zero ? 5 : 6);
+      } else {
+        kind = 8;  // a column tied with a row of this warp
+      }
     } else if (c1 <= lo_wa) {  // every pair causal: which of the two terms can be nonzero?
       const float gap = s_first + stx[buf][kColTile - 1].x;  // t'(first row) - t'(latest column)
       const bool bg_zero = gap >= kBgZeroGap, trig_zero = wn * gap <= -kTrigZeroExp;
@@ -629,11 +781,52 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
       for (int p = 0; p < kPairs; ++p) acc.v[s][p] = make_float2(0.f, 0.f);
     float2 X[kPairs], Y[kPairs], TR[kPairs];  // stored row coordinates and times, tiles with trigger terms
     if (kind == 0) {
+      row_coords<true>(S, row_a0, sk, XS, YS);
       tile_pass<0, GRAD, MIX>(sxs[buf], stx[buf], srt[buf], XS, YS, T, T, LO, row_a0, c0, excl, A2, CN, CN, CN2, CN2,
                               CN, acc);
     } else if (kind == 4) {
+      row_coords<true>(S, row_a0, sk, XS, YS);
       tile_pass_sym_pairs<GRAD>(sxs[buf], stx[buf], XS, YS, T, acc, R.fixsum, S.npad, c0, pow2f(R.fix_bits[0]),
                                 &s_bad);
+    } else if (kind >= 5) {
+      if constexpr (MIX == 1) {
+        row_coords<false>(S, row_a0, sk, X, Y);
+        const float2 WN = slope(R.omega);
+        const float sref = -sxs[buf][kColTile - 1].w;  // t_ref: the tile's latest column (stored time)
+        const float2 SREF = make_float2(sref, sref);
+        const float fs = pow2f(R.fix_bits[0]);
+        if (kind == 8) {  // rare (ties across the tile's edge): the background, then the masked trigger
+          tile_pass_sym_near<GRAD, true, false, false>(sxs[buf], X, Y, T, T, LO, c0, A2, CN, WN, SREF, acc, R.fixsum,
+                                                       S.npad, fs, &s_bad);
+          row_times(S, row_a0, TR);
+          tile_pass_sym_near<GRAD, false, true, true>(sxs[buf], X, Y, T, TR, LO, c0, A2, CN, WN, SREF, acc, R.fixsum,
+                                                      S.npad, fs, &s_bad);
+        } else if (kind == 6) {
+          tile_pass_sym_near<GRAD, true, true, false>(sxs[buf], X, Y, T, T, LO, c0, A2, CN, WN, SREF, acc, R.fixsum,
+                                                      S.npad, fs, &s_bad);
+        } else if (kind == 5) {
+          tile_pass_sym_near<GRAD, true, false, false>(sxs[buf], X, Y, T, T, LO, c0, A2, CN, WN, SREF, acc, R.fixsum,
+                                                       S.npad, fs, &s_bad);
+        } else {
+          tile_pass_sym_near<GRAD, false, true, false>(sxs[buf], X, Y, T, T, LO, c0, A2, CN, WN, SREF, acc, R.fixsum,
+                                                       S.npad, fs, &s_bad);
+        }
+        if (kind == 6 || kind == 7) {  // the separable trigger's row factor, as below
+          row_times(S, row_a0, TR);
+          const float2 sr = make_float2(-sref, -sref);
+#pragma unroll
+          for (int p = 0; p < kPairs; ++p) {
+            const float2 d = __fadd2_rn(TR[p], sr);
+            const float2 w = __fmul2_rn(d, WN);
+            const float2 a = make_float2(ex2(w.x), ex2(w.y));
+            if (GRAD) {
+              acc.v[5][p] = __fmul2_rn(__ffma2_rn(d, acc.v[1][p], acc.v[5][p]), a);
+              acc.v[4][p] = __fmul2_rn(acc.v[4][p], a);
+            }
+            acc.v[1][p] = __fmul2_rn(acc.v[1][p], a);
+          }
+        }
+      }
     } else if (kind == 1 || kind == 3) {
       row_coords<false>(S, row_a0, sk, X, Y);
       row_times(S, row_a0, TR);
@@ -696,7 +889,8 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
     }  // kind -1: every term of the tile is exactly zero for this warp
     // fold the tile's sums into float64; a tile without trigger (background) terms leaves
     // those sums at zero, so they are skipped
-    const bool fold_bg = kind == 0 || kind == 1 || kind == 2 || kind == 4, fold_trig = kind >= 1 && kind <= 3;
+    const bool fold_bg = kind == 0 || kind == 1 || kind == 2 || kind == 4 || kind == 5 || kind == 6 || kind == 8;
+    const bool fold_trig = (kind >= 1 && kind <= 3) || kind >= 6;
     if (kind == 2) comps = 3;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
@@ -709,10 +903,7 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
         sacc[(s * kRowsPerThread + 2 * p + 1) * kThreads + tid] += (double)acc.v[s][p].y;
       }
     }
-    if (has_next) {
-      if (next_paired) store_cols_pairs(nxt, ct + 1, tid, n, t_origin, sk, sxs[buf ^ 1], stx[buf ^ 1]);
-      else store_cols(nxt, ct + 1, tid, n, t_origin, sk, sxs[buf ^ 1], stx[buf ^ 1], srt[buf ^ 1]);
-    }
+    if (has_next) stage(nxt, ct + 1, next_lay, buf ^ 1);
     cta_sync();
   }
   // this thread's rows: la = warp * kWarpRows + lane + 32 k, sums at sacc[(s R + k) T + tid]
@@ -767,6 +958,8 @@ __device__ SymPlan sym_plan_warp(const Request &R, int I, int2 win) {
   const float *t = R.set.t32;
   const int lane = threadIdx.x & 31;
   const SymK own = sym_k(R, W, (double)__ldg(t + (size_t)I * kRowTile));
+  // shared near tiles: the plan needs no later row tile (e_col, which no kernel reads, stays 0)
+  if (R.sym == 2) return sym_plan_near(win, max(win.x, 2 * own.ib), I, 0);
   int e_col = 0, kmax = I;
   for (int base = I + 1; base < R.set.nrt; base += 32) {
     const int K = base + lane;
@@ -787,7 +980,8 @@ __device__ SymPlan sym_plan_warp(const Request &R, int I, int2 win) {
     e_col += __shfl_xor_sync(0xffffffffu, e_col, off);
     kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, off));
   }
-  return SymPlan{max(win.x, 2 * own.ib), min(win.y, 2 * kmax + 2), e_col};
+  const int sym_end = max(win.x, 2 * own.ib);
+  return SymPlan{sym_end, sym_end, min(win.y, 2 * kmax + 2), e_col};
 }
 
 template <bool GRAD, int MIX>
@@ -821,7 +1015,7 @@ __global__ void __launch_bounds__(kThreads, MIX > 1 ? (GRAD ? HK_MIN_CTAS_MIX : 
     cta_sync();
     w = s_win;
   }
-  SymPlan plan{w.x, w.y, 0};
+  SymPlan plan{w.x, w.x, w.y, 0};
   if (R.sym) {  // far and near column tiles of this row tile (the host enables sym only with a table)
     __shared__ SymPlan s_plan;
     if (threadIdx.x < 32) {
@@ -832,13 +1026,17 @@ __global__ void __launch_bounds__(kThreads, MIX > 1 ? (GRAD ? HK_MIN_CTAS_MIX : 
     plan = s_plan;
     w.y = plan.end;
   }
-  // leaves: equal shares of the window's cost, a far column tile weighing HK_FAR_WEIGHT / 10 near
-  // ones (without sym every tile weighs the same)
-  const long long fw = R.sym ? HK_FAR_WEIGHT : 10, nf = plan.sym_end - w.x, nn = w.y - plan.sym_end;
-  const long long total = nf * fw + nn * 10;
+  // leaves: equal shares of the window's cost, a far column tile weighing HK_FAR_WEIGHT / 10 and a
+  // shared near one HK_SNEAR_WEIGHT / 10 row-by-row ones (without sym every tile weighs the same)
+  const long long fw = R.sym ? HK_FAR_WEIGHT : 10, sw = HK_SNEAR_WEIGHT;
+  const long long nf = plan.sym_end - w.x, nsn = plan.near_end - plan.sym_end, nn = w.y - plan.near_end;
+  const long long total = nf * fw + nsn * sw + nn * 10;
   auto at = [&](int l) {  // column tile where leaf l starts
-    const long long pos = total * l / ns;
-    return pos < nf * fw ? w.x + (int)(pos / fw) : plan.sym_end + (int)((pos - nf * fw) / 10);
+    long long pos = total * l / ns;
+    if (pos < nf * fw) return w.x + (int)(pos / fw);
+    pos -= nf * fw;
+    if (pos < nsn * sw) return plan.sym_end + (int)(pos / sw);
+    return plan.near_end + (int)((pos - nsn * sw) / 10);
   };
   const int c_begin = at(l0), c_end = at(l1);
   run_piece<GRAD, MIX>(B, R, it, c_begin, c_end, plan, sxs, stx, srt, sacc);

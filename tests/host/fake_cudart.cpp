@@ -156,6 +156,7 @@ static bool check_symmetry(const Request &R) {
     if (R.rt_done[I] != 0u) return sym_fail("rt_done not zero", S.n, I, 0);
   for (size_t i = 0; i < (size_t)num_sums(R.grad != 0, R.mix) * S.npad; ++i)
     if (R.fixsum[i] != 0) return sym_fail("fixsum not zero", S.n, (int)i, 0);
+  if (R.sym != (R.mix > 1 || !HK_SYM_NEAR ? 1 : 2)) return sym_fail("level", S.n, R.sym, R.mix);
   if (S.nct > 1024) return true;  // the block table below grows as nct^2
   g_sym_checked++;
   auto tfirst = [&](int K) { return (double)S.t32[(size_t)K * kRowTile]; };
@@ -167,7 +168,8 @@ static bool check_symmetry(const Request &R) {
     plan[I] = sym_plan_scan(R, S.win32, I, win[I], tfirst);
     const int real = (S.n + kColTile - 1) / kColTile;  // column tiles holding real events
     if (plan[I].sym_end < win[I].x || plan[I].sym_end > 2 * I || plan[I].end < std::min(2 * I + 2, real) ||
-        plan[I].end > win[I].y)
+        plan[I].end > win[I].y || plan[I].near_end < plan[I].sym_end || plan[I].near_end > 2 * I ||
+        (R.sym != 2 && plan[I].near_end != plan[I].sym_end))
       return sym_fail("plan bounds", S.n, I, plan[I].sym_end * 10000 + plan[I].end);
   }
   const size_t nct = (size_t)S.nct;
@@ -178,10 +180,10 @@ static bool check_symmetry(const Request &R) {
       cov[(size_t)(2 * I + 1) * nct + J]++;
     }
   for (int K = 0; K < S.nrt; ++K)
-    for (int H = win[K].x; H < plan[K].sym_end; ++H) {  // column side of K's far tiles
+    for (int H = win[K].x; H < plan[K].near_end; ++H) {  // column side of K's far and shared near tiles
       cov[(size_t)H * nct + 2 * K]++;
       cov[(size_t)H * nct + 2 * K + 1]++;
-      ecol[H / 2]++;
+      if (H < plan[K].sym_end) ecol[H / 2]++;
     }
   for (int I = 0; I < S.nrt; ++I)
     if (ecol[I] != plan[I].e_col) return sym_fail("e_col", S.n, I, ecol[I] * 10000 + plan[I].e_col);
