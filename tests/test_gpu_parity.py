@@ -201,8 +201,9 @@ def test_exact_zero_window_matches_dense(ctx, mode):
 @pytest.mark.parametrize("n,T", [(20000, 5000.0), (20000, 300.0), (6000, 3000.0), (85000, 5000.0)],
                          ids=["n20k-long", "n20k-dense", "n6k", "n85k"])
 def test_shared_background_matches_row_by_row(ctx, n, T):
-    """The mixed path's shared background terms (far column tiles evaluated once for both events,
-    column sums in exact fixed point) against row-by-row evaluation of every ordered pair
+    """The mixed path's shared background terms (the column tiles before a row tile's own, far and
+    near, evaluated once for both events, column sums in exact fixed point) against row-by-row
+    evaluation of every ordered pair
     (HAWKES_FLAG_NO_SYMMETRY), for reaches on either side of the trigger's; both within the mixed
     tolerance of each other, per-event terms included, and bitwise repeatable."""
     from paper_2005_10123_gb300 import binding
@@ -226,6 +227,35 @@ def test_shared_background_matches_row_by_row(ctx, n, T):
             np.testing.assert_allclose(xia, xib, rtol=2e-6, atol=2e-6 * np.max(xib))
             w = ctx.hawkes_pair_work(sid, th, 1)
             assert w["evaluated"] <= w["visited"]
+    finally:
+        ctx.hawkes_set_flags(0)
+        ctx.hawkes_release_events(sid)
+
+
+def test_shared_near_tiles_with_ties(ctx):
+    """Times on a quarter-day grid put tied events on both sides of many tile edges, so shared
+    near tiles hold columns tied with a row of the warp (their trigger terms then test each pair
+    against the tie index): the default path against row by row (HAWKES_FLAG_NO_SYMMETRY) and
+    against the oracle, for a trigger reach of a few tiles and one of a fraction of a tile."""
+    from paper_2005_10123_gb300 import binding
+    ev = synth.simulate(6000, 600.0, seed=41)
+    ev.t = np.round(ev.t * 4) / 4
+    t32 = ev.t.astype(np.float32)
+    edges = np.arange(256, ev.n, 256)
+    assert np.count_nonzero(t32[edges - 1] == t32[edges]) >= 5  # ties across row-tile edges
+    sid = ctx.hawkes_upload_events(ev.x, ev.y, ev.t)
+    try:
+        for th in [(0.05, 0.7, 5.0, 0.5, 2.0, 0.2), (0.05, 0.7, 30.0, 0.5, 0.2, 0.2)]:
+            ctx.hawkes_set_flags(binding.HAWKES_FLAG_NO_SYMMETRY)
+            b, gb = ctx.hawkes_loglik_grad(sid, th, 1)
+            ctx.hawkes_set_flags(0)
+            a, ga = ctx.hawkes_loglik_grad(sid, th, 1)
+            assert rel(a, b) <= 2e-7, (th, a, b)
+            assert grad_err(ga, gb) <= 2e-7, (th, ga, gb)
+            ref = ev.rounded32()
+            rll, rg = oracle.loglik(ref.x, ref.y, ref.t, th, grad=True)
+            assert rel(a, rll) <= TOL_MIXED_LL, (a, rll)
+            assert grad_err(ga, rg) <= TOL_MIXED_G, (ga, rg)
     finally:
         ctx.hawkes_set_flags(0)
         ctx.hawkes_release_events(sid)
