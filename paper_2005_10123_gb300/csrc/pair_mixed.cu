@@ -59,10 +59,10 @@
 #define HK_COL_UNROLL_LL 8  // loglik only
 #endif
 #ifndef HK_SYM_UNROLL
-#define HK_SYM_UNROLL 4  // steps unrolled in the far (shared-background) tile pass, loglik + gradient
+#define HK_SYM_UNROLL 1  // steps unrolled in the far (shared-background) tile pass, loglik + gradient
 #endif
 #ifndef HK_SYM_UNROLL_LL
-#define HK_SYM_UNROLL_LL HK_SYM_UNROLL  // the same, loglik only
+#define HK_SYM_UNROLL_LL 3  // the same, loglik only
 #endif
 #ifndef HK_NEAR_UNROLL
 #define HK_NEAR_UNROLL 2  // steps unrolled in the shared near tile pass, loglik + gradient
