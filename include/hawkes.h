@@ -82,7 +82,6 @@ extern "C" {
  * shares background terms: e_b(n, n') = e_b(n', n), so for the column tiles before a row tile's
  * own each background term is formed once and added to both events' rows; the trigger terms of
  * those tiles (nonzero only within the trigger's reach, see below) go to the later event's row
- * alone. With a two-component mixture only the tiles beyond the trigger's reach are shared.
  * Every event's sums (its row's, and the shares of the tiles holding it) are then added as exact
  * fixed-point integers: 2^-F resolution with
  * F = 62 - ceil(log2 N_padded) for the background sums (about 3e-14 at N = 85,000, against a

@@ -348,7 +348,6 @@ int set_mixture(const hawkes_mix_params *m, int mode, double span, Request *R, M
   R->trig_cut = std::max(R->trig_cut, trig2);
   R->cut_early = std::max(R->cut_early, early2);
   R->mix = 2;
-  if (R->sym) R->sym = 1;  // the shared near tiles take one trigger component
   set_fix_bits(R, R->grad, 2, R->h, R->omega, h2, om2, span);
   return HAWKES_OK;
 }

@@ -162,7 +162,7 @@ struct Request {
   // row and its column. Every event's sums, from its row's items and from the far column tiles
   // holding it, go to fixsum as exact fixed-point integers (no partial-sum slots, no merge tree).
   int sym;             // 1: on (mixed, fused, set with a time table, no exclude-self/dense/no-symmetry);
-                       // 2: the near column tiles before the row tile shared too (one trigger)
+                       // 2: the near column tiles before the row tile shared too
   signed char fix_bits[kMaxSums];  // sym: sum s enters fixsum as round(v 2^fix_bits[s]) (fix_bits_for)
   double trig_cut;     // days: columns earlier than t_n - trig_cut give trigger terms that contribute
                        // nothing (with the self term below 2^-40 (mixed) or 2^-70 (float64) of

@@ -402,24 +402,28 @@ __device__ __forceinline__ void tile_pass_sym_pairs(const float4 *__restrict__ s
   }
 }
 
-// A shared near column tile (SymPlan, R.sym == 2; one trigger component): the column tile lies
-// before this row tile, within the trigger's reach, and each background term serves its row and
-// its column as in the far pass, while the trigger terms serve the rows only (the columns are the
-// earlier events). Pair layout (store_cols_near): sN[m] = {-x_a, -x_b, -y_a, -y_b} (stored
-// coordinates) and sN[kThreads + m] = {-t'_a, -t'_b, -t_a, -t_b} (scaled and stored times). The
-// terms take the row-by-row kinds' forms, q = a2 r^2 + dt'^2 and the trigger's r^2 from the
-// stored coordinates. BG: background terms, shared (their column shares reach fixsum rows 0, 2
-// and 3 as in tile_pass_sym_pairs). TRIG: trigger terms; separable (the column factor
-// WN (t_ref - t_n') with t_ref = SREF, the caller applies the row factor) unless MASK, which
-// forms WN (t_n - t_n') per pair and keeps the terms with n' < lo(n) (ties with a row).
-template <bool GRAD, bool BG, bool TRIG, bool MASK>
+// A shared near column tile (SymPlan, R.sym == 2): the column tile lies before this row tile,
+// within the trigger's reach, and each background term serves its row and its column as in the
+// far pass, while the trigger terms serve the rows only (the columns are the earlier events).
+// Pair layout (store_cols_near): sN[m] = {-x_a, -x_b, -y_a, -y_b} (stored coordinates) and
+// sN[kThreads + m] = {-t'_a, -t'_b, -t_a, -t_b} (scaled and stored times). The terms take the
+// row-by-row kinds' forms, q = a2 r^2 + dt'^2 and the trigger's r^2 from the stored coordinates.
+// BG: background terms, shared (their column shares reach fixsum rows 0, 2 and 3 as in
+// tile_pass_sym_pairs). COMP: the trigger components formed (bit 0: component 1 with CN, WN;
+// bit 1: component 2 with CN2, WN2, into the sums after the single-kernel ones; 0: none);
+// separable (the column factor WN (t_ref - t_n') with t_ref = SREF, the caller applies the row
+// factor) unless MASK, which forms WN (t_n - t_n') per pair and keeps the terms with n' < lo(n)
+// (ties with a row).
+template <bool GRAD, int MIX, bool BG, int COMP, bool MASK>
 __device__ __forceinline__ void tile_pass_sym_near(const float4 *__restrict__ sN, const float2 (&X)[kPairs],
                                                    const float2 (&Y)[kPairs], const float2 (&T)[kPairs],
                                                    const float2 (&TR)[kPairs], const int (&LO)[kRowsPerThread],
-                                                   int c0, float2 A2, float2 CN, float2 WN, float2 SREF,
-                                                   Acc32<num_sums(GRAD, 1)> &acc, long long *__restrict__ fixsum,
-                                                   int npad, float fix_scale, int *bad) {
+                                                   int c0, float2 A2, float2 CN, float2 WN, float2 CN2, float2 WN2,
+                                                   float2 SREF, Acc32<num_sums(GRAD, MIX)> &acc,
+                                                   long long *__restrict__ fixsum, int npad, float fix_scale, int *bad) {
   constexpr int kNearUnroll = GRAD ? HK_NEAR_UNROLL : HK_NEAR_UNROLL_LL;
+  constexpr int S2 = GRAD ? 6 : 2;  // component 2's trigger sums
+  constexpr bool kC1 = (COMP & 1) != 0, kC2 = MIX > 1 && (COMP & 2) != 0, TRIG = kC1 || kC2;
   const int lane = threadIdx.x & 31;
 #pragma unroll 1
   for (int h = 0; h < kColTile / 64; ++h) {
@@ -432,12 +436,18 @@ __device__ __forceinline__ void tile_pass_sym_near(const float4 *__restrict__ sN
       const float2 cy[2] = {make_float2(C.z, C.w), make_float2(C.w, C.z)};
       const float2 ct[2] = {make_float2(D.x, D.y), make_float2(D.y, D.x)};
       const float2 cr[2] = {make_float2(D.z, D.w), make_float2(D.w, D.z)};  // -t (stored)
-      float2 dref[2], bj[2];
+      float2 dref[2], bj[2], bj2[2];
       if (TRIG && !MASK) {
         dref[0] = add2(SREF, cr[0]);  // t_ref - t_n' >= 0
-        bj[0] = mul2(dref[0], WN);
         dref[1] = make_float2(dref[0].y, dref[0].x);
-        bj[1] = make_float2(bj[0].y, bj[0].x);
+        if (kC1) {
+          bj[0] = mul2(dref[0], WN);
+          bj[1] = make_float2(bj[0].y, bj[0].x);
+        }
+        if (kC2) {
+          bj2[0] = mul2(dref[0], WN2);
+          bj2[1] = make_float2(bj2[0].y, bj2[0].x);
+        }
       }
       float2 ps[2], pq[2], pu[2];  // per variant, summed over the row pairs (BG)
 #pragma unroll
@@ -471,23 +481,36 @@ __device__ __forceinline__ void tile_pass_sym_near(const float4 *__restrict__ sN
             }
           }
           if (TRIG) {
-            float2 arg, dtr;
-            if (MASK) {
-              dtr = add2(TR[p], cr[v]);
-              arg = fma2(rho, CN, mul2(dtr, WN));
-            } else {
-              arg = fma2(rho, CN, bj[v]);
+            // variant 0 pairs the rows with (a, b), variant 1 with (b, a)
+            const int ca = c0 + 2 * m;
+            const bool keep_x = !MASK || ca + v < LO[2 * p], keep_y = !MASK || ca + 1 - v < LO[2 * p + 1];
+            float2 dtr;
+            if (MASK) dtr = add2(TR[p], cr[v]);
+            if (kC1) {
+              const float2 arg = MASK ? fma2(rho, CN, mul2(dtr, WN)) : fma2(rho, CN, bj[v]);
+              float2 es = make_float2(ex2(arg.x), ex2(arg.y));
+              if (MASK) {
+                es.x = keep_x ? es.x : 0.f;
+                es.y = keep_y ? es.y : 0.f;
+              }
+              acc.v[1][p] = acc2(acc.v[1][p], es);
+              if (GRAD) {
+                acc.v[4][p] = accfma2(rho, es, acc.v[4][p]);
+                acc.v[5][p] = accfma2(MASK ? dtr : dref[v], es, acc.v[5][p]);
+              }
             }
-            float2 es = make_float2(ex2(arg.x), ex2(arg.y));
-            if (MASK) {  // variant 0 pairs the rows with (a, b), variant 1 with (b, a)
-              const int ca = c0 + 2 * m;
-              es.x = (ca + v < LO[2 * p]) ? es.x : 0.f;
-              es.y = (ca + 1 - v < LO[2 * p + 1]) ? es.y : 0.f;
-            }
-            acc.v[1][p] = acc2(acc.v[1][p], es);
-            if (GRAD) {
-              acc.v[4][p] = accfma2(rho, es, acc.v[4][p]);
-              acc.v[5][p] = accfma2(MASK ? dtr : dref[v], es, acc.v[5][p]);
+            if (kC2) {
+              const float2 arg2 = MASK ? fma2(rho, CN2, mul2(dtr, WN2)) : fma2(rho, CN2, bj2[v]);
+              float2 es2 = make_float2(ex2(arg2.x), ex2(arg2.y));
+              if (MASK) {
+                es2.x = keep_x ? es2.x : 0.f;
+                es2.y = keep_y ? es2.y : 0.f;
+              }
+              acc.v[S2][p] = acc2(acc.v[S2][p], es2);
+              if (GRAD) {
+                acc.v[S2 + 1][p] = accfma2(rho, es2, acc.v[S2 + 1][p]);
+                acc.v[S2 + 2][p] = accfma2(MASK ? dtr : dref[v], es2, acc.v[S2 + 2][p]);
+              }
             }
           }
         }
@@ -712,6 +735,33 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
     const float w = (float)(-omega * kLog2eD);
     return make_float2(w, w);
   };
+  // row factor 2^(WN (t_n - t_ref)) of a separable trigger tile (each component's own, for the
+  // components in comps); U_s gets the row part of dt = (t_n - t_ref) + (t_ref - t_n'), both >= 0
+  auto row_factor = [&](float sref, float2 WN, float2 WN2, int comps, const float2 (&TR)[kPairs], Acc32<NS> &acc) {
+    const float2 sr = make_float2(-sref, -sref);
+#pragma unroll
+    for (int p = 0; p < kPairs; ++p) {
+      const float2 d = __fadd2_rn(TR[p], sr);
+      if (MIX == 1 || (comps & 1)) {
+        const float2 w = __fmul2_rn(d, WN);
+        const float2 a = make_float2(ex2(w.x), ex2(w.y));
+        if (GRAD) {
+          acc.v[5][p] = __fmul2_rn(__ffma2_rn(d, acc.v[1][p], acc.v[5][p]), a);
+          acc.v[4][p] = __fmul2_rn(acc.v[4][p], a);
+        }
+        acc.v[1][p] = __fmul2_rn(acc.v[1][p], a);
+      }
+      if (MIX > 1 && (comps & 2)) {
+        const float2 w2 = __fmul2_rn(d, WN2);
+        const float2 a2 = make_float2(ex2(w2.x), ex2(w2.y));
+        if (GRAD) {
+          acc.v[S2 + 2][p] = __fmul2_rn(__ffma2_rn(d, acc.v[S2][p], acc.v[S2 + 2][p]), a2);
+          acc.v[S2 + 1][p] = __fmul2_rn(acc.v[S2 + 1][p], a2);
+        }
+        acc.v[S2][p] = __fmul2_rn(acc.v[S2][p], a2);
+      }
+    }
+  };
   const float s_first = __shfl_sync(0xffffffffu, T[0].x, 0);            // scaled time of the warp's
   const float s_last = __shfl_sync(0xffffffffu, T[kPairs - 1].y, 31);  // first and last rows
 
@@ -728,7 +778,7 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
   // far tiles are staged in pair layout (tile_pass_sym_pairs), shared near ones in their own pair
   // layout (tile_pass_sym_near), the rest one column at a time (tile_pass)
   auto layout = [&](int c) {
-    return R.sym && c < plan.sym_end ? 1 : MIX == 1 && c >= plan.sym_end && c < plan.near_end ? 2 : 0;
+    return R.sym && c < plan.sym_end ? 1 : c >= plan.sym_end && c < plan.near_end ? 2 : 0;
   };
   auto load = [&](int c, int lay) { return lay ? load_cols_pairs(S, c, tid) : load_cols(S, c, tid); };
   auto stage = [&](const RawCols &r, int c, int lay, int b) {
@@ -753,11 +803,13 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
     if (R.sym && ct < plan.sym_end) {  // far: background only, shared with the columns' rows
       const float gap = s_first + reinterpret_cast<const float2 *>(stx[buf])[kColTile / 2 - 1].y;  // the latest column
       kind = gap >= kBgZeroGap ? -1 : 4;
-    } else if (MIX == 1 && ct < plan.near_end) {  // shared near tile: the same classes as below
+    } else if (ct < plan.near_end) {  // shared near tile: the same classes as below
       if (c1 <= lo_wa) {
         const float gap = s_first + sxs[buf][kColTile - 1].y;  // t'(first row) - t'(latest column)
         const bool bg_zero = gap >= kBgZeroGap, trig_zero = wn * gap <= -kTrigZeroExp;
         kind = bg_zero ? (trig_zero ? -1 : 7) : (trig_zero ? 5 : 6);
+        if (MIX > 1)
+          comps = (R.wn * gap <= -kTrigZeroExp ? 0 : 1) | (B.mix2.wn2 * gap <= -kTrigZeroExp ? 0 : 2);
       } else {
         kind = 8;  // a column tied with a row of this warp
       }
@@ -789,43 +841,43 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
       tile_pass_sym_pairs<GRAD>(sxs[buf], stx[buf], XS, YS, T, acc, R.fixsum, S.npad, c0, pow2f(R.fix_bits[0]),
                                 &s_bad);
     } else if (kind >= 5) {
-      if constexpr (MIX == 1) {
-        row_coords<false>(S, row_a0, sk, X, Y);
-        const float2 WN = slope(R.omega);
-        const float sref = -sxs[buf][kColTile - 1].w;  // t_ref: the tile's latest column (stored time)
-        const float2 SREF = make_float2(sref, sref);
-        const float fs = pow2f(R.fix_bits[0]);
-        if (kind == 8) {  // rare (ties across the tile's edge): the background, then the masked trigger
-          tile_pass_sym_near<GRAD, true, false, false>(sxs[buf], X, Y, T, T, LO, c0, A2, CN, WN, SREF, acc, R.fixsum,
-                                                       S.npad, fs, &s_bad);
-          row_times(S, row_a0, TR);
-          tile_pass_sym_near<GRAD, false, true, true>(sxs[buf], X, Y, T, TR, LO, c0, A2, CN, WN, SREF, acc, R.fixsum,
-                                                      S.npad, fs, &s_bad);
-        } else if (kind == 6) {
-          tile_pass_sym_near<GRAD, true, true, false>(sxs[buf], X, Y, T, T, LO, c0, A2, CN, WN, SREF, acc, R.fixsum,
-                                                      S.npad, fs, &s_bad);
-        } else if (kind == 5) {
-          tile_pass_sym_near<GRAD, true, false, false>(sxs[buf], X, Y, T, T, LO, c0, A2, CN, WN, SREF, acc, R.fixsum,
-                                                       S.npad, fs, &s_bad);
+      row_coords<false>(S, row_a0, sk, X, Y);
+      const float2 WN = slope(R.omega), WN2 = MIX > 1 ? slope(B.mix2.omega2) : WN;
+      const float sref = -sxs[buf][kColTile - 1].w;  // t_ref: the tile's latest column (stored time)
+      const float2 SREF = make_float2(sref, sref);
+      const float fs = pow2f(R.fix_bits[0]);
+      auto near = [&](auto bg_c, auto comp_c, auto mask_c) {
+        tile_pass_sym_near<GRAD, MIX, decltype(bg_c)::value, decltype(comp_c)::value, decltype(mask_c)::value>(
+            sxs[buf], X, Y, T, TR, LO, c0, A2, CN, WN, CN2, WN2, SREF, acc, R.fixsum, S.npad, fs, &s_bad);
+      };
+      using BY = std::integral_constant<bool, true>;
+      using BN = std::integral_constant<bool, false>;
+      using C0 = std::integral_constant<int, 0>;
+      using C1 = std::integral_constant<int, 1>;
+      using C2 = std::integral_constant<int, 2>;
+      using CA = std::integral_constant<int, (MIX > 1 ? 3 : 1)>;  // every component
+      if (kind == 8) {  // rare (ties across the tile's edge): the background, then the masked trigger
+        near(BY{}, C0{}, BN{});
+        row_times(S, row_a0, TR);
+        near(BN{}, CA{}, BY{});
+      } else if (kind == 5) {
+        near(BY{}, C0{}, BN{});
+      } else {
+        if constexpr (MIX == 1) {
+          if (kind == 6) near(BY{}, C1{}, BN{});
+          else near(BN{}, C1{}, BN{});
+        } else if (comps == 3) {
+          if (kind == 6) near(BY{}, CA{}, BN{});
+          else near(BN{}, CA{}, BN{});
+        } else if (comps == 1) {
+          if (kind == 6) near(BY{}, C1{}, BN{});
+          else near(BN{}, C1{}, BN{});
         } else {
-          tile_pass_sym_near<GRAD, false, true, false>(sxs[buf], X, Y, T, T, LO, c0, A2, CN, WN, SREF, acc, R.fixsum,
-                                                       S.npad, fs, &s_bad);
+          if (kind == 6) near(BY{}, C2{}, BN{});
+          else near(BN{}, C2{}, BN{});
         }
-        if (kind == 6 || kind == 7) {  // the separable trigger's row factor, as below
-          row_times(S, row_a0, TR);
-          const float2 sr = make_float2(-sref, -sref);
-#pragma unroll
-          for (int p = 0; p < kPairs; ++p) {
-            const float2 d = __fadd2_rn(TR[p], sr);
-            const float2 w = __fmul2_rn(d, WN);
-            const float2 a = make_float2(ex2(w.x), ex2(w.y));
-            if (GRAD) {
-              acc.v[5][p] = __fmul2_rn(__ffma2_rn(d, acc.v[1][p], acc.v[5][p]), a);
-              acc.v[4][p] = __fmul2_rn(acc.v[4][p], a);
-            }
-            acc.v[1][p] = __fmul2_rn(acc.v[1][p], a);
-          }
-        }
+        row_times(S, row_a0, TR);
+        row_factor(sref, WN, WN2, comps, TR, acc);
       }
     } else if (kind == 1 || kind == 3) {
       row_coords<false>(S, row_a0, sk, X, Y);
@@ -855,31 +907,7 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
         if (kind == 1) pass(K1{}, C2{});
         else pass(K3{}, C2{});
       }
-      // row factor 2^(WN (t_n - t_ref)) of the separable trigger term (each component's own);
-      // U_s gets the row part of dt = (t_n - t_ref) + (t_ref - t_n'), both parts >= 0
-      const float2 sr = make_float2(-sref, -sref);
-#pragma unroll
-      for (int p = 0; p < kPairs; ++p) {
-        const float2 d = __fadd2_rn(TR[p], sr);
-        if (MIX == 1 || (comps & 1)) {
-          const float2 w = __fmul2_rn(d, WN);
-          const float2 a = make_float2(ex2(w.x), ex2(w.y));
-          if (GRAD) {
-            acc.v[5][p] = __fmul2_rn(__ffma2_rn(d, acc.v[1][p], acc.v[5][p]), a);
-            acc.v[4][p] = __fmul2_rn(acc.v[4][p], a);
-          }
-          acc.v[1][p] = __fmul2_rn(acc.v[1][p], a);
-        }
-        if (MIX > 1 && (comps & 2)) {
-          const float2 w2 = __fmul2_rn(d, WN2);
-          const float2 a2 = make_float2(ex2(w2.x), ex2(w2.y));
-          if (GRAD) {
-            acc.v[S2 + 2][p] = __fmul2_rn(__ffma2_rn(d, acc.v[S2][p], acc.v[S2 + 2][p]), a2);
-            acc.v[S2 + 1][p] = __fmul2_rn(acc.v[S2 + 1][p], a2);
-          }
-          acc.v[S2][p] = __fmul2_rn(acc.v[S2][p], a2);
-        }
-      }
+      row_factor(sref, WN, WN2, comps, TR, acc);
     } else if (kind == 2) {
       row_coords<false>(S, row_a0, sk, X, Y);
       row_times(S, row_a0, TR);
@@ -891,7 +919,7 @@ __device__ void run_piece(const Batch &B, const Request &R, const PairItem &it, 
     // those sums at zero, so they are skipped
     const bool fold_bg = kind == 0 || kind == 1 || kind == 2 || kind == 4 || kind == 5 || kind == 6 || kind == 8;
     const bool fold_trig = (kind >= 1 && kind <= 3) || kind >= 6;
-    if (kind == 2) comps = 3;
+    if (kind == 2 || kind == 8) comps = 3;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       const bool trig_sum = GRAD ? (s == 1 || s >= 4) : s >= 1;  // S_s, R_s, U_s (each component)

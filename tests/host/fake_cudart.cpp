@@ -156,7 +156,7 @@ static bool check_symmetry(const Request &R) {
     if (R.rt_done[I] != 0u) return sym_fail("rt_done not zero", S.n, I, 0);
   for (size_t i = 0; i < (size_t)num_sums(R.grad != 0, R.mix) * S.npad; ++i)
     if (R.fixsum[i] != 0) return sym_fail("fixsum not zero", S.n, (int)i, 0);
-  if (R.sym != (R.mix > 1 || !HK_SYM_NEAR ? 1 : 2)) return sym_fail("level", S.n, R.sym, R.mix);
+  if (R.sym != (HK_SYM_NEAR ? 2 : 1)) return sym_fail("level", S.n, R.sym, R.mix);
   if (S.nct > 1024) return true;  // the block table below grows as nct^2
   g_sym_checked++;
   auto tfirst = [&](int K) { return (double)S.t32[(size_t)K * kRowTile]; };
