@@ -138,14 +138,17 @@ namespace hk {
 
 // With the shared background (Request::sym): the completion counters and fixed-point sums start
 // at zero, and the far/near plan of every row tile (SymPlan, as the kernels compute it from
-// the set's time table) covers every ordered block (rows of column tile H, columns of column tile
-// J) at most once, and exactly once where a term can be nonzero (J inside the window of H's row
-// tile, and, for a later J, H inside the window of J's row tile); e_col(I) counts the far column
-// tiles of later row tiles that hold I's columns.
+// the set's time table, far and shared near tiles) covers every ordered block (rows of column
+// tile H, columns of column tile J) at most once, and exactly once where a term can be nonzero (J
+// inside the window of H's row tile, and, for a later J, H inside the window of J's row tile), at
+// the launch's plan level and at the other one; e_col(I) counts the far column tiles of later row
+// tiles that hold I's columns.
 static bool sym_fail(const char *what, int a, int b, int c) {
   std::fprintf(stderr, "symmetric plan check failed: %s (%d, %d, %d)\n", what, a, b, c);
   return false;
 }
+
+static bool check_plan_coverage(const Request &R);
 
 static bool check_symmetry(const Request &R) {
   const SetView &S = R.set;
@@ -159,6 +162,16 @@ static bool check_symmetry(const Request &R) {
   if (R.sym != (HK_SYM_NEAR ? 2 : 1)) return sym_fail("level", S.n, R.sym, R.mix);
   if (S.nct > 1024) return true;  // the block table below grows as nct^2
   g_sym_checked++;
+  // the launch's own plan level, then the other one (the build switch HK_SYM_NEAR picks between
+  // them), on the same set and reaches
+  Request other = R;
+  other.sym = 3 - R.sym;
+  return check_plan_coverage(R) && check_plan_coverage(other);
+}
+
+// Block coverage of one request's plan (SymPlan at its level R.sym) over its set.
+static bool check_plan_coverage(const Request &R) {
+  const SetView &S = R.set;
   auto tfirst = [&](int K) { return (double)S.t32[(size_t)K * kRowTile]; };
   std::vector<int2> win(S.nrt);
   std::vector<SymPlan> plan(S.nrt);
