@@ -378,6 +378,54 @@ def probe_units():
     return 0
 
 
+def n_sweep(args):
+    """Time against N at a fixed time span (the paper's Fig. 1, right: seconds against N from 10k
+    to 90k for one log-likelihood, quadratic in N). Seeded synthetic sets of N events over 5,000
+    days (the density, and so the pairs within reach, grow with N), Theta0; per N the median of
+    device-timed evaluations with the L2 flushed before each: mixed loglik+grad, mixed loglik and
+    FP64 loglik, with the ordered pairs each visits (hawkes_pair_work). One JSON line."""
+    import torch
+    from paper_2005_10123_gb300 import binding
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = binding.Context(device=0, stream=stream.cuda_stream)
+    out = torch.zeros(7, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def timed(sid, mode, grad, reps):
+        for _ in range(3):
+            ctx.hawkes_loglik_async(sid, THETA0, mode, grad, out.data_ptr())
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.hawkes_loglik_async(sid, THETA0, mode, grad, out.data_ptr())
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ts.sort()
+        return ts[len(ts) // 2]
+
+    rows = []
+    for n in args.n_sweep:
+        ev = synth.simulate(n, 5000.0, seed=20051 + n).rounded32()
+        sid = ctx.hawkes_upload_events(ev.x, ev.y, ev.t)
+        g_ms = timed(sid, binding.HAWKES_MIXED, True, 20)
+        l_ms = timed(sid, binding.HAWKES_MIXED, False, 20)
+        d_ms = timed(sid, binding.HAWKES_FP64, False, 3)
+        rows.append({"n": n, "mixed_loglik_grad_ms": g_ms, "mixed_loglik_ms": l_ms, "fp64_loglik_ms": d_ms,
+                     "mixed_grad_pair_evals_per_s": float(n) * n / (g_ms * 1e-3),
+                     "visited_mixed": ctx.hawkes_pair_work(sid, THETA0, binding.HAWKES_MIXED)["visited"],
+                     "visited_fp64": ctx.hawkes_pair_work(sid, THETA0, binding.HAWKES_FP64)["visited"]})
+        ctx.hawkes_release_events(sid)
+    print(json.dumps({"n_sweep": rows, "span_days": 5000.0, "theta": list(THETA0),
+                      "l2": "flushed before each evaluation (256 MB write)"}))
+    ctx.close()
+    return 0
+
+
 def run_reference(args):
     rank, world, _ = _dist_env()
     if rank != 0:
@@ -660,9 +708,15 @@ def main():
                     help="run only warm-up + steps of the mixed loglik+grad call (the case profiled with ncu)")
     ap.add_argument("--probe-units", action="store_true",
                     help="measure the float32-pipe and ex2 rates and ex2.approx's error profile, then exit")
+    ap.add_argument("--n-sweep", type=int, nargs="*", default=None, metavar="N",
+                    help="time loglik and loglik+grad against N at a fixed span (default 10k..90k), then exit")
     args = ap.parse_args()
     if args.probe_units:
         return probe_units()
+    if args.n_sweep is not None:
+        if not args.n_sweep:
+            args.n_sweep = list(range(10000, 100000, 10000))
+        return n_sweep(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
